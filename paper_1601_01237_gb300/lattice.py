@@ -1,0 +1,222 @@
+"""Python binding of the C ABI in include/lbm.h.
+
+Argument marshalling only: every step of the update runs in the CUDA library
+(libmclbm.so).  The module-level functions carry the C names one to one; the
+``Lattice`` class wraps a handle for convenience.  Host arrays are numpy
+arrays; device arrays are torch CUDA tensors (torch provides device memory and
+streams, nothing else).
+"""
+import ctypes
+
+import numpy as np
+
+from . import _native as nat
+from ._native import check, lib
+
+Q = 19
+
+
+def _ptr(x):
+    """(address, on_device) of a numpy array or a torch tensor."""
+    if x is None:
+        return None, 0
+    if isinstance(x, np.ndarray):
+        assert x.flags["C_CONTIGUOUS"], "arrays must be C-contiguous"
+        return x.ctypes.data, 0
+    # torch tensor
+    assert x.is_contiguous(), "tensors must be contiguous"
+    return x.data_ptr(), 1 if x.is_cuda else 0
+
+
+# --------------------------------------------------------------------------
+# C-named functions
+
+def lbm_lattice_dirs():
+    c = (ctypes.c_int * (Q * 3))()
+    w = (ctypes.c_double * Q)()
+    check(lib().lbm_lattice_dirs(c, w))
+    return np.array(c, dtype=np.int64).reshape(Q, 3), np.array(w)
+
+
+def lbm_create(params):
+    h = ctypes.c_void_p()
+    check(lib().lbm_create(ctypes.byref(params), ctypes.byref(h)))
+    return h
+
+
+def lbm_init_fields(h, rho1, rho2, u=None):
+    p1, d1 = _ptr(rho1)
+    p2, d2 = _ptr(rho2)
+    pu, du = _ptr(u)
+    on_dev = d1
+    assert d2 == on_dev and (u is None or du == on_dev), "mixed host/device inputs"
+    check(lib().lbm_init_fields(h, p1, p2, pu, on_dev), h)
+
+
+def lbm_step(h, n_steps):
+    check(lib().lbm_step(h, int(n_steps)), h)
+
+
+def lbm_moments(h, rho1=None, rho2=None, uF=None, out_f64=True):
+    ptrs = [_ptr(x) for x in (rho1, rho2, uF)]
+    devs = {d for (p, d), x in zip(ptrs, (rho1, rho2, uF)) if x is not None}
+    assert len(devs) <= 1, "mixed host/device outputs"
+    on_dev = devs.pop() if devs else 0
+    check(lib().lbm_moments(h, int(bool(out_f64)), ptrs[0][0], ptrs[1][0], ptrs[2][0], on_dev), h)
+
+
+def lbm_reduce(h):
+    out = (ctypes.c_double * 6)()
+    check(lib().lbm_reduce(h, out), h)
+    return list(out)
+
+
+def lbm_get_populations(h, out):
+    p, d = _ptr(out)
+    check(lib().lbm_get_populations(h, p, d), h)
+
+
+def lbm_set_populations(h, src):
+    p, d = _ptr(src)
+    check(lib().lbm_set_populations(h, p, d), h)
+
+
+def lbm_state_bytes(h):
+    n = ctypes.c_size_t()
+    check(lib().lbm_state_bytes(h, ctypes.byref(n)), h)
+    return n.value
+
+
+def lbm_get_state(h, dev_buf):
+    p, d = _ptr(dev_buf)
+    assert d == 1, "state buffers live on the device"
+    check(lib().lbm_get_state(h, p, dev_buf.numel() * dev_buf.element_size()), h)
+
+
+def lbm_set_state(h, dev_buf):
+    p, d = _ptr(dev_buf)
+    assert d == 1, "state buffers live on the device"
+    check(lib().lbm_set_state(h, p, dev_buf.numel() * dev_buf.element_size()), h)
+
+
+def lbm_step_count(h):
+    n = ctypes.c_long()
+    check(lib().lbm_step_count(h, ctypes.byref(n)), h)
+    return n.value
+
+
+def lbm_sync(h):
+    check(lib().lbm_sync(h), h)
+
+
+def lbm_destroy(h):
+    lib().lbm_destroy(h)
+
+
+# --------------------------------------------------------------------------
+
+def make_params(shape, tau=(1.0, 1.0), G12=0.0, G21=None, g_ext=(0.0, 0.0, 0.0), periodic=(1, 1, 1),
+                rho_s=(0.0, 0.0), rho0_dev=0.0, storage="f32", collision="bgk", wall_model="mirror",
+                stream=None):
+    """lbm_params for a lattice of shape (nz, ny, nx).  G12, G21 are the signed
+    G^{12}, G^{21} of Eq. 7 (G21 defaults to G12)."""
+    nz, ny, nx = shape
+    p = nat.lbm_params()
+    p.nx, p.ny, p.nz = int(nx), int(ny), int(nz)
+    for d in range(3):
+        p.periodic[d] = int(periodic[d])
+        p.g_ext[d] = float(g_ext[d])
+    p.tau[0], p.tau[1] = float(tau[0]), float(tau[1])
+    p.G[0][0] = 0.0
+    p.G[1][1] = 0.0
+    p.G[0][1] = float(G12)
+    p.G[1][0] = float(G12 if G21 is None else G21)
+    p.rho_s[0], p.rho_s[1] = float(rho_s[0]), float(rho_s[1])
+    p.rho0_dev = float(rho0_dev)
+    p.storage = nat.STORAGE[storage]
+    p.collision = nat.COLLISION[collision]
+    p.wall_model = nat.WALL_MODEL[wall_model]
+    p.stream = stream
+    return p
+
+
+class Lattice:
+    """A two-component D3Q19 lattice living on the current CUDA device."""
+
+    def __init__(self, shape, **kw):
+        if kw.get("stream", None) is None and kw.pop("torch_stream", True):
+            import torch
+            kw["stream"] = torch.cuda.current_stream().cuda_stream
+        self.shape = tuple(int(s) for s in shape)
+        self.N = int(np.prod(self.shape))
+        self.params = make_params(self.shape, **kw)
+        self.storage = kw.get("storage", "f32")
+        self.h = lbm_create(self.params)
+
+    def close(self):
+        if self.h is not None:
+            lbm_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def init_fields(self, rho1, rho2, u=None):
+        if isinstance(rho1, np.ndarray):
+            rho1 = np.ascontiguousarray(rho1, dtype=np.float64)
+            rho2 = np.ascontiguousarray(rho2, dtype=np.float64)
+            u = None if u is None else np.ascontiguousarray(u, dtype=np.float64)
+        lbm_init_fields(self.h, rho1, rho2, u)
+
+    def step(self, n=1):
+        lbm_step(self.h, n)
+
+    def moments(self, out_f64=True):
+        """Host copies (rho1, rho2, uF) shaped (nz,ny,nx), (nz,ny,nx), (nz,ny,nx,3)."""
+        dt = np.float64 if out_f64 else np.float32
+        r1 = np.empty(self.shape, dt)
+        r2 = np.empty(self.shape, dt)
+        uF = np.empty(self.shape + (3,), dt)
+        lbm_moments(self.h, r1, r2, uF, out_f64)
+        return r1, r2, uF
+
+    def moments_device(self, rho1=None, rho2=None, uF=None, out_f64=False):
+        lbm_moments(self.h, rho1, rho2, uF, out_f64)
+
+    def reduce(self):
+        v = lbm_reduce(self.h)
+        return {"mass1": v[0], "mass2": v[1], "momentum": v[2:5], "max_uF": v[5]}
+
+    def get_populations(self):
+        """Host copy of f_i^a(x, t), shape (2, 19, nz, ny, nx), library direction order."""
+        out = np.empty((2, Q) + self.shape)
+        lbm_get_populations(self.h, out)
+        return out
+
+    def set_populations(self, f):
+        f = np.ascontiguousarray(f, dtype=np.float64) if isinstance(f, np.ndarray) else f
+        lbm_set_populations(self.h, f)
+
+    def state_bytes(self):
+        return lbm_state_bytes(self.h)
+
+    def get_state(self, buf):
+        lbm_get_state(self.h, buf)
+
+    def set_state(self, buf):
+        lbm_set_state(self.h, buf)
+
+    def step_count(self):
+        return lbm_step_count(self.h)
+
+    def sync(self):
+        lbm_sync(self.h)

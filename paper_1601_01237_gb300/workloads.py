@@ -1,0 +1,153 @@
+"""Seeded synthetic inputs shaped like the paper's test cases.
+
+This module holds input recipes only (density fields, noise, lattice sizes and
+parameters); none of the method's arithmetic.  Both the CUDA path and the
+oracle consume what it produces.
+
+Recipes (Otomo et al., arXiv:1601.01237):
+  * droplet / sphere: tanh profile rho^1(r) = rho_out + (rho_in - rho_out)/2 *
+    (1 - tanh((r - R)/W)), component 2 mirrored so rho^1 + rho^2 is uniform
+    (the static-droplet tests of Sec. 3);
+  * ellipsoid: the same profile with r measured in units of the semi-axes;
+  * spinodal mixture: rho^a = rho0 (1 + amp * U(-1, 1)), U from SplitMix64 over
+    the linear cell index with seed + a;
+  * hemisphere on a wall: a sphere centred on the wall plane z = -1/2 (the
+    wall-attached droplet of Sec. 4.2).
+
+Interaction strength: the configurations quote G as a repulsion strength for
+weights normalised to a unit second moment (w_i / T0).  Eq. 7 uses the lattice
+weights w_i with a signed G, so the lattice value is G_eq7 = -G_cfg / T0 =
+-3 G_cfg (repulsive).
+"""
+import math
+
+import numpy as np
+
+T0 = 1.0 / 3.0
+MASK64 = (1 << 64) - 1
+
+
+def g_from_config(G_cfg):
+    """Signed G^{12} of Eq. 7 for a configuration's repulsion strength."""
+    return -G_cfg / T0
+
+
+def splitmix64(seed, n):
+    """First n outputs of SplitMix64 (Steele, Lea & Flood 2014) seeded with seed,
+    as uint64; output k is the generator advanced k+1 times."""
+    with np.errstate(over="ignore"):
+        k = np.arange(1, n + 1, dtype=np.uint64)
+        z = np.uint64(seed & MASK64) + k * np.uint64(0x9E3779B97F4A7C15)
+        z = (z ^ (z >> np.uint64(30))) * np.uint64(0xBF58476D1CE4E5B9)
+        z = (z ^ (z >> np.uint64(27))) * np.uint64(0x94D049BB133111EB)
+        z = z ^ (z >> np.uint64(31))
+    return z
+
+
+def uniform_pm1(seed, n):
+    """n doubles uniform in [-1, 1) from the top 53 bits of SplitMix64."""
+    u = (splitmix64(seed, n) >> np.uint64(11)).astype(np.float64) * (1.0 / (1 << 53))
+    return 2.0 * u - 1.0
+
+
+def _radius(shape, center, scale=(1.0, 1.0, 1.0)):
+    nz, ny, nx = shape
+    z, y, x = np.meshgrid(np.arange(nz, dtype=np.float64), np.arange(ny, dtype=np.float64),
+                          np.arange(nx, dtype=np.float64), indexing="ij")
+    cz, cy, cx = center
+    sz, sy, sx = scale
+    return np.sqrt(((x - cx) / sx) ** 2 + ((y - cy) / sy) ** 2 + ((z - cz) / sz) ** 2)
+
+
+def tanh_profile(r, R, rho_in, rho_out, width):
+    rho1 = rho_out + 0.5 * (rho_in - rho_out) * (1.0 - np.tanh((r - R) / width))
+    rho2 = rho_in + rho_out - rho1
+    return rho1, rho2
+
+
+def droplet(shape, R, rho_in=1.0, rho_out=0.03, width=2.0, center=None):
+    """Circular (nz = 1) or spherical droplet of component 1 centred on the
+    lattice: returns (rho1, rho2) of shape (nz, ny, nx)."""
+    nz, ny, nx = shape
+    if center is None:
+        center = ((nz - 1) / 2.0, (ny - 1) / 2.0, (nx - 1) / 2.0)
+    r = _radius(shape, center)
+    if nz == 1:
+        r = _radius(shape, (0.0, center[1], center[2]))
+    return tanh_profile(r, R, rho_in, rho_out, width)
+
+
+def ellipsoid(shape, semi_axes, rho_in=1.0, rho_out=0.03, width=2.0):
+    """Ellipsoidal droplet with semi-axes (a_x, a_y, a_z), centred."""
+    nz, ny, nx = shape
+    ax, ay, az = semi_axes
+    center = ((nz - 1) / 2.0, (ny - 1) / 2.0, (nx - 1) / 2.0)
+    # distance along the ray scaled back to lattice units with the mean axis
+    s = _radius(shape, center, scale=(az, ay, ax))
+    R = (ax * ay * az) ** (1.0 / 3.0)
+    return tanh_profile(s * R, R, rho_in, rho_out, width)
+
+
+def hemisphere(shape, R, rho_in=1.0, rho_out=0.03, width=2.0):
+    """Droplet of component 1 sitting on the wall z = -1/2, centred in x, y."""
+    nz, ny, nx = shape
+    r = _radius(shape, (-0.5, (ny - 1) / 2.0, (nx - 1) / 2.0))
+    return tanh_profile(r, R, rho_in, rho_out, width)
+
+
+def spinodal(shape, rho0=0.5, amp=0.01, seed=20160105):
+    """Uniform mixture with +-amp relative seeded noise per component."""
+    n = int(np.prod(shape))
+    r1 = rho0 * (1.0 + amp * uniform_pm1(seed + 0, n))
+    r2 = rho0 * (1.0 + amp * uniform_pm1(seed + 1, n))
+    return r1.reshape(shape), r2.reshape(shape)
+
+
+def random_state(shape, seed, rho_lo=0.2, rho_hi=1.0, u_max=0.05):
+    """Random densities in [rho_lo, rho_hi] and velocities with |u_d| <= u_max,
+    for parity tests of the raw update."""
+    n = int(np.prod(shape))
+    r1 = rho_lo + (rho_hi - rho_lo) * 0.5 * (1.0 + uniform_pm1(seed * 4 + 1, n))
+    r2 = rho_lo + (rho_hi - rho_lo) * 0.5 * (1.0 + uniform_pm1(seed * 4 + 2, n))
+    u = u_max * uniform_pm1(seed * 4 + 3, 3 * n)
+    return r1.reshape(shape), r2.reshape(shape), u.reshape(shape + (3,))
+
+
+# ---------------------------------------------------------------------------
+# The five cases and the 512^3 throughput case.  "G" is the signed Eq. 7 value.
+CONFIGS = {
+    "c0_droplet2d_f64": dict(shape=(1, 64, 64), storage="f64", tau=(1.0, 1.0), G=g_from_config(0.9),
+                             R=16, steps=2000, init="droplet"),
+    "c1_droplet3d_f32": dict(shape=(128, 128, 128), storage="f32", tau=(1.0, 1.0), G=g_from_config(0.9),
+                             R=16, steps=10000, init="droplet",
+                             radii=(12, 16, 20, 24, 32), taus=(0.55, 0.8, 1.0)),
+    "c2_spinodal256": dict(shape=(256, 256, 256), storage="f32", tau=(0.7, 0.7), G=g_from_config(1.2),
+                           steps=5000, init="spinodal"),
+    "c3_adjoint96": dict(shape=(96, 96, 96), storage="f32", tau=(1.0, 1.0), G=g_from_config(0.9),
+                         R=20, steps=500, init="droplet", ckpt_every=25, target_axes=(24, 20, 16)),
+    "c4_wall512": dict(shape=(384, 512, 512), storage="f32", tau=(0.55, 0.55), G=g_from_config(0.9),
+                       R=48, steps=20000, init="hemisphere", collision="regularized",
+                       periodic=(1, 1, 0), g_mag=1e-5, tilt_deg=30.0),
+    "perf512_spinodal_f32": dict(shape=(512, 512, 512), storage="f32", tau=(0.7, 0.7), G=g_from_config(1.2),
+                                 init="spinodal"),
+}
+
+
+def tilted_gravity(g_mag, tilt_deg):
+    """Body acceleration of magnitude g_mag tilted by tilt_deg from -z toward +x."""
+    t = math.radians(tilt_deg)
+    return (g_mag * math.sin(t), 0.0, -g_mag * math.cos(t))
+
+
+def fields_for(name, shape=None, **over):
+    """(rho1, rho2) for a named case, optionally on another shape."""
+    c = dict(CONFIGS[name], **over)
+    shape = tuple(shape or c["shape"])
+    kind = c["init"]
+    if kind == "droplet":
+        return droplet(shape, c["R"])
+    if kind == "spinodal":
+        return spinodal(shape)
+    if kind == "hemisphere":
+        return hemisphere(shape, c["R"])
+    raise KeyError(kind)
