@@ -1,0 +1,368 @@
+#!/usr/bin/env python
+"""Throughput benchmark of the two-component D3Q19 Shan-Chen LBM step on GB300.
+
+One "step" is one full time step (moments, Eq. 7 interaction, collision with
+forcing, streaming) over the whole lattice.  Default workload: the 512^3
+periodic spinodal mixture, FP32 populations, BGK, tau = 0.7.  The metric is
+MLUPS (million two-component cell updates per second) for the whole job.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Multi-GPU (torchrun, N > 1): each rank advances its own independent replica
+(the benchmark runs replicas only: one GPU per process, no exchange), value =
+cells of all ranks x K / (max over ranks of the timed region).
+
+--impl reference times the FP64 CPU oracle (the baseline of this project) on
+a bounded 64^3 cut of the same workload, on rank 0 only.
+"""
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from paper_1601_01237_gb300 import workloads as wl  # noqa: E402
+
+METRIC = "MLUPS (2-comp D3Q19)"
+UNIT = "MLUPS"
+FALLBACK_HBM_GBS = 6800.0
+BYTES_PER_VALUE = {"f64": 8, "f32": 4, "f16_dev": 2, "bf16_dev": 2}
+ORACLE_SAMPLE_SHAPE = (64, 64, 64)
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--workload", default="perf512_spinodal_f32", choices=sorted(wl.CONFIGS))
+    ap.add_argument("--storage", default=None, help="override the workload's population storage")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    return ap.parse_args()
+
+
+def workload_desc(name, cfg, storage):
+    nz, ny, nx = cfg["shape"]
+    return {
+        "workload": "%s: %dx%dx%d two-component D3Q19, %s populations, %s, tau=%s, G_eq7=%.3g, %s" % (
+            name, nx, ny, nz, storage, cfg.get("collision", "bgk"), cfg["tau"][0], cfg["G"],
+            "periodic" if all(cfg.get("periodic", (1, 1, 1))) else "z walls"),
+        "shape_zyx": list(cfg["shape"]),
+        "storage": storage,
+        "collision": cfg.get("collision", "bgk"),
+        "tau": list(cfg["tau"]),
+        "G12_eq7": cfg["G"],
+    }
+
+
+# --------------------------------------------------------------------------
+class ClockSampler:
+    """nvidia-smi clock / throttle sampling during the timed region."""
+
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_index):
+        self.dev = device_index
+        self.proc = None
+        self.lines = []
+        self.thread = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.dev), "--query-gpu=" + self.FIELDS,
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+            return
+        self.thread = threading.Thread(target=self._read, daemon=True)
+        self.thread.start()
+        time.sleep(0.3)
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if not self.proc:
+            return None
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        if self.thread:
+            self.thread.join(timeout=2)
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 8:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                smax.append(float(parts[1]))
+            except ValueError:
+                continue
+            for n, v in zip(names, parts[4:8]):
+                if v.lower() in ("active", "1"):
+                    reasons.add(n)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(smax), "samples": len(sm),
+                "reasons": sorted(reasons)}
+
+
+def measured_hbm_peak():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        d = json.load(open(path))
+    except (OSError, ValueError):
+        return FALLBACK_HBM_GBS, "fallback (MEASURED_PEAKS.json absent)"
+    for key in ("hbm_gbs", "hbm_GBps", "hbm_copy_gbs", "hbm"):
+        v = d.get(key)
+        if isinstance(v, (int, float)):
+            return float(v), "measured (MEASURED_PEAKS.json %s)" % key
+        if isinstance(v, dict):
+            for k2 in ("gbs", "value", "GBps"):
+                if isinstance(v.get(k2), (int, float)):
+                    return float(v[k2]), "measured (MEASURED_PEAKS.json %s.%s)" % (key, k2)
+    return FALLBACK_HBM_GBS, "fallback (no HBM figure in MEASURED_PEAKS.json)"
+
+
+def kernel_source_hash():
+    h = hashlib.sha256()
+    csrc = os.path.join(ROOT, "paper_1601_01237_gb300", "csrc")
+    for f in sorted(os.listdir(csrc)):
+        if f.endswith((".cu", ".cuh", ".h")):
+            h.update(open(os.path.join(csrc, f), "rb").read())
+    return h.hexdigest()[:16]
+
+
+def ncu_traffic(kernel, storage, cells):
+    """DRAM bytes per launch from the committed ncu summary, scaled by cells,
+    or None when the kernels changed since the capture."""
+    path = os.path.join(ROOT, "profiles", "dram_traffic.json")
+    try:
+        d = json.load(open(path))
+    except (OSError, ValueError):
+        return None
+    e = d.get("%s/%s" % (kernel, storage))
+    if not e or e.get("kernel_source_sha") != kernel_source_hash():
+        return None
+    return e["dram_bytes_per_cell"] * cells
+
+
+def algorithmic_bytes_per_cell(kernel, storage):
+    """Minimum HBM bytes per cell of one launch: every population read once
+    and written once (2 components x 19 values x s bytes x 2); the density
+    pass of the two-kernel step reads the populations and writes 2 densities;
+    the collision pass also reads the 2 densities."""
+    s = BYTES_PER_VALUE[storage]
+    r = 8 if storage == "f64" else 4
+    if kernel == "k_density":
+        return 2 * 19 * s + 2 * r
+    if kernel == "k_collide":
+        return 2 * 19 * s * 2 + 2 * r
+    return 2 * 19 * s * 2
+
+
+# --------------------------------------------------------------------------
+def run_reference(args, rank, world):
+    """The FP64 CPU oracle, timed on a bounded cut of the workload."""
+    if rank != 0:
+        return None
+    import oracle
+    cfg = dict(wl.CONFIGS[args.workload])
+    shape = ORACLE_SAMPLE_SHAPE if len(cfg["shape"]) == 3 and cfg["shape"][0] > 1 else cfg["shape"]
+    r1, r2 = wl.fields_for(args.workload, shape=shape)
+    p = oracle.make_params(shape, tau=cfg["tau"], G12=cfg["G"], periodic=cfg.get("periodic", (1, 1, 1)),
+                           collision=cfg.get("collision", "bgk"),
+                           g_ext=wl.tilted_gravity(cfg["g_mag"], cfg["tilt_deg"]) if "g_mag" in cfg else (0, 0, 0))
+    f = oracle.init(p, r1, r2)
+    oracle.step(p, f, args.warmup)
+    t0 = time.perf_counter()
+    oracle.step(p, f, args.steps)
+    dt = time.perf_counter() - t0
+    cells = int(np.prod(shape))
+    value = cells * args.steps / dt / 1e6
+    storage = args.storage or cfg["storage"]
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt / args.steps * 1e3,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic", "config": workload_desc(args.workload, cfg, storage),
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+                         "sample": "%dx%dx%d cut of the workload, %d steps after %d warm-up" % (
+                             shape[2], shape[1], shape[0], args.steps, args.warmup)},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    return line
+
+
+def cpu_baseline(args, cfg):
+    """The oracle as it stands, single-threaded, on a bounded 64^3 cut
+    (about 10-20 s of CPU work)."""
+    import oracle
+    shape = ORACLE_SAMPLE_SHAPE
+    r1, r2 = wl.fields_for(args.workload, shape=shape)
+    p = oracle.make_params(shape, tau=cfg["tau"], G12=cfg["G"], periodic=cfg.get("periodic", (1, 1, 1)),
+                           collision=cfg.get("collision", "bgk"))
+    f = oracle.init(p, r1, r2)
+    oracle.step(p, f, 1)
+    n = 30
+    t0 = time.perf_counter()
+    oracle.step(p, f, n)
+    dt = time.perf_counter() - t0
+    return {"value": int(np.prod(shape)) * n / dt / 1e6, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": "64x64x64 cut of the workload, %d steps, FP64, one thread" % n}
+
+
+def run_ours(args, rank, world, local_rank):
+    import torch
+    from paper_1601_01237_gb300 import Lattice
+    dist = world > 1
+    torch.cuda.set_device(local_rank)
+    cfg = dict(wl.CONFIGS[args.workload])
+    storage = args.storage or cfg["storage"]
+    shape = tuple(cfg["shape"])
+    cells = int(np.prod(shape))
+    g_ext = wl.tilted_gravity(cfg["g_mag"], cfg["tilt_deg"]) if "g_mag" in cfg else (0.0, 0.0, 0.0)
+    kw = dict(storage=storage, tau=cfg["tau"], G12=cfg["G"], periodic=cfg.get("periodic", (1, 1, 1)),
+              collision=cfg.get("collision", "bgk"), g_ext=g_ext,
+              rho0_dev=0.5 if storage.endswith("_dev") else 0.0)
+    r1, r2 = wl.fields_for(args.workload)
+    stream = torch.cuda.current_stream()
+    lat = Lattice(shape, stream=stream.cuda_stream, **kw)
+    d1 = torch.from_numpy(r1).cuda()
+    d2 = torch.from_numpy(r2).cuda()
+    lat.init_fields(d1, d2)
+    del d1, d2
+    lat.step(args.warmup)
+    torch.cuda.synchronize()
+
+    # ---- timed region: K steps, per-kernel events inside -----------------
+    sampler = ClockSampler(local_rank)
+    sampler.start()
+    if dist:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    kern = lat.step_timed(args.steps)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    if dist:
+        torch.distributed.barrier()
+    clocks = sampler.stop()
+    ms = e0.elapsed_time(e1)
+    ms_t = torch.tensor([ms], dtype=torch.float64, device="cuda")
+    if dist:
+        torch.distributed.all_reduce(ms_t, op=torch.distributed.ReduceOp.MAX)
+    ms_max = ms_t.item()
+    value = cells * world * args.steps / (ms_max / 1e3) / 1e6
+    red = lat.reduce()
+
+    # ---- roofline of the dominant kernel ----------------------------------
+    dom = max(kern, key=lambda k: kern[k][0])
+    dom_ms, dom_n = kern[dom]
+    per_launch_s = dom_ms / dom_n / 1e3
+    alg = algorithmic_bytes_per_cell(dom, storage) * cells
+    peak, peak_src = measured_hbm_peak()
+    achieved = alg / per_launch_s / 1e9
+    roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                "traffic": ncu_traffic(dom, storage, cells), "kernel": dom,
+                "algorithmic_bytes_per_launch": alg, "launch_ms": per_launch_s * 1e3,
+                "peak_source": peak_src,
+                "kernels": {k: {"ms_per_launch": v[0] / v[1], "launches": v[1],
+                                "share": v[0] / sum(x[0] for x in kern.values())} for k, v in kern.items()}}
+    step_bytes = 2 * 19 * BYTES_PER_VALUE[storage] * 2 * cells
+    roofline["step_frac_of_peak"] = step_bytes / (ms_max / args.steps / 1e3) / 1e9 / peak
+
+    # ---- end to end through the public API with host buffers -------------
+    e2e = None
+    if not args.no_e2e:
+        h1 = torch.from_numpy(r1).pin_memory()
+        h2 = torch.from_numpy(r2).pin_memory()
+        torch.cuda.synchronize()
+        if dist:
+            torch.distributed.barrier()
+        t0 = time.perf_counter()
+        lat.init_fields(h1, h2)          # H2D of the initial fields (pinned host)
+        lat.step(args.steps)
+        out = lat.reduce()               # D2H of the step's result (FP64 reductions)
+        torch.cuda.synchronize()
+        dt = time.perf_counter() - t0
+        dt_t = torch.tensor([dt], dtype=torch.float64, device="cuda")
+        if dist:
+            torch.distributed.all_reduce(dt_t, op=torch.distributed.ReduceOp.MAX)
+        from paper_1601_01237_gb300.lattice import lib  # noqa: F401
+        e2e = {"value": cells * world * args.steps / dt_t.item() / 1e6, "unit": UNIT,
+               "h2d_bytes_per_step": 2 * cells * 8 / args.steps,
+               "d2h_bytes_per_step": (1216 * 8 * 8) / args.steps,
+               "note": "lbm_init_fields from pinned host + lbm_step(K) + lbm_reduce to host, per step amortised",
+               "mass_check": abs(out["mass1"] - red["mass1"]) / red["mass1"] < 1e-3}
+    lat.close()
+
+    if rank != 0:
+        return None
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64" if storage == "f64" else "f32",
+        "data": "synthetic",
+        "config": dict(workload_desc(args.workload, cfg, storage),
+                       l2="inputs larger than L2: %.1f GB of populations per copy" % (
+                           2 * 19 * BYTES_PER_VALUE[storage] * cells / 1e9),
+                       parallelism="replicas" if world > 1 else "single GPU"),
+        "roofline": roofline,
+        "gpu_launches": sum(v[1] for v in kern.values()),
+        "clocks": clocks,
+        "e2e": e2e,
+        "mass": [red["mass1"], red["mass2"]],
+    }
+    if world == 1 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline(args, cfg)
+    return line
+
+
+def main():
+    args = parse()
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        line = run_reference(args, rank, world)
+        if line:
+            print(json.dumps(line), flush=True)
+        return
+    if world > 1:
+        import torch
+        torch.cuda.set_device(local_rank)
+        torch.distributed.init_process_group("nccl")
+    line = run_ours(args, rank, world, local_rank)
+    if line:
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        import torch
+        torch.distributed.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,171 @@
+/*
+ * lbm.h - C ABI of the GB300 two-component D3Q19 Shan-Chen lattice Boltzmann
+ * library (Otomo et al., "Studies of accurate multi-component lattice
+ * Boltzmann models on benchmark cases required for engineering
+ * applications", arXiv:1601.01237).
+ *
+ * One time step (Sec. 2, Eq. 1) advances the populations f_i^a(x, t) of the
+ * two components a = 1, 2 on a D3Q19 lattice:
+ *   1. moments rho^a = sum_i f_i^a, u = sum_a sum_i c_i f_i^a / rho (Eqs. 4-6);
+ *   2. Shan-Chen interaction F^{ab} = G^{ab} rho^a sum_i w_i c_i rho^b(x + c_i)
+ *      (Eq. 7), plus the wall interaction F_w^{ab} of Eq. 13 at solid
+ *      neighbours, giving g^a = sum_b (F^{ab} + F_w^{ab}) / rho^a + g_ext;
+ *   3. collision toward the third-order equilibrium f^eq(rho^a, u) of Eq. 3
+ *      (T0 = 1/3): BGK (Eq. 2) or the regularized filter (Eqs. 10-11), plus the
+ *      forcing term F_i^a = f^eq_i(rho^a, u + g^a) - f^eq_i(rho^a, u);
+ *   4. streaming f_i^a(x + c_i, t + 1) = f*_i^a(x, t), periodic, or half-way
+ *      bounce-back at solid walls (Sec. 4.1).
+ *
+ * Conventions shared by every call:
+ *   - Fields are indexed [z][y][x] with x fastest; cell = (z*ny + y)*nx + x.
+ *   - Every call returns an lbm_status; none exits or aborts.  On failure a
+ *     message is available from lbm_last_error().
+ *   - Pointers flagged `on_device` are CUDA device pointers on the device that
+ *     was current at lbm_create; otherwise host pointers.  Caller-owned buffers
+ *     are never retained: inputs are copied, outputs are written before the
+ *     call returns (host) or in stream order (device).
+ *   - All device work is issued on the lattice's stream (lbm_params.stream, or
+ *     a stream the library creates when it is NULL).  Device outputs are valid
+ *     once that stream has reached the call; host outputs are valid on return.
+ *   - Errors of kernels already in flight surface at the next call that
+ *     synchronizes (lbm_moments with host outputs, lbm_reduce, lbm_sync).
+ */
+#ifndef LBM_H
+#define LBM_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    LBM_OK = 0,
+    LBM_EINVAL = 1,    /* invalid argument (sizes, tau <= 1/2, NULL pointer, ...) */
+    LBM_ENOMEM = 2,    /* device allocation failed */
+    LBM_ECUDA = 3,     /* CUDA runtime error (launch or asynchronous fault) */
+    LBM_ENOTSUP = 4,   /* valid request this library does not implement */
+    LBM_ENUMERIC = 5   /* non-finite or non-positive density met */
+} lbm_status;
+
+/* Population storage.  Arithmetic is FP64 for LBM_F64 and FP32 otherwise.
+ * The *_DEV formats store the deviation f_i - w_i * rho0_dev in 16 bits. */
+typedef enum {
+    LBM_F64 = 0,
+    LBM_F32 = 1,
+    LBM_F16_DEV = 2,
+    LBM_BF16_DEV = 3
+} lbm_storage;
+
+typedef enum {
+    LBM_BGK = 0,          /* Eq. 2 */
+    LBM_REGULARIZED = 1   /* Eqs. 10-11, second-order Hermite projection */
+} lbm_collision;
+
+/* Density a solid site presents to the interaction sum of Eq. 13. */
+typedef enum {
+    LBM_WALL_POTENTIAL = 0, /* rho'_b = rho_s^b (point-wise wall potential, Sec. 4) */
+    LBM_WALL_MIRROR = 1     /* rho'_b = rho_b(mirror cell) + rho_s^b: zero normal
+                               derivative as Eq. 13 asks (modified model, Sec. 4.1) */
+} lbm_wall_model;
+
+typedef struct {
+    int nx, ny, nz;        /* lattice cells along x, y, z (each >= 1) */
+    int periodic[3];       /* 1 = periodic.  periodic[0] and periodic[1] must be 1;
+                              periodic[2] = 0 puts half-way bounce-back walls at
+                              z = -1/2 and z = nz - 1/2 */
+    double tau[2];         /* relaxation times tau_1, tau_2 (Eq. 2), each > 1/2 */
+    double G[2][2];        /* G^{ab} of Eq. 7, signed exactly as printed there
+                              (repulsion between components is G < 0).
+                              G[0][0] and G[1][1] must be 0 (Sec. 2). */
+    double g_ext[3];       /* body acceleration added to every g^a */
+    double rho_s[2];       /* wall potential rho_s^a (Sec. 4.2) */
+    double rho0_dev;       /* reference density of the *_DEV storage formats */
+    int storage;           /* lbm_storage */
+    int collision;         /* lbm_collision */
+    int wall_model;        /* lbm_wall_model (used only when periodic[2] == 0) */
+    void *stream;          /* cudaStream_t to issue work on; NULL = library-owned stream */
+} lbm_params;
+
+typedef struct lbm_lattice lbm_lattice;   /* opaque handle */
+
+/* The library's D3Q19 direction order (the lattice of Sec. 2): c[i] and w[i].
+ * Populations passed through lbm_get_populations / lbm_set_populations use it.
+ * Either pointer may be NULL. */
+lbm_status lbm_lattice_dirs(int c[19][3], double w[19]);
+
+/* Validate *params, allocate device storage for two population copies and the
+ * density scratch, and return a handle in *out.  Errors: LBM_EINVAL (bad
+ * sizes, tau <= 1/2, NULL pointers, F64 with rho0_dev != 0), LBM_ENOTSUP
+ * (non-zero G^{aa}, x/y walls), LBM_ENOMEM, LBM_ECUDA.  The handle owns its
+ * device memory until lbm_destroy. */
+lbm_status lbm_create(const lbm_params *params, lbm_lattice **out);
+
+/* Initial state f_i^a(x, 0) = f^eq_i(rho^a_0(x), u_0(x)) (Eq. 3).  rho1, rho2:
+ * N = nx*ny*nz doubles each; u: 3N doubles [cell][3] or NULL for u = 0.
+ * Host or device pointers (on_device); contents are copied.  Resets the step
+ * counter to 0.  Errors: LBM_EINVAL, LBM_ECUDA. */
+lbm_status lbm_init_fields(lbm_lattice *h, const double *rho1, const double *rho2,
+                           const double *u, int on_device);
+
+/* Advance n_steps >= 0 full time steps (moments, interaction force, collision
+ * with forcing, streaming; Sec. 2 and Eq. 1 or Eq. 10).  Asynchronous on the
+ * lattice's stream.  Errors: LBM_EINVAL (n_steps < 0), LBM_ECUDA. */
+lbm_status lbm_step(lbm_lattice *h, long n_steps);
+
+/* lbm_step with per-kernel timing: advances n_steps > 0 steps exactly as
+ * lbm_step does, recording a CUDA event pair around every kernel launch on the
+ * lattice's stream, then synchronizes.  kernel_ms[k] receives the total device
+ * time of kernel kind k over the n_steps, launches[k] its launch count, and
+ * names[k] (static strings) its name, for k < *n_kinds <= 4.  Used by the
+ * benchmark for per-launch durations.  Errors: LBM_EINVAL, LBM_ECUDA. */
+lbm_status lbm_step_timed(lbm_lattice *h, long n_steps, double kernel_ms[4], long launches[4],
+                          const char *names[4], int *n_kinds);
+
+/* Output fields of the current state: rho^1, rho^2 (N values each) and the
+ * velocity u_F = u + g/2 (Eqs. 8-9; 3N values [cell][3]).  Element type is
+ * double when out_f64 != 0, else float.  Any output pointer may be NULL.
+ * Host outputs synchronize the stream; device outputs are stream-ordered. */
+lbm_status lbm_moments(lbm_lattice *h, int out_f64, void *rho1, void *rho2, void *uF,
+                       int on_device);
+
+/* FP64 reductions of the current state into out[6]:
+ *   out[0] = sum rho^1, out[1] = sum rho^2,
+ *   out[2..4] = sum rho u_F (total momentum), out[5] = max |u_F|.
+ * Synchronizes the stream.  Returns LBM_ENUMERIC if a density is non-finite
+ * or not positive. */
+lbm_status lbm_reduce(lbm_lattice *h, double out[6]);
+
+/* Copy the populations f_i^a(x, t) of the current state, as doubles laid out
+ * [a][i][z][y][x] in the lbm_lattice_dirs order (2*19*N values), to or from a
+ * caller buffer (host or device).  Used for checkpoints and for population-level
+ * checks; set also resets nothing else (the step counter is kept). */
+lbm_status lbm_get_populations(lbm_lattice *h, double *out, int on_device);
+lbm_status lbm_set_populations(lbm_lattice *h, const double *in, int on_device);
+
+/* Raw state (the storage-format populations) for fast checkpoints:
+ * lbm_state_bytes gives the size; get/set copy it to or from a
+ * caller device buffer of at least that many bytes. */
+lbm_status lbm_state_bytes(const lbm_lattice *h, size_t *bytes);
+lbm_status lbm_get_state(lbm_lattice *h, void *dev_buf, size_t bytes);
+lbm_status lbm_set_state(lbm_lattice *h, const void *dev_buf, size_t bytes);
+
+/* Number of time steps taken since the last lbm_init_fields. */
+lbm_status lbm_step_count(const lbm_lattice *h, long *steps);
+
+/* Wait for all work issued on the lattice's stream; reports asynchronous
+ * errors as LBM_ECUDA. */
+lbm_status lbm_sync(lbm_lattice *h);
+
+/* Release every resource of the handle.  NULL-safe. */
+void lbm_destroy(lbm_lattice *h);
+
+/* Message of the last failure on this thread (empty string if none).  The
+ * handle may be NULL. */
+const char *lbm_last_error(const lbm_lattice *h);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* LBM_H */

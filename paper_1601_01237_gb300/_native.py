@@ -42,6 +42,8 @@ SIGNATURES = [
     ("lbm_create", _I, [ctypes.POINTER(lbm_params), ctypes.POINTER(_VP)]),
     ("lbm_init_fields", _I, [_VP, _VP, _VP, _VP, _I]),
     ("lbm_step", _I, [_VP, _L]),
+    ("lbm_step_timed", _I, [_VP, _L, _DP, ctypes.POINTER(_L), ctypes.POINTER(ctypes.c_char_p),
+                            ctypes.POINTER(_I)]),
     ("lbm_moments", _I, [_VP, _I, _VP, _VP, _VP, _I]),
     ("lbm_reduce", _I, [_VP, _DP]),
     ("lbm_get_populations", _I, [_VP, _VP, _I]),

@@ -1,0 +1,191 @@
+// D3Q19 lattice, storage formats and the per-cell physics shared by the
+// library's kernels (Otomo et al., arXiv:1601.01237, Sec. 2).
+//
+// Direction order of this library: 0 = rest, then opposite pairs side by side
+// (1,2) = +-x, (3,4) = +-y, (5,6) = +-z, then the twelve face diagonals as
+// (7,8) (9,10) (11,12) (13,14) (15,16) (17,18).  opp(i) = i + 1 for odd i,
+// i - 1 for even i > 0.  Weights: 1/3 rest, 1/18 axis links, 1/36 diagonals
+// (the textbook D3Q19 set; the paper names the set but does not print it).
+#pragma once
+
+#include <cuda_fp16.h>
+#include <cuda_bf16.h>
+#include <stdint.h>
+
+namespace lbm {
+
+constexpr int Q = 19;
+
+// Components of c_i, two bits per direction (value + 1), direction 0 in the
+// lowest bits.
+//            i:  0  1  2  3  4  5  6  7  8  9 10 11 12 13 14 15 16 17 18
+//   cx        :  0  1 -1  0  0  0  0  1 -1  1 -1  1 -1  1 -1  0  0  0  0
+//   cy        :  0  0  0  1 -1  0  0  1 -1 -1  1  0  0  0  0  1 -1  1 -1
+//   cz        :  0  0  0  0  0  1 -1  0  0  0  0  1 -1 -1  1  1 -1 -1  1
+__host__ __device__ constexpr uint64_t pack_dirs(const int (&v)[Q])
+{
+    uint64_t r = 0;
+    for (int i = Q - 1; i >= 0; --i) r = (r << 2) | (uint64_t)(v[i] + 1);
+    return r;
+}
+constexpr int kCX[Q] = {0, 1, -1, 0, 0, 0, 0, 1, -1, 1, -1, 1, -1, 1, -1, 0, 0, 0, 0};
+constexpr int kCY[Q] = {0, 0, 0, 1, -1, 0, 0, 1, -1, -1, 1, 0, 0, 0, 0, 1, -1, 1, -1};
+constexpr int kCZ[Q] = {0, 0, 0, 0, 0, 1, -1, 0, 0, 0, 0, 1, -1, -1, 1, 1, -1, -1, 1};
+constexpr uint64_t kPackX = pack_dirs(kCX);
+constexpr uint64_t kPackY = pack_dirs(kCY);
+constexpr uint64_t kPackZ = pack_dirs(kCZ);
+
+__host__ __device__ constexpr int cx(int i) { return (int)((kPackX >> (2 * i)) & 3u) - 1; }
+__host__ __device__ constexpr int cy(int i) { return (int)((kPackY >> (2 * i)) & 3u) - 1; }
+__host__ __device__ constexpr int cz(int i) { return (int)((kPackZ >> (2 * i)) & 3u) - 1; }
+__host__ __device__ constexpr int opp(int i) { return i == 0 ? 0 : ((i & 1) ? i + 1 : i - 1); }
+__host__ __device__ constexpr double wd(int i) { return i == 0 ? 1.0 / 3.0 : (i < 7 ? 1.0 / 18.0 : 1.0 / 36.0); }
+
+template <class R>
+__host__ __device__ constexpr R w(int i) { return (R)wd(i); }
+
+// ---------------------------------------------------------------------------
+// Storage formats.  R = arithmetic type, T = stored type.  The *_DEV formats
+// keep d_i = f_i - w_i rho0 in 16 bits.
+enum StorageKind { ST_F64 = 0, ST_F32 = 1, ST_F16_DEV = 2, ST_BF16_DEV = 3 };
+
+template <int S> struct Store;
+
+template <> struct Store<ST_F64> {
+    using T = double;
+    using R = double;
+    __device__ static __forceinline__ R load(const T *p, R) { return __ldg(p); }
+    __device__ static __forceinline__ void store(T *p, R v, R) { *p = v; }
+};
+template <> struct Store<ST_F32> {
+    using T = float;
+    using R = float;
+    __device__ static __forceinline__ R load(const T *p, R) { return __ldg(p); }
+    __device__ static __forceinline__ void store(T *p, R v, R) { *p = v; }
+};
+template <> struct Store<ST_F16_DEV> {
+    using T = __half;
+    using R = float;
+    __device__ static __forceinline__ R load(const T *p, R ref) { return __half2float(__ldg(p)) + ref; }
+    __device__ static __forceinline__ void store(T *p, R v, R ref) { *p = __float2half_rn(v - ref); }
+};
+template <> struct Store<ST_BF16_DEV> {
+    using T = __nv_bfloat16;
+    using R = float;
+    __device__ static __forceinline__ R load(const T *p, R ref) { return __bfloat162float(__ldg(p)) + ref; }
+    __device__ static __forceinline__ void store(T *p, R v, R ref) { *p = __float2bfloat16_rn(v - ref); }
+};
+
+// ---------------------------------------------------------------------------
+// Kernel-side parameters (by value).
+template <class R>
+struct Phys {
+    int nx, ny, nz;
+    long long N;            // nx*ny*nz
+    int wall_z;             // 1: half-way bounce-back walls at z = -1/2 and nz - 1/2
+    int wall_mirror;        // 1: rho' = mirror + rho_s, 0: rho' = rho_s
+    R omega[2];             // 1 / tau_a
+    R G12, G21;             // G^{12}, G^{21} of Eq. 7 (signed)
+    R gext[3];
+    R rho_s[2];
+    R rho0;                 // reference density of deviation storage (0 otherwise)
+};
+
+// Third-order equilibrium of Eq. 3 with T0 = 1/3, for direction i and its
+// opposite at once: f^eq_i = rho w_i (E + O), f^eq_opp(i) = rho w_i (E - O) with
+//   E = 1 - u^2/(2T0) + (c.u)^2/(2T0^2)
+//   O = (c.u)/T0 - (c.u) u^2/(2T0^2) + (c.u)^3/(6T0^3).
+template <class R>
+__device__ __forceinline__ void feq_pair(R rw, R cu, R usq, R &fp, R &fm)
+{
+    const R cu2 = cu * cu;
+    const R E = R(1) - R(1.5) * usq + R(4.5) * cu2;
+    const R O = cu * (R(3) - R(4.5) * usq + R(4.5) * cu2);
+    fp = rw * (E + O);
+    fm = rw * (E - O);
+}
+
+template <class R>
+__device__ __forceinline__ R cdot(int i, R ux, R uy, R uz)
+{
+    R r = R(0);
+    if (cx(i) == 1) r += ux; else if (cx(i) == -1) r -= ux;
+    if (cy(i) == 1) r += uy; else if (cy(i) == -1) r -= uy;
+    if (cz(i) == 1) r += uz; else if (cz(i) == -1) r -= uz;
+    return r;
+}
+
+// Collision of one component in place: f[] holds the pre-collision f_i^a and
+// receives the post-collision f*_i^a (Eq. 1 with Eq. 2, or Eq. 10), including
+// the forcing term F_i = f^eq_i(rho, u + g) - f^eq_i(rho, u).
+//   BGK:          f* = f^eq(u + g) + (1 - 1/tau) (f - f^eq(u))
+//   regularized:  f* = f^eq(u + g) + (1 - 1/tau) w_i/(2 T0^2) Q_i : Pi^neq,
+//                 Pi^neq = sum_i c_i c_i f_i - rho (T0 I + u u).
+template <class R, bool REG>
+__device__ __forceinline__ void collide(R (&f)[Q], R rho, R ux, R uy, R uz,
+                                        R gx, R gy, R gz, R omega)
+{
+    const R usq = ux * ux + uy * uy + uz * uz;
+    const R vx = ux + gx, vy = uy + gy, vz = uz + gz;
+    const R vsq = vx * vx + vy * vy + vz * vz;
+    const R keep = R(1) - omega;
+    if (!REG) {
+        {
+            const R e0 = rho * w<R>(0) * (R(1) - R(1.5) * usq);
+            const R s0 = rho * w<R>(0) * (R(1) - R(1.5) * vsq);
+            f[0] = s0 + keep * (f[0] - e0);
+        }
+#pragma unroll
+        for (int i = 1; i < Q; i += 2) {
+            const R rw = rho * w<R>(i);
+            R ep, em, sp, sm;
+            feq_pair<R>(rw, cdot<R>(i, ux, uy, uz), usq, ep, em);
+            feq_pair<R>(rw, cdot<R>(i, vx, vy, vz), vsq, sp, sm);
+            f[i] = sp + keep * (f[i] - ep);
+            f[i + 1] = sm + keep * (f[i + 1] - em);
+        }
+    } else {
+        // second moment of f: sum_i c_ia c_ib f_i
+        R pxx = 0, pyy = 0, pzz = 0, pxy = 0, pxz = 0, pyz = 0;
+#pragma unroll
+        for (int i = 1; i < Q; ++i) {
+            const R v = f[i];
+            if (cx(i)) pxx += v;
+            if (cy(i)) pyy += v;
+            if (cz(i)) pzz += v;
+            if (cx(i) && cy(i)) { if (cx(i) == cy(i)) pxy += v; else pxy -= v; }
+            if (cx(i) && cz(i)) { if (cx(i) == cz(i)) pxz += v; else pxz -= v; }
+            if (cy(i) && cz(i)) { if (cy(i) == cz(i)) pyz += v; else pyz -= v; }
+        }
+        const R T0 = R(1) / R(3);
+        pxx -= rho * (T0 + ux * ux);
+        pyy -= rho * (T0 + uy * uy);
+        pzz -= rho * (T0 + uz * uz);
+        pxy -= rho * ux * uy;
+        pxz -= rho * ux * uz;
+        pyz -= rho * uy * uz;
+        const R trace_T0 = T0 * (pxx + pyy + pzz);
+        // f^neq_i = 4.5 w_i (c_i c_i : Pi - T0 tr Pi)
+        {
+            const R s0 = rho * w<R>(0) * (R(1) - R(1.5) * vsq);
+            f[0] = s0 + keep * (R(4.5) * w<R>(0) * (-trace_T0));
+        }
+#pragma unroll
+        for (int i = 1; i < Q; i += 2) {
+            R cc = R(0);
+            if (cx(i)) cc += pxx;
+            if (cy(i)) cc += pyy;
+            if (cz(i)) cc += pzz;
+            if (cx(i) && cy(i)) cc += (cx(i) == cy(i) ? R(2) : R(-2)) * pxy;
+            if (cx(i) && cz(i)) cc += (cx(i) == cz(i) ? R(2) : R(-2)) * pxz;
+            if (cy(i) && cz(i)) cc += (cy(i) == cz(i) ? R(2) : R(-2)) * pyz;
+            const R fneq = R(4.5) * w<R>(i) * (cc - trace_T0);   // same for i and opp(i)
+            R sp, sm;
+            feq_pair<R>(rho * w<R>(i), cdot<R>(i, vx, vy, vz), vsq, sp, sm);
+            f[i] = sp + keep * fneq;
+            f[i + 1] = sm + keep * fneq;
+        }
+    }
+}
+
+}  // namespace lbm

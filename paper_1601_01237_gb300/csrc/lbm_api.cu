@@ -1,0 +1,451 @@
+// C ABI of the library (declared in include/lbm.h): argument validation,
+// device memory, the stream, and the order of kernel launches of a time step.
+#include <cuda_runtime.h>
+#include <math.h>
+#include <stdarg.h>
+#include <stdio.h>
+#include <stdlib.h>
+#include <string.h>
+
+#include <string>
+#include <vector>
+
+#include "../../include/lbm.h"
+#include "d3q19.cuh"
+#include "lbm_internal.h"
+
+struct lbm_lattice {
+    lbm_params params;
+    lbm::HostPhys phys;
+    int device;
+    cudaStream_t stream;
+    bool own_stream;
+    void *f[2];          // population copies (storage format)
+    int cur;             // index of the copy holding the current state
+    void *rho;           // density scratch of the two-kernel step (2*N reals)
+    double *partials;    // reduction partials (device)
+    double *partials_h;  // reduction partials (pinned host)
+    long steps;
+    int use_fused;
+};
+
+namespace {
+
+thread_local std::string g_err;
+
+lbm_status fail(lbm_status st, const char *fmt, ...) __attribute__((format(printf, 2, 3)));
+lbm_status fail(lbm_status st, const char *fmt, ...)
+{
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    g_err = buf;
+    return st;
+}
+
+lbm_status cuda_fail(cudaError_t e, const char *where)
+{
+    if (e == cudaErrorMemoryAllocation)
+        return fail(LBM_ENOMEM, "%s: %s", where, cudaGetErrorString(e));
+    return fail(LBM_ECUDA, "%s: %s", where, cudaGetErrorString(e));
+}
+
+#define CK(expr, where)                                   \
+    do {                                                  \
+        cudaError_t e_ = (expr);                          \
+        if (e_ != cudaSuccess) return cuda_fail(e_, where); \
+    } while (0)
+
+// Make the handle's device current for the duration of a call.
+struct DeviceGuard {
+    int prev = -1;
+    explicit DeviceGuard(int dev)
+    {
+        if (cudaGetDevice(&prev) != cudaSuccess) prev = -1;
+        if (prev != dev) cudaSetDevice(dev);
+    }
+    ~DeviceGuard()
+    {
+        int now = -1;
+        if (prev >= 0 && cudaGetDevice(&now) == cudaSuccess && now != prev) cudaSetDevice(prev);
+    }
+};
+
+bool env_flag(const char *name, int dflt)
+{
+    const char *v = getenv(name);
+    if (!v || !*v) return dflt != 0;
+    return atoi(v) != 0;
+}
+
+lbm_status copy_in(const lbm_lattice *h, void *dst, const void *src, size_t bytes, int on_device)
+{
+    CK(cudaMemcpyAsync(dst, src, bytes, on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice,
+                       h->stream),
+       "copy to device");
+    return LBM_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+lbm_status lbm_lattice_dirs(int c[19][3], double w[19])
+{
+    for (int i = 0; i < lbm::Q; ++i) {
+        if (c) {
+            c[i][0] = lbm::cx(i);
+            c[i][1] = lbm::cy(i);
+            c[i][2] = lbm::cz(i);
+        }
+        if (w) w[i] = lbm::wd(i);
+    }
+    return LBM_OK;
+}
+
+lbm_status lbm_create(const lbm_params *pp, lbm_lattice **out)
+{
+    if (!pp || !out) return fail(LBM_EINVAL, "lbm_create: NULL argument");
+    *out = nullptr;
+    const lbm_params &p = *pp;
+    if (p.nx < 1 || p.ny < 1 || p.nz < 1)
+        return fail(LBM_EINVAL, "lbm_create: sizes must be >= 1 (got %d x %d x %d)", p.nx, p.ny, p.nz);
+    const long long N = (long long)p.nx * p.ny * p.nz;
+    if (N > (1LL << 40)) return fail(LBM_EINVAL, "lbm_create: lattice too large");
+    for (int a = 0; a < 2; ++a)
+        if (!(p.tau[a] > 0.5) || !isfinite(p.tau[a]))
+            return fail(LBM_EINVAL, "lbm_create: tau[%d] = %g must be a finite value > 1/2", a, p.tau[a]);
+    if (p.G[0][0] != 0.0 || p.G[1][1] != 0.0)
+        return fail(LBM_ENOTSUP, "lbm_create: G^{aa} must be 0 (single-component phase transitions are "
+                                 "excluded)");
+    for (int a = 0; a < 2; ++a)
+        for (int b = 0; b < 2; ++b)
+            if (!isfinite(p.G[a][b])) return fail(LBM_EINVAL, "lbm_create: G must be finite");
+    for (int d = 0; d < 3; ++d)
+        if (!isfinite(p.g_ext[d])) return fail(LBM_EINVAL, "lbm_create: g_ext must be finite");
+    if (!isfinite(p.rho_s[0]) || !isfinite(p.rho_s[1]) || !isfinite(p.rho0_dev))
+        return fail(LBM_EINVAL, "lbm_create: rho_s and rho0_dev must be finite");
+    if (p.storage < LBM_F64 || p.storage > LBM_BF16_DEV)
+        return fail(LBM_EINVAL, "lbm_create: unknown storage %d", p.storage);
+    if (p.storage == LBM_F64 && p.rho0_dev != 0.0)
+        return fail(LBM_EINVAL, "lbm_create: rho0_dev applies to the 16-bit deviation formats only");
+    if (p.storage == LBM_F32 && p.rho0_dev != 0.0)
+        return fail(LBM_EINVAL, "lbm_create: rho0_dev applies to the 16-bit deviation formats only");
+    if (p.collision != LBM_BGK && p.collision != LBM_REGULARIZED)
+        return fail(LBM_EINVAL, "lbm_create: unknown collision %d", p.collision);
+    if (p.wall_model != LBM_WALL_POTENTIAL && p.wall_model != LBM_WALL_MIRROR)
+        return fail(LBM_EINVAL, "lbm_create: unknown wall model %d", p.wall_model);
+    for (int d = 0; d < 3; ++d)
+        if (p.periodic[d] != 0 && p.periodic[d] != 1)
+            return fail(LBM_EINVAL, "lbm_create: periodic[%d] must be 0 or 1", d);
+    if (!p.periodic[0] || !p.periodic[1])
+        return fail(LBM_ENOTSUP, "lbm_create: walls are supported along z only");
+
+    lbm_lattice *h = (lbm_lattice *)calloc(1, sizeof(lbm_lattice));
+    if (!h) return fail(LBM_ENOMEM, "lbm_create: host allocation failed");
+    h->params = p;
+    lbm::HostPhys &ph = h->phys;
+    ph.nx = p.nx; ph.ny = p.ny; ph.nz = p.nz; ph.N = N;
+    ph.wall_z = p.periodic[2] ? 0 : 1;
+    ph.wall_mirror = p.wall_model == LBM_WALL_MIRROR;
+    ph.storage = p.storage;
+    ph.collision = p.collision;
+    ph.tau[0] = p.tau[0]; ph.tau[1] = p.tau[1];
+    ph.G12 = p.G[0][1]; ph.G21 = p.G[1][0];
+    for (int d = 0; d < 3; ++d) ph.gext[d] = p.g_ext[d];
+    ph.rho_s[0] = p.rho_s[0]; ph.rho_s[1] = p.rho_s[1];
+    ph.rho0 = p.rho0_dev;
+    h->use_fused = env_flag("LBM_FUSED", 1) && lbm::fused_supported(ph);
+
+    cudaError_t e = cudaGetDevice(&h->device);
+    if (e != cudaSuccess) { free(h); return cuda_fail(e, "lbm_create: cudaGetDevice"); }
+    if (p.stream) {
+        h->stream = (cudaStream_t)p.stream;
+        h->own_stream = false;
+    } else {
+        e = cudaStreamCreateWithFlags(&h->stream, cudaStreamNonBlocking);
+        if (e != cudaSuccess) { free(h); return cuda_fail(e, "lbm_create: stream"); }
+        h->own_stream = true;
+    }
+    const size_t pop_bytes = (size_t)2 * lbm::Q * (size_t)N * lbm::storage_bytes(p.storage);
+    const size_t rho_bytes = (size_t)2 * (size_t)N * lbm::real_bytes(p.storage);
+    const int nb = lbm::reduce_blocks();
+    if ((e = cudaMalloc(&h->f[0], pop_bytes)) != cudaSuccess ||
+        (e = cudaMalloc(&h->f[1], pop_bytes)) != cudaSuccess ||
+        (e = cudaMalloc(&h->rho, rho_bytes)) != cudaSuccess ||
+        (e = cudaMalloc((void **)&h->partials, (size_t)nb * 8 * sizeof(double))) != cudaSuccess ||
+        (e = cudaMallocHost((void **)&h->partials_h, (size_t)nb * 8 * sizeof(double))) != cudaSuccess) {
+        lbm_status st = cuda_fail(e, "lbm_create: allocation");
+        lbm_destroy(h);
+        return st;
+    }
+    // A fresh lattice holds the uniform state rho^1 = rho^2 = 0 until initialised:
+    // zero the populations so that nothing reads uninitialised memory.
+    if ((e = cudaMemsetAsync(h->f[0], 0, pop_bytes, h->stream)) != cudaSuccess ||
+        (e = cudaMemsetAsync(h->f[1], 0, pop_bytes, h->stream)) != cudaSuccess ||
+        (e = cudaStreamSynchronize(h->stream)) != cudaSuccess) {
+        lbm_status st = cuda_fail(e, "lbm_create: clear");
+        lbm_destroy(h);
+        return st;
+    }
+    h->cur = 0;
+    h->steps = 0;
+    *out = h;
+    return LBM_OK;
+}
+
+void lbm_destroy(lbm_lattice *h)
+{
+    if (!h) return;
+    DeviceGuard g(h->device);
+    if (h->stream) cudaStreamSynchronize(h->stream);
+    cudaFree(h->f[0]);
+    cudaFree(h->f[1]);
+    cudaFree(h->rho);
+    cudaFree(h->partials);
+    if (h->partials_h) cudaFreeHost(h->partials_h);
+    if (h->own_stream && h->stream) cudaStreamDestroy(h->stream);
+    free(h);
+}
+
+lbm_status lbm_init_fields(lbm_lattice *h, const double *rho1, const double *rho2, const double *u,
+                           int on_device)
+{
+    if (!h || !rho1 || !rho2) return fail(LBM_EINVAL, "lbm_init_fields: NULL argument");
+    DeviceGuard g(h->device);
+    const size_t N = (size_t)h->phys.N;
+    const double *d1 = rho1, *d2 = rho2, *du = u;
+    void *tmp = nullptr;
+    if (!on_device) {
+        // stage host fields through one temporary device buffer
+        CK(cudaMallocAsync(&tmp, sizeof(double) * N * (u ? 5 : 2), h->stream), "lbm_init_fields: staging");
+        double *t = (double *)tmp;
+        lbm_status st;
+        if ((st = copy_in(h, t, rho1, sizeof(double) * N, 0)) != LBM_OK) return st;
+        if ((st = copy_in(h, t + N, rho2, sizeof(double) * N, 0)) != LBM_OK) return st;
+        if (u && (st = copy_in(h, t + 2 * N, u, sizeof(double) * 3 * N, 0)) != LBM_OK) return st;
+        d1 = t;
+        d2 = t + N;
+        du = u ? t + 2 * N : nullptr;
+    }
+    h->cur = 0;
+    h->steps = 0;
+    CK(lbm::launch_init_feq(h->phys, d1, d2, du, h->f[0], h->stream), "lbm_init_fields: launch");
+    if (tmp) {
+        CK(cudaFreeAsync(tmp, h->stream), "lbm_init_fields: free staging");
+        CK(cudaStreamSynchronize(h->stream), "lbm_init_fields: sync");
+    }
+    return LBM_OK;
+}
+
+lbm_status lbm_step(lbm_lattice *h, long n_steps)
+{
+    if (!h) return fail(LBM_EINVAL, "lbm_step: NULL handle");
+    if (n_steps < 0) return fail(LBM_EINVAL, "lbm_step: n_steps = %ld < 0", n_steps);
+    DeviceGuard g(h->device);
+    for (long t = 0; t < n_steps; ++t) {
+        cudaError_t e;
+        if (h->use_fused)
+            e = lbm::launch_step_fused(h->phys, h->f[h->cur], h->f[h->cur ^ 1], h->stream);
+        else
+            e = lbm::launch_step_split(h->phys, h->f[h->cur], h->f[h->cur ^ 1], h->rho, h->stream);
+        if (e != cudaSuccess) return cuda_fail(e, "lbm_step: launch");
+        h->cur ^= 1;
+        ++h->steps;
+    }
+    return LBM_OK;
+}
+
+lbm_status lbm_step_timed(lbm_lattice *h, long n_steps, double kernel_ms[4], long launches[4],
+                          const char *names[4], int *n_kinds)
+{
+    if (!h || !kernel_ms || !launches || !names || !n_kinds)
+        return fail(LBM_EINVAL, "lbm_step_timed: NULL argument");
+    if (n_steps <= 0) return fail(LBM_EINVAL, "lbm_step_timed: n_steps = %ld must be > 0", n_steps);
+    DeviceGuard g(h->device);
+    const int kinds = h->use_fused ? 1 : 2;
+    const size_t nev = (size_t)n_steps * (kinds + 1);
+    std::vector<cudaEvent_t> ev(nev, nullptr);
+    lbm_status st = LBM_OK;
+    for (size_t k = 0; k < nev && st == LBM_OK; ++k) {
+        cudaError_t e = cudaEventCreate(&ev[k]);
+        if (e != cudaSuccess) st = cuda_fail(e, "lbm_step_timed: event");
+    }
+    for (long t = 0; t < n_steps && st == LBM_OK; ++t) {
+        cudaEvent_t *evt = &ev[(size_t)t * (kinds + 1)];
+        cudaError_t e;
+        if (h->use_fused)
+            e = lbm::launch_step_fused(h->phys, h->f[h->cur], h->f[h->cur ^ 1], h->stream, evt);
+        else
+            e = lbm::launch_step_split(h->phys, h->f[h->cur], h->f[h->cur ^ 1], h->rho, h->stream, evt);
+        if (e != cudaSuccess) { st = cuda_fail(e, "lbm_step_timed: launch"); break; }
+        h->cur ^= 1;
+        ++h->steps;
+    }
+    if (st == LBM_OK) {
+        cudaError_t e = cudaStreamSynchronize(h->stream);
+        if (e != cudaSuccess) st = cuda_fail(e, "lbm_step_timed: sync");
+    }
+    if (st == LBM_OK) {
+        static const char *kFused[1] = {"k_step_fused"};
+        static const char *kSplit[2] = {"k_density", "k_collide"};
+        for (int k = 0; k < 4; ++k) { kernel_ms[k] = 0; launches[k] = 0; names[k] = nullptr; }
+        for (long t = 0; t < n_steps && st == LBM_OK; ++t)
+            for (int k = 0; k < kinds; ++k) {
+                float ms = 0;
+                cudaError_t e = cudaEventElapsedTime(&ms, ev[(size_t)t * (kinds + 1) + k],
+                                                     ev[(size_t)t * (kinds + 1) + k + 1]);
+                if (e != cudaSuccess) { st = cuda_fail(e, "lbm_step_timed: elapsed"); break; }
+                kernel_ms[k] += ms;
+                launches[k] += 1;
+            }
+        for (int k = 0; k < kinds; ++k) names[k] = h->use_fused ? kFused[k] : kSplit[k];
+        *n_kinds = kinds;
+    }
+    for (cudaEvent_t e : ev)
+        if (e) cudaEventDestroy(e);
+    return st;
+}
+
+lbm_status lbm_moments(lbm_lattice *h, int out_f64, void *rho1, void *rho2, void *uF, int on_device)
+{
+    if (!h) return fail(LBM_EINVAL, "lbm_moments: NULL handle");
+    if (!rho1 && !rho2 && !uF) return LBM_OK;
+    DeviceGuard g(h->device);
+    const size_t N = (size_t)h->phys.N;
+    const size_t es = out_f64 ? 8 : 4;
+    if (on_device) {
+        CK(lbm::launch_moments(h->phys, h->f[h->cur], h->rho, out_f64, rho1, rho2, uF, h->stream),
+           "lbm_moments: launch");
+        return LBM_OK;
+    }
+    void *tmp = nullptr;
+    CK(cudaMallocAsync(&tmp, es * N * 5, h->stream), "lbm_moments: staging");
+    char *t = (char *)tmp;
+    CK(lbm::launch_moments(h->phys, h->f[h->cur], h->rho, out_f64, rho1 ? t : nullptr,
+                           rho2 ? t + es * N : nullptr, uF ? t + 2 * es * N : nullptr, h->stream),
+       "lbm_moments: launch");
+    if (rho1) CK(cudaMemcpyAsync(rho1, t, es * N, cudaMemcpyDeviceToHost, h->stream), "lbm_moments: copy");
+    if (rho2) CK(cudaMemcpyAsync(rho2, t + es * N, es * N, cudaMemcpyDeviceToHost, h->stream), "lbm_moments: copy");
+    if (uF) CK(cudaMemcpyAsync(uF, t + 2 * es * N, 3 * es * N, cudaMemcpyDeviceToHost, h->stream), "lbm_moments: copy");
+    CK(cudaFreeAsync(tmp, h->stream), "lbm_moments: free staging");
+    CK(cudaStreamSynchronize(h->stream), "lbm_moments: sync");
+    return LBM_OK;
+}
+
+lbm_status lbm_reduce(lbm_lattice *h, double out[6])
+{
+    if (!h || !out) return fail(LBM_EINVAL, "lbm_reduce: NULL argument");
+    DeviceGuard g(h->device);
+    const int nb = lbm::reduce_blocks();
+    CK(lbm::launch_reduce(h->phys, h->f[h->cur], h->rho, h->partials, h->stream), "lbm_reduce: launch");
+    CK(cudaMemcpyAsync(h->partials_h, h->partials, (size_t)nb * 8 * sizeof(double), cudaMemcpyDeviceToHost,
+                       h->stream),
+       "lbm_reduce: copy");
+    CK(cudaStreamSynchronize(h->stream), "lbm_reduce: sync");
+    double acc[6] = {0, 0, 0, 0, 0, 0}, bad = 0;
+    for (int b = 0; b < nb; ++b) {
+        const double *q = h->partials_h + (size_t)b * 8;
+        for (int k = 0; k < 5; ++k) acc[k] += q[k];
+        acc[5] = fmax(acc[5], q[5]);
+        bad += q[6];
+    }
+    for (int k = 0; k < 6; ++k) out[k] = acc[k];
+    if (bad > 0 || !isfinite(acc[0]) || !isfinite(acc[1]))
+        return fail(LBM_ENUMERIC, "lbm_reduce: %.0f cells with a non-finite or non-positive density", bad);
+    return LBM_OK;
+}
+
+lbm_status lbm_get_populations(lbm_lattice *h, double *out, int on_device)
+{
+    if (!h || !out) return fail(LBM_EINVAL, "lbm_get_populations: NULL argument");
+    DeviceGuard g(h->device);
+    const size_t bytes = sizeof(double) * 2 * lbm::Q * (size_t)h->phys.N;
+    if (on_device) {
+        CK(lbm::launch_get_populations(h->phys, h->f[h->cur], out, h->stream), "lbm_get_populations");
+        return LBM_OK;
+    }
+    void *tmp = nullptr;
+    CK(cudaMallocAsync(&tmp, bytes, h->stream), "lbm_get_populations: staging");
+    CK(lbm::launch_get_populations(h->phys, h->f[h->cur], (double *)tmp, h->stream), "lbm_get_populations");
+    CK(cudaMemcpyAsync(out, tmp, bytes, cudaMemcpyDeviceToHost, h->stream), "lbm_get_populations: copy");
+    CK(cudaFreeAsync(tmp, h->stream), "lbm_get_populations: free");
+    CK(cudaStreamSynchronize(h->stream), "lbm_get_populations: sync");
+    return LBM_OK;
+}
+
+lbm_status lbm_set_populations(lbm_lattice *h, const double *in, int on_device)
+{
+    if (!h || !in) return fail(LBM_EINVAL, "lbm_set_populations: NULL argument");
+    DeviceGuard g(h->device);
+    const size_t bytes = sizeof(double) * 2 * lbm::Q * (size_t)h->phys.N;
+    const double *src = in;
+    void *tmp = nullptr;
+    if (!on_device) {
+        CK(cudaMallocAsync(&tmp, bytes, h->stream), "lbm_set_populations: staging");
+        lbm_status st = copy_in(h, tmp, in, bytes, 0);
+        if (st != LBM_OK) return st;
+        src = (const double *)tmp;
+    }
+    CK(lbm::launch_set_populations(h->phys, src, h->f[h->cur], h->stream), "lbm_set_populations");
+    if (tmp) {
+        CK(cudaFreeAsync(tmp, h->stream), "lbm_set_populations: free");
+        CK(cudaStreamSynchronize(h->stream), "lbm_set_populations: sync");
+    }
+    return LBM_OK;
+}
+
+lbm_status lbm_state_bytes(const lbm_lattice *h, size_t *bytes)
+{
+    if (!h || !bytes) return fail(LBM_EINVAL, "lbm_state_bytes: NULL argument");
+    *bytes = (size_t)2 * lbm::Q * (size_t)h->phys.N * lbm::storage_bytes(h->phys.storage);
+    return LBM_OK;
+}
+
+lbm_status lbm_get_state(lbm_lattice *h, void *dev_buf, size_t bytes)
+{
+    size_t need = 0;
+    lbm_status st = lbm_state_bytes(h, &need);
+    if (st != LBM_OK) return st;
+    if (!dev_buf || bytes < need)
+        return fail(LBM_EINVAL, "lbm_get_state: buffer of %zu bytes, need %zu", bytes, need);
+    DeviceGuard g(h->device);
+    CK(cudaMemcpyAsync(dev_buf, h->f[h->cur], need, cudaMemcpyDeviceToDevice, h->stream), "lbm_get_state");
+    return LBM_OK;
+}
+
+lbm_status lbm_set_state(lbm_lattice *h, const void *dev_buf, size_t bytes)
+{
+    size_t need = 0;
+    lbm_status st = lbm_state_bytes(h, &need);
+    if (st != LBM_OK) return st;
+    if (!dev_buf || bytes < need)
+        return fail(LBM_EINVAL, "lbm_set_state: buffer of %zu bytes, need %zu", bytes, need);
+    DeviceGuard g(h->device);
+    CK(cudaMemcpyAsync(h->f[h->cur], dev_buf, need, cudaMemcpyDeviceToDevice, h->stream), "lbm_set_state");
+    return LBM_OK;
+}
+
+lbm_status lbm_step_count(const lbm_lattice *h, long *steps)
+{
+    if (!h || !steps) return fail(LBM_EINVAL, "lbm_step_count: NULL argument");
+    *steps = h->steps;
+    return LBM_OK;
+}
+
+lbm_status lbm_sync(lbm_lattice *h)
+{
+    if (!h) return fail(LBM_EINVAL, "lbm_sync: NULL handle");
+    DeviceGuard g(h->device);
+    CK(cudaStreamSynchronize(h->stream), "lbm_sync");
+    return LBM_OK;
+}
+
+const char *lbm_last_error(const lbm_lattice *)
+{
+    return g_err.c_str();
+}
+
+}  // extern "C"

@@ -1,0 +1,517 @@
+// Forward-step kernels of the two-component D3Q19 Shan-Chen LBM
+// (Otomo et al., arXiv:1601.01237, Sec. 2 and Sec. 4.1), plus state set-up,
+// output fields and FP64 reductions.
+//
+// Two-kernel design:
+//   k_density : f* (pull-gathered) -> rho^a(x)                     (Eq. 4)
+//   k_collide : f* (pull-gathered), rho^b stencil -> f* (next)     (Eqs. 3-7, 13, 1/2/10)
+// Populations are stored post-collision at their origin cell; a cell's
+// pre-collision population f_i(x, t) is gathered from x - c_i (streaming is
+// the gather), or is the reversed population of x itself when x - c_i lies
+// behind a half-way bounce-back wall.
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "d3q19.cuh"
+#include "lbm_internal.h"
+
+namespace lbm {
+
+namespace {
+
+constexpr int kThreads = 256;
+
+// Neighbourhood of one cell: offsets of x-1, x, x+1 (and likewise y, z) as
+// linear cell offsets with periodic wrap.  Index k = d + 1 for neighbour x + d.
+struct Nbr {
+    long long cell;
+    long long xo[3], yo[3], zo[3];
+    bool zlo_wall, zhi_wall;   // z - 1 (resp. z + 1) is a wall site
+    int z;
+};
+
+template <class R>
+__device__ __forceinline__ bool decode_cell(const Phys<R> &p, long long cell, Nbr &n)
+{
+    if (cell >= p.N) return false;
+    const long long plane = (long long)p.nx * p.ny;
+    const int z = (int)(cell / plane);
+    const long long rem = cell - (long long)z * plane;
+    const int y = (int)(rem / p.nx);
+    const int x = (int)(rem - (long long)y * p.nx);
+    n.cell = cell;
+    n.z = z;
+    n.xo[0] = (x == 0 ? p.nx - 1 : x - 1);
+    n.xo[1] = x;
+    n.xo[2] = (x == p.nx - 1 ? 0 : x + 1);
+    n.yo[0] = (long long)(y == 0 ? p.ny - 1 : y - 1) * p.nx;
+    n.yo[1] = (long long)y * p.nx;
+    n.yo[2] = (long long)(y == p.ny - 1 ? 0 : y + 1) * p.nx;
+    n.zo[0] = (long long)(z == 0 ? p.nz - 1 : z - 1) * plane;
+    n.zo[1] = (long long)z * plane;
+    n.zo[2] = (long long)(z == p.nz - 1 ? 0 : z + 1) * plane;
+    n.zlo_wall = p.wall_z && z == 0;
+    n.zhi_wall = p.wall_z && z == p.nz - 1;
+    return true;
+}
+
+// Pre-collision populations of both components at one cell (streaming as a
+// gather, with half-way bounce-back at z walls).
+template <int S>
+__device__ __forceinline__ void gather(const typename Store<S>::T *__restrict__ f,
+                                       const Phys<typename Store<S>::R> &p, const Nbr &n,
+                                       typename Store<S>::R (&fa)[2][Q])
+{
+    using R = typename Store<S>::R;
+#pragma unroll
+    for (int a = 0; a < 2; ++a) {
+#pragma unroll
+        for (int i = 0; i < Q; ++i) {
+            const R ref = w<R>(i) * p.rho0;
+            const bool wall = (cz(i) == 1 && n.zlo_wall) || (cz(i) == -1 && n.zhi_wall);
+            long long idx;
+            if (wall)
+                idx = (long long)(a * Q + opp(i)) * p.N + n.cell;
+            else
+                idx = (long long)(a * Q + i) * p.N + n.zo[1 - cz(i)] + n.yo[1 - cy(i)] + n.xo[1 - cx(i)];
+            fa[a][i] = Store<S>::load(f + idx, ref);
+        }
+    }
+}
+
+// Interaction sum of Eqs. 7 and 13 for both density fields at one cell:
+//   S^b = sum_{i != 0} w_i c_i rho^b(x + c_i),
+// where a wall site contributes rho'_b = rho_b(mirror) + rho_s^b (modified
+// model) or rho_s^b (point-wise potential).  The mirror of a wall site
+// x + c_i across the z wall is x + c_i with its z component replaced by z.
+template <class R>
+__device__ __forceinline__ void interaction_sums(const R *__restrict__ rho, const Phys<R> &p,
+                                                 const Nbr &n, R (&S)[2][3])
+{
+#pragma unroll
+    for (int b = 0; b < 2; ++b) {
+        R sx = 0, sy = 0, sz = 0;
+        const R *rb = rho + (long long)b * p.N;
+#pragma unroll
+        for (int i = 1; i < Q; ++i) {
+            const bool wall = (cz(i) == -1 && n.zlo_wall) || (cz(i) == 1 && n.zhi_wall);
+            R r;
+            if (wall) {
+                r = p.rho_s[b];
+                if (p.wall_mirror) r += __ldg(rb + n.zo[1] + n.yo[1 + cy(i)] + n.xo[1 + cx(i)]);
+            } else {
+                r = __ldg(rb + n.zo[1 + cz(i)] + n.yo[1 + cy(i)] + n.xo[1 + cx(i)]);
+            }
+            const R wr = w<R>(i) * r;
+            if (cx(i) == 1) sx += wr; else if (cx(i) == -1) sx -= wr;
+            if (cy(i) == 1) sy += wr; else if (cy(i) == -1) sy -= wr;
+            if (cz(i) == 1) sz += wr; else if (cz(i) == -1) sz -= wr;
+        }
+        S[b][0] = sx; S[b][1] = sy; S[b][2] = sz;
+    }
+}
+
+template <class R>
+__device__ __forceinline__ void local_moments(const R (&fa)[2][Q], R &r1, R &r2, R &ux, R &uy, R &uz)
+{
+    R rr[2], jx = 0, jy = 0, jz = 0;
+#pragma unroll
+    for (int a = 0; a < 2; ++a) {
+        R s = 0;
+#pragma unroll
+        for (int i = 0; i < Q; ++i) {
+            const R v = fa[a][i];
+            s += v;
+            if (cx(i) == 1) jx += v; else if (cx(i) == -1) jx -= v;
+            if (cy(i) == 1) jy += v; else if (cy(i) == -1) jy -= v;
+            if (cz(i) == 1) jz += v; else if (cz(i) == -1) jz -= v;
+        }
+        rr[a] = s;
+    }
+    r1 = rr[0];
+    r2 = rr[1];
+    const R inv = R(1) / (r1 + r2);
+    ux = jx * inv;
+    uy = jy * inv;
+    uz = jz * inv;
+}
+
+// ---------------------------------------------------------------------------
+template <int S>
+__global__ void __launch_bounds__(kThreads)
+k_density(const typename Store<S>::T *__restrict__ f, typename Store<S>::R *__restrict__ rho,
+          Phys<typename Store<S>::R> p)
+{
+    using R = typename Store<S>::R;
+    Nbr n;
+    if (!decode_cell(p, (long long)blockIdx.x * kThreads + threadIdx.x, n)) return;
+    R fa[2][Q];
+    gather<S>(f, p, n, fa);
+#pragma unroll
+    for (int a = 0; a < 2; ++a) {
+        R s = 0;
+#pragma unroll
+        for (int i = 0; i < Q; ++i) s += fa[a][i];
+        rho[(long long)a * p.N + n.cell] = s;
+    }
+}
+
+template <int S, bool REG>
+__global__ void __launch_bounds__(kThreads)
+k_collide(const typename Store<S>::T *__restrict__ fin, typename Store<S>::T *__restrict__ fout,
+          const typename Store<S>::R *__restrict__ rho, Phys<typename Store<S>::R> p)
+{
+    using R = typename Store<S>::R;
+    Nbr n;
+    if (!decode_cell(p, (long long)blockIdx.x * kThreads + threadIdx.x, n)) return;
+    R fa[2][Q];
+    gather<S>(fin, p, n, fa);
+    R r1, r2, ux, uy, uz;
+    local_moments(fa, r1, r2, ux, uy, uz);
+    R Sb[2][3];
+    interaction_sums(rho, p, n, Sb);
+    // g^a = sum_b F^{ab} / rho^a + g_ext with F^{ab} = G^{ab} rho^a S^b (G^{aa} = 0)
+    const R g1x = p.G12 * Sb[1][0] + p.gext[0], g1y = p.G12 * Sb[1][1] + p.gext[1],
+            g1z = p.G12 * Sb[1][2] + p.gext[2];
+    const R g2x = p.G21 * Sb[0][0] + p.gext[0], g2y = p.G21 * Sb[0][1] + p.gext[1],
+            g2z = p.G21 * Sb[0][2] + p.gext[2];
+    collide<R, REG>(fa[0], r1, ux, uy, uz, g1x, g1y, g1z, p.omega[0]);
+    collide<R, REG>(fa[1], r2, ux, uy, uz, g2x, g2y, g2z, p.omega[1]);
+#pragma unroll
+    for (int a = 0; a < 2; ++a)
+#pragma unroll
+        for (int i = 0; i < Q; ++i)
+            Store<S>::store(fout + (long long)(a * Q + i) * p.N + n.cell, fa[a][i], w<R>(i) * p.rho0);
+}
+
+// Stored value s_j(y): the population that the gather of step 0 reads as
+// f_j(y + c_j), or, when y + c_j is a wall site, as f_opp(j)(y).
+template <int S>
+__global__ void __launch_bounds__(kThreads)
+k_init_feq(const double *__restrict__ rho1, const double *__restrict__ rho2,
+           const double *__restrict__ u, typename Store<S>::T *__restrict__ f,
+           Phys<typename Store<S>::R> p)
+{
+    using R = typename Store<S>::R;
+    Nbr n;
+    if (!decode_cell(p, (long long)blockIdx.x * kThreads + threadIdx.x, n)) return;
+#pragma unroll
+    for (int j = 0; j < Q; ++j) {
+        const bool wall = (cz(j) == -1 && n.zlo_wall) || (cz(j) == 1 && n.zhi_wall);
+        const long long src = wall ? n.cell : n.zo[1 + cz(j)] + n.yo[1 + cy(j)] + n.xo[1 + cx(j)];
+        const int k = wall ? opp(j) : j;
+        double ux = 0, uy = 0, uz = 0;
+        if (u) { ux = u[3 * src]; uy = u[3 * src + 1]; uz = u[3 * src + 2]; }
+        const double usq = ux * ux + uy * uy + uz * uz;
+        const double cu = cdot<double>(k, ux, uy, uz);
+        const double P = 1.0 - 1.5 * usq + cu * (3.0 - 4.5 * usq) + 4.5 * cu * cu * (1.0 + cu);
+        Store<S>::store(f + (long long)j * p.N + n.cell, (R)(rho1[src] * wd(k) * P), w<R>(j) * p.rho0);
+        Store<S>::store(f + (long long)(Q + j) * p.N + n.cell, (R)(rho2[src] * wd(k) * P), w<R>(j) * p.rho0);
+    }
+}
+
+template <int S>
+__global__ void __launch_bounds__(kThreads)
+k_set_pop(const double *__restrict__ src, typename Store<S>::T *__restrict__ f,
+          Phys<typename Store<S>::R> p)
+{
+    using R = typename Store<S>::R;
+    Nbr n;
+    if (!decode_cell(p, (long long)blockIdx.x * kThreads + threadIdx.x, n)) return;
+#pragma unroll
+    for (int a = 0; a < 2; ++a)
+#pragma unroll
+        for (int j = 0; j < Q; ++j) {
+            const bool wall = (cz(j) == -1 && n.zlo_wall) || (cz(j) == 1 && n.zhi_wall);
+            const long long sc = wall ? n.cell : n.zo[1 + cz(j)] + n.yo[1 + cy(j)] + n.xo[1 + cx(j)];
+            const int k = wall ? opp(j) : j;
+            Store<S>::store(f + (long long)(a * Q + j) * p.N + n.cell,
+                            (R)src[(long long)(a * Q + k) * p.N + sc], w<R>(j) * p.rho0);
+        }
+}
+
+template <int S>
+__global__ void __launch_bounds__(kThreads)
+k_get_pop(const typename Store<S>::T *__restrict__ f, double *__restrict__ dst,
+          Phys<typename Store<S>::R> p)
+{
+    using R = typename Store<S>::R;
+    Nbr n;
+    if (!decode_cell(p, (long long)blockIdx.x * kThreads + threadIdx.x, n)) return;
+    R fa[2][Q];
+    gather<S>(f, p, n, fa);
+#pragma unroll
+    for (int a = 0; a < 2; ++a)
+#pragma unroll
+        for (int i = 0; i < Q; ++i) dst[(long long)(a * Q + i) * p.N + n.cell] = (double)fa[a][i];
+}
+
+// Velocity of Eq. 8: u_F = u + g/2 with g = sum_a g^a rho^a / rho (Eq. 9).
+template <class R>
+__device__ __forceinline__ void velocity_uF(const Phys<R> &p, R r1, R r2, R ux, R uy, R uz,
+                                            const R (&Sb)[2][3], R &fx, R &fy, R &fz)
+{
+    const R g1[3] = {p.G12 * Sb[1][0] + p.gext[0], p.G12 * Sb[1][1] + p.gext[1], p.G12 * Sb[1][2] + p.gext[2]};
+    const R g2[3] = {p.G21 * Sb[0][0] + p.gext[0], p.G21 * Sb[0][1] + p.gext[1], p.G21 * Sb[0][2] + p.gext[2]};
+    const R half_inv = R(0.5) / (r1 + r2);
+    fx = ux + (g1[0] * r1 + g2[0] * r2) * half_inv;
+    fy = uy + (g1[1] * r1 + g2[1] * r2) * half_inv;
+    fz = uz + (g1[2] * r1 + g2[2] * r2) * half_inv;
+}
+
+template <int S, class O>
+__global__ void __launch_bounds__(kThreads)
+k_moments(const typename Store<S>::T *__restrict__ f, const typename Store<S>::R *__restrict__ rho,
+          O *__restrict__ o1, O *__restrict__ o2, O *__restrict__ ouF, Phys<typename Store<S>::R> p)
+{
+    using R = typename Store<S>::R;
+    Nbr n;
+    if (!decode_cell(p, (long long)blockIdx.x * kThreads + threadIdx.x, n)) return;
+    R fa[2][Q];
+    gather<S>(f, p, n, fa);
+    R r1, r2, ux, uy, uz;
+    local_moments(fa, r1, r2, ux, uy, uz);
+    if (o1) o1[n.cell] = (O)r1;
+    if (o2) o2[n.cell] = (O)r2;
+    if (ouF) {
+        R Sb[2][3];
+        interaction_sums(rho, p, n, Sb);
+        R fx, fy, fz;
+        velocity_uF(p, r1, r2, ux, uy, uz, Sb, fx, fy, fz);
+        ouF[3 * n.cell] = (O)fx;
+        ouF[3 * n.cell + 1] = (O)fy;
+        ouF[3 * n.cell + 2] = (O)fz;
+    }
+}
+
+constexpr int kReduceBlocks = 1216;   // 152 SMs x 8
+
+template <int S>
+__global__ void __launch_bounds__(kThreads)
+k_reduce(const typename Store<S>::T *__restrict__ f, const typename Store<S>::R *__restrict__ rho,
+         double *__restrict__ partials, Phys<typename Store<S>::R> p)
+{
+    using R = typename Store<S>::R;
+    double acc[6] = {0, 0, 0, 0, 0, 0};
+    double bad = 0;
+    for (long long c = (long long)blockIdx.x * kThreads + threadIdx.x; c < p.N;
+         c += (long long)gridDim.x * kThreads) {
+        Nbr n;
+        decode_cell(p, c, n);
+        R fa[2][Q];
+        gather<S>(f, p, n, fa);
+        R r1, r2, ux, uy, uz;
+        local_moments(fa, r1, r2, ux, uy, uz);
+        R Sb[2][3];
+        interaction_sums(rho, p, n, Sb);
+        R fx, fy, fz;
+        velocity_uF(p, r1, r2, ux, uy, uz, Sb, fx, fy, fz);
+        const double rho_t = (double)r1 + (double)r2;
+        if (!(r1 > R(0)) || !(r2 > R(0)) || !isfinite((double)r1) || !isfinite((double)r2)) bad += 1;
+        acc[0] += (double)r1;
+        acc[1] += (double)r2;
+        acc[2] += rho_t * (double)fx;
+        acc[3] += rho_t * (double)fy;
+        acc[4] += rho_t * (double)fz;
+        const double m = sqrt((double)fx * fx + (double)fy * fy + (double)fz * fz);
+        acc[5] = fmax(acc[5], m);
+    }
+    // fixed-order block reduction (deterministic)
+    __shared__ double sh[7][kThreads];
+    for (int k = 0; k < 6; ++k) sh[k][threadIdx.x] = acc[k];
+    sh[6][threadIdx.x] = bad;
+    __syncthreads();
+    for (int stride = kThreads / 2; stride > 0; stride >>= 1) {
+        if (threadIdx.x < stride) {
+            for (int k = 0; k < 7; ++k) {
+                if (k == 5)
+                    sh[k][threadIdx.x] = fmax(sh[k][threadIdx.x], sh[k][threadIdx.x + stride]);
+                else
+                    sh[k][threadIdx.x] += sh[k][threadIdx.x + stride];
+            }
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x < 7) partials[(long long)blockIdx.x * 8 + threadIdx.x] = sh[threadIdx.x][0];
+    if (threadIdx.x == 7) partials[(long long)blockIdx.x * 8 + 7] = 0.0;
+}
+
+template <class R>
+Phys<R> make_phys(const HostPhys &h)
+{
+    Phys<R> p;
+    p.nx = h.nx; p.ny = h.ny; p.nz = h.nz; p.N = h.N;
+    p.wall_z = h.wall_z;
+    p.wall_mirror = h.wall_mirror;
+    p.omega[0] = (R)(1.0 / h.tau[0]);
+    p.omega[1] = (R)(1.0 / h.tau[1]);
+    p.G12 = (R)h.G12; p.G21 = (R)h.G21;
+    for (int d = 0; d < 3; ++d) p.gext[d] = (R)h.gext[d];
+    p.rho_s[0] = (R)h.rho_s[0]; p.rho_s[1] = (R)h.rho_s[1];
+    p.rho0 = (R)h.rho0;
+    return p;
+}
+
+inline unsigned grid_for(long long N) { return (unsigned)((N + kThreads - 1) / kThreads); }
+
+template <int S>
+cudaError_t step_split_t(const HostPhys &h, const void *fin, void *fout, void *rho, cudaStream_t s,
+                         cudaEvent_t *ev)
+{
+    using T = typename Store<S>::T;
+    using R = typename Store<S>::R;
+    const Phys<R> p = make_phys<R>(h);
+    const unsigned g = grid_for(h.N);
+    if (ev) cudaEventRecord(ev[0], s);
+    k_density<S><<<g, kThreads, 0, s>>>((const T *)fin, (R *)rho, p);
+    if (ev) cudaEventRecord(ev[1], s);
+    if (h.collision == LBM_REGULARIZED)
+        k_collide<S, true><<<g, kThreads, 0, s>>>((const T *)fin, (T *)fout, (const R *)rho, p);
+    else
+        k_collide<S, false><<<g, kThreads, 0, s>>>((const T *)fin, (T *)fout, (const R *)rho, p);
+    if (ev) cudaEventRecord(ev[2], s);
+    return cudaGetLastError();
+}
+
+template <int S>
+cudaError_t init_t(const HostPhys &h, const double *r1, const double *r2, const double *u, void *f,
+                   cudaStream_t s)
+{
+    using T = typename Store<S>::T;
+    using R = typename Store<S>::R;
+    k_init_feq<S><<<grid_for(h.N), kThreads, 0, s>>>(r1, r2, u, (T *)f, make_phys<R>(h));
+    return cudaGetLastError();
+}
+
+template <int S>
+cudaError_t setpop_t(const HostPhys &h, const double *src, void *f, cudaStream_t s)
+{
+    using T = typename Store<S>::T;
+    using R = typename Store<S>::R;
+    k_set_pop<S><<<grid_for(h.N), kThreads, 0, s>>>(src, (T *)f, make_phys<R>(h));
+    return cudaGetLastError();
+}
+
+template <int S>
+cudaError_t getpop_t(const HostPhys &h, const void *f, double *dst, cudaStream_t s)
+{
+    using T = typename Store<S>::T;
+    using R = typename Store<S>::R;
+    k_get_pop<S><<<grid_for(h.N), kThreads, 0, s>>>((const T *)f, dst, make_phys<R>(h));
+    return cudaGetLastError();
+}
+
+template <int S>
+cudaError_t moments_t(const HostPhys &h, const void *f, void *rho, int out_f64, void *o1, void *o2,
+                      void *ouF, cudaStream_t s)
+{
+    using T = typename Store<S>::T;
+    using R = typename Store<S>::R;
+    const Phys<R> p = make_phys<R>(h);
+    const unsigned g = grid_for(h.N);
+    if (ouF) k_density<S><<<g, kThreads, 0, s>>>((const T *)f, (R *)rho, p);
+    if (out_f64)
+        k_moments<S, double><<<g, kThreads, 0, s>>>((const T *)f, (const R *)rho, (double *)o1,
+                                                    (double *)o2, (double *)ouF, p);
+    else
+        k_moments<S, float><<<g, kThreads, 0, s>>>((const T *)f, (const R *)rho, (float *)o1,
+                                                   (float *)o2, (float *)ouF, p);
+    return cudaGetLastError();
+}
+
+template <int S>
+cudaError_t reduce_t(const HostPhys &h, const void *f, void *rho, double *partials, cudaStream_t s)
+{
+    using T = typename Store<S>::T;
+    using R = typename Store<S>::R;
+    const Phys<R> p = make_phys<R>(h);
+    k_density<S><<<grid_for(h.N), kThreads, 0, s>>>((const T *)f, (R *)rho, p);
+    k_reduce<S><<<kReduceBlocks, kThreads, 0, s>>>((const T *)f, (const R *)rho, partials, p);
+    return cudaGetLastError();
+}
+
+}  // namespace
+
+cudaError_t launch_step_split(const HostPhys &p, const void *f_in, void *f_out, void *rho, cudaStream_t s,
+                              cudaEvent_t *ev)
+{
+    switch (p.storage) {
+    case ST_F64: return step_split_t<ST_F64>(p, f_in, f_out, rho, s, ev);
+    case ST_F32: return step_split_t<ST_F32>(p, f_in, f_out, rho, s, ev);
+    case ST_F16_DEV: return step_split_t<ST_F16_DEV>(p, f_in, f_out, rho, s, ev);
+    case ST_BF16_DEV: return step_split_t<ST_BF16_DEV>(p, f_in, f_out, rho, s, ev);
+    default: return cudaErrorInvalidValue;
+    }
+}
+
+cudaError_t launch_init_feq(const HostPhys &p, const double *r1, const double *r2, const double *u,
+                            void *f, cudaStream_t s)
+{
+    switch (p.storage) {
+    case ST_F64: return init_t<ST_F64>(p, r1, r2, u, f, s);
+    case ST_F32: return init_t<ST_F32>(p, r1, r2, u, f, s);
+    case ST_F16_DEV: return init_t<ST_F16_DEV>(p, r1, r2, u, f, s);
+    case ST_BF16_DEV: return init_t<ST_BF16_DEV>(p, r1, r2, u, f, s);
+    default: return cudaErrorInvalidValue;
+    }
+}
+
+cudaError_t launch_set_populations(const HostPhys &p, const double *src, void *f, cudaStream_t s)
+{
+    switch (p.storage) {
+    case ST_F64: return setpop_t<ST_F64>(p, src, f, s);
+    case ST_F32: return setpop_t<ST_F32>(p, src, f, s);
+    case ST_F16_DEV: return setpop_t<ST_F16_DEV>(p, src, f, s);
+    case ST_BF16_DEV: return setpop_t<ST_BF16_DEV>(p, src, f, s);
+    default: return cudaErrorInvalidValue;
+    }
+}
+
+cudaError_t launch_get_populations(const HostPhys &p, const void *f, double *dst, cudaStream_t s)
+{
+    switch (p.storage) {
+    case ST_F64: return getpop_t<ST_F64>(p, f, dst, s);
+    case ST_F32: return getpop_t<ST_F32>(p, f, dst, s);
+    case ST_F16_DEV: return getpop_t<ST_F16_DEV>(p, f, dst, s);
+    case ST_BF16_DEV: return getpop_t<ST_BF16_DEV>(p, f, dst, s);
+    default: return cudaErrorInvalidValue;
+    }
+}
+
+cudaError_t launch_moments(const HostPhys &p, const void *f, void *rho, int out_f64, void *o1, void *o2,
+                           void *ouF, cudaStream_t s)
+{
+    switch (p.storage) {
+    case ST_F64: return moments_t<ST_F64>(p, f, rho, out_f64, o1, o2, ouF, s);
+    case ST_F32: return moments_t<ST_F32>(p, f, rho, out_f64, o1, o2, ouF, s);
+    case ST_F16_DEV: return moments_t<ST_F16_DEV>(p, f, rho, out_f64, o1, o2, ouF, s);
+    case ST_BF16_DEV: return moments_t<ST_BF16_DEV>(p, f, rho, out_f64, o1, o2, ouF, s);
+    default: return cudaErrorInvalidValue;
+    }
+}
+
+int reduce_blocks() { return kReduceBlocks; }
+
+cudaError_t launch_reduce(const HostPhys &p, const void *f, void *rho, double *partials, cudaStream_t s)
+{
+    switch (p.storage) {
+    case ST_F64: return reduce_t<ST_F64>(p, f, rho, partials, s);
+    case ST_F32: return reduce_t<ST_F32>(p, f, rho, partials, s);
+    case ST_F16_DEV: return reduce_t<ST_F16_DEV>(p, f, rho, partials, s);
+    case ST_BF16_DEV: return reduce_t<ST_BF16_DEV>(p, f, rho, partials, s);
+    default: return cudaErrorInvalidValue;
+    }
+}
+
+size_t storage_bytes(int storage)
+{
+    switch (storage) {
+    case ST_F64: return 8;
+    case ST_F32: return 4;
+    default: return 2;
+    }
+}
+
+size_t real_bytes(int storage) { return storage == ST_F64 ? 8 : 4; }
+
+}  // namespace lbm

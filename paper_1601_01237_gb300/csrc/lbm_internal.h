@@ -1,0 +1,66 @@
+// Internal interface between the C ABI (lbm_api.cu) and the kernel launchers.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stddef.h>
+
+#include "../../include/lbm.h"
+
+namespace lbm {
+
+// Launch geometry and physics of one lattice, in host form.
+struct HostPhys {
+    int nx, ny, nz;
+    long long N;
+    int wall_z;
+    int wall_mirror;
+    int storage;
+    int collision;
+    double tau[2];
+    double G12, G21;
+    double gext[3];
+    double rho_s[2];
+    double rho0;
+};
+
+// Populations are stored as 2*19*N values of the storage type, laid out
+// [a][i][cell], holding the post-collision values f*_i^a at their origin cell
+// ("pull" streaming: f_i^a(x, t) = f*_i^a(x - c_i, t - 1), or the reversed
+// population of x itself when x - c_i is a wall site).
+
+// One full time step with the two-kernel design: density pass into rho
+// (scratch, 2*N arithmetic values), then force + collision + streaming from
+// f_in into f_out.
+// ev (optional, 3 events): recorded before the density pass, between the
+// passes and after the collision pass.
+cudaError_t launch_step_split(const HostPhys &p, const void *f_in, void *f_out, void *rho,
+                              cudaStream_t s, cudaEvent_t *ev = nullptr);
+
+// One full time step with the fused single-pass kernel (no scratch).
+// ev (optional, 2 events): recorded before and after the launch.
+cudaError_t launch_step_fused(const HostPhys &p, const void *f_in, void *f_out, cudaStream_t s,
+                              cudaEvent_t *ev = nullptr);
+bool fused_supported(const HostPhys &p);
+
+// State set-up: populations from (rho1, rho2, u) via f^eq (u may be NULL),
+// or from explicit populations f[a][i][cell] in library order (doubles).
+cudaError_t launch_init_feq(const HostPhys &p, const double *rho1, const double *rho2,
+                            const double *u, void *f, cudaStream_t s);
+cudaError_t launch_set_populations(const HostPhys &p, const double *src, void *f, cudaStream_t s);
+cudaError_t launch_get_populations(const HostPhys &p, const void *f, double *dst, cudaStream_t s);
+
+// Output fields (rho1, rho2, u_F), each pointer optional; out_f64 selects the
+// element type.  Uses rho (scratch) for the density pass.
+cudaError_t launch_moments(const HostPhys &p, const void *f, void *rho, int out_f64,
+                           void *rho1, void *rho2, void *uF, cudaStream_t s);
+
+// FP64 reduction partials: nblocks x 8 doubles
+// (mass1, mass2, px, py, pz, max|uF|, bad-density count, unused).
+int reduce_blocks();
+cudaError_t launch_reduce(const HostPhys &p, const void *f, void *rho, double *partials,
+                          cudaStream_t s);
+
+size_t storage_bytes(int storage);   // bytes per stored population value
+size_t real_bytes(int storage);      // bytes per arithmetic value
+
+}  // namespace lbm

@@ -57,6 +57,17 @@ def lbm_step(h, n_steps):
     check(lib().lbm_step(h, int(n_steps)), h)
 
 
+def lbm_step_timed(h, n_steps):
+    """Advance n_steps with per-kernel CUDA events; returns
+    {kernel name: (total ms, launches)}."""
+    ms = (ctypes.c_double * 4)()
+    nl = (ctypes.c_long * 4)()
+    names = (ctypes.c_char_p * 4)()
+    nk = ctypes.c_int()
+    check(lib().lbm_step_timed(h, int(n_steps), ms, nl, names, ctypes.byref(nk)), h)
+    return {names[k].decode(): (ms[k], nl[k]) for k in range(nk.value)}
+
+
 def lbm_moments(h, rho1=None, rho2=None, uF=None, out_f64=True):
     ptrs = [_ptr(x) for x in (rho1, rho2, uF)]
     devs = {d for (p, d), x in zip(ptrs, (rho1, rho2, uF)) if x is not None}
@@ -179,6 +190,9 @@ class Lattice:
 
     def step(self, n=1):
         lbm_step(self.h, n)
+
+    def step_timed(self, n):
+        return lbm_step_timed(self.h, n)
 
     def moments(self, out_f64=True):
         """Host copies (rho1, rho2, uF) shaped (nz,ny,nx), (nz,ny,nx), (nz,ny,nx,3)."""

@@ -17,7 +17,12 @@ Recipes (Otomo et al., arXiv:1601.01237):
 Interaction strength: the configurations quote G as a repulsion strength for
 weights normalised to a unit second moment (w_i / T0).  Eq. 7 uses the lattice
 weights w_i with a signed G, so the lattice value is G_eq7 = -G_cfg / T0 =
--3 G_cfg (repulsive).
+-3 G_cfg (repulsive).  Where that value makes the FP64 oracle diverge (the
+spinodal mixture at tau = 0.7 with G_eq7 = -3.6, and tau = 0.55 with -2.7,
+both within a few hundred steps), the cases use G_eq7 = -1.2 instead, which
+is still above the discrete spinodal threshold |G| rho0 = 1 - 1/(2 tau) of the
+BGK scheme and above the droplet's coexistence threshold for the regularized
+one.
 """
 import math
 
@@ -121,14 +126,14 @@ CONFIGS = {
     "c1_droplet3d_f32": dict(shape=(128, 128, 128), storage="f32", tau=(1.0, 1.0), G=g_from_config(0.9),
                              R=16, steps=10000, init="droplet",
                              radii=(12, 16, 20, 24, 32), taus=(0.55, 0.8, 1.0)),
-    "c2_spinodal256": dict(shape=(256, 256, 256), storage="f32", tau=(0.7, 0.7), G=g_from_config(1.2),
+    "c2_spinodal256": dict(shape=(256, 256, 256), storage="f32", tau=(0.7, 0.7), G=-1.2,
                            steps=5000, init="spinodal"),
     "c3_adjoint96": dict(shape=(96, 96, 96), storage="f32", tau=(1.0, 1.0), G=g_from_config(0.9),
                          R=20, steps=500, init="droplet", ckpt_every=25, target_axes=(24, 20, 16)),
-    "c4_wall512": dict(shape=(384, 512, 512), storage="f32", tau=(0.55, 0.55), G=g_from_config(0.9),
+    "c4_wall512": dict(shape=(384, 512, 512), storage="f32", tau=(0.55, 0.55), G=-1.2,
                        R=48, steps=20000, init="hemisphere", collision="regularized",
                        periodic=(1, 1, 0), g_mag=1e-5, tilt_deg=30.0),
-    "perf512_spinodal_f32": dict(shape=(512, 512, 512), storage="f32", tau=(0.7, 0.7), G=g_from_config(1.2),
+    "perf512_spinodal_f32": dict(shape=(512, 512, 512), storage="f32", tau=(0.7, 0.7), G=-1.2,
                                  init="spinodal"),
 }
 

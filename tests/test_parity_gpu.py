@@ -1,0 +1,234 @@
+"""GPU parity: the CUDA library (through its C ABI) against the FP64 oracle on
+the same seeded inputs.
+
+Tolerances:
+  * FP64 storage: populations and fields within 1e-12 (one step) and 1e-10
+    (hundreds of steps) relative to the field's maximum.
+  * FP32 storage: max |d rho| / rho <= 1e-5 after 1000 steps (stable cases).
+  * FP16 / BF16 deviation storage: error reported by the low-precision tests.
+"""
+import numpy as np
+import pytest
+
+from _helpers import Q, direction_map, gpu_run, oracle_run, rel_err
+from paper_1601_01237_gb300 import workloads as wl
+
+pytestmark = pytest.mark.gpu
+
+G_DROP = wl.g_from_config(0.9)
+
+CASES = [
+    # (name, shape, kwargs)
+    ("periodic_bgk", (3, 7, 5), dict(tau=(0.8, 1.3), G12=-1.5)),
+    ("periodic_bgk_asymG", (4, 6, 9), dict(tau=(0.7, 0.7), G12=-1.2, G21=-0.9, g_ext=(1e-4, -2e-4, 3e-5))),
+    ("periodic_reg", (5, 4, 6), dict(tau=(0.6, 1.1), G12=-1.4, collision="regularized")),
+    ("wall_mirror_bgk", (6, 5, 7), dict(tau=(0.9, 0.9), G12=-1.5, periodic=(1, 1, 0), g_ext=(1e-4, 0, -2e-4))),
+    ("wall_mirror_rhos_reg", (5, 6, 4), dict(tau=(0.7, 1.2), G12=-1.3, periodic=(1, 1, 0), rho_s=(0.05, 0.1),
+                                             collision="regularized")),
+    ("wall_potential_bgk", (4, 5, 6), dict(tau=(1.0, 0.8), G12=-1.1, periodic=(1, 1, 0), rho_s=(0.0, 0.2),
+                                           wall_model="potential")),
+    ("single_layer_walls", (1, 6, 5), dict(tau=(0.9, 0.9), G12=-1.0, periodic=(1, 1, 0))),
+    ("nx1_ny1", (7, 1, 1), dict(tau=(0.8, 0.8), G12=-1.2)),
+    ("quasi2d", (1, 9, 11), dict(tau=(1.0, 1.0), G12=G_DROP)),
+]
+
+
+def _kw_gpu(kw):
+    out = dict(kw)
+    return out
+
+
+@pytest.mark.parametrize("name,shape,kw", CASES, ids=[c[0] for c in CASES])
+def test_populations_one_step_f64(gpu_lib, name, shape, kw):
+    """Every population after 1 and 3 steps from a random state, FP64."""
+    perm = direction_map()
+    r1, r2, u = wl.random_state(shape, seed=11, u_max=0.04)
+    for nsteps in (0, 1, 3):
+        p, f_or = oracle_run(shape, r1, r2, u, nsteps, **kw)
+        lat = gpu_run(shape, r1, r2, u, nsteps, storage="f64", **_kw_gpu(kw))
+        f_gpu = lat.get_populations()
+        lat.close()
+        f_ref = f_or[:, perm]
+        assert f_gpu.shape == f_ref.shape
+        err = rel_err(f_gpu, f_ref)
+        assert err < 1e-13, (name, nsteps, err)
+
+
+@pytest.mark.parametrize("name,shape,kw", CASES[:6], ids=[c[0] for c in CASES[:6]])
+def test_fields_many_steps_f64(gpu_lib, name, shape, kw):
+    """rho^1, rho^2 and u_F (Eqs. 4, 8) after 200 steps, FP64."""
+    import oracle
+    r1, r2, u = wl.random_state(shape, seed=5, u_max=0.02)
+    p, f_or = oracle_run(shape, r1, r2, u, 200, **kw)
+    a, b, uF = oracle.moments(p, f_or)
+    lat = gpu_run(shape, r1, r2, u, 200, storage="f64", **kw)
+    ga, gb, guF = lat.moments(out_f64=True)
+    lat.close()
+    assert rel_err(ga, a) < 1e-11
+    assert rel_err(gb, b) < 1e-11
+    assert np.max(np.abs(guF - uF)) < 1e-11 * max(np.abs(uF).max(), 1e-3)
+
+
+def test_droplet_c0_f64(gpu_lib):
+    """The quasi-2D droplet case (64x64x1, R = 16, tau = 1, FP64), 300 steps."""
+    import oracle
+    shape = (1, 64, 64)
+    r1, r2 = wl.droplet(shape, 16)
+    p, f_or = oracle_run(shape, r1, r2, None, 300, G12=G_DROP)
+    a, b, uF = oracle.moments(p, f_or)
+    lat = gpu_run(shape, r1, r2, None, 300, storage="f64", G12=G_DROP)
+    ga, gb, guF = lat.moments()
+    red = lat.reduce()
+    lat.close()
+    assert rel_err(ga, a) < 1e-10 and rel_err(gb, b) < 1e-10
+    assert np.max(np.abs(guF - uF)) < 1e-10 * np.abs(uF).max()
+    assert abs(red["mass1"] - a.sum()) < 1e-10 * a.sum()
+    assert abs(red["mass2"] - b.sum()) < 1e-10 * b.sum()
+    assert abs(red["max_uF"] - np.sqrt((uF ** 2).sum(-1)).max()) < 1e-10
+
+
+def test_f32_droplet_1000_steps(gpu_lib):
+    """FP32 storage and arithmetic: max |d rho|/rho <= 1e-5 after 1000 steps
+    (3D droplet on 24^3, tau = 1)."""
+    import oracle
+    shape = (24, 24, 24)
+    r1, r2 = wl.droplet(shape, 7)
+    p, f_or = oracle_run(shape, r1, r2, None, 1000, G12=G_DROP)
+    a, b, uF = oracle.moments(p, f_or)
+    lat = gpu_run(shape, r1, r2, None, 1000, storage="f32", G12=G_DROP)
+    ga, gb, guF = lat.moments()
+    lat.close()
+    e1 = np.max(np.abs(ga - a) / a)
+    e2 = np.max(np.abs(gb - b) / b)
+    print("FP32 1000 steps: max|drho1|/rho1 = %.3g, max|drho2|/rho2 = %.3g" % (e1, e2))
+    assert e1 <= 1e-5 and e2 <= 1e-5
+
+
+def test_f32_regularized_wall(gpu_lib):
+    """FP32, regularized collision, mirror wetting walls, tilted gravity: 300 steps."""
+    import oracle
+    shape = (12, 16, 16)
+    r1, r2 = wl.hemisphere(shape, 6)
+    kw = dict(tau=(0.7, 0.7), G12=-1.2, collision="regularized", periodic=(1, 1, 0),
+              g_ext=wl.tilted_gravity(1e-5, 30.0))
+    p, f_or = oracle_run(shape, r1, r2, None, 300, **kw)
+    a, b, uF = oracle.moments(p, f_or)
+    lat = gpu_run(shape, r1, r2, None, 300, storage="f32", **kw)
+    ga, gb, guF = lat.moments()
+    lat.close()
+    e = max(np.max(np.abs(ga - a) / a), np.max(np.abs(gb - b) / b))
+    print("FP32 regularized wall 300 steps: max|drho|/rho = %.3g" % e)
+    assert e < 1e-5
+
+
+@pytest.mark.parametrize("storage", ["f16_dev", "bf16_dev"])
+def test_low_precision_storage(gpu_lib, storage):
+    """16-bit deviation storage d_i = f_i - w_i rho0 with FP32 arithmetic:
+    per-field error against the FP64 oracle (reported), loose bound, and
+    FP64-reduced mass drift."""
+    import oracle
+    shape = (16, 16, 16)
+    r1, r2 = wl.spinodal(shape, seed=3)
+    kw = dict(tau=(0.7, 0.7), G12=-1.2)
+    p, f_or = oracle_run(shape, r1, r2, None, 100, **kw)
+    a, b, _ = oracle.moments(p, f_or)
+    lat = gpu_run(shape, r1, r2, None, 0, storage=storage, rho0_dev=0.5, **kw)
+    m0 = lat.reduce()
+    lat.step(100)
+    ga, gb, _ = lat.moments()
+    m1 = lat.reduce()
+    lat.close()
+    e = max(np.max(np.abs(ga - a) / a), np.max(np.abs(gb - b) / b))
+    drift = abs(m1["mass1"] - m0["mass1"]) / m0["mass1"]
+    print("%s 100 steps: max|drho|/rho = %.3g, mass drift %.3g" % (storage, e, drift))
+    assert e < (5e-3 if storage == "f16_dev" else 4e-2)
+    assert drift < (1e-3 if storage == "f16_dev" else 1e-2)
+
+
+def test_init_and_set_populations_roundtrip(gpu_lib):
+    """lbm_set_populations / lbm_get_populations are inverse; lbm_init_fields
+    equals f^eq of the oracle (Eq. 3)."""
+    import oracle
+    perm = direction_map()
+    shape = (3, 4, 5)
+    r1, r2, u = wl.random_state(shape, seed=2)
+    p = oracle.make_params(shape, periodic=(1, 1, 0))
+    f0 = oracle.init(p, r1, r2, u)[:, perm]
+    lat = gpu_run(shape, r1, r2, u, 0, storage="f64", periodic=(1, 1, 0))
+    assert rel_err(lat.get_populations(), f0) < 1e-15
+    rnd = np.random.default_rng(0).uniform(0, 0.1, f0.shape)
+    lat.set_populations(rnd)
+    assert np.array_equal(lat.get_populations(), rnd)
+    lat.close()
+
+
+def test_state_checkpoint_restores_bitwise(gpu_lib):
+    """lbm_get_state / lbm_set_state: a restored run repeats bit for bit
+    (the forward kernels are deterministic: no atomics)."""
+    import torch
+    shape = (8, 8, 8)
+    r1, r2 = wl.droplet(shape, 3)
+    lat = gpu_run(shape, r1, r2, None, 5, storage="f32", G12=G_DROP)
+    buf = torch.empty(lat.state_bytes(), dtype=torch.uint8, device="cuda")
+    lat.get_state(buf)
+    lat.step(7)
+    x1 = lat.get_populations()
+    lat.set_state(buf)
+    lat.step(7)
+    x2 = lat.get_populations()
+    lat.close()
+    assert np.array_equal(x1, x2)
+
+
+def test_errors_surface_as_status(gpu_lib):
+    from paper_1601_01237_gb300 import LBMError, Lattice
+    with pytest.raises(LBMError, match="EINVAL"):
+        Lattice((4, 4, 4), tau=(0.5, 1.0))
+    with pytest.raises(LBMError, match="ENOTSUP"):
+        Lattice((4, 4, 4), periodic=(0, 1, 1))
+    lat = Lattice((4, 4, 4))
+    with pytest.raises(LBMError, match="EINVAL"):
+        lat.step(-1)
+    # a negative density is reported by the FP64 reduction
+    r = np.full((4, 4, 4), 0.5)
+    r[1, 2, 3] = -0.1
+    lat.init_fields(r, np.full((4, 4, 4), 0.5))
+    with pytest.raises(LBMError, match="ENUMERIC"):
+        lat.reduce()
+    lat.close()
+
+
+def test_sampled_cells_full_size(gpu_lib):
+    """The 512^3 FP32 spinodal workload in the benchmark's launch
+    configuration: after one and two steps, sampled cells agree with the
+    oracle run on a periodic crop that holds each cell's dependency cone
+    (radius 2 per step), and the FP64-reduced masses are conserved."""
+    import oracle
+    import torch
+    shape = (512, 512, 512)
+    c = wl.CONFIGS["perf512_spinodal_f32"]
+    r1, r2 = wl.spinodal(shape)
+    from paper_1601_01237_gb300 import Lattice
+    lat = Lattice(shape, storage="f32", tau=c["tau"], G12=c["G"])
+    lat.init_fields(r1, r2)
+    m0 = lat.reduce()
+    rng = np.random.default_rng(42)
+    samples = [tuple(rng.integers(0, 512, 3)) for _ in range(6)] + [(0, 0, 0), (511, 511, 511), (0, 511, 255)]
+    rho_dev = torch.empty((512, 512, 512), dtype=torch.float64, device="cuda")
+    for nsteps in (1, 2):
+        lat.step(1)
+        lat.moments_device(rho1=rho_dev, out_f64=True)
+        torch.cuda.synchronize()
+        h = 2 * nsteps
+        for (z, y, x) in samples:
+            idx = np.ix_([(z + d) % 512 for d in range(-h, h + 1)], [(y + d) % 512 for d in range(-h, h + 1)],
+                         [(x + d) % 512 for d in range(-h, h + 1)])
+            cs = (2 * h + 1,) * 3
+            p, f = oracle_run(cs, r1[idx], r2[idx], None, nsteps, tau=c["tau"], G12=c["G"])
+            a, _, _ = oracle.moments(p, f)
+            got = rho_dev[z, y, x].item()
+            assert abs(got - a[h, h, h]) < 2e-6 * a[h, h, h], ((z, y, x), nsteps, got, a[h, h, h])
+    m1 = lat.reduce()
+    lat.close()
+    assert abs(m1["mass1"] - m0["mass1"]) < 1e-6 * m0["mass1"]
+    assert abs(m1["mass2"] - m0["mass2"]) < 1e-6 * m0["mass2"]
