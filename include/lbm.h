@@ -157,6 +157,34 @@ lbm_status lbm_step_count(const lbm_lattice *h, long *steps);
  * errors as LBM_ECUDA. */
 lbm_status lbm_sync(lbm_lattice *h);
 
+/* Largest lattice (nx*ny*nz cells) that lbm_step_noalloc accepts: 128^3. */
+#define LBM_NOALLOC_MAX_CELLS 2097152L
+
+/* One time step for callers that cannot allocate device memory.  The paper
+ * has no counterpart to this call; it exists for integrations where the
+ * caller owns every device buffer and cudaMalloc is not allowed at step time
+ * (for example host code running under a memory-pool policy that forbids
+ * allocation, or a real-time loop that must not take the allocator's locks).
+ *
+ * It advances the state in f_in by one step into f_out with the two-kernel
+ * step (density pass, then force + collision + streaming).  f_in and f_out are
+ * distinct caller-owned device buffers in the raw state format (the layout
+ * lbm_get_state writes; lbm_state_bytes of a lattice with the same params).
+ * *params is validated as by lbm_create, except that params->stream = NULL
+ * means the default stream.  No handle is created and nothing is allocated:
+ * the density scratch is a static device array of 32 MiB built into the
+ * library, held on every device that loads it until the process exits.
+ *
+ * Limits and sharing: lattices above LBM_NOALLOC_MAX_CELLS cells are rejected
+ * with LBM_EINVAL.  The scratch is written in full by the density pass before
+ * the collision reads it, so nothing needs clearing between calls, but every
+ * call shares it: calls whose work overlaps on the GPU (other streams, other
+ * host threads) race and must be serialised by the caller.  The first call on
+ * a device looks up the scratch's device address (set-up); make that first
+ * call before any stream capture.  Asynchronous on the stream; errors:
+ * LBM_EINVAL, LBM_ENOTSUP, LBM_ECUDA. */
+lbm_status lbm_step_noalloc(const lbm_params *params, const void *f_in, void *f_out);
+
 /* Release every resource of the handle.  NULL-safe. */
 void lbm_destroy(lbm_lattice *h);
 

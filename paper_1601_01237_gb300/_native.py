@@ -53,6 +53,7 @@ SIGNATURES = [
     ("lbm_set_state", _I, [_VP, _VP, _SZ]),
     ("lbm_step_count", _I, [_VP, ctypes.POINTER(_L)]),
     ("lbm_sync", _I, [_VP]),
+    ("lbm_step_noalloc", _I, [ctypes.POINTER(lbm_params), _VP, _VP]),
     ("lbm_destroy", None, [_VP]),
     ("lbm_last_error", ctypes.c_char_p, [_VP]),
 ]

@@ -443,6 +443,57 @@ lbm_status lbm_sync(lbm_lattice *h)
     return LBM_OK;
 }
 
+lbm_status lbm_step_noalloc(const lbm_params *pp, const void *f_in, void *f_out)
+{
+    if (!pp || !f_in || !f_out) return fail(LBM_EINVAL, "lbm_step_noalloc: NULL argument");
+    if (f_in == f_out) return fail(LBM_EINVAL, "lbm_step_noalloc: f_in and f_out must be distinct buffers");
+    const lbm_params &p = *pp;
+    if (p.nx < 1 || p.ny < 1 || p.nz < 1)
+        return fail(LBM_EINVAL, "lbm_step_noalloc: sizes must be >= 1 (got %d x %d x %d)", p.nx, p.ny, p.nz);
+    const long long N = (long long)p.nx * p.ny * p.nz;
+    if (N > lbm::kNoallocMaxCells)
+        return fail(LBM_EINVAL, "lbm_step_noalloc: %lld cells exceed the static scratch limit of %lld "
+                                "(LBM_NOALLOC_MAX_CELLS); use lbm_create/lbm_step", N, lbm::kNoallocMaxCells);
+    for (int a = 0; a < 2; ++a)
+        if (!(p.tau[a] > 0.5) || !isfinite(p.tau[a]))
+            return fail(LBM_EINVAL, "lbm_step_noalloc: tau[%d] = %g must be a finite value > 1/2", a, p.tau[a]);
+    if (p.G[0][0] != 0.0 || p.G[1][1] != 0.0)
+        return fail(LBM_ENOTSUP, "lbm_step_noalloc: G^{aa} must be 0");
+    for (int a = 0; a < 2; ++a)
+        for (int b = 0; b < 2; ++b)
+            if (!isfinite(p.G[a][b])) return fail(LBM_EINVAL, "lbm_step_noalloc: G must be finite");
+    for (int d = 0; d < 3; ++d)
+        if (!isfinite(p.g_ext[d])) return fail(LBM_EINVAL, "lbm_step_noalloc: g_ext must be finite");
+    if (!isfinite(p.rho_s[0]) || !isfinite(p.rho_s[1]) || !isfinite(p.rho0_dev))
+        return fail(LBM_EINVAL, "lbm_step_noalloc: rho_s and rho0_dev must be finite");
+    if (p.storage < LBM_F64 || p.storage > LBM_BF16_DEV)
+        return fail(LBM_EINVAL, "lbm_step_noalloc: unknown storage %d", p.storage);
+    if ((p.storage == LBM_F64 || p.storage == LBM_F32) && p.rho0_dev != 0.0)
+        return fail(LBM_EINVAL, "lbm_step_noalloc: rho0_dev applies to the 16-bit deviation formats only");
+    if (p.collision != LBM_BGK && p.collision != LBM_REGULARIZED)
+        return fail(LBM_EINVAL, "lbm_step_noalloc: unknown collision %d", p.collision);
+    if (p.wall_model != LBM_WALL_POTENTIAL && p.wall_model != LBM_WALL_MIRROR)
+        return fail(LBM_EINVAL, "lbm_step_noalloc: unknown wall model %d", p.wall_model);
+    for (int d = 0; d < 3; ++d)
+        if (p.periodic[d] != 0 && p.periodic[d] != 1)
+            return fail(LBM_EINVAL, "lbm_step_noalloc: periodic[%d] must be 0 or 1", d);
+    if (!p.periodic[0] || !p.periodic[1])
+        return fail(LBM_ENOTSUP, "lbm_step_noalloc: walls are supported along z only");
+    lbm::HostPhys ph;
+    ph.nx = p.nx; ph.ny = p.ny; ph.nz = p.nz; ph.N = N;
+    ph.wall_z = p.periodic[2] ? 0 : 1;
+    ph.wall_mirror = p.wall_model == LBM_WALL_MIRROR;
+    ph.storage = p.storage;
+    ph.collision = p.collision;
+    ph.tau[0] = p.tau[0]; ph.tau[1] = p.tau[1];
+    ph.G12 = p.G[0][1]; ph.G21 = p.G[1][0];
+    for (int d = 0; d < 3; ++d) ph.gext[d] = p.g_ext[d];
+    ph.rho_s[0] = p.rho_s[0]; ph.rho_s[1] = p.rho_s[1];
+    ph.rho0 = p.rho0_dev;
+    CK(lbm::launch_step_split_noalloc(ph, f_in, f_out, (cudaStream_t)p.stream), "lbm_step_noalloc");
+    return LBM_OK;
+}
+
 const char *lbm_last_error(const lbm_lattice *)
 {
     return g_err.c_str();

@@ -514,4 +514,44 @@ size_t storage_bytes(int storage)
 
 size_t real_bytes(int storage) { return storage == ST_F64 ? 8 : 4; }
 
+// ---------------------------------------------------------------------------
+// Allocation-free variant of the two-kernel step.  Its density scratch is a
+// file-scope device array (2 components x kNoallocMaxCells x 8 bytes = 32 MiB),
+// present on every device that loads the library.  Host code cannot use the
+// array's name as a device address, so the address is looked up once per
+// device with cudaGetSymbolAddress while that device is current.
+static __device__ __align__(256) unsigned char g_noalloc_rho[2 * kNoallocMaxCells * sizeof(double)];
+
+namespace {
+
+constexpr int kMaxDevices = 64;
+void *g_noalloc_ptr[kMaxDevices] = {};
+
+cudaError_t noalloc_scratch(void **out)
+{
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if (dev < 0 || dev >= kMaxDevices) return cudaErrorInvalidDevice;
+    void *ptr = __atomic_load_n(&g_noalloc_ptr[dev], __ATOMIC_ACQUIRE);
+    if (!ptr) {
+        e = cudaGetSymbolAddress(&ptr, g_noalloc_rho);
+        if (e != cudaSuccess) return e;
+        __atomic_store_n(&g_noalloc_ptr[dev], ptr, __ATOMIC_RELEASE);
+    }
+    *out = ptr;
+    return cudaSuccess;
+}
+
+}  // namespace
+
+cudaError_t launch_step_split_noalloc(const HostPhys &p, const void *f_in, void *f_out, cudaStream_t s)
+{
+    if (p.N > kNoallocMaxCells) return cudaErrorInvalidValue;
+    void *rho = nullptr;
+    cudaError_t e = noalloc_scratch(&rho);
+    if (e != cudaSuccess) return e;
+    return launch_step_split(p, f_in, f_out, rho, s);
+}
+
 }  // namespace lbm

@@ -60,6 +60,11 @@ int reduce_blocks();
 cudaError_t launch_reduce(const HostPhys &p, const void *f, void *rho, double *partials,
                           cudaStream_t s);
 
+// Two-kernel step whose density scratch is the library's static device array
+// (no allocation).  N must not exceed kNoallocMaxCells.
+constexpr long long kNoallocMaxCells = 2097152;   // 128^3
+cudaError_t launch_step_split_noalloc(const HostPhys &p, const void *f_in, void *f_out, cudaStream_t s);
+
 size_t storage_bytes(int storage);   // bytes per stored population value
 size_t real_bytes(int storage);      // bytes per arithmetic value
 

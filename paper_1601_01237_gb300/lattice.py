@@ -120,6 +120,18 @@ def lbm_sync(h):
     check(lib().lbm_sync(h), h)
 
 
+NOALLOC_MAX_CELLS = 2097152   # LBM_NOALLOC_MAX_CELLS of include/lbm.h
+
+
+def lbm_step_noalloc(params, f_in, f_out):
+    """One step from f_in to f_out (raw-state device buffers owned by the
+    caller) without any device allocation; see include/lbm.h."""
+    pi, di = _ptr(f_in)
+    po, do = _ptr(f_out)
+    assert di == 1 and do == 1, "state buffers live on the device"
+    check(lib().lbm_step_noalloc(ctypes.byref(params), pi, po))
+
+
 def lbm_destroy(h):
     lib().lbm_destroy(h)
 
