@@ -157,6 +157,34 @@ lbm_status lbm_step_count(const lbm_lattice *h, long *steps);
  * errors as LBM_ECUDA. */
 lbm_status lbm_sync(lbm_lattice *h);
 
+/* Differentiation (reverse mode).  The paper has no adjoint; these calls give
+ * gradients of a loss L(rho^1_N, rho^2_N) of the final densities with respect
+ * to the initial densities, G^{12}, G^{21}, tau_1 and tau_2, by a hand-written
+ * reverse pass through the update of Sec. 2 (Eqs. 1-7, 10-11, 13).
+ *
+ * lbm_record runs n_steps >= 1 forward exactly as lbm_step does and keeps the
+ * raw state every ckpt_every >= 1 steps (a library-owned checkpoint store of
+ * ceil(n_steps / ckpt_every) states, replaced by the next lbm_record).
+ * Synchronizes.  Errors: LBM_EINVAL, LBM_ENOMEM, LBM_ECUDA. */
+lbm_status lbm_record(lbm_lattice *h, long n_steps, int ckpt_every);
+
+/* Reverse pass over the last lbm_record.  Inputs dL_drho1, dL_drho2: N values
+ * each (double), dL/drho^a of the recorded run's final state; either may be
+ * NULL (zero).  Outputs (each may be NULL): dL_drho1_0, dL_drho2_0 (N doubles),
+ * the gradient with respect to the initial densities of a run started by
+ * lbm_init_fields with u = NULL (f = w_i rho at rest); dL_dparams[4] (host) =
+ * dL/dG^{12}, dL/dG^{21}, dL/dtau_1, dL/dtau_2 (for a tied G^{12} = G^{21},
+ * sum the first two).  All array pointers are host (on_device = 0) or device
+ * (on_device = 1) memory.  The forward states of each checkpoint segment are
+ * recomputed (time-checkpointing); working memory (adjoint fields and one
+ * segment of states) is allocated for the call and released.  Leaves the
+ * lattice state at the end of the recorded run.  Synchronizes.  Errors:
+ * LBM_EINVAL (no recording), LBM_ENOTSUP (initial-density gradient requested
+ * for a recording that did not start at rest from lbm_init_fields),
+ * LBM_ENOMEM, LBM_ECUDA. */
+lbm_status lbm_adjoint(lbm_lattice *h, const double *dL_drho1, const double *dL_drho2, int on_device,
+                       double *dL_drho1_0, double *dL_drho2_0, double dL_dparams[4]);
+
 /* Largest lattice (nx*ny*nz cells) that lbm_step_noalloc accepts: 128^3. */
 #define LBM_NOALLOC_MAX_CELLS 2097152L
 

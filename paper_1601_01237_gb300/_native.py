@@ -7,7 +7,9 @@ import ctypes
 import os
 
 HERE = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(HERE, "libmclbm.so")
+# LBM_LIBRARY may point at another build of the same C ABI (e.g. a kernel
+# variant under evaluation); by default the in-tree build is loaded.
+LIB_PATH = os.environ.get("LBM_LIBRARY") or os.path.join(HERE, "libmclbm.so")
 
 # lbm_status codes
 LBM_OK, LBM_EINVAL, LBM_ENOMEM, LBM_ECUDA, LBM_ENOTSUP, LBM_ENUMERIC = range(6)
@@ -53,6 +55,8 @@ SIGNATURES = [
     ("lbm_set_state", _I, [_VP, _VP, _SZ]),
     ("lbm_step_count", _I, [_VP, ctypes.POINTER(_L)]),
     ("lbm_sync", _I, [_VP]),
+    ("lbm_record", _I, [_VP, _L, _I]),
+    ("lbm_adjoint", _I, [_VP, _VP, _VP, _I, _VP, _VP, _DP]),
     ("lbm_step_noalloc", _I, [ctypes.POINTER(lbm_params), _VP, _VP]),
     ("lbm_destroy", None, [_VP]),
     ("lbm_last_error", ctypes.c_char_p, [_VP]),

@@ -43,6 +43,11 @@ __host__ __device__ constexpr double wd(int i) { return i == 0 ? 1.0 / 3.0 : (i 
 
 template <class R>
 __host__ __device__ constexpr R w(int i) { return (R)wd(i); }
+// Weights as exact integer numerators over 36 (12, 2, 1): the collision forms
+// rho w_i as (rho / 36) k_i, so that the FP32 weights sum to one exactly.  The
+// rounded FP32 values of 1/3, 1/18, 1/36 sum to 1 + 1.5e-8, which would add
+// that fraction of mass times 1/tau at every BGK collision.
+__host__ __device__ constexpr int k36(int i) { return i == 0 ? 12 : (i < 7 ? 2 : 1); }
 
 // ---------------------------------------------------------------------------
 // Storage formats.  R = arithmetic type, T = stored type.  The *_DEV formats
@@ -120,7 +125,8 @@ __device__ __forceinline__ R cdot(int i, R ux, R uy, R uz)
 // the forcing term F_i = f^eq_i(rho, u + g) - f^eq_i(rho, u).
 //   BGK:          f* = f^eq(u + g) + (1 - 1/tau) (f - f^eq(u))
 //   regularized:  f* = f^eq(u + g) + (1 - 1/tau) w_i/(2 T0^2) Q_i : Pi^neq,
-//                 Pi^neq = sum_i c_i c_i f_i - rho (T0 I + u u).
+//                 Pi^neq = sum_i c_i c_i f_i - rho (T0 I + u u);
+//                 w_i/(2 T0^2) = k_i / 8 and Q_i : Pi = c_i c_i : Pi - tr(Pi)/3.
 template <class R, bool REG>
 __device__ __forceinline__ void collide(R (&f)[Q], R rho, R ux, R uy, R uz,
                                         R gx, R gy, R gz, R omega)
@@ -129,15 +135,16 @@ __device__ __forceinline__ void collide(R (&f)[Q], R rho, R ux, R uy, R uz,
     const R vx = ux + gx, vy = uy + gy, vz = uz + gz;
     const R vsq = vx * vx + vy * vy + vz * vz;
     const R keep = R(1) - omega;
+    const R rq = rho / R(36);
     if (!REG) {
         {
-            const R e0 = rho * w<R>(0) * (R(1) - R(1.5) * usq);
-            const R s0 = rho * w<R>(0) * (R(1) - R(1.5) * vsq);
+            const R e0 = rq * R(12) * (R(1) - R(1.5) * usq);
+            const R s0 = rq * R(12) * (R(1) - R(1.5) * vsq);
             f[0] = s0 + keep * (f[0] - e0);
         }
 #pragma unroll
         for (int i = 1; i < Q; i += 2) {
-            const R rw = rho * w<R>(i);
+            const R rw = rq * R(k36(i));
             R ep, em, sp, sm;
             feq_pair<R>(rw, cdot<R>(i, ux, uy, uz), usq, ep, em);
             feq_pair<R>(rw, cdot<R>(i, vx, vy, vz), vsq, sp, sm);
@@ -164,11 +171,11 @@ __device__ __forceinline__ void collide(R (&f)[Q], R rho, R ux, R uy, R uz,
         pxy -= rho * ux * uy;
         pxz -= rho * ux * uz;
         pyz -= rho * uy * uz;
-        const R trace_T0 = T0 * (pxx + pyy + pzz);
-        // f^neq_i = 4.5 w_i (c_i c_i : Pi - T0 tr Pi)
+        const R t = (pxx + pyy + pzz) / R(3);
+        // f^neq_i = (k_i / 8) (c_i c_i : Pi - tr(Pi) / 3)
         {
-            const R s0 = rho * w<R>(0) * (R(1) - R(1.5) * vsq);
-            f[0] = s0 + keep * (R(4.5) * w<R>(0) * (-trace_T0));
+            const R s0 = rq * R(12) * (R(1) - R(1.5) * vsq);
+            f[0] = s0 + keep * (R(-1.5) * t);
         }
 #pragma unroll
         for (int i = 1; i < Q; i += 2) {
@@ -179,9 +186,9 @@ __device__ __forceinline__ void collide(R (&f)[Q], R rho, R ux, R uy, R uz,
             if (cx(i) && cy(i)) cc += (cx(i) == cy(i) ? R(2) : R(-2)) * pxy;
             if (cx(i) && cz(i)) cc += (cx(i) == cz(i) ? R(2) : R(-2)) * pxz;
             if (cy(i) && cz(i)) cc += (cy(i) == cz(i) ? R(2) : R(-2)) * pyz;
-            const R fneq = R(4.5) * w<R>(i) * (cc - trace_T0);   // same for i and opp(i)
+            const R fneq = R(k36(i)) * R(0.125) * (cc - t);   // same for i and opp(i)
             R sp, sm;
-            feq_pair<R>(rho * w<R>(i), cdot<R>(i, vx, vy, vz), vsq, sp, sm);
+            feq_pair<R>(rq * R(k36(i)), cdot<R>(i, vx, vy, vz), vsq, sp, sm);
             f[i] = sp + keep * fneq;
             f[i + 1] = sm + keep * fneq;
         }

@@ -27,6 +27,13 @@ struct lbm_lattice {
     double *partials_h;  // reduction partials (pinned host)
     long steps;
     int use_fused;
+    int init_at_rest;    // current run started from lbm_init_fields with u = NULL
+    // recording for the reverse pass
+    void *ckpt;          // checkpoint store (rec_nck raw states)
+    long rec_steps;
+    int rec_every;
+    long rec_nck;
+    int rec_at_rest;     // the recording started at rest right after lbm_init_fields
 };
 
 namespace {
@@ -204,6 +211,7 @@ void lbm_destroy(lbm_lattice *h)
     cudaFree(h->f[0]);
     cudaFree(h->f[1]);
     cudaFree(h->rho);
+    cudaFree(h->ckpt);
     cudaFree(h->partials);
     if (h->partials_h) cudaFreeHost(h->partials_h);
     if (h->own_stream && h->stream) cudaStreamDestroy(h->stream);
@@ -232,6 +240,7 @@ lbm_status lbm_init_fields(lbm_lattice *h, const double *rho1, const double *rho
     }
     h->cur = 0;
     h->steps = 0;
+    h->init_at_rest = u == nullptr;
     CK(lbm::launch_init_feq(h->phys, d1, d2, du, h->f[0], h->stream), "lbm_init_fields: launch");
     if (tmp) {
         CK(cudaFreeAsync(tmp, h->stream), "lbm_init_fields: free staging");
@@ -389,6 +398,7 @@ lbm_status lbm_set_populations(lbm_lattice *h, const double *in, int on_device)
         if (st != LBM_OK) return st;
         src = (const double *)tmp;
     }
+    h->init_at_rest = 0;
     CK(lbm::launch_set_populations(h->phys, src, h->f[h->cur], h->stream), "lbm_set_populations");
     if (tmp) {
         CK(cudaFreeAsync(tmp, h->stream), "lbm_set_populations: free");
@@ -424,6 +434,7 @@ lbm_status lbm_set_state(lbm_lattice *h, const void *dev_buf, size_t bytes)
     if (!dev_buf || bytes < need)
         return fail(LBM_EINVAL, "lbm_set_state: buffer of %zu bytes, need %zu", bytes, need);
     DeviceGuard g(h->device);
+    h->init_at_rest = 0;
     CK(cudaMemcpyAsync(h->f[h->cur], dev_buf, need, cudaMemcpyDeviceToDevice, h->stream), "lbm_set_state");
     return LBM_OK;
 }
@@ -440,6 +451,123 @@ lbm_status lbm_sync(lbm_lattice *h)
     if (!h) return fail(LBM_EINVAL, "lbm_sync: NULL handle");
     DeviceGuard g(h->device);
     CK(cudaStreamSynchronize(h->stream), "lbm_sync");
+    return LBM_OK;
+}
+
+lbm_status lbm_record(lbm_lattice *h, long n_steps, int ckpt_every)
+{
+    if (!h) return fail(LBM_EINVAL, "lbm_record: NULL handle");
+    if (n_steps < 1 || ckpt_every < 1)
+        return fail(LBM_EINVAL, "lbm_record: n_steps = %ld and ckpt_every = %d must be >= 1", n_steps, ckpt_every);
+    DeviceGuard g(h->device);
+    size_t sb = 0;
+    lbm_state_bytes(h, &sb);
+    const long nck = (n_steps + ckpt_every - 1) / ckpt_every;
+    cudaFree(h->ckpt);
+    h->ckpt = nullptr;
+    h->rec_steps = 0;
+    CK(cudaMalloc(&h->ckpt, sb * (size_t)nck), "lbm_record: checkpoint store");
+    h->rec_at_rest = h->init_at_rest && h->steps == 0;
+    for (long t = 0; t < n_steps; ++t) {
+        if (t % ckpt_every == 0)
+            CK(cudaMemcpyAsync((char *)h->ckpt + sb * (size_t)(t / ckpt_every), h->f[h->cur], sb,
+                               cudaMemcpyDeviceToDevice, h->stream),
+               "lbm_record: checkpoint");
+        lbm_status st = lbm_step(h, 1);
+        if (st != LBM_OK) return st;
+    }
+    CK(cudaStreamSynchronize(h->stream), "lbm_record: sync");
+    h->rec_steps = n_steps;
+    h->rec_every = ckpt_every;
+    h->rec_nck = nck;
+    return LBM_OK;
+}
+
+lbm_status lbm_adjoint(lbm_lattice *h, const double *dL_drho1, const double *dL_drho2, int on_device,
+                       double *dL_drho1_0, double *dL_drho2_0, double dL_dparams[4])
+{
+    if (!h) return fail(LBM_EINVAL, "lbm_adjoint: NULL handle");
+    if (h->rec_steps < 1 || !h->ckpt) return fail(LBM_EINVAL, "lbm_adjoint: no recorded run (call lbm_record)");
+    if ((dL_drho1_0 || dL_drho2_0) && !h->rec_at_rest)
+        return fail(LBM_ENOTSUP, "lbm_adjoint: initial-density gradients need a recording that starts at rest "
+                                 "right after lbm_init_fields(u = NULL)");
+    DeviceGuard g(h->device);
+    const size_t N = (size_t)h->phys.N;
+    const size_t rb = lbm::real_bytes(h->phys.storage);
+    size_t sb = 0;
+    lbm_state_bytes(h, &sb);
+    const long E = h->rec_every;
+    const int nb = lbm::adjoint_blocks();
+    // working memory: lambda, lambda_loc, a, one segment of states, gradient staging, partials
+    void *lam = nullptr, *lam_loc = nullptr, *abuf = nullptr, *seg = nullptr, *io = nullptr;
+    double *part = nullptr;
+    std::vector<double> parth((size_t)nb * 4);
+    cudaError_t e;
+    lbm_status st = LBM_OK;
+    auto cleanup = [&]() {
+        cudaFree(lam); cudaFree(lam_loc); cudaFree(abuf); cudaFree(seg); cudaFree(io); cudaFree(part);
+    };
+#define CKA(expr, where)                                  \
+    do {                                                  \
+        e = (expr);                                       \
+        if (e != cudaSuccess) { st = cuda_fail(e, where); cleanup(); return st; } \
+    } while (0)
+    CKA(cudaMalloc(&lam, rb * 2 * lbm::Q * N), "lbm_adjoint: lambda");
+    CKA(cudaMalloc(&lam_loc, rb * 2 * lbm::Q * N), "lbm_adjoint: lambda_loc");
+    CKA(cudaMalloc(&abuf, rb * 6 * N), "lbm_adjoint: a");
+    CKA(cudaMalloc(&seg, sb * (size_t)(E + 1)), "lbm_adjoint: segment states");
+    CKA(cudaMalloc((void **)&part, sizeof(double) * 4 * nb), "lbm_adjoint: partials");
+    CKA(cudaMalloc(&io, sizeof(double) * 2 * N), "lbm_adjoint: staging");
+    CKA(cudaMemsetAsync(part, 0, sizeof(double) * 4 * nb, h->stream), "lbm_adjoint: clear");
+    double *io1 = (double *)io, *io2 = (double *)io + N;
+    const double *g1 = dL_drho1, *g2 = dL_drho2;
+    if (!on_device) {
+        if (dL_drho1) CKA(cudaMemcpyAsync(io1, dL_drho1, sizeof(double) * N, cudaMemcpyHostToDevice, h->stream), "lbm_adjoint: copy");
+        if (dL_drho2) CKA(cudaMemcpyAsync(io2, dL_drho2, sizeof(double) * N, cudaMemcpyHostToDevice, h->stream), "lbm_adjoint: copy");
+        g1 = dL_drho1 ? io1 : nullptr;
+        g2 = dL_drho2 ? io2 : nullptr;
+    }
+    CKA(lbm::launch_adjoint_seed(h->phys, g1, g2, 1, lam, h->stream), "lbm_adjoint: seed");
+    const bool use_fused = h->use_fused;
+    for (long k = h->rec_nck - 1; k >= 0; --k) {
+        const long t0 = k * E;
+        const long t1 = (t0 + E < h->rec_steps) ? t0 + E : h->rec_steps;
+        // recompute the segment's forward states f^{t0} .. f^{t1-1}
+        CKA(cudaMemcpyAsync(seg, (char *)h->ckpt + sb * (size_t)k, sb, cudaMemcpyDeviceToDevice, h->stream),
+            "lbm_adjoint: restore");
+        for (long t = t0; t + 1 < t1; ++t) {
+            const void *fi = (char *)seg + sb * (size_t)(t - t0);
+            void *fo = (char *)seg + sb * (size_t)(t - t0 + 1);
+            if (use_fused) CKA(lbm::launch_step_fused(h->phys, fi, fo, h->stream), "lbm_adjoint: recompute");
+            else CKA(lbm::launch_step_split(h->phys, fi, fo, h->rho, h->stream), "lbm_adjoint: recompute");
+        }
+        for (long t = t1 - 1; t >= t0; --t) {
+            const void *fn = (char *)seg + sb * (size_t)(t - t0);
+            CKA(lbm::launch_density(h->phys, fn, h->rho, h->stream), "lbm_adjoint: density");
+            CKA(lbm::launch_adjoint_step(h->phys, fn, h->rho, lam, lam_loc, abuf, lam, part, h->stream),
+                "lbm_adjoint: step");
+        }
+    }
+    if (dL_drho1_0 || dL_drho2_0) {
+        double *o1 = on_device ? dL_drho1_0 : (dL_drho1_0 ? io1 : nullptr);
+        double *o2 = on_device ? dL_drho2_0 : (dL_drho2_0 ? io2 : nullptr);
+        CKA(lbm::launch_adjoint_rho0(h->phys, lam, o1, o2, h->stream), "lbm_adjoint: rho0");
+        if (!on_device) {
+            if (dL_drho1_0) CKA(cudaMemcpyAsync(dL_drho1_0, io1, sizeof(double) * N, cudaMemcpyDeviceToHost, h->stream), "lbm_adjoint: copy out");
+            if (dL_drho2_0) CKA(cudaMemcpyAsync(dL_drho2_0, io2, sizeof(double) * N, cudaMemcpyDeviceToHost, h->stream), "lbm_adjoint: copy out");
+        }
+    }
+    CKA(cudaMemcpyAsync(parth.data(), part, sizeof(double) * 4 * nb, cudaMemcpyDeviceToHost, h->stream),
+        "lbm_adjoint: partials");
+    CKA(cudaStreamSynchronize(h->stream), "lbm_adjoint: sync");
+#undef CKA
+    if (dL_dparams) {
+        double acc[4] = {0, 0, 0, 0};
+        for (int b = 0; b < nb; ++b)
+            for (int q = 0; q < 4; ++q) acc[q] += parth[(size_t)b * 4 + q];
+        for (int q = 0; q < 4; ++q) dL_dparams[q] = acc[q];
+    }
+    cleanup();
     return LBM_OK;
 }
 

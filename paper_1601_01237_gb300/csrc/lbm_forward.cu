@@ -492,6 +492,27 @@ cudaError_t launch_moments(const HostPhys &p, const void *f, void *rho, int out_
 
 int reduce_blocks() { return kReduceBlocks; }
 
+cudaError_t launch_density(const HostPhys &h, const void *f, void *rho, cudaStream_t s)
+{
+    switch (h.storage) {
+    case ST_F64:
+        k_density<ST_F64><<<grid_for(h.N), kThreads, 0, s>>>((const double *)f, (double *)rho, make_phys<double>(h));
+        break;
+    case ST_F32:
+        k_density<ST_F32><<<grid_for(h.N), kThreads, 0, s>>>((const float *)f, (float *)rho, make_phys<float>(h));
+        break;
+    case ST_F16_DEV:
+        k_density<ST_F16_DEV><<<grid_for(h.N), kThreads, 0, s>>>((const __half *)f, (float *)rho, make_phys<float>(h));
+        break;
+    case ST_BF16_DEV:
+        k_density<ST_BF16_DEV><<<grid_for(h.N), kThreads, 0, s>>>((const __nv_bfloat16 *)f, (float *)rho,
+                                                                  make_phys<float>(h));
+        break;
+    default: return cudaErrorInvalidValue;
+    }
+    return cudaGetLastError();
+}
+
 cudaError_t launch_reduce(const HostPhys &p, const void *f, void *rho, double *partials, cudaStream_t s)
 {
     switch (p.storage) {

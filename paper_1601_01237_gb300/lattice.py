@@ -120,6 +120,24 @@ def lbm_sync(h):
     check(lib().lbm_sync(h), h)
 
 
+def lbm_record(h, n_steps, ckpt_every):
+    check(lib().lbm_record(h, int(n_steps), int(ckpt_every)), h)
+
+
+def lbm_adjoint(h, dL_drho1=None, dL_drho2=None, out_rho1_0=None, out_rho2_0=None):
+    """Reverse pass over the last lbm_record.  Inputs and outputs are all host
+    (numpy float64) or all device (torch float64) arrays; returns
+    [dL/dG12, dL/dG21, dL/dtau1, dL/dtau2]."""
+    arrs = [x for x in (dL_drho1, dL_drho2, out_rho1_0, out_rho2_0) if x is not None]
+    devs = {_ptr(x)[1] for x in arrs}
+    assert len(devs) <= 1, "mixed host/device arrays"
+    on_dev = devs.pop() if devs else 0
+    par = (ctypes.c_double * 4)()
+    check(lib().lbm_adjoint(h, _ptr(dL_drho1)[0], _ptr(dL_drho2)[0], on_dev, _ptr(out_rho1_0)[0],
+                            _ptr(out_rho2_0)[0], par), h)
+    return list(par)
+
+
 NOALLOC_MAX_CELLS = 2097152   # LBM_NOALLOC_MAX_CELLS of include/lbm.h
 
 
@@ -202,6 +220,12 @@ class Lattice:
 
     def step(self, n=1):
         lbm_step(self.h, n)
+
+    def record(self, n, ckpt_every):
+        lbm_record(self.h, n, ckpt_every)
+
+    def adjoint(self, dL_drho1=None, dL_drho2=None, out_rho1_0=None, out_rho2_0=None):
+        return lbm_adjoint(self.h, dL_drho1, dL_drho2, out_rho1_0, out_rho2_0)
 
     def step_timed(self, n):
         return lbm_step_timed(self.h, n)

@@ -1,0 +1,145 @@
+"""Gradients of the hand-written reverse pass (lbm_record / lbm_adjoint)
+against central finite differences of the FP64 oracle.
+
+Case (the differentiation configuration): a 96^3 droplet (R = 20) and a
+target from an ellipsoidal initialisation with semi-axes (24, 20, 16); the
+check runs on an 8^3 periodic crop of both at the interface, centred at
+(x, y, z) = (68, 48, 48), for 20 steps with checkpoints every 5.
+Loss L = sum_x (rho^1_N - rho^1_target)^2; gradients with respect to every
+initial rho^1 cell, the tied G^{12} = G^{21} and tau_1; central differences
+with h = 1e-3.  Bar: relative error <= 1e-4.
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_1601_01237_gb300 import workloads as wl
+
+pytestmark = pytest.mark.gpu
+
+H = 1e-3
+STEPS = 20
+CKPT = 5
+
+
+def crop_case():
+    full1, full2 = wl.droplet((96, 96, 96), 20)
+    tgt, _ = wl.ellipsoid((96, 96, 96), (24, 20, 16))
+    sl = (slice(44, 52), slice(44, 52), slice(64, 72))
+    return full1[sl].copy(), full2[sl].copy(), tgt[sl].copy()
+
+
+def oracle_loss(r1, r2, tgt, G, tau1, tau2, steps, **kw):
+    p = oracle.make_params(r1.shape, tau=(tau1, tau2), G12=G, G21=G, **kw)
+    f = oracle.init(p, r1, r2)
+    oracle.step(p, f, steps)
+    a, _, _ = oracle.moments(p, f)
+    return float(((a - tgt) ** 2).sum())
+
+
+def fd_grads(r1, r2, tgt, G, tau1, tau2, steps, cells=None, **kw):
+    L = lambda **o: oracle_loss(o.get("r1", r1), r2, tgt, o.get("G", G), o.get("tau1", tau1), tau2, steps, **kw)
+    gG = (L(G=G + H) - L(G=G - H)) / (2 * H)
+    gT = (L(tau1=tau1 + H) - L(tau1=tau1 - H)) / (2 * H)
+    gr = np.zeros(r1.shape)
+    idx = list(np.ndindex(r1.shape)) if cells is None else cells
+    for c in idx:
+        rp = r1.copy(); rp[c] += H
+        rm = r1.copy(); rm[c] -= H
+        gr[c] = (L(r1=rp) - L(r1=rm)) / (2 * H)
+    return gG, gT, gr
+
+
+def gpu_grads(r1, r2, tgt, G, tau1, tau2, steps, storage, **kw):
+    from paper_1601_01237_gb300 import Lattice
+    lat = Lattice(r1.shape, storage=storage, tau=(tau1, tau2), G12=G, G21=G, **kw)
+    lat.init_fields(r1, r2)
+    lat.record(steps, CKPT)
+    a, _, _ = lat.moments()
+    d1 = np.empty(r1.shape)
+    par = lat.adjoint(2 * (a - tgt), None, d1, None)
+    lat.close()
+    return par[0] + par[1], par[2], d1
+
+
+@pytest.fixture(scope="module")
+def fd_reference():
+    r1, r2, tgt = crop_case()
+    G = wl.g_from_config(0.9)
+    return (r1, r2, tgt, G) + fd_grads(r1, r2, tgt, G, 1.0, 1.0, STEPS)
+
+
+@pytest.mark.parametrize("storage", ["f64", "f32"])
+def test_adjoint_matches_finite_differences(gpu_lib, fd_reference, storage):
+    r1, r2, tgt, G, fG, fT, fr = fd_reference
+    gG, gT, gr = gpu_grads(r1, r2, tgt, G, 1.0, 1.0, STEPS, storage)
+    eG = abs(gG - fG) / abs(fG)
+    eT = abs(gT - fT) / abs(fT)
+    er = np.linalg.norm(gr - fr) / np.linalg.norm(fr)
+    print("%s adjoint vs FD: dG %.3g (%.6g vs %.6g), dtau1 %.3g, drho1_0 %.3g" % (storage, eG, gG, fG, eT, er))
+    assert eG <= 1e-4 and eT <= 1e-4 and er <= 1e-4
+    big = np.abs(fr) > 1e-3 * np.abs(fr).max()
+    assert np.max(np.abs(gr - fr)[big] / np.abs(fr)[big]) <= 1e-3
+
+
+@pytest.mark.parametrize("collision", ["bgk", "regularized"])
+def test_adjoint_walls_and_forcing(gpu_lib, collision):
+    """Reverse pass through mirror wetting walls, bounce-back, g_ext, unequal
+    tau and the regularized operator (FP64), on sampled cells."""
+    shape = (6, 5, 7)
+    r1, r2, _ = wl.random_state(shape, seed=17, u_max=0.0)
+    tgt = np.roll(r1, 2, axis=2)
+    kw = dict(periodic=(1, 1, 0), g_ext=(2e-4, -1e-4, 3e-4), collision=collision, rho_s=(0.03, 0.0))
+    G, t1, t2, steps = -1.3, 0.8, 1.2, 6
+    rng = np.random.default_rng(3)
+    cells = [tuple(int(v) for v in (rng.integers(0, 6), rng.integers(0, 5), rng.integers(0, 7))) for _ in range(10)]
+    cells += [(0, 2, 3), (5, 1, 1)]   # both wall layers
+    fG, fT, fr = fd_grads(r1, r2, tgt, G, t1, t2, steps, cells=cells, **kw)
+    from paper_1601_01237_gb300 import Lattice
+    lat = Lattice(shape, storage="f64", tau=(t1, t2), G12=G, G21=G, **kw)
+    lat.init_fields(r1, r2)
+    lat.record(steps, 4)
+    a, _, _ = lat.moments()
+    d1 = np.empty(shape)
+    par = lat.adjoint(2 * (a - tgt), None, d1, None)
+    lat.close()
+    print("%s walls: dG %.6g vs %.6g, dtau1 %.6g vs %.6g" % (collision, par[0] + par[1], fG, par[2], fT))
+    assert abs(par[0] + par[1] - fG) <= 1e-5 * abs(fG)
+    assert abs(par[2] - fT) <= 1e-5 * abs(fT)
+    scale = np.abs([fr[q] for q in cells]).max()
+    for c in cells:
+        assert abs(d1[c] - fr[c]) <= 1e-5 * scale, (c, d1[c], fr[c])
+
+
+def test_autograd_rollout_matches_adjoint(gpu_lib):
+    """torch.autograd through LBMRollout equals the direct lbm_adjoint call."""
+    import torch
+    from paper_1601_01237_gb300.adjoint import LBMRollout
+    r1, r2, tgt = crop_case()
+    G = wl.g_from_config(0.9)
+    gG, gT, gr = gpu_grads(r1, r2, tgt, G, 1.0, 1.0, STEPS, "f64")
+    x1 = torch.tensor(r1, device="cuda", requires_grad=True)
+    x2 = torch.tensor(r2, device="cuda", requires_grad=True)
+    Gt = torch.tensor(G, dtype=torch.float64, requires_grad=True)
+    Tt = torch.tensor(1.0, dtype=torch.float64, requires_grad=True)
+    y1, _ = LBMRollout.apply(x1, x2, Gt, Tt, r1.shape, STEPS, CKPT, {"storage": "f64"})
+    loss = ((y1 - torch.tensor(tgt, device="cuda")) ** 2).sum()
+    loss.backward()
+    assert np.allclose(x1.grad.cpu().numpy(), gr, rtol=1e-12, atol=1e-14)
+    assert abs(Gt.grad.item() - gG) <= 1e-12 * abs(gG)
+    assert abs(Tt.grad.item() - gT) <= 1e-12 * abs(gT)
+
+
+def test_adjoint_errors(gpu_lib):
+    from paper_1601_01237_gb300 import LBMError, Lattice
+    lat = Lattice((4, 4, 4), storage="f32")
+    lat.init_fields(np.full((4, 4, 4), 0.5), np.full((4, 4, 4), 0.5))
+    with pytest.raises(LBMError, match="EINVAL"):
+        lat.adjoint(np.zeros((4, 4, 4)))
+    lat.step(2)
+    lat.record(3, 1)
+    with pytest.raises(LBMError, match="ENOTSUP"):
+        lat.adjoint(np.zeros((4, 4, 4)), None, np.empty((4, 4, 4)))
+    par = lat.adjoint(np.zeros((4, 4, 4)))
+    assert par == [0.0, 0.0, 0.0, 0.0]
+    lat.close()
