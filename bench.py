@@ -49,6 +49,7 @@ def parse():
     ap.add_argument("--storage", default=None, help="override the workload's population storage")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-adjoint", action="store_true")
     return ap.parse_args()
 
 
@@ -233,6 +234,45 @@ def cpu_baseline(args, cfg):
             "sample": "64x64x64 cut of the workload, %d steps, FP64, one thread" % n}
 
 
+def adjoint_ratio(stream):
+    """Adjoint/forward time ratio on the differentiation case: 96^3 droplet
+    (R = 20), FP32, 500 steps, checkpoints every 25.  Forward = lbm_step(500);
+    reverse = lbm_adjoint over an lbm_record of the same 500 steps, including
+    its recomputation of every checkpoint segment."""
+    import torch
+    from paper_1601_01237_gb300 import Lattice
+    c = wl.CONFIGS["c3_adjoint96"]
+    shape, n, every = c["shape"], c["steps"], c["ckpt_every"]
+    r1, r2 = wl.droplet(shape, c["R"])
+    tgt, _ = wl.ellipsoid(shape, c["target_axes"])
+    lat = Lattice(shape, storage=c["storage"], tau=c["tau"], G12=c["G"], stream=stream.cuda_stream)
+    d1, d2 = torch.from_numpy(r1).cuda(), torch.from_numpy(r2).cuda()
+    lat.init_fields(d1, d2)
+    lat.step(20)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    lat.step(n)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    fwd_ms = e0.elapsed_time(e1) / n
+    lat.init_fields(d1, d2)
+    lat.record(n, every)
+    out1 = torch.empty(shape, dtype=torch.float64, device="cuda")
+    lat.moments_device(rho1=out1, out_f64=True)
+    g = 2.0 * (out1 - torch.from_numpy(tgt).cuda())
+    gr0 = torch.empty(shape, dtype=torch.float64, device="cuda")
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    par = lat.adjoint(g, None, gr0, None)
+    torch.cuda.synchronize()
+    adj_ms = (time.perf_counter() - t0) * 1e3 / n
+    lat.close()
+    return {"workload": "96^3 droplet R=20, FP32, %d steps, checkpoints every %d" % (n, every),
+            "forward_ms_per_step": fwd_ms, "adjoint_ms_per_step": adj_ms, "ratio": adj_ms / fwd_ms,
+            "dL_dG12_tied": par[0] + par[1], "dL_dtau1": par[2]}
+
+
 def run_ours(args, rank, world, local_rank):
     import torch
     from paper_1601_01237_gb300 import Lattice
@@ -337,6 +377,8 @@ def run_ours(args, rank, world, local_rank):
         "e2e": e2e,
         "mass": [red["mass1"], red["mass2"]],
     }
+    if not args.no_adjoint:
+        line["adjoint"] = adjoint_ratio(torch.cuda.current_stream())
     if world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(args, cfg)
     return line
