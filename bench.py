@@ -183,6 +183,23 @@ def algorithmic_bytes_per_cell(kernel, storage):
     return 2 * 19 * s * 2
 
 
+def max_over_ranks(x, device="cpu"):
+    """Maximum of a per-rank scalar over all ranks (identity without a
+    process group)."""
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    if dist.is_available() and dist.is_initialized() and dist.get_world_size() > 1:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return t.item()
+
+
+def job_mlups(cells_per_rank, world, steps, max_seconds):
+    """Whole-job throughput: every rank advances its own replica of
+    cells_per_rank cells by `steps`; the job takes the slowest rank's time."""
+    return cells_per_rank * world * steps / max_seconds / 1e6
+
+
 # --------------------------------------------------------------------------
 def run_reference(args, rank, world):
     """The FP64 CPU oracle, timed on a bounded cut of the workload."""
@@ -312,11 +329,8 @@ def run_ours(args, rank, world, local_rank):
         torch.distributed.barrier()
     clocks = sampler.stop()
     ms = e0.elapsed_time(e1)
-    ms_t = torch.tensor([ms], dtype=torch.float64, device="cuda")
-    if dist:
-        torch.distributed.all_reduce(ms_t, op=torch.distributed.ReduceOp.MAX)
-    ms_max = ms_t.item()
-    value = cells * world * args.steps / (ms_max / 1e3) / 1e6
+    ms_max = max_over_ranks(ms, device="cuda")
+    value = job_mlups(cells, world, args.steps, ms_max / 1e3)
     red = lat.reduce()
 
     # ---- roofline of the dominant kernel ----------------------------------
@@ -348,12 +362,8 @@ def run_ours(args, rank, world, local_rank):
         lat.step(args.steps)
         out = lat.reduce()               # D2H of the step's result (FP64 reductions)
         torch.cuda.synchronize()
-        dt = time.perf_counter() - t0
-        dt_t = torch.tensor([dt], dtype=torch.float64, device="cuda")
-        if dist:
-            torch.distributed.all_reduce(dt_t, op=torch.distributed.ReduceOp.MAX)
-        from paper_1601_01237_gb300.lattice import lib  # noqa: F401
-        e2e = {"value": cells * world * args.steps / dt_t.item() / 1e6, "unit": UNIT,
+        dt = max_over_ranks(time.perf_counter() - t0, device="cuda")
+        e2e = {"value": job_mlups(cells, world, args.steps, dt), "unit": UNIT,
                "h2d_bytes_per_step": 2 * cells * 8 / args.steps,
                "d2h_bytes_per_step": (1216 * 8 * 8) / args.steps,
                "note": "lbm_init_fields from pinned host + lbm_step(K) + lbm_reduce to host, per step amortised",

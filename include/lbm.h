@@ -136,6 +136,25 @@ lbm_status lbm_moments(lbm_lattice *h, int out_f64, void *rho1, void *rho2, void
  * or not positive. */
 lbm_status lbm_reduce(lbm_lattice *h, double out[6]);
 
+/* Pressure jump across a droplet interface (Young-Laplace, Eq. 12), reduced
+ * in FP64 on the GPU.  The pressure is the bulk pressure of the Eq. 7 force,
+ * p = T0 (rho^1 + rho^2) - G^{12} T0 rho^1 rho^2 (T0 = 1/3; a reading: the
+ * paper does not define p).  out[0] = mean p over cells with distance
+ * < r_in from center[3] (x, y, z lattice coordinates; minimum image along
+ * periodic axes), out[1] = mean p over cells with distance > r_out, out[2] =
+ * out[0] - out[1].  Synchronizes.  Errors: LBM_EINVAL (NULL, r_in <= 0,
+ * an empty region), LBM_ECUDA. */
+lbm_status lbm_pressure_jump(lbm_lattice *h, const double center[3], double r_in, double r_out, double out[3]);
+
+/* Droplet statistics of component 1 for the wall cases (Sec. 4.2), FP64 on
+ * the GPU.  Droplet = cells with rho^1 > threshold.  out[0] = droplet volume
+ * (cells), out[1..3] = its centre of mass (mean x, y, z relative to origin[3],
+ * minimum image along periodic axes), out[4] = mass of component 1 inside it,
+ * out[5] = mean rho^1 of the wall layer z = 0 outside the droplet (thin-film
+ * density), out[6] = number of those cells.  Synchronizes.  Errors:
+ * LBM_EINVAL, LBM_ECUDA. */
+lbm_status lbm_droplet_stats(lbm_lattice *h, double threshold, const double origin[3], double out[7]);
+
 /* Copy the populations f_i^a(x, t) of the current state, as doubles laid out
  * [a][i][z][y][x] in the lbm_lattice_dirs order (2*19*N values), to or from a
  * caller buffer (host or device).  Used for checkpoints and for population-level

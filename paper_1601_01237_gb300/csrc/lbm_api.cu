@@ -367,6 +367,58 @@ lbm_status lbm_reduce(lbm_lattice *h, double out[6])
     return LBM_OK;
 }
 
+namespace {
+
+lbm_status diag_run(lbm_lattice *h, int which, const double *vec3, double a0, double a1, double *sums, int nsums)
+{
+    const int nb = lbm::diag_blocks(), ns = lbm::diag_slots();
+    CK(lbm::launch_density(h->phys, h->f[h->cur], h->rho, h->stream), "diagnostics: density");
+    if (which == 0)
+        CK(lbm::launch_pressure(h->phys, h->rho, vec3, a0, a1, h->partials, h->stream), "diagnostics: pressure");
+    else
+        CK(lbm::launch_droplet(h->phys, h->rho, a0, vec3, h->partials, h->stream), "diagnostics: droplet");
+    CK(cudaMemcpyAsync(h->partials_h, h->partials, sizeof(double) * (size_t)nb * ns, cudaMemcpyDeviceToHost,
+                       h->stream),
+       "diagnostics: copy");
+    CK(cudaStreamSynchronize(h->stream), "diagnostics: sync");
+    for (int k = 0; k < nsums; ++k) sums[k] = 0;
+    for (int b = 0; b < nb; ++b)
+        for (int k = 0; k < nsums; ++k) sums[k] += h->partials_h[(size_t)b * ns + k];
+    return LBM_OK;
+}
+
+}  // namespace
+
+lbm_status lbm_pressure_jump(lbm_lattice *h, const double center[3], double r_in, double r_out, double out[3])
+{
+    if (!h || !center || !out) return fail(LBM_EINVAL, "lbm_pressure_jump: NULL argument");
+    if (!(r_in > 0) || !(r_out >= r_in)) return fail(LBM_EINVAL, "lbm_pressure_jump: need 0 < r_in <= r_out");
+    DeviceGuard g(h->device);
+    double s[4];
+    lbm_status st = diag_run(h, 0, center, r_in, r_out, s, 4);
+    if (st != LBM_OK) return st;
+    if (s[1] < 1 || s[3] < 1) return fail(LBM_EINVAL, "lbm_pressure_jump: empty inner or outer region");
+    out[0] = s[0] / s[1];
+    out[1] = s[2] / s[3];
+    out[2] = out[0] - out[1];
+    return LBM_OK;
+}
+
+lbm_status lbm_droplet_stats(lbm_lattice *h, double threshold, const double origin[3], double out[7])
+{
+    if (!h || !origin || !out) return fail(LBM_EINVAL, "lbm_droplet_stats: NULL argument");
+    DeviceGuard g(h->device);
+    double s[7];
+    lbm_status st = diag_run(h, 1, origin, threshold, 0.0, s, 7);
+    if (st != LBM_OK) return st;
+    out[0] = s[0];
+    for (int d = 0; d < 3; ++d) out[1 + d] = s[0] > 0 ? s[1 + d] / s[0] : 0.0;
+    out[4] = s[4];
+    out[5] = s[6] > 0 ? s[5] / s[6] : 0.0;
+    out[6] = s[6];
+    return LBM_OK;
+}
+
 lbm_status lbm_get_populations(lbm_lattice *h, double *out, int on_device)
 {
     if (!h || !out) return fail(LBM_EINVAL, "lbm_get_populations: NULL argument");

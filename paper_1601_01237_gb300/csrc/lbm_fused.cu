@@ -3,15 +3,23 @@
 // interaction force (Eqs. 7, 13), collision with forcing (Eqs. 1-3, 10-11) and
 // streaming in one kernel, with no global scratch.
 //
-// Each CTA owns a TX x TY column tile of the xy plane and marches along z over
-// a chunk of LZ planes.  The force at plane z needs rho^b at planes z-1, z, z+1
-// over the tile plus a one-cell halo; those densities live in a ring of three
-// shared-memory planes.  Iteration z gathers (pull streaming) the populations
-// of plane z+1, sums them into rho(z+1) for the ring, and parks them in a
-// shared-memory stash; then it collides plane z with the populations parked
-// in the previous iteration.  Every interior population is read from HBM once; the
-// halo ring re-reads the neighbouring tiles' populations, which the
-// neighbouring CTAs stream at about the same time (L2 hits).
+// Each CTA owns a 32 x 8 column tile of the xy plane and marches along z over
+// a chunk of 64 planes, one thread per column.  The force at plane z needs
+// rho^b at planes z-1, z, z+1 over the tile plus a one-cell halo; those
+// densities live in a ring of three shared-memory planes.  Iteration z:
+//   A. every thread pull-gathers its column's 38 populations at plane z+1
+//      (rho into the ring, momentum into a moment buffer, populations into a
+//      shared-memory stash) and, for the halo ring of plane z+2, 12 or 13 of
+//      the 38 populations of one halo cell (84 halo cells x 3 groups), summed
+//      into fixed-order partial densities; the halo densities of plane z+1
+//      (partials gathered one iteration earlier) are completed in the ring;
+//   B. every thread collides its column at plane z from the stash and stores
+//      the post-collision populations,
+// with a barrier after each phase.  Interior and halo loads of an iteration
+// are issued together and balanced over all threads; every interior
+// population is read from HBM once and written once, and the halo re-reads
+// neighbouring tiles' populations that the neighbouring CTAs stream at about
+// the same time (L2 hits).
 #include <cuda_runtime.h>
 
 #include "d3q19.cuh"
@@ -25,178 +33,198 @@ constexpr int kTX = 32;
 constexpr int kTY = 8;
 constexpr int kThreadsF = kTX * kTY;
 constexpr int kHalo = 2 * (kTX + 2) + 2 * kTY;   // perimeter cells of the (TX+2) x (TY+2) box
+constexpr int kGroups = 3;                        // halo populations split 13 + 13 + 12
+constexpr int kPer = 13;
 constexpr int kLZ = 64;                           // planes per CTA
-
-__device__ __forceinline__ int wrapi(int v, int n)
-{
-    return v < 0 ? v + n : (v >= n ? v - n : v);
-}
-
-// Pull-gather the populations of cell (x, y, z) (all in range) into fa and
-// return their sums rho^1, rho^2.  xo/yo hold the wrapped x-1, x, x+1 and row
-// offsets of y-1, y, y+1.
-template <int S>
-__device__ __forceinline__ void gather_cell(const typename Store<S>::T *__restrict__ f,
-                                            const Phys<typename Store<S>::R> &p, const int (&xo)[3],
-                                            const long long (&yo)[3], int z,
-                                            typename Store<S>::R (&fa)[2][Q])
-{
-    using R = typename Store<S>::R;
-    const long long plane = (long long)p.nx * p.ny;
-    const long long zc = (long long)z * plane;
-    const long long zm = (long long)(z == 0 ? p.nz - 1 : z - 1) * plane;
-    const long long zp = (long long)(z == p.nz - 1 ? 0 : z + 1) * plane;
-    const bool lo_wall = p.wall_z && z == 0;
-    const bool hi_wall = p.wall_z && z == p.nz - 1;
-#pragma unroll
-    for (int a = 0; a < 2; ++a) {
-#pragma unroll
-        for (int i = 0; i < Q; ++i) {
-            const bool wall = (cz(i) == 1 && lo_wall) || (cz(i) == -1 && hi_wall);
-            long long idx;
-            if (wall) {
-                idx = (long long)(a * Q + opp(i)) * p.N + zc + yo[1] + xo[1];
-            } else {
-                const long long zs = cz(i) == 1 ? zm : (cz(i) == -1 ? zp : zc);
-                idx = (long long)(a * Q + i) * p.N + zs + yo[1 - cy(i)] + xo[1 - cx(i)];
-            }
-            fa[a][i] = Store<S>::load(f + idx, w<R>(i) * p.rho0);
-        }
-    }
-}
-
-template <int S>
-__device__ __forceinline__ void gather_rho(const typename Store<S>::T *__restrict__ f,
-                                           const Phys<typename Store<S>::R> &p, const int (&xo)[3],
-                                           const long long (&yo)[3], int z, typename Store<S>::R &r1,
-                                           typename Store<S>::R &r2)
-{
-    using R = typename Store<S>::R;
-    R fa[2][Q];
-    gather_cell<S>(f, p, xo, yo, z, fa);
-    R s1 = 0, s2 = 0;
-#pragma unroll
-    for (int i = 0; i < Q; ++i) { s1 += fa[0][i]; s2 += fa[1][i]; }
-    r1 = s1;
-    r2 = s2;
-}
+constexpr int Q2 = 2 * Q;
+static_assert(kGroups * kHalo <= kThreadsF, "one halo group per thread");
 
 template <class R>
-struct RhoRing {
-    R v[3][2][kTY + 2][kTX + 2];
+struct FusedSmem {
+    R ring[3][2][kTY + 2][kTX + 2];        // rho^1, rho^2 of planes z-1, z, z+1 (+ halo)
+    R hpart[2][kGroups][2][kHalo];         // halo partial densities of the next two planes
+    R mom[2][3][kThreadsF];                // sum_a sum_i c_i f_i of the stashed planes
+    R stash[2][Q2][kThreadsF];             // pre-collision populations of planes z, z+1
 };
 
-// Fill ring slot `slot` with rho^1, rho^2 of plane zp (zp may be -1 or nz:
-// a wall ghost plane under half-way walls, else wrapped periodically).  When
-// `stash` is given, interior threads also park their column's 38 populations
-// there ([value][thread], conflict-free) for the collision of that plane.
-template <int S>
-__device__ __forceinline__ void fill_plane(const typename Store<S>::T *__restrict__ f,
-                                           const Phys<typename Store<S>::R> &p, RhoRing<typename Store<S>::R> &ring,
-                                           int slot, int zp, int tx0, int ty0, typename Store<S>::R *stash)
+// A lattice column (x, y) with its wrapped neighbour offsets.
+struct Col {
+    int xo[3];   // x-1, x, x+1
+    int yo[3];   // (y-1, y, y+1) * nx
+};
+
+__device__ __forceinline__ Col make_col(int gx, int gy, int nx, int ny)
 {
-    using R = typename Store<S>::R;
-    const int tid = threadIdx.x;
-    bool ghost = false;
-    int zg = zp;
-    if (zp < 0 || zp >= p.nz) {
-        if (p.wall_z) {
-            ghost = true;
-            zg = zp < 0 ? 0 : p.nz - 1;   // mirror plane across the wall
-        } else {
-            zg = wrapi(zp, p.nz);
-        }
-    }
-    // interior slot of this thread (wrapped coordinates)
-    {
-        const int lx = tid % kTX, ly = tid / kTX;
-        const int gx = (tx0 + lx) % p.nx, gy = (ty0 + ly) % p.ny;
-        const int xo[3] = {gx == 0 ? p.nx - 1 : gx - 1, gx, gx == p.nx - 1 ? 0 : gx + 1};
-        const long long yo[3] = {(long long)(gy == 0 ? p.ny - 1 : gy - 1) * p.nx, (long long)gy * p.nx,
-                                 (long long)(gy == p.ny - 1 ? 0 : gy + 1) * p.nx};
-        R r1, r2;
-        if (ghost && !p.wall_mirror) {
-            r1 = p.rho_s[0];
-            r2 = p.rho_s[1];
-        } else {
-            R fa[2][Q];
-            gather_cell<S>(f, p, xo, yo, zg, fa);
-            R s1 = 0, s2 = 0;
-#pragma unroll
-            for (int i = 0; i < Q; ++i) { s1 += fa[0][i]; s2 += fa[1][i]; }
-            r1 = s1;
-            r2 = s2;
-            if (ghost) {
-                r1 += p.rho_s[0];
-                r2 += p.rho_s[1];
-            } else if (stash) {
-#pragma unroll
-                for (int a = 0; a < 2; ++a)
-#pragma unroll
-                    for (int i = 0; i < Q; ++i) stash[(a * Q + i) * kThreadsF + tid] = fa[a][i];
-            }
-        }
-        ring.v[slot][0][ly + 1][lx + 1] = r1;
-        ring.v[slot][1][ly + 1][lx + 1] = r2;
-    }
-    // halo perimeter
-    if (tid < kHalo) {
-        int hx, hy;
-        if (tid < kTX + 2) { hx = tid; hy = 0; }
-        else if (tid < 2 * (kTX + 2)) { hx = tid - (kTX + 2); hy = kTY + 1; }
-        else { const int k = tid - 2 * (kTX + 2); hx = k < kTY ? 0 : kTX + 1; hy = 1 + (k % kTY); }
-        // tile-relative coordinates may run past the domain by more than one
-        // cell when the domain is smaller than a tile: reduce fully.
-        int gx = (tx0 - 1 + hx) % p.nx; if (gx < 0) gx += p.nx;
-        int gy = (ty0 - 1 + hy) % p.ny; if (gy < 0) gy += p.ny;
-        const int xo[3] = {gx == 0 ? p.nx - 1 : gx - 1, gx, gx == p.nx - 1 ? 0 : gx + 1};
-        const long long yo[3] = {(long long)(gy == 0 ? p.ny - 1 : gy - 1) * p.nx, (long long)gy * p.nx,
-                                 (long long)(gy == p.ny - 1 ? 0 : gy + 1) * p.nx};
-        R r1, r2;
-        if (ghost && !p.wall_mirror) {
-            r1 = p.rho_s[0];
-            r2 = p.rho_s[1];
-        } else {
-            gather_rho<S>(f, p, xo, yo, zg, r1, r2);
-            if (ghost) { r1 += p.rho_s[0]; r2 += p.rho_s[1]; }
-        }
-        ring.v[slot][0][hy][hx] = r1;
-        ring.v[slot][1][hy][hx] = r2;
-    }
+    Col c;
+    c.xo[0] = gx == 0 ? nx - 1 : gx - 1;
+    c.xo[1] = gx;
+    c.xo[2] = gx == nx - 1 ? 0 : gx + 1;
+    c.yo[0] = (gy == 0 ? ny - 1 : gy - 1) * nx;
+    c.yo[1] = gy * nx;
+    c.yo[2] = (gy == ny - 1 ? 0 : gy + 1) * nx;
+    return c;
 }
 
-// Force, collision and store of the interior cell of this thread at plane z,
-// from the populations parked in `stash`.
+// Plane set-up for a gather at plane zp: the plane actually read (zp wrapped,
+// or the mirror plane of a wall ghost) and its z neighbour offsets.
+struct PlaneRef {
+    int zc, zm, zp;        // offsets of planes z, z-1, z+1 (wrapped)
+    bool lo_wall, hi_wall; // half-way wall below / above plane z
+    bool ghost;            // zp is a wall ghost plane (density = mirror + rho_s)
+    bool constant;         // ghost plane with the point-wise wall potential: rho = rho_s
+};
+
+template <class R>
+__device__ __forceinline__ PlaneRef plane_ref(const Phys<R> &p, int zp)
+{
+    PlaneRef r;
+    int z = zp;
+    r.ghost = false;
+    if (zp < 0 || zp >= p.nz) {
+        if (p.wall_z) {
+            r.ghost = true;
+            z = zp < 0 ? 0 : p.nz - 1;
+        } else {
+            z = ((zp % p.nz) + p.nz) % p.nz;
+        }
+    }
+    r.constant = r.ghost && !p.wall_mirror;
+    const int plane = p.nx * p.ny;
+    r.zc = z * plane;
+    r.zm = (z == 0 ? p.nz - 1 : z - 1) * plane;
+    r.zp = (z == p.nz - 1 ? 0 : z + 1) * plane;
+    r.lo_wall = p.wall_z && z == 0;
+    r.hi_wall = p.wall_z && z == p.nz - 1;
+    return r;
+}
+
+// Element index (within its population array) and array number of the
+// pull-gathered population i of component a at column c of plane pr.
+template <int I>
+__device__ __forceinline__ int gather_elem(const PlaneRef &pr, const Col &c, int &arr_dir)
+{
+    const bool wall = (cz(I) == 1 && pr.lo_wall) || (cz(I) == -1 && pr.hi_wall);
+    if (wall) {
+        arr_dir = opp(I);
+        return pr.zc + c.yo[1] + c.xo[1];
+    }
+    arr_dir = I;
+    const int zs = cz(I) == 1 ? pr.zm : (cz(I) == -1 ? pr.zp : pr.zc);
+    return zs + c.yo[1 - cy(I)] + c.xo[1 - cx(I)];
+}
+
+template <int S, int I>
+__device__ __forceinline__ void load_dir(const typename Store<S>::T *__restrict__ f, long long N,
+                                         typename Store<S>::R rho0, const PlaneRef &pr, const Col &c,
+                                         typename Store<S>::R (&v)[Q2])
+{
+    using R = typename Store<S>::R;
+    int d;
+    const int e = gather_elem<I>(pr, c, d);
+    v[I] = Store<S>::load(f + (long long)d * N + e, w<R>(I) * rho0);
+    v[Q + I] = Store<S>::load(f + (long long)(Q + d) * N + e, w<R>(I) * rho0);
+}
+
+template <int S, int I>
+struct GatherAll {
+    __device__ __forceinline__ static void run(const typename Store<S>::T *__restrict__ f, long long N,
+                                               typename Store<S>::R rho0, const PlaneRef &pr, const Col &c,
+                                               typename Store<S>::R (&v)[Q2])
+    {
+        load_dir<S, I>(f, N, rho0, pr, c, v);
+        GatherAll<S, I + 1>::run(f, N, rho0, pr, c, v);
+    }
+};
+template <int S>
+struct GatherAll<S, Q> {
+    __device__ __forceinline__ static void run(const typename Store<S>::T *__restrict__, long long,
+                                               typename Store<S>::R, const PlaneRef &, const Col &,
+                                               typename Store<S>::R (&)[Q2]) {}
+};
+
+// rho^1, rho^2 and momentum of a gathered population set.
+template <class R>
+__device__ __forceinline__ void sums(const R (&v)[Q2], R &r1, R &r2, R &jx, R &jy, R &jz)
+{
+    R s1 = 0, s2 = 0, ax = 0, ay = 0, az = 0;
+#pragma unroll
+    for (int i = 0; i < Q; ++i) {
+        s1 += v[i];
+        s2 += v[Q + i];
+        const R t = v[i] + v[Q + i];
+        if (cx(i) == 1) ax += t; else if (cx(i) == -1) ax -= t;
+        if (cy(i) == 1) ay += t; else if (cy(i) == -1) ay -= t;
+        if (cz(i) == 1) az += t; else if (cz(i) == -1) az -= t;
+    }
+    r1 = s1; r2 = s2; jx = ax; jy = ay; jz = az;
+}
+
+// Partial gather of one halo cell: the populations q in [Q0, Q1) of the 38
+// (component q / 19, direction q % 19), summed per component.
+template <int S, int QQ, int Q1>
+struct HaloRange {
+    __device__ __forceinline__ static void load(const typename Store<S>::T *__restrict__ f, long long N,
+                                                typename Store<S>::R rho0, const PlaneRef &pr, const Col &c,
+                                                typename Store<S>::R (&v)[kPer], int k)
+    {
+        using R = typename Store<S>::R;
+        constexpr int a = QQ / Q, i = QQ % Q;
+        int d;
+        const int e = gather_elem<i>(pr, c, d);
+        v[k] = Store<S>::load(f + (long long)(a * Q + d) * N + e, w<R>(i) * rho0);
+        HaloRange<S, QQ + 1, Q1>::load(f, N, rho0, pr, c, v, k + 1);
+    }
+    __device__ __forceinline__ static void sum(const typename Store<S>::R (&v)[kPer], int k,
+                                               typename Store<S>::R &s0, typename Store<S>::R &s1)
+    {
+        if (QQ / Q == 0) s0 += v[k]; else s1 += v[k];
+        HaloRange<S, QQ + 1, Q1>::sum(v, k + 1, s0, s1);
+    }
+};
+template <int S, int Q1>
+struct HaloRange<S, Q1, Q1> {
+    __device__ __forceinline__ static void load(const typename Store<S>::T *__restrict__, long long,
+                                                typename Store<S>::R, const PlaneRef &, const Col &,
+                                                typename Store<S>::R (&)[kPer], int) {}
+    __device__ __forceinline__ static void sum(const typename Store<S>::R (&)[kPer], int,
+                                               typename Store<S>::R &, typename Store<S>::R &) {}
+};
+
+template <int S>
+__device__ __forceinline__ void halo_load(const typename Store<S>::T *__restrict__ f, const Phys<typename Store<S>::R> &p,
+                                          const PlaneRef &pr, const Col &c, int g, typename Store<S>::R (&v)[kPer])
+{
+    if (g == 0) HaloRange<S, 0, kPer>::load(f, p.N, p.rho0, pr, c, v, 0);
+    else if (g == 1) HaloRange<S, kPer, 2 * kPer>::load(f, p.N, p.rho0, pr, c, v, 0);
+    else HaloRange<S, 2 * kPer, Q2>::load(f, p.N, p.rho0, pr, c, v, 0);
+}
+
+template <int S>
+__device__ __forceinline__ void halo_sum(const typename Store<S>::R (&v)[kPer], int g, typename Store<S>::R &s0,
+                                         typename Store<S>::R &s1)
+{
+    s0 = 0;
+    s1 = 0;
+    if (g == 0) HaloRange<S, 0, kPer>::sum(v, 0, s0, s1);
+    else if (g == 1) HaloRange<S, kPer, 2 * kPer>::sum(v, 0, s0, s1);
+    else HaloRange<S, 2 * kPer, Q2>::sum(v, 0, s0, s1);
+}
+
+// Collision of both components at the thread's interior cell of plane z (the
+// populations come from the stash, densities from the ring, momentum from the
+// moment buffer), forcing term included, result stored at the cell.
 template <int S, bool REG>
-__device__ __forceinline__ void collide_store(typename Store<S>::T *__restrict__ fout,
-                                              const Phys<typename Store<S>::R> &p,
-                                              const RhoRing<typename Store<S>::R> &ring, const int (&slot)[3],
-                                              int z, int x, int y, const typename Store<S>::R *stash)
+__device__ __forceinline__ void collide_cell(typename Store<S>::T *__restrict__ fout, const Phys<typename Store<S>::R> &p,
+                                             const FusedSmem<typename Store<S>::R> &sm, int sl_m, int sl_c, int sl_p,
+                                             int st, long long cell)
 {
     using R = typename Store<S>::R;
     const int tid = threadIdx.x;
     const int lx = tid % kTX + 1, ly = tid / kTX + 1;
-    R fa[2][Q];
-#pragma unroll
-    for (int a = 0; a < 2; ++a)
-#pragma unroll
-        for (int i = 0; i < Q; ++i) fa[a][i] = stash[(a * Q + i) * kThreadsF + tid];
-    R r[2], jx = 0, jy = 0, jz = 0;
-#pragma unroll
-    for (int a = 0; a < 2; ++a) {
-        R s = 0;
-#pragma unroll
-        for (int i = 0; i < Q; ++i) {
-            const R v = fa[a][i];
-            s += v;
-            if (cx(i) == 1) jx += v; else if (cx(i) == -1) jx -= v;
-            if (cy(i) == 1) jy += v; else if (cy(i) == -1) jy -= v;
-            if (cz(i) == 1) jz += v; else if (cz(i) == -1) jz -= v;
-        }
-        r[a] = s;
-    }
-    const R inv = R(1) / (r[0] + r[1]);
-    const R ux = jx * inv, uy = jy * inv, uz = jz * inv;
+    const R r1 = sm.ring[sl_c][0][ly][lx];
+    const R r2 = sm.ring[sl_c][1][ly][lx];
+    const R inv = R(1) / (r1 + r2);
+    const R ux = sm.mom[st][0][tid] * inv, uy = sm.mom[st][1][tid] * inv, uz = sm.mom[st][2][tid] * inv;
     // S^b = sum_{i != 0} w_i c_i rho^b(x + c_i)  (Eq. 7; ghost planes carry Eq. 13's rho')
     R Sb[2][3];
 #pragma unroll
@@ -204,26 +232,160 @@ __device__ __forceinline__ void collide_store(typename Store<S>::T *__restrict__
         R sx = 0, sy = 0, sz = 0;
 #pragma unroll
         for (int i = 1; i < Q; ++i) {
-            const R wr = w<R>(i) * ring.v[slot[1 + cz(i)]][b][ly + cy(i)][lx + cx(i)];
+            const int sl = cz(i) == -1 ? sl_m : (cz(i) == 1 ? sl_p : sl_c);
+            const R wr = w<R>(i) * sm.ring[sl][b][ly + cy(i)][lx + cx(i)];
             if (cx(i) == 1) sx += wr; else if (cx(i) == -1) sx -= wr;
             if (cy(i) == 1) sy += wr; else if (cy(i) == -1) sy -= wr;
             if (cz(i) == 1) sz += wr; else if (cz(i) == -1) sz -= wr;
         }
         Sb[b][0] = sx; Sb[b][1] = sy; Sb[b][2] = sz;
     }
-    collide<R, REG>(fa[0], r[0], ux, uy, uz, p.G12 * Sb[1][0] + p.gext[0], p.G12 * Sb[1][1] + p.gext[1],
-                    p.G12 * Sb[1][2] + p.gext[2], p.omega[0]);
-    collide<R, REG>(fa[1], r[1], ux, uy, uz, p.G21 * Sb[0][0] + p.gext[0], p.G21 * Sb[0][1] + p.gext[1],
-                    p.G21 * Sb[0][2] + p.gext[2], p.omega[1]);
-    const long long cell = ((long long)z * p.ny + y) * p.nx + x;
+    // g^a = sum_b F^{ab} / rho^a + g_ext = G^{ab} S^b + g_ext
+    const R v1x = ux + p.G12 * Sb[1][0] + p.gext[0], v1y = uy + p.G12 * Sb[1][1] + p.gext[1],
+            v1z = uz + p.G12 * Sb[1][2] + p.gext[2];
+    const R v2x = ux + p.G21 * Sb[0][0] + p.gext[0], v2y = uy + p.G21 * Sb[0][1] + p.gext[1],
+            v2z = uz + p.G21 * Sb[0][2] + p.gext[2];
+    const R usq = ux * ux + uy * uy + uz * uz;
+    const R v1sq = v1x * v1x + v1y * v1y + v1z * v1z;
+    const R v2sq = v2x * v2x + v2y * v2y + v2z * v2z;
+    const R Au = R(1) - R(1.5) * usq, Bu = R(3) - R(4.5) * usq;
+    const R A1 = R(1) - R(1.5) * v1sq, B1 = R(3) - R(4.5) * v1sq;
+    const R A2 = R(1) - R(1.5) * v2sq, B2 = R(3) - R(4.5) * v2sq;
+    const R keep1 = R(1) - p.omega[0], keep2 = R(1) - p.omega[1];
+    const R *s0 = &sm.stash[st][0][tid];
+    const R rq1 = r1 / R(36), rq2 = r2 / R(36);   // rho w_i = (rho / 36) k_i
+    typename Store<S>::T *o = fout + cell;
+    const long long N = p.N;
+    const R ref0 = p.rho0;
+
+    // Regularized: second moments of f - f^eq(u): Pi = sum c c f - rho (T0 I + u u)
+    R P1[6], P2[6], t1 = 0, t2 = 0;
+    if (REG) {
 #pragma unroll
-    for (int a = 0; a < 2; ++a)
+        for (int k = 0; k < 6; ++k) { P1[k] = 0; P2[k] = 0; }
 #pragma unroll
-        for (int i = 0; i < Q; ++i)
-            Store<S>::store(fout + (long long)(a * Q + i) * p.N + cell, fa[a][i], w<R>(i) * p.rho0);
+        for (int i = 1; i < Q; ++i) {
+            const R fa = s0[i * kThreadsF], fb = s0[(Q + i) * kThreadsF];
+            if (cx(i)) { P1[0] += fa; P2[0] += fb; }
+            if (cy(i)) { P1[1] += fa; P2[1] += fb; }
+            if (cz(i)) { P1[2] += fa; P2[2] += fb; }
+            if (cx(i) && cy(i)) { if (cx(i) == cy(i)) { P1[3] += fa; P2[3] += fb; } else { P1[3] -= fa; P2[3] -= fb; } }
+            if (cx(i) && cz(i)) { if (cx(i) == cz(i)) { P1[4] += fa; P2[4] += fb; } else { P1[4] -= fa; P2[4] -= fb; } }
+            if (cy(i) && cz(i)) { if (cy(i) == cz(i)) { P1[5] += fa; P2[5] += fb; } else { P1[5] -= fa; P2[5] -= fb; } }
+        }
+        const R T0 = R(1) / R(3);
+        P1[0] -= r1 * (T0 + ux * ux); P2[0] -= r2 * (T0 + ux * ux);
+        P1[1] -= r1 * (T0 + uy * uy); P2[1] -= r2 * (T0 + uy * uy);
+        P1[2] -= r1 * (T0 + uz * uz); P2[2] -= r2 * (T0 + uz * uz);
+        P1[3] -= r1 * ux * uy; P2[3] -= r2 * ux * uy;
+        P1[4] -= r1 * ux * uz; P2[4] -= r2 * ux * uz;
+        P1[5] -= r1 * uy * uz; P2[5] -= r2 * uy * uz;
+        t1 = (P1[0] + P1[1] + P1[2]) / R(3);
+        t2 = (P2[0] + P2[1] + P2[2]) / R(3);
+    }
+    // rest population (k_0 = 12)
+    {
+        const R w0 = w<R>(0);
+        R o1, o2;
+        if (!REG) {
+            o1 = rq1 * R(12) * (A1 - keep1 * Au) + keep1 * s0[0];
+            o2 = rq2 * R(12) * (A2 - keep2 * Au) + keep2 * s0[Q * kThreadsF];
+        } else {
+            o1 = rq1 * R(12) * A1 - keep1 * R(1.5) * t1;
+            o2 = rq2 * R(12) * A2 - keep2 * R(1.5) * t2;
+        }
+        Store<S>::store(o, o1, w0 * ref0);
+        Store<S>::store(o + (long long)Q * N, o2, w0 * ref0);
+    }
+#pragma unroll
+    for (int i = 1; i < Q; i += 2) {
+        const R cu = cdot<R>(i, ux, uy, uz);
+        const R c1 = cdot<R>(i, v1x, v1y, v1z);
+        const R c2 = cdot<R>(i, v2x, v2y, v2z);
+        // E = A + 4.5 (c.v)^2, O = (c.v) (B + 4.5 (c.v)^2): f^eq_+- = rho w (E +- O)
+        const R E1 = A1 + R(4.5) * c1 * c1, O1 = c1 * (B1 + R(4.5) * c1 * c1);
+        const R E2 = A2 + R(4.5) * c2 * c2, O2 = c2 * (B2 + R(4.5) * c2 * c2);
+        const R rw1 = rq1 * R(k36(i)), rw2 = rq2 * R(k36(i));
+        R o1p, o1m, o2p, o2m;
+        if (!REG) {
+            // f* = f^eq(v) + keep (f - f^eq(u)); f^eq(u) shares its polynomial between components
+            const R Eu = Au + R(4.5) * cu * cu, Ou = cu * (Bu + R(4.5) * cu * cu);
+            const R P1e = rw1 * (E1 - keep1 * Eu), M1 = rw1 * (O1 - keep1 * Ou);
+            const R P2e = rw2 * (E2 - keep2 * Eu), M2 = rw2 * (O2 - keep2 * Ou);
+            o1p = P1e + M1 + keep1 * s0[i * kThreadsF];
+            o1m = P1e - M1 + keep1 * s0[(i + 1) * kThreadsF];
+            o2p = P2e + M2 + keep2 * s0[(Q + i) * kThreadsF];
+            o2m = P2e - M2 + keep2 * s0[(Q + i + 1) * kThreadsF];
+        } else {
+            // f* = f^eq(v) + keep (k_i / 8) (c c : Pi - tr(Pi) / 3)
+            R cc1 = 0, cc2 = 0;
+            if (cx(i)) { cc1 += P1[0]; cc2 += P2[0]; }
+            if (cy(i)) { cc1 += P1[1]; cc2 += P2[1]; }
+            if (cz(i)) { cc1 += P1[2]; cc2 += P2[2]; }
+            if (cx(i) && cy(i)) { const R sg = cx(i) == cy(i) ? R(2) : R(-2); cc1 += sg * P1[3]; cc2 += sg * P2[3]; }
+            if (cx(i) && cz(i)) { const R sg = cx(i) == cz(i) ? R(2) : R(-2); cc1 += sg * P1[4]; cc2 += sg * P2[4]; }
+            if (cy(i) && cz(i)) { const R sg = cy(i) == cz(i) ? R(2) : R(-2); cc1 += sg * P1[5]; cc2 += sg * P2[5]; }
+            const R n1 = keep1 * (R(k36(i)) * R(0.125)) * (cc1 - t1);
+            const R n2 = keep2 * (R(k36(i)) * R(0.125)) * (cc2 - t2);
+            o1p = rw1 * (E1 + O1) + n1;
+            o1m = rw1 * (E1 - O1) + n1;
+            o2p = rw2 * (E2 + O2) + n2;
+            o2m = rw2 * (E2 - O2) + n2;
+        }
+        const R ref = w<R>(i) * ref0;
+        Store<S>::store(o + (long long)i * N, o1p, ref);
+        Store<S>::store(o + (long long)(i + 1) * N, o1m, ref);
+        Store<S>::store(o + (long long)(Q + i) * N, o2p, ref);
+        Store<S>::store(o + (long long)(Q + i + 1) * N, o2m, ref);
+    }
 }
 
-constexpr size_t kStashBytes = 2 * 2 * Q * kThreadsF * sizeof(float);   // two planes, FP32
+// Interior part of plane zp for this thread's column: rho^1, rho^2 into ring
+// slot `slot`; when st >= 0 the populations and momentum into stash slot st.
+template <int S>
+__device__ __forceinline__ void interior_plane(const typename Store<S>::T *__restrict__ f,
+                                               const Phys<typename Store<S>::R> &p, FusedSmem<typename Store<S>::R> &sm,
+                                               int slot, int st, const PlaneRef &pr, const typename Store<S>::R (&v)[Q2])
+{
+    using R = typename Store<S>::R;
+    const int tid = threadIdx.x;
+    const int lx = tid % kTX + 1, ly = tid / kTX + 1;
+    R r1 = p.rho_s[0], r2 = p.rho_s[1];
+    if (!pr.constant) {
+        R a1, a2, jx, jy, jz;
+        sums(v, a1, a2, jx, jy, jz);
+        if (pr.ghost) {
+            r1 += a1; r2 += a2;
+        } else {
+            r1 = a1; r2 = a2;
+            if (st >= 0) {
+#pragma unroll
+                for (int k = 0; k < Q2; ++k) sm.stash[st][k][tid] = v[k];
+                sm.mom[st][0][tid] = jx; sm.mom[st][1][tid] = jy; sm.mom[st][2][tid] = jz;
+            }
+        }
+    }
+    sm.ring[slot][0][ly][lx] = r1;
+    sm.ring[slot][1][ly][lx] = r2;
+}
+
+// Halo densities of a plane in ring slot `slot` from the three partials.
+template <class R>
+__device__ __forceinline__ void halo_combine(const Phys<R> &p, FusedSmem<R> &sm, int slot, int hs,
+                                             const PlaneRef &pr, int h, int hx, int hy)
+{
+    R r1, r2;
+    if (pr.constant) {
+        r1 = p.rho_s[0];
+        r2 = p.rho_s[1];
+    } else {
+        r1 = sm.hpart[hs][0][0][h] + sm.hpart[hs][1][0][h] + sm.hpart[hs][2][0][h];
+        r2 = sm.hpart[hs][0][1][h] + sm.hpart[hs][1][1][h] + sm.hpart[hs][2][1][h];
+        if (pr.ghost) { r1 += p.rho_s[0]; r2 += p.rho_s[1]; }
+    }
+    sm.ring[slot][0][hy][hx] = r1;
+    sm.ring[slot][1][hy][hx] = r2;
+}
 
 template <int S, bool REG>
 __global__ void __launch_bounds__(kThreadsF, 2)
@@ -232,34 +394,101 @@ k_step_fused(const typename Store<S>::T *__restrict__ fin, typename Store<S>::T 
 {
     using R = typename Store<S>::R;
     static_assert(sizeof(R) == sizeof(float), "the fused step runs FP32 arithmetic");
-    __shared__ RhoRing<R> ring;
-    extern __shared__ float stash_mem[];
-    R *stash[2] = {(R *)stash_mem, (R *)stash_mem + 2 * Q * kThreadsF};
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    FusedSmem<R> &sm = *reinterpret_cast<FusedSmem<R> *>(smem_raw);
+    const int tid = threadIdx.x;
     const int tx0 = (blockIdx.x % ntx) * kTX;
     const int ty0 = (blockIdx.x / ntx) * kTY;
     const int z0 = blockIdx.y * kLZ;
     const int z1 = min(z0 + kLZ, p.nz);
-    const int x = tx0 + threadIdx.x % kTX;
-    const int y = ty0 + threadIdx.x / kTX;
+    const int lx = tid % kTX, ly = tid / kTX;
+    const int x = tx0 + lx, y = ty0 + ly;
     const bool active = x < p.nx && y < p.ny;
+    // interior column (wrapped so that ragged tiles fill their ring slots
+    // with the periodic images their active neighbours read)
+    const Col ci = make_col((tx0 + lx) % p.nx, (ty0 + ly) % p.ny, p.nx, p.ny);
+    // halo cell h and population group g of this thread (tid < 3 * 84)
+    const bool has_halo = tid < kGroups * kHalo;
+    const int h = tid % kHalo, g = tid / kHalo;
+    auto halo_pos = [](int hh, int &hx, int &hy) {
+        if (hh < kTX + 2) { hx = hh; hy = 0; }
+        else if (hh < 2 * (kTX + 2)) { hx = hh - (kTX + 2); hy = kTY + 1; }
+        else { const int k = hh - 2 * (kTX + 2); hx = k < kTY ? 0 : kTX + 1; hy = 1 + (k % kTY); }
+    };
+    int hx, hy;
+    halo_pos(h, hx, hy);
+    int hgx = (tx0 - 1 + hx) % p.nx; if (hgx < 0) hgx += p.nx;
+    int hgy = (ty0 - 1 + hy) % p.ny; if (hgy < 0) hgy += p.ny;
+    const Col ch = make_col(hgx, hgy, p.nx, p.ny);
 
-    // ring slot of plane z is (z - z0 + 1) mod 3; stash slot alternates
-    fill_plane<S>(fin, p, ring, 0, z0 - 1, tx0, ty0, nullptr);
-    fill_plane<S>(fin, p, ring, 1, z0, tx0, ty0, stash[0]);
-    int s_m = 0, s_c = 1, s_p = 2, st = 0;
+    // ring slot of plane q: (q - z0 + 1) % 3; stash, moment and halo-partial
+    // slot of plane q: (q - z0) & 1.
+    // prologue: planes z0-1 and z0 in full, halo partials of z0+1
+    for (int q = z0 - 1; q <= z0; ++q) {
+        const PlaneRef pr = plane_ref(p, q);
+        R v[Q2];
+        if (!pr.constant) GatherAll<S, 0>::run(fin, p.N, p.rho0, pr, ci, v);
+        interior_plane<S>(fin, p, sm, q - z0 + 1, q == z0 ? 0 : -1, pr, v);
+        if (tid < kHalo) {
+            R r1 = p.rho_s[0], r2 = p.rho_s[1];
+            if (!pr.constant) {
+                R hv[Q2];
+                GatherAll<S, 0>::run(fin, p.N, p.rho0, pr, ch, hv);
+                R a1, a2, jx, jy, jz;
+                sums(hv, a1, a2, jx, jy, jz);
+                if (pr.ghost) { r1 += a1; r2 += a2; } else { r1 = a1; r2 = a2; }
+            }
+            sm.ring[q - z0 + 1][0][hy][hx] = r1;
+            sm.ring[q - z0 + 1][1][hy][hx] = r2;
+        }
+    }
+    {
+        const PlaneRef pr = plane_ref(p, z0 + 1);
+        if (has_halo) {
+            R hv[kPer];
+            R s1 = 0, s2 = 0;
+            if (!pr.constant) {
+                halo_load<S>(fin, p, pr, ch, g, hv);
+                halo_sum<S>(hv, g, s1, s2);
+            }
+            sm.hpart[1][g][0][h] = s1;
+            sm.hpart[1][g][1][h] = s2;
+        }
+    }
+    __syncthreads();
+
+    const long long cell_xy = (long long)y * p.nx + x;
+    int s_m = 0, s_c = 1, s_p = 2;
     for (int z = z0; z < z1; ++z) {
-        fill_plane<S>(fin, p, ring, s_p, z + 1, tx0, ty0, z + 1 < z1 ? stash[st ^ 1] : nullptr);
+        const int k = z - z0;
+        // ---- phase A: gathers of plane z+1 (interior) and z+2 (halo partials)
+        const PlaneRef pr1 = plane_ref(p, z + 1);
+        const bool need2 = z + 2 <= z1;           // rho(z+2) feeds the collision of z+1
+        const PlaneRef pr2 = plane_ref(p, z + 2);
+        R v[Q2];
+        R hv[kPer];
+        if (!pr1.constant) GatherAll<S, 0>::run(fin, p.N, p.rho0, pr1, ci, v);
+        if (need2 && has_halo && !pr2.constant) halo_load<S>(fin, p, pr2, ch, g, hv);
+        if (tid < kHalo) halo_combine<R>(p, sm, s_p, (k + 1) & 1, pr1, h, hx, hy);
+        interior_plane<S>(fin, p, sm, s_p, z + 1 < z1 ? ((k + 1) & 1) : -1, pr1, v);
+        if (need2 && has_halo) {
+            R s1 = 0, s2 = 0;
+            if (!pr2.constant) halo_sum<S>(hv, g, s1, s2);
+            sm.hpart[k & 1][g][0][h] = s1;
+            sm.hpart[k & 1][g][1][h] = s2;
+        }
         __syncthreads();
-        const int sl[3] = {s_m, s_c, s_p};
-        if (active) collide_store<S, REG>(fout, p, ring, sl, z, x, y, stash[st]);
+        // ---- phase B: collision of plane z
+        if (active)
+            collide_cell<S, REG>(fout, p, sm, s_m, s_c, s_p, k & 1, (long long)z * p.nx * p.ny + cell_xy);
         __syncthreads();
         const int t = s_m;
         s_m = s_c;
         s_c = s_p;
         s_p = t;
-        st ^= 1;
     }
 }
+
 template <class R>
 Phys<R> make_phys_f(const HostPhys &h)
 {
@@ -276,6 +505,8 @@ Phys<R> make_phys_f(const HostPhys &h)
     return p;
 }
 
+constexpr size_t kSmemBytes = sizeof(FusedSmem<float>);
+
 template <int S>
 cudaError_t fused_t(const HostPhys &h, const void *fin, void *fout, cudaStream_t s, cudaEvent_t *ev)
 {
@@ -288,18 +519,18 @@ cudaError_t fused_t(const HostPhys &h, const void *fin, void *fout, cudaStream_t
     static bool attr_set = false;
     if (!attr_set) {
         cudaError_t e = cudaFuncSetAttribute(k_step_fused<S, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             (int)kStashBytes);
+                                             (int)kSmemBytes);
         if (e == cudaSuccess)
             e = cudaFuncSetAttribute(k_step_fused<S, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                     (int)kStashBytes);
+                                     (int)kSmemBytes);
         if (e != cudaSuccess) return e;
         attr_set = true;
     }
     if (ev) cudaEventRecord(ev[0], s);
     if (h.collision == LBM_REGULARIZED)
-        k_step_fused<S, true><<<grid, kThreadsF, kStashBytes, s>>>((const T *)fin, (T *)fout, p, ntx);
+        k_step_fused<S, true><<<grid, kThreadsF, kSmemBytes, s>>>((const T *)fin, (T *)fout, p, ntx);
     else
-        k_step_fused<S, false><<<grid, kThreadsF, kStashBytes, s>>>((const T *)fin, (T *)fout, p, ntx);
+        k_step_fused<S, false><<<grid, kThreadsF, kSmemBytes, s>>>((const T *)fin, (T *)fout, p, ntx);
     if (ev) cudaEventRecord(ev[1], s);
     return cudaGetLastError();
 }
@@ -308,7 +539,8 @@ cudaError_t fused_t(const HostPhys &h, const void *fin, void *fout, cudaStream_t
 
 bool fused_supported(const HostPhys &p)
 {
-    return p.storage != ST_F64 &&
+    // 32-bit element offsets inside one population array
+    return p.storage != ST_F64 && p.N < (1LL << 31) &&
            (long long)((p.nx + kTX - 1) / kTX) * ((p.ny + kTY - 1) / kTY) < (1LL << 31) &&
            (p.nz + kLZ - 1) / kLZ < 65536;
 }

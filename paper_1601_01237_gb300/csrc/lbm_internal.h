@@ -80,6 +80,15 @@ cudaError_t launch_adjoint_rho0(const HostPhys &p, const void *lam, double *g1, 
 // density pass only (rho = sum_i f_i, pull-gathered) into rho
 cudaError_t launch_density(const HostPhys &p, const void *f, void *rho, cudaStream_t s);
 
+// FP64 diagnostics over the density fields in rho (diag_blocks() x
+// diag_slots() partial doubles).
+int diag_blocks();
+int diag_slots();
+cudaError_t launch_pressure(const HostPhys &h, const void *rho, const double center[3], double r_in, double r_out,
+                            double *partials, cudaStream_t s);
+cudaError_t launch_droplet(const HostPhys &h, const void *rho, double threshold, const double origin[3],
+                           double *partials, cudaStream_t s);
+
 size_t storage_bytes(int storage);   // bytes per stored population value
 size_t real_bytes(int storage);      // bytes per arithmetic value
 

@@ -14,6 +14,7 @@ from . import _native as nat
 from ._native import check, lib
 
 Q = 19
+CUDA_STREAM_LEGACY = 0x1   # cudaStreamLegacy
 
 
 def _ptr(x):
@@ -80,6 +81,22 @@ def lbm_reduce(h):
     out = (ctypes.c_double * 6)()
     check(lib().lbm_reduce(h, out), h)
     return list(out)
+
+
+def lbm_pressure_jump(h, center, r_in, r_out):
+    """(p_in, p_out, dp) with p = T0 rho - G12 T0 rho1 rho2; center = (x, y, z)."""
+    c = (ctypes.c_double * 3)(*[float(v) for v in center])
+    out = (ctypes.c_double * 3)()
+    check(lib().lbm_pressure_jump(h, c, float(r_in), float(r_out), out), h)
+    return tuple(out)
+
+
+def lbm_droplet_stats(h, threshold, origin=(0.0, 0.0, 0.0)):
+    o = (ctypes.c_double * 3)(*[float(v) for v in origin])
+    out = (ctypes.c_double * 7)()
+    check(lib().lbm_droplet_stats(h, float(threshold), o, out), h)
+    return {"volume": out[0], "com": (out[1], out[2], out[3]), "mass": out[4], "film_rho": out[5],
+            "film_cells": out[6]}
 
 
 def lbm_get_populations(h, out):
@@ -177,7 +194,10 @@ def make_params(shape, tau=(1.0, 1.0), G12=0.0, G21=None, g_ext=(0.0, 0.0, 0.0),
     p.storage = nat.STORAGE[storage]
     p.collision = nat.COLLISION[collision]
     p.wall_model = nat.WALL_MODEL[wall_model]
-    p.stream = stream
+    # A handle of 0 is the legacy default stream (torch's default stream);
+    # the C ABI reserves NULL for "library-owned stream", so pass the
+    # runtime's explicit legacy-stream handle instead.
+    p.stream = CUDA_STREAM_LEGACY if stream == 0 else stream
     return p
 
 
@@ -245,6 +265,12 @@ class Lattice:
     def reduce(self):
         v = lbm_reduce(self.h)
         return {"mass1": v[0], "mass2": v[1], "momentum": v[2:5], "max_uF": v[5]}
+
+    def pressure_jump(self, center, r_in, r_out):
+        return lbm_pressure_jump(self.h, center, r_in, r_out)
+
+    def droplet_stats(self, threshold, origin=(0.0, 0.0, 0.0)):
+        return lbm_droplet_stats(self.h, threshold, origin)
 
     def get_populations(self):
         """Host copy of f_i^a(x, t), shape (2, 19, nz, ny, nx), library direction order."""
