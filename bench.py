@@ -146,12 +146,18 @@ def measured_hbm_peak():
     return FALLBACK_HBM_GBS, "fallback (no HBM figure in MEASURED_PEAKS.json)"
 
 
-def kernel_source_hash():
+# source files that define each timed kernel (a change to any of them voids
+# the committed DRAM-traffic figure of that kernel)
+KERNEL_SOURCES = {"k_step_fused": ("d3q19.cuh", "lbm_fused.cu"),
+                  "k_density": ("d3q19.cuh", "lbm_forward.cu"),
+                  "k_collide": ("d3q19.cuh", "lbm_forward.cu")}
+
+
+def kernel_source_hash(kernel):
     h = hashlib.sha256()
     csrc = os.path.join(ROOT, "paper_1601_01237_gb300", "csrc")
-    for f in sorted(os.listdir(csrc)):
-        if f.endswith((".cu", ".cuh", ".h")):
-            h.update(open(os.path.join(csrc, f), "rb").read())
+    for f in KERNEL_SOURCES[kernel]:
+        h.update(open(os.path.join(csrc, f), "rb").read())
     return h.hexdigest()[:16]
 
 
@@ -164,7 +170,7 @@ def ncu_traffic(kernel, storage, cells):
     except (OSError, ValueError):
         return None
     e = d.get("%s/%s" % (kernel, storage))
-    if not e or e.get("kernel_source_sha") != kernel_source_hash():
+    if not e or e.get("kernel_source_sha") != kernel_source_hash(kernel):
         return None
     return e["dram_bytes_per_cell"] * cells
 

@@ -7,17 +7,20 @@
 //   f*(y) = C(f^n(y), S(y)),  S^b(y) = sum_k w_k c_k rho^b(y + c_k),
 //   f^{n+1}_i(y + c_i) = f*_i(y)      (or f^{n+1}_opp(i)(y) at a wall),
 // so one reverse step is
-//   mu_i(y)      = lambda^{n+1}_i(y + c_i)   (or lambda^{n+1}_opp(i)(y) at a wall)
-//   lambda_loc   = (dC/df)^T mu,   a^b(y) = (dC/dS^b)^T mu
-//   lambda^n_i(x) = lambda_loc_i(x) + D^b(x),   D^b(x) = dL/drho^b(x)
-//                 = sum_k w_k c_k . a^b(x - c_k)  (+ mirror-wall terms),
-// with b the component of population i.  Parameter sensitivities
+//   lambda^n_i(x) = lambda_loc^n_i(x) + D^n_b(x)    (b = component of i),
+//   lambda_loc^n  = (dC/df)^T mu,   a^n_b(y) = (dC/dS^b)^T mu,
+//   D^n_b(x)      = dL/drho^b(x) = sum_k w_k c_k . a^n_b(x - c_k)
+//                   (+ mirror-wall terms),
+//   mu_i(y)       = lambda^{n+1}_i(y + c_i)  (or lambda^{n+1}_opp(i)(y) at a wall).
+// lambda itself is never stored: the reverse step gathers
+// mu_i(y) = lambda_loc^{n+1}_i(y + c_i) + D^{n+1}_b(y + c_i) from the previous
+// step's lambda_loc and the small field D^{n+1}.  Parameter sensitivities
 // dL/dG^{ab} and dL/dtau_a are accumulated per block in FP64.
 //
-// Kernels: k_adj_seed (lambda^N from dL/drho at the last step),
-// k_adj_local (mu gather + local reverse pass), k_adj_finish (stencil
-// transpose), k_adj_rho0 (dL/drho_0 = sum_i w_i lambda^0_i for an initial
-// state f^eq(rho_0, u = 0)).
+// Kernels: k_adj_seed (lambda_loc^N = dL/drho at the last step, D^N = 0),
+// k_adj_D (D from a), k_adj_local (mu gather + local reverse pass),
+// k_adj_rho0 (dL/drho_0 = sum_i w_i lambda^0_i for an initial state
+// f^eq(rho_0, u = 0)).
 #include <cuda_runtime.h>
 
 #include "d3q19.cuh"
@@ -28,37 +31,41 @@ namespace lbm {
 namespace {
 
 constexpr int kThreadsA = 256;
-constexpr int kAdjBlocks = 1216;
+constexpr int kAdjBlocksPerSM = 2;   // k_adj_local: 128 registers x 256 threads
 
+// A cell and its wrapped neighbour offsets.  Cell indices fit 32 bits (a
+// lattice of 2^32 cells would need 650 GB of populations); element offsets
+// into the 2 x 19 arrays are formed in 64 bits.
 struct Nb {
-    long long cell;
-    long long xo[3], yo[3], zo[3];
+    unsigned cell;
+    unsigned xo[3], yo[3], zo[3];
     bool zlo, zhi;   // z - 1 (resp. z + 1) is a wall site
 };
 
 template <class R>
-__device__ __forceinline__ void nb_of(const Phys<R> &p, long long cell, Nb &n)
+__device__ __forceinline__ void nb_of(const Phys<R> &p, unsigned cell, Nb &n)
 {
-    const long long plane = (long long)p.nx * p.ny;
-    const int z = (int)(cell / plane);
-    const long long rem = cell - (long long)z * plane;
-    const int y = (int)(rem / p.nx);
-    const int x = (int)(rem - (long long)y * p.nx);
+    const unsigned nx = (unsigned)p.nx, ny = (unsigned)p.ny, nz = (unsigned)p.nz;
+    const unsigned plane = nx * ny;
+    const unsigned z = cell / plane;
+    const unsigned rem = cell - z * plane;
+    const unsigned y = rem / nx;
+    const unsigned x = rem - y * nx;
     n.cell = cell;
-    n.xo[0] = x == 0 ? p.nx - 1 : x - 1;
+    n.xo[0] = x == 0 ? nx - 1 : x - 1;
     n.xo[1] = x;
-    n.xo[2] = x == p.nx - 1 ? 0 : x + 1;
-    n.yo[0] = (long long)(y == 0 ? p.ny - 1 : y - 1) * p.nx;
-    n.yo[1] = (long long)y * p.nx;
-    n.yo[2] = (long long)(y == p.ny - 1 ? 0 : y + 1) * p.nx;
-    n.zo[0] = (long long)(z == 0 ? p.nz - 1 : z - 1) * plane;
-    n.zo[1] = (long long)z * plane;
-    n.zo[2] = (long long)(z == p.nz - 1 ? 0 : z + 1) * plane;
+    n.xo[2] = x == nx - 1 ? 0 : x + 1;
+    n.yo[0] = (y == 0 ? ny - 1 : y - 1) * nx;
+    n.yo[1] = y * nx;
+    n.yo[2] = (y == ny - 1 ? 0 : y + 1) * nx;
+    n.zo[0] = (z == 0 ? nz - 1 : z - 1) * plane;
+    n.zo[1] = z * plane;
+    n.zo[2] = (z == nz - 1 ? 0 : z + 1) * plane;
     n.zlo = p.wall_z && z == 0;
-    n.zhi = p.wall_z && z == p.nz - 1;
+    n.zhi = p.wall_z && z == nz - 1;
 }
 
-__device__ __forceinline__ long long at(const Nb &n, int dx, int dy, int dz)
+__device__ __forceinline__ unsigned at(const Nb &n, int dx, int dy, int dz)
 {
     return n.zo[1 + dz] + n.yo[1 + dy] + n.xo[1 + dx];
 }
@@ -68,278 +75,272 @@ __device__ __forceinline__ R gradP_alpha(R cv, R vsq) { return R(3) + R(9) * cv 
 template <class R>
 __device__ __forceinline__ R P_of(R cv, R vsq) { return R(1) + R(3) * cv + R(4.5) * cv * cv - R(1.5) * vsq + R(4.5) * cv * cv * cv - R(4.5) * cv * vsq; }
 
-// One cell of the local reverse pass.
+// Local reverse pass of one component a at one cell, run by a pair of lanes
+// (lane l: component 0, lane l ^ 16: component 1, same cell).  The two
+// components are coupled only through the mixture momentum and density, whose
+// sums and sensitivities the pair exchanges by shuffles; each lane holds its
+// component's 19 populations and 19 incoming sensitivities
+//   mu_i(y) = lambda^{n+1}_i(y + c_i) = lambda_loc^{n+1}_i(y + c_i) + D^{n+1}_a(y + c_i)
+// (or lambda^{n+1}_opp(i)(y) at a wall), and writes lambda_loc^n_i(y) of its
+// component and a^n_b(y) of the other component b = 1 - a.
 template <int S, bool REG>
-__device__ void adj_cell(const typename Store<S>::T *__restrict__ f, const typename Store<S>::R *__restrict__ rho,
-                         const typename Store<S>::R *__restrict__ lam_next, typename Store<S>::R *__restrict__ lam_loc,
-                         typename Store<S>::R *__restrict__ aout, const Phys<typename Store<S>::R> &p, const Nb &n,
-                         double (&par)[4])
+__device__ __forceinline__ void adj_half(const typename Store<S>::T *__restrict__ f,
+                                         const typename Store<S>::R *__restrict__ rho,
+                                         const typename Store<S>::R *__restrict__ lam_next,
+                                         const typename Store<S>::R *__restrict__ Dn,
+                                         typename Store<S>::R *__restrict__ lam_loc, typename Store<S>::R *__restrict__ aout,
+                                         const Phys<typename Store<S>::R> &p, const Nb &n, int a, bool store,
+                                         double &par_g, double &par_t)
 {
     using R = typename Store<S>::R;
     const long long N = p.N;
+    const unsigned full = 0xffffffffu;
     // ---- forward recomputation ------------------------------------------
-    R fa[2][Q];
+    R fa[Q];
 #pragma unroll
-    for (int a = 0; a < 2; ++a)
-#pragma unroll
-        for (int i = 0; i < Q; ++i) {
-            const bool wall = (cz(i) == 1 && n.zlo) || (cz(i) == -1 && n.zhi);
-            const long long idx = wall ? (long long)(a * Q + opp(i)) * N + n.cell
-                                       : (long long)(a * Q + i) * N + at(n, -cx(i), -cy(i), -cz(i));
-            fa[a][i] = Store<S>::load(f + idx, w<R>(i) * p.rho0);
-        }
-    R r[2], jx = 0, jy = 0, jz = 0;
-#pragma unroll
-    for (int a = 0; a < 2; ++a) {
-        R s = 0;
-#pragma unroll
-        for (int i = 0; i < Q; ++i) {
-            s += fa[a][i];
-            if (cx(i) == 1) jx += fa[a][i]; else if (cx(i) == -1) jx -= fa[a][i];
-            if (cy(i) == 1) jy += fa[a][i]; else if (cy(i) == -1) jy -= fa[a][i];
-            if (cz(i) == 1) jz += fa[a][i]; else if (cz(i) == -1) jz -= fa[a][i];
-        }
-        r[a] = s;
+    for (int i = 0; i < Q; ++i) {
+        const bool wall = (cz(i) == 1 && n.zlo) || (cz(i) == -1 && n.zhi);
+        const long long idx = wall ? (long long)(a * Q + opp(i)) * N + n.cell
+                                   : (long long)(a * Q + i) * N + at(n, -cx(i), -cy(i), -cz(i));
+        fa[i] = Store<S>::load(f + idx, w<R>(i) * p.rho0);
     }
-    const R rt = r[0] + r[1];
-    const R u[3] = {jx / rt, jy / rt, jz / rt};
-    R Sb[2][3];
+    R ra = 0, jx = 0, jy = 0, jz = 0;
 #pragma unroll
-    for (int b = 0; b < 2; ++b) {
-        R s3[3] = {0, 0, 0};
-        const R *rb = rho + (long long)b * N;
+    for (int i = 0; i < Q; ++i) {
+        ra += fa[i];
+        if (cx(i) == 1) jx += fa[i]; else if (cx(i) == -1) jx -= fa[i];
+        if (cy(i) == 1) jy += fa[i]; else if (cy(i) == -1) jy -= fa[i];
+        if (cz(i) == 1) jz += fa[i]; else if (cz(i) == -1) jz -= fa[i];
+    }
+    // mixture density and momentum: both lanes of the pair form the same sums
+    const R rt = ra + __shfl_xor_sync(full, ra, 16);
+    const R u0 = (jx + __shfl_xor_sync(full, jx, 16)) / rt;
+    const R u1 = (jy + __shfl_xor_sync(full, jy, 16)) / rt;
+    const R u2 = (jz + __shfl_xor_sync(full, jz, 16)) / rt;
+    const R usq = u0 * u0 + u1 * u1 + u2 * u2;
+    // S^b of the other component b (Eq. 7; wall sites carry Eq. 13's rho')
+    const int b = 1 - a;
+    R Sb0 = 0, Sb1 = 0, Sb2 = 0;
+    {
+        const R *rbp = rho + (long long)b * N;
 #pragma unroll
         for (int i = 1; i < Q; ++i) {
             const bool wall = (cz(i) == -1 && n.zlo) || (cz(i) == 1 && n.zhi);
             R rv;
             if (wall) {
                 rv = p.rho_s[b];
-                if (p.wall_mirror) rv += rb[at(n, cx(i), cy(i), 0)];
+                if (p.wall_mirror) rv += rbp[at(n, cx(i), cy(i), 0)];
             } else {
-                rv = rb[at(n, cx(i), cy(i), cz(i))];
+                rv = rbp[at(n, cx(i), cy(i), cz(i))];
             }
             const R wr = w<R>(i) * rv;
-            s3[0] += cx(i) * wr; s3[1] += cy(i) * wr; s3[2] += cz(i) * wr;
+            if (cx(i) == 1) Sb0 += wr; else if (cx(i) == -1) Sb0 -= wr;
+            if (cy(i) == 1) Sb1 += wr; else if (cy(i) == -1) Sb1 -= wr;
+            if (cz(i) == 1) Sb2 += wr; else if (cz(i) == -1) Sb2 -= wr;
         }
-        Sb[b][0] = s3[0]; Sb[b][1] = s3[1]; Sb[b][2] = s3[2];
     }
-    const R Gab[2] = {p.G12, p.G21};
-    R v[2][3];
+    const R Ga = a == 0 ? p.G12 : p.G21;
+    const R v0 = u0 + Ga * Sb0 + p.gext[0], v1 = u1 + Ga * Sb1 + p.gext[1], v2 = u2 + Ga * Sb2 + p.gext[2];
+    const R vsq = v0 * v0 + v1 * v1 + v2 * v2;
+    const R omega = a == 0 ? p.omega[0] : p.omega[1];
+    const R keep = R(1) - omega;
+    const R rq = ra / R(36);
+    // regularized: Pi = sum c c f - rho (T0 I + u u), as xx, yy, zz, xy, xz, yz
+    R Pi[6] = {0, 0, 0, 0, 0, 0}, tr = 0;
+    if (REG) {
+        const R T0 = R(1) / R(3);
 #pragma unroll
-    for (int a = 0; a < 2; ++a)
-#pragma unroll
-        for (int d = 0; d < 3; ++d) v[a][d] = u[d] + Gab[a] * Sb[1 - a][d] + p.gext[d];
-    const R usq = u[0] * u[0] + u[1] * u[1] + u[2] * u[2];
-
-    // ---- mu = lambda^{n+1} gathered along +c_i -----------------------------
-    R mu[2][Q];
-#pragma unroll
-    for (int a = 0; a < 2; ++a)
-#pragma unroll
-        for (int i = 0; i < Q; ++i) {
-            const bool wall = (cz(i) == -1 && n.zlo) || (cz(i) == 1 && n.zhi);
-            const long long idx = wall ? (long long)(a * Q + opp(i)) * N + n.cell
-                                       : (long long)(a * Q + i) * N + at(n, cx(i), cy(i), cz(i));
-            mu[a][i] = lam_next[idx];
+        for (int i = 1; i < Q; ++i) {
+            if (cx(i)) Pi[0] += fa[i];
+            if (cy(i)) Pi[1] += fa[i];
+            if (cz(i)) Pi[2] += fa[i];
+            if (cx(i) && cy(i)) Pi[3] += R(cx(i) * cy(i)) * fa[i];
+            if (cx(i) && cz(i)) Pi[4] += R(cx(i) * cz(i)) * fa[i];
+            if (cy(i) && cz(i)) Pi[5] += R(cy(i) * cz(i)) * fa[i];
         }
-
+        Pi[0] -= ra * (T0 + u0 * u0);
+        Pi[1] -= ra * (T0 + u1 * u1);
+        Pi[2] -= ra * (T0 + u2 * u2);
+        Pi[3] -= ra * u0 * u1;
+        Pi[4] -= ra * u0 * u2;
+        Pi[5] -= ra * u1 * u2;
+        tr = Pi[0] + Pi[1] + Pi[2];
+    }
+    // ---- incoming sensitivities ---------------------------------------------
+    R mu[Q];
+#pragma unroll
+    for (int i = 0; i < Q; ++i) {
+        const bool wall = (cz(i) == -1 && n.zlo) || (cz(i) == 1 && n.zhi);
+        const unsigned cell = wall ? n.cell : at(n, cx(i), cy(i), cz(i));
+        const int d = wall ? opp(i) : i;
+        mu[i] = lam_next[(long long)(a * Q + d) * N + cell] + Dn[(long long)a * N + cell];
+    }
     // ---- reverse pass -------------------------------------------------------
-    R lam[2][Q];
-    R ubar[3] = {0, 0, 0};
-    R rbar[2] = {0, 0};
+    // BGK:         f* = E(rho, v) + keep (f - E(rho, u))
+    // regularized: f* = E(rho, v) + keep (k_i / 8) (c c : Pi - tr(Pi) / 3)
+    // with E_i(rho, x) = (rho / 36) k_i P(c_i . x, x . x)
+    R Kbar = 0, rbar = 0;
+    R vbx = 0, vby = 0, vbz = 0, vbv = 0, ubx = 0, uby = 0, ubz = 0, ubv = 0;
+    R pb[6] = {0, 0, 0, 0, 0, 0};
 #pragma unroll
-    for (int a = 0; a < 2; ++a) {
-        const R omega = p.omega[a];
-        const R keep = R(1) - omega;
-        const R ra = r[a];
-        const R rq = ra / R(36);
-        const R vsq = v[a][0] * v[a][0] + v[a][1] * v[a][1] + v[a][2] * v[a][2];
-        R Kbar = 0;            // dL/dkeep
-        R vb_c[3] = {0, 0, 0}; // sum_i mu_i k_i alpha_i(v) c_i
-        R vb_v = 0;            // sum_i mu_i k_i beta_i(v)
-        R ub_c[3] = {0, 0, 0}; // same at u (BGK only)
-        R ub_v = 0;
-        R rb = 0;
-        // regularized: Pi and its adjoint
-        R Pi[3][3] = {{0, 0, 0}, {0, 0, 0}, {0, 0, 0}};
-        R tr = 0;
-        if (REG) {
-#pragma unroll
-            for (int i = 0; i < Q; ++i) {
-                const int c[3] = {cx(i), cy(i), cz(i)};
-#pragma unroll
-                for (int x = 0; x < 3; ++x)
-#pragma unroll
-                    for (int y = 0; y < 3; ++y) Pi[x][y] += R(c[x] * c[y]) * fa[a][i];
-            }
-            const R T0 = R(1) / R(3);
-#pragma unroll
-            for (int x = 0; x < 3; ++x)
-#pragma unroll
-                for (int y = 0; y < 3; ++y) Pi[x][y] -= ra * ((x == y ? T0 : R(0)) + u[x] * u[y]);
-            tr = Pi[0][0] + Pi[1][1] + Pi[2][2];
+    for (int i = 0; i < Q; ++i) {
+        const R m = mu[i];
+        const R ki = R(k36(i));
+        const R mk = m * ki;
+        const R cv = cdot<R>(i, v0, v1, v2);
+        rbar += mk * P_of(cv, vsq);
+        const R al = gradP_alpha(cv, vsq) * mk;
+        if (cx(i) == 1) vbx += al; else if (cx(i) == -1) vbx -= al;
+        if (cy(i) == 1) vby += al; else if (cy(i) == -1) vby -= al;
+        if (cz(i) == 1) vbz += al; else if (cz(i) == -1) vbz -= al;
+        vbv += mk * (R(3) + R(9) * cv);
+        if (!REG) {
+            const R cu = cdot<R>(i, u0, u1, u2);
+            const R Pu = P_of(cu, usq);
+            Kbar += m * (fa[i] - rq * ki * Pu);
+            rbar -= keep * mk * Pu;
+            const R alu = gradP_alpha(cu, usq) * mk;
+            if (cx(i) == 1) ubx += alu; else if (cx(i) == -1) ubx -= alu;
+            if (cy(i) == 1) uby += alu; else if (cy(i) == -1) uby -= alu;
+            if (cz(i) == 1) ubz += alu; else if (cz(i) == -1) ubz -= alu;
+            ubv += mk * (R(3) + R(9) * cu);
+        } else {
+            const int c0 = cx(i), c1 = cy(i), c2 = cz(i);
+            const R ccP = R(c0 * c0) * Pi[0] + R(c1 * c1) * Pi[1] + R(c2 * c2) * Pi[2] + R(2 * c0 * c1) * Pi[3] +
+                          R(2 * c0 * c2) * Pi[4] + R(2 * c1 * c2) * Pi[5];
+            Kbar += mk * R(0.125) * (ccP - tr / R(3));
+            const R nb = keep * mk * R(0.125);
+            pb[0] += nb * (R(c0 * c0) - R(1) / R(3));
+            pb[1] += nb * (R(c1 * c1) - R(1) / R(3));
+            pb[2] += nb * (R(c2 * c2) - R(1) / R(3));
+            if (c0 && c1) pb[3] += nb * R(c0 * c1);
+            if (c0 && c2) pb[4] += nb * R(c0 * c2);
+            if (c1 && c2) pb[5] += nb * R(c1 * c2);
         }
-        R Pbar[3][3] = {{0, 0, 0}, {0, 0, 0}, {0, 0, 0}};
+    }
+    rbar /= R(36);
+    // dL/dv^a
+    const R vbar0 = rq * (vbx - v0 * vbv), vbar1 = rq * (vby - v1 * vbv), vbar2 = rq * (vbz - v2 * vbv);
+    R ub0 = vbar0, ub1 = vbar1, ub2 = vbar2;
+    if (!REG) {
+        ub0 -= keep * rq * (ubx - u0 * ubv);
+        ub1 -= keep * rq * (uby - u1 * ubv);
+        ub2 -= keep * rq * (ubz - u2 * ubv);
+    } else {
+        // pb holds dL/dPi for xx, yy, zz and one of each symmetric off-diagonal pair
+        const R T0 = R(1) / R(3);
+        rbar -= pb[0] * (T0 + u0 * u0) + pb[1] * (T0 + u1 * u1) + pb[2] * (T0 + u2 * u2) +
+                R(2) * (pb[3] * u0 * u1 + pb[4] * u0 * u2 + pb[5] * u1 * u2);
+        ub0 -= R(2) * ra * (pb[0] * u0 + pb[3] * u1 + pb[4] * u2);
+        ub1 -= R(2) * ra * (pb[3] * u0 + pb[1] * u1 + pb[5] * u2);
+        ub2 -= R(2) * ra * (pb[4] * u0 + pb[5] * u1 + pb[2] * u2);
+    }
+    // u = j / rho over both components: dL/dj = ubar / rho, dL/drho += -(ubar . u) / rho
+    const R U0 = ub0 + __shfl_xor_sync(full, ub0, 16);
+    const R U1 = ub1 + __shfl_xor_sync(full, ub1, 16);
+    const R U2 = ub2 + __shfl_xor_sync(full, ub2, 16);
+    const R jb0 = U0 / rt, jb1 = U1 / rt, jb2 = U2 / rt;
+    const R base = rbar - (U0 * u0 + U1 * u1 + U2 * u2) / rt;
+    if (store) {
+        R *lo = lam_loc + (long long)a * Q * N + n.cell;
 #pragma unroll
         for (int i = 0; i < Q; ++i) {
-            const int c[3] = {cx(i), cy(i), cz(i)};
-            const R ki = R(k36(i));
-            const R m = mu[a][i];
-            const R cv = R(c[0]) * v[a][0] + R(c[1]) * v[a][1] + R(c[2]) * v[a][2];
-            // E_i(rho, v) = rq k_i P_i(v)
-            rb += m * (ki / R(36)) * P_of(cv, vsq);
-            const R mk = m * ki;
-            const R al = gradP_alpha(cv, vsq), be = R(3) + R(9) * cv;
-#pragma unroll
-            for (int d = 0; d < 3; ++d) vb_c[d] += mk * al * R(c[d]);
-            vb_v += mk * be;
+            R l = base + cdot<R>(i, jb0, jb1, jb2);
             if (!REG) {
-                const R cu = R(c[0]) * u[0] + R(c[1]) * u[1] + R(c[2]) * u[2];
-                const R Eu = rq * ki * P_of(cu, usq);
-                // f* = E(rho, v) + keep (f - E(rho, u))
-                lam[a][i] = keep * m;
-                Kbar += m * (fa[a][i] - Eu);
-                rb -= keep * m * (ki / R(36)) * P_of(cu, usq);
-                const R alu = gradP_alpha(cu, usq), beu = R(3) + R(9) * cu;
-#pragma unroll
-                for (int d = 0; d < 3; ++d) ub_c[d] += mk * alu * R(c[d]);
-                ub_v += mk * beu;
+                l += keep * mu[i];
             } else {
-                // f* = E(rho, v) + keep (k_i/8) (c c : Pi - tr Pi / 3)
-                R ccP = 0;
-#pragma unroll
-                for (int x = 0; x < 3; ++x)
-#pragma unroll
-                    for (int y = 0; y < 3; ++y) ccP += R(c[x] * c[y]) * Pi[x][y];
-                const R Ni = ki * R(0.125) * (ccP - tr / R(3));
-                Kbar += m * Ni;
-                const R nb = keep * m * ki * R(0.125);
-#pragma unroll
-                for (int x = 0; x < 3; ++x)
-#pragma unroll
-                    for (int y = 0; y < 3; ++y) Pbar[x][y] += nb * (R(c[x] * c[y]) - (x == y ? R(1) / R(3) : R(0)));
-                lam[a][i] = 0;
+                const int c0 = cx(i), c1 = cy(i), c2 = cz(i);
+                l += R(c0 * c0) * pb[0] + R(c1 * c1) * pb[1] + R(c2 * c2) * pb[2] + R(2 * c0 * c1) * pb[3] +
+                     R(2 * c0 * c2) * pb[4] + R(2 * c1 * c2) * pb[5];
             }
+            lo[(long long)i * N] = l;
         }
-        // dL/dv^a, dL/du (through E(rho, u) for BGK), dL/drho^a
-        R vbar[3];
-#pragma unroll
-        for (int d = 0; d < 3; ++d) vbar[d] = rq * (vb_c[d] - v[a][d] * vb_v);
-        if (!REG) {
-#pragma unroll
-            for (int d = 0; d < 3; ++d) ubar[d] += -keep * rq * (ub_c[d] - u[d] * ub_v);
-        } else {
-            // Pi = sum c c f - rho (T0 I + u u)
-            const R T0 = R(1) / R(3);
-#pragma unroll
-            for (int i = 0; i < Q; ++i) {
-                const int c[3] = {cx(i), cy(i), cz(i)};
-                R s = 0;
-#pragma unroll
-                for (int x = 0; x < 3; ++x)
-#pragma unroll
-                    for (int y = 0; y < 3; ++y) s += Pbar[x][y] * R(c[x] * c[y]);
-                lam[a][i] += s;
-            }
-#pragma unroll
-            for (int x = 0; x < 3; ++x)
-#pragma unroll
-                for (int y = 0; y < 3; ++y) {
-                    rb -= Pbar[x][y] * ((x == y ? T0 : R(0)) + u[x] * u[y]);
-                    ubar[x] -= ra * Pbar[x][y] * u[y];
-                    ubar[y] -= ra * Pbar[x][y] * u[x];
-                }
-        }
-#pragma unroll
-        for (int d = 0; d < 3; ++d) ubar[d] += vbar[d];
-        rbar[a] = rb;
         // g^a = G^{ab} S^b + g_ext:  dL/dS^b = G^{ab} vbar,  dL/dG^{ab} = vbar . S^b
-        const int b = 1 - a;
-#pragma unroll
-        for (int d = 0; d < 3; ++d) aout[((long long)b * 3 + d) * N + n.cell] = Gab[a] * vbar[d];
-        par[a] += (double)(vbar[0] * Sb[b][0] + vbar[1] * Sb[b][1] + vbar[2] * Sb[b][2]);
+        aout[((long long)b * 3 + 0) * N + n.cell] = Ga * vbar0;
+        aout[((long long)b * 3 + 1) * N + n.cell] = Ga * vbar1;
+        aout[((long long)b * 3 + 2) * N + n.cell] = Ga * vbar2;
+        par_g += (double)(vbar0 * Sb0 + vbar1 * Sb1 + vbar2 * Sb2);
         // keep = 1 - 1/tau: dkeep/dtau = 1/tau^2
-        par[2 + a] += (double)(Kbar * omega * omega);
+        par_t += (double)(Kbar * omega * omega);
     }
-    // u = j / rho: dL/dj = ubar / rho, dL/drho += -(ubar . u) / rho
-    const R jb[3] = {ubar[0] / rt, ubar[1] / rt, ubar[2] / rt};
-    const R rtb = -(ubar[0] * u[0] + ubar[1] * u[1] + ubar[2] * u[2]) / rt;
-#pragma unroll
-    for (int a = 0; a < 2; ++a)
-#pragma unroll
-        for (int i = 0; i < Q; ++i)
-            lam_loc[(long long)(a * Q + i) * N + n.cell] =
-                lam[a][i] + rbar[a] + rtb + R(cx(i)) * jb[0] + R(cy(i)) * jb[1] + R(cz(i)) * jb[2];
 }
 
+// Grid-stride over groups of 16 cells per warp; lanes 0-15 take component 0
+// and lanes 16-31 component 1 of the same 16 cells.  Per-block FP64 partials
+// of dL/dG^{12}, dL/dG^{21}, dL/dtau_1, dL/dtau_2 accumulate over the steps.
 template <int S, bool REG>
-__global__ void __launch_bounds__(kThreadsA)
+__global__ void __launch_bounds__(kThreadsA, 2)
 k_adj_local(const typename Store<S>::T *__restrict__ f, const typename Store<S>::R *__restrict__ rho,
-            const typename Store<S>::R *__restrict__ lam_next, typename Store<S>::R *__restrict__ lam_loc,
-            typename Store<S>::R *__restrict__ aout, double *__restrict__ partials, Phys<typename Store<S>::R> p)
+            const typename Store<S>::R *__restrict__ lam_next, const typename Store<S>::R *__restrict__ Dn,
+            typename Store<S>::R *__restrict__ lam_loc, typename Store<S>::R *__restrict__ aout,
+            double *__restrict__ partials, Phys<typename Store<S>::R> p)
 {
-    double par[4] = {0, 0, 0, 0};
-    for (long long c = (long long)blockIdx.x * kThreadsA + threadIdx.x; c < p.N;
-         c += (long long)gridDim.x * kThreadsA) {
+    const int lane = threadIdx.x & 31;
+    const int a = lane >> 4;
+    const long long warps = (long long)gridDim.x * (kThreadsA / 32);
+    const long long groups = (p.N + 15) / 16;
+    double pg = 0, pt = 0;
+    for (long long wg = (long long)blockIdx.x * (kThreadsA / 32) + (threadIdx.x >> 5); wg < groups; wg += warps) {
+        const long long c = wg * 16 + (lane & 15);
+        const bool valid = c < p.N;
         Nb n;
-        nb_of(p, c, n);
-        adj_cell<S, REG>(f, rho, lam_next, lam_loc, aout, p, n, par);
+        nb_of(p, (unsigned)(valid ? c : p.N - 1), n);
+        adj_half<S, REG>(f, rho, lam_next, Dn, lam_loc, aout, p, n, a, valid, pg, pt);
     }
+    // lanes of component a hold parts of par[a] and par[2 + a]
     __shared__ double sh[4][kThreadsA];
-    for (int k = 0; k < 4; ++k) sh[k][threadIdx.x] = par[k];
+    const int t = threadIdx.x;
+    for (int k = 0; k < 4; ++k) sh[k][t] = 0;
+    sh[a][t] = pg;
+    sh[2 + a][t] = pt;
     __syncthreads();
     for (int s = kThreadsA / 2; s > 0; s >>= 1) {
-        if (threadIdx.x < s)
-            for (int k = 0; k < 4; ++k) sh[k][threadIdx.x] += sh[k][threadIdx.x + s];
+        if (t < s)
+            for (int k = 0; k < 4; ++k) sh[k][t] += sh[k][t + s];
         __syncthreads();
     }
-    if (threadIdx.x < 4) partials[(long long)blockIdx.x * 4 + threadIdx.x] += sh[threadIdx.x][0];
+    if (t < 4) partials[(long long)blockIdx.x * 4 + t] += sh[t][0];
 }
 
-// lambda^n = lambda_loc + D^b(x), D^b(x) = sum_k w_k c_k . a^b(x - c_k), plus
-// the mirror-wall terms: a wall site x' + c_k seen from x' presents the
-// density of its mirror cell x' + (c_kx, c_ky, 0).
+// c_k . a(src), loading only the components along which c_k is non-zero.
+template <class R>
+__device__ __forceinline__ R cdot_a(int k, const R *__restrict__ ab, long long N, unsigned src)
+{
+    R s = 0;
+    if (cx(k)) s += R(cx(k)) * ab[src];
+    if (cy(k)) s += R(cy(k)) * ab[N + src];
+    if (cz(k)) s += R(cz(k)) * ab[2 * N + src];
+    return s;
+}
+
+// D_b(x) = dL/drho^b(x) = sum_k w_k c_k . a_b(x - c_k), plus the mirror-wall
+// terms: a wall site y + c_k seen from y presents the density of its mirror
+// cell y + (c_kx, c_ky, 0).
 template <class R>
 __global__ void __launch_bounds__(kThreadsA)
-k_adj_finish(const R *__restrict__ lam_loc, const R *__restrict__ a, R *__restrict__ lam, Phys<R> p)
+k_adj_D(const R *__restrict__ a, R *__restrict__ D, Phys<R> p)
 {
     const long long c = (long long)blockIdx.x * kThreadsA + threadIdx.x;
     if (c >= p.N) return;
     Nb n;
-    nb_of(p, c, n);
+    nb_of(p, (unsigned)c, n);
     const long long N = p.N;
-    R D[2];
 #pragma unroll
     for (int b = 0; b < 2; ++b) {
         R s = 0;
         const R *ab = a + (long long)b * 3 * N;
 #pragma unroll
         for (int k = 1; k < Q; ++k) {
-            // regular term: x - c_k is a fluid cell whose neighbour x + 0 is this cell
+            // regular term: x - c_k is a fluid cell whose neighbour x is this cell
             const bool src_wall = (cz(k) == 1 && n.zlo) || (cz(k) == -1 && n.zhi);
-            if (!src_wall) {
-                const long long src = at(n, -cx(k), -cy(k), -cz(k));
-                s += w<R>(k) * (R(cx(k)) * ab[src] + R(cy(k)) * ab[N + src] + R(cz(k)) * ab[2 * N + src]);
-            }
-            // mirror term: the cell y = x - (c_kx, c_ky, 0) of this plane sees the
-            // wall site y + c_k, whose density is this cell's
+            if (!src_wall) s += w<R>(k) * cdot_a(k, ab, N, at(n, -cx(k), -cy(k), -cz(k)));
             if (p.wall_mirror) {
                 const bool mirror = (cz(k) == -1 && n.zlo) || (cz(k) == 1 && n.zhi);
-                if (mirror) {
-                    const long long src = at(n, -cx(k), -cy(k), 0);
-                    s += w<R>(k) * (R(cx(k)) * ab[src] + R(cy(k)) * ab[N + src] + R(cz(k)) * ab[2 * N + src]);
-                }
+                if (mirror) s += w<R>(k) * cdot_a(k, ab, N, at(n, -cx(k), -cy(k), 0));
             }
         }
-        D[b] = s;
+        D[(long long)b * N + c] = s;
     }
-#pragma unroll
-    for (int b = 0; b < 2; ++b)
-#pragma unroll
-        for (int i = 0; i < Q; ++i) {
-            const long long idx = (long long)(b * Q + i) * N + c;
-            lam[idx] = lam_loc[idx] + D[b];
-        }
 }
 
 template <class R, class G>
@@ -357,9 +358,11 @@ k_adj_seed(const G *__restrict__ g1, const G *__restrict__ g2, R *__restrict__ l
     }
 }
 
+// dL/drho^a_0 = sum_i w_i lambda^0_i = sum_i w_i lambda_loc^0_i + D^0_a (sum_i w_i = 1).
 template <class R>
 __global__ void __launch_bounds__(kThreadsA)
-k_adj_rho0(const R *__restrict__ lam, double *__restrict__ g1, double *__restrict__ g2, long long N)
+k_adj_rho0(const R *__restrict__ lam, const R *__restrict__ D, double *__restrict__ g1, double *__restrict__ g2,
+           long long N)
 {
     const long long c = (long long)blockIdx.x * kThreadsA + threadIdx.x;
     if (c >= N) return;
@@ -369,8 +372,8 @@ k_adj_rho0(const R *__restrict__ lam, double *__restrict__ g1, double *__restric
         s1 += wd(i) * (double)lam[(long long)i * N + c];
         s2 += wd(i) * (double)lam[(long long)(Q + i) * N + c];
     }
-    if (g1) g1[c] = s1;
-    if (g2) g2[c] = s2;
+    if (g1) g1[c] = s1 + (double)D[c];
+    if (g2) g2[c] = s2 + (double)D[N + c];
 }
 
 template <class R>
@@ -392,34 +395,46 @@ Phys<R> make_phys_a(const HostPhys &h)
 inline unsigned gridA(long long N) { return (unsigned)((N + kThreadsA - 1) / kThreadsA); }
 
 template <int S>
-cudaError_t adj_step_t(const HostPhys &h, const void *f, const void *rho, const void *lam_next, void *lam_loc,
-                       void *a, void *lam_out, double *partials, cudaStream_t s)
+cudaError_t adj_step_t(const HostPhys &h, const void *f, const void *rho, const void *lam_next, const void *Dn,
+                       void *lam_loc, void *a, void *Dout, double *partials, cudaStream_t s)
 {
     using T = typename Store<S>::T;
     using R = typename Store<S>::R;
     const Phys<R> p = make_phys_a<R>(h);
     if (h.collision == LBM_REGULARIZED)
-        k_adj_local<S, true><<<kAdjBlocks, kThreadsA, 0, s>>>((const T *)f, (const R *)rho, (const R *)lam_next,
-                                                              (R *)lam_loc, (R *)a, partials, p);
+        k_adj_local<S, true><<<adjoint_blocks(), kThreadsA, 0, s>>>((const T *)f, (const R *)rho, (const R *)lam_next,
+                                                              (const R *)Dn, (R *)lam_loc, (R *)a, partials, p);
     else
-        k_adj_local<S, false><<<kAdjBlocks, kThreadsA, 0, s>>>((const T *)f, (const R *)rho, (const R *)lam_next,
-                                                               (R *)lam_loc, (R *)a, partials, p);
-    k_adj_finish<R><<<gridA(h.N), kThreadsA, 0, s>>>((const R *)lam_loc, (const R *)a, (R *)lam_out, p);
+        k_adj_local<S, false><<<adjoint_blocks(), kThreadsA, 0, s>>>((const T *)f, (const R *)rho, (const R *)lam_next,
+                                                               (const R *)Dn, (R *)lam_loc, (R *)a, partials, p);
+    k_adj_D<R><<<gridA(h.N), kThreadsA, 0, s>>>((const R *)a, (R *)Dout, p);
     return cudaGetLastError();
 }
 
 }  // namespace
 
-int adjoint_blocks() { return kAdjBlocks; }
+// One resident wave of k_adj_local: kAdjBlocksPerSM CTAs on every SM.
+int adjoint_blocks()
+{
+    static int blocks = 0;
+    if (!blocks) {
+        int dev = 0, sms = 0;
+        if (cudaGetDevice(&dev) != cudaSuccess ||
+            cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || sms <= 0)
+            sms = 152;
+        blocks = kAdjBlocksPerSM * sms;
+    }
+    return blocks;
+}
 
 cudaError_t launch_adjoint_step(const HostPhys &p, const void *f, const void *rho, const void *lam_next,
-                                void *lam_loc, void *a, void *lam_out, double *partials, cudaStream_t s)
+                                const void *Dn, void *lam_loc, void *a, void *Dout, double *partials, cudaStream_t s)
 {
     switch (p.storage) {
-    case ST_F64: return adj_step_t<ST_F64>(p, f, rho, lam_next, lam_loc, a, lam_out, partials, s);
-    case ST_F32: return adj_step_t<ST_F32>(p, f, rho, lam_next, lam_loc, a, lam_out, partials, s);
-    case ST_F16_DEV: return adj_step_t<ST_F16_DEV>(p, f, rho, lam_next, lam_loc, a, lam_out, partials, s);
-    case ST_BF16_DEV: return adj_step_t<ST_BF16_DEV>(p, f, rho, lam_next, lam_loc, a, lam_out, partials, s);
+    case ST_F64: return adj_step_t<ST_F64>(p, f, rho, lam_next, Dn, lam_loc, a, Dout, partials, s);
+    case ST_F32: return adj_step_t<ST_F32>(p, f, rho, lam_next, Dn, lam_loc, a, Dout, partials, s);
+    case ST_F16_DEV: return adj_step_t<ST_F16_DEV>(p, f, rho, lam_next, Dn, lam_loc, a, Dout, partials, s);
+    case ST_BF16_DEV: return adj_step_t<ST_BF16_DEV>(p, f, rho, lam_next, Dn, lam_loc, a, Dout, partials, s);
     default: return cudaErrorInvalidValue;
     }
 }
@@ -437,12 +452,13 @@ cudaError_t launch_adjoint_seed(const HostPhys &p, const void *g1, const void *g
     return cudaGetLastError();
 }
 
-cudaError_t launch_adjoint_rho0(const HostPhys &p, const void *lam, double *g1, double *g2, cudaStream_t s)
+cudaError_t launch_adjoint_rho0(const HostPhys &p, const void *lam, const void *D, double *g1, double *g2,
+                                cudaStream_t s)
 {
     if (p.storage == ST_F64)
-        k_adj_rho0<double><<<gridA(p.N), kThreadsA, 0, s>>>((const double *)lam, g1, g2, p.N);
+        k_adj_rho0<double><<<gridA(p.N), kThreadsA, 0, s>>>((const double *)lam, (const double *)D, g1, g2, p.N);
     else
-        k_adj_rho0<float><<<gridA(p.N), kThreadsA, 0, s>>>((const float *)lam, g1, g2, p.N);
+        k_adj_rho0<float><<<gridA(p.N), kThreadsA, 0, s>>>((const float *)lam, (const float *)D, g1, g2, p.N);
     return cudaGetLastError();
 }
 

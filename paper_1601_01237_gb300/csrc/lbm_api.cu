@@ -8,6 +8,7 @@
 #include <string.h>
 
 #include <string>
+#include <utility>
 #include <vector>
 
 #include "../../include/lbm.h"
@@ -543,6 +544,7 @@ lbm_status lbm_adjoint(lbm_lattice *h, const double *dL_drho1, const double *dL_
     if ((dL_drho1_0 || dL_drho2_0) && !h->rec_at_rest)
         return fail(LBM_ENOTSUP, "lbm_adjoint: initial-density gradients need a recording that starts at rest "
                                  "right after lbm_init_fields(u = NULL)");
+    if (h->phys.N > 0xffffffffLL) return fail(LBM_ENOTSUP, "lbm_adjoint: more than 2^32 cells");
     DeviceGuard g(h->device);
     const size_t N = (size_t)h->phys.N;
     const size_t rb = lbm::real_bytes(h->phys.storage);
@@ -550,14 +552,17 @@ lbm_status lbm_adjoint(lbm_lattice *h, const double *dL_drho1, const double *dL_
     lbm_state_bytes(h, &sb);
     const long E = h->rec_every;
     const int nb = lbm::adjoint_blocks();
-    // working memory: lambda, lambda_loc, a, one segment of states, gradient staging, partials
-    void *lam = nullptr, *lam_loc = nullptr, *abuf = nullptr, *seg = nullptr, *io = nullptr;
+    // working memory: lambda_loc (two, ping-pong), a, D (two), one segment of
+    // states and of their densities, gradient staging, partials
+    void *lam = nullptr, *lam_loc = nullptr, *abuf = nullptr, *seg = nullptr, *io = nullptr, *dbuf = nullptr;
+    void *rseg = nullptr;
     double *part = nullptr;
     std::vector<double> parth((size_t)nb * 4);
     cudaError_t e;
     lbm_status st = LBM_OK;
     auto cleanup = [&]() {
-        cudaFree(lam); cudaFree(lam_loc); cudaFree(abuf); cudaFree(seg); cudaFree(io); cudaFree(part);
+        cudaFree(lam); cudaFree(lam_loc); cudaFree(abuf); cudaFree(seg); cudaFree(io); cudaFree(part); cudaFree(dbuf);
+        cudaFree(rseg);
     };
 #define CKA(expr, where)                                  \
     do {                                                  \
@@ -567,7 +572,10 @@ lbm_status lbm_adjoint(lbm_lattice *h, const double *dL_drho1, const double *dL_
     CKA(cudaMalloc(&lam, rb * 2 * lbm::Q * N), "lbm_adjoint: lambda");
     CKA(cudaMalloc(&lam_loc, rb * 2 * lbm::Q * N), "lbm_adjoint: lambda_loc");
     CKA(cudaMalloc(&abuf, rb * 6 * N), "lbm_adjoint: a");
+    CKA(cudaMalloc(&dbuf, rb * 4 * N), "lbm_adjoint: D");
+    CKA(cudaMemsetAsync(dbuf, 0, rb * 4 * N, h->stream), "lbm_adjoint: clear D");
     CKA(cudaMalloc(&seg, sb * (size_t)(E + 1)), "lbm_adjoint: segment states");
+    CKA(cudaMalloc(&rseg, rb * 2 * N * (size_t)E), "lbm_adjoint: segment densities");
     CKA(cudaMalloc((void **)&part, sizeof(double) * 4 * nb), "lbm_adjoint: partials");
     CKA(cudaMalloc(&io, sizeof(double) * 2 * N), "lbm_adjoint: staging");
     CKA(cudaMemsetAsync(part, 0, sizeof(double) * 4 * nb, h->stream), "lbm_adjoint: clear");
@@ -580,30 +588,39 @@ lbm_status lbm_adjoint(lbm_lattice *h, const double *dL_drho1, const double *dL_
         g2 = dL_drho2 ? io2 : nullptr;
     }
     CKA(lbm::launch_adjoint_seed(h->phys, g1, g2, 1, lam, h->stream), "lbm_adjoint: seed");
+    void *d_cur = dbuf, *d_nxt = (char *)dbuf + rb * 2 * N;   // D^N = 0 (cleared above)
     const bool use_fused = h->use_fused;
     for (long k = h->rec_nck - 1; k >= 0; --k) {
         const long t0 = k * E;
         const long t1 = (t0 + E < h->rec_steps) ? t0 + E : h->rec_steps;
-        // recompute the segment's forward states f^{t0} .. f^{t1-1}
+        // recompute the segment's forward states f^{t0} .. f^{t1-1} and their
+        // densities rho^{t0} .. rho^{t1-1} (the last from a density pass)
         CKA(cudaMemcpyAsync(seg, (char *)h->ckpt + sb * (size_t)k, sb, cudaMemcpyDeviceToDevice, h->stream),
             "lbm_adjoint: restore");
         for (long t = t0; t + 1 < t1; ++t) {
             const void *fi = (char *)seg + sb * (size_t)(t - t0);
             void *fo = (char *)seg + sb * (size_t)(t - t0 + 1);
-            if (use_fused) CKA(lbm::launch_step_fused(h->phys, fi, fo, h->stream), "lbm_adjoint: recompute");
-            else CKA(lbm::launch_step_split(h->phys, fi, fo, h->rho, h->stream), "lbm_adjoint: recompute");
+            void *rt = (char *)rseg + rb * 2 * N * (size_t)(t - t0);
+            if (use_fused) CKA(lbm::launch_step_fused(h->phys, fi, fo, h->stream, nullptr, rt), "lbm_adjoint: recompute");
+            else CKA(lbm::launch_step_split(h->phys, fi, fo, rt, h->stream), "lbm_adjoint: recompute");
         }
+        CKA(lbm::launch_density(h->phys, (char *)seg + sb * (size_t)(t1 - 1 - t0),
+                                (char *)rseg + rb * 2 * N * (size_t)(t1 - 1 - t0), h->stream),
+            "lbm_adjoint: density");
         for (long t = t1 - 1; t >= t0; --t) {
             const void *fn = (char *)seg + sb * (size_t)(t - t0);
-            CKA(lbm::launch_density(h->phys, fn, h->rho, h->stream), "lbm_adjoint: density");
-            CKA(lbm::launch_adjoint_step(h->phys, fn, h->rho, lam, lam_loc, abuf, lam, part, h->stream),
+            const void *rn = (char *)rseg + rb * 2 * N * (size_t)(t - t0);
+            // (lambda_loc, D) ping-pong: step t reads (lam, d_cur) and writes (lam_loc, d_nxt)
+            CKA(lbm::launch_adjoint_step(h->phys, fn, rn, lam, d_cur, lam_loc, abuf, d_nxt, part, h->stream),
                 "lbm_adjoint: step");
+            std::swap(lam, lam_loc);
+            std::swap(d_cur, d_nxt);
         }
     }
     if (dL_drho1_0 || dL_drho2_0) {
         double *o1 = on_device ? dL_drho1_0 : (dL_drho1_0 ? io1 : nullptr);
         double *o2 = on_device ? dL_drho2_0 : (dL_drho2_0 ? io2 : nullptr);
-        CKA(lbm::launch_adjoint_rho0(h->phys, lam, o1, o2, h->stream), "lbm_adjoint: rho0");
+        CKA(lbm::launch_adjoint_rho0(h->phys, lam, d_cur, o1, o2, h->stream), "lbm_adjoint: rho0");
         if (!on_device) {
             if (dL_drho1_0) CKA(cudaMemcpyAsync(dL_drho1_0, io1, sizeof(double) * N, cudaMemcpyDeviceToHost, h->stream), "lbm_adjoint: copy out");
             if (dL_drho2_0) CKA(cudaMemcpyAsync(dL_drho2_0, io2, sizeof(double) * N, cudaMemcpyDeviceToHost, h->stream), "lbm_adjoint: copy out");

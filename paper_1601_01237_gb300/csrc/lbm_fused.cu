@@ -4,22 +4,27 @@
 // streaming in one kernel, with no global scratch.
 //
 // Each CTA owns a 32 x 8 column tile of the xy plane and marches along z over
-// a chunk of 64 planes, one thread per column.  The force at plane z needs
-// rho^b at planes z-1, z, z+1 over the tile plus a one-cell halo; those
-// densities live in a ring of three shared-memory planes.  Iteration z:
+// a chunk of planes (64, or 8 for small lattices), one thread per column.
+// The force at plane z needs rho^b at planes z-1, z, z+1 over the tile plus a
+// one-cell halo; those densities live in a ring of four shared-memory planes.
+// Iteration z:
 //   A. every thread pull-gathers its column's 38 populations at plane z+1
 //      (rho into the ring, momentum into a moment buffer, populations into a
 //      shared-memory stash) and, for the halo ring of plane z+2, 12 or 13 of
 //      the 38 populations of one halo cell (84 halo cells x 3 groups), summed
 //      into fixed-order partial densities; the halo densities of plane z+1
 //      (partials gathered one iteration earlier) are completed in the ring;
-//   B. every thread collides its column at plane z from the stash and stores
-//      the post-collision populations,
-// with a barrier after each phase.  Interior and halo loads of an iteration
-// are issued together and balanced over all threads; every interior
-// population is read from HBM once and written once, and the halo re-reads
-// neighbouring tiles' populations that the neighbouring CTAs stream at about
-// the same time (L2 hits).
+//   -- one barrier --
+//   B. every thread collides its column at plane z from its stash entries and
+//      stores the post-collision populations.
+// Phase A of iteration z+1 writes only the ring slot of plane z+2, the
+// thread's own stash and moment entries and the halo partials of plane z+3,
+// none of which phase B of iteration z reads, so one barrier per plane
+// suffices and fast warps start the next plane's loads while slow warps
+// finish their collisions.  Interior and halo loads are balanced over all
+// threads; every interior population is read from HBM once and written once,
+// and the halo re-reads neighbouring tiles' populations that the
+// neighbouring CTAs stream at about the same time (L2 hits).
 #include <cuda_runtime.h>
 
 #include "d3q19.cuh"
@@ -35,13 +40,14 @@ constexpr int kThreadsF = kTX * kTY;
 constexpr int kHalo = 2 * (kTX + 2) + 2 * kTY;   // perimeter cells of the (TX+2) x (TY+2) box
 constexpr int kGroups = 3;                        // halo populations split 13 + 13 + 12
 constexpr int kPer = 13;
-constexpr int kLZ = 64;                           // planes per CTA
+constexpr int kLZmax = 64;                        // planes per CTA (large lattices)
+constexpr int kLZsmall = 8;                       // planes per CTA (small lattices)
 constexpr int Q2 = 2 * Q;
 static_assert(kGroups * kHalo <= kThreadsF, "one halo group per thread");
 
 template <class R>
 struct FusedSmem {
-    R ring[3][2][kTY + 2][kTX + 2];        // rho^1, rho^2 of planes z-1, z, z+1 (+ halo)
+    R ring[4][2][kTY + 2][kTX + 2];        // rho^1, rho^2 of planes z-1 .. z+2 (+ halo)
     R hpart[2][kGroups][2][kHalo];         // halo partial densities of the next two planes
     R mom[2][3][kThreadsF];                // sum_a sum_i c_i f_i of the stashed planes
     R stash[2][Q2][kThreadsF];             // pre-collision populations of planes z, z+1
@@ -74,14 +80,14 @@ struct PlaneRef {
     bool constant;         // ghost plane with the point-wise wall potential: rho = rho_s
 };
 
-template <class R>
+template <bool WALLZ, class R>
 __device__ __forceinline__ PlaneRef plane_ref(const Phys<R> &p, int zp)
 {
     PlaneRef r;
     int z = zp;
     r.ghost = false;
     if (zp < 0 || zp >= p.nz) {
-        if (p.wall_z) {
+        if (WALLZ) {
             r.ghost = true;
             z = zp < 0 ? 0 : p.nz - 1;
         } else {
@@ -93,8 +99,8 @@ __device__ __forceinline__ PlaneRef plane_ref(const Phys<R> &p, int zp)
     r.zc = z * plane;
     r.zm = (z == 0 ? p.nz - 1 : z - 1) * plane;
     r.zp = (z == p.nz - 1 ? 0 : z + 1) * plane;
-    r.lo_wall = p.wall_z && z == 0;
-    r.hi_wall = p.wall_z && z == p.nz - 1;
+    r.lo_wall = WALLZ && z == 0;
+    r.hi_wall = WALLZ && z == p.nz - 1;
     return r;
 }
 
@@ -113,6 +119,8 @@ __device__ __forceinline__ int gather_elem(const PlaneRef &pr, const Col &c, int
     return zs + c.yo[1 - cy(I)] + c.xo[1 - cx(I)];
 }
 
+// Element offsets inside one component's 19 arrays fit 32 bits (19 N < 2^32,
+// checked on the host): one multiply-add per load instead of 64-bit index math.
 template <int S, int I>
 __device__ __forceinline__ void load_dir(const typename Store<S>::T *__restrict__ f, long long N,
                                          typename Store<S>::R rho0, const PlaneRef &pr, const Col &c,
@@ -121,8 +129,9 @@ __device__ __forceinline__ void load_dir(const typename Store<S>::T *__restrict_
     using R = typename Store<S>::R;
     int d;
     const int e = gather_elem<I>(pr, c, d);
-    v[I] = Store<S>::load(f + (long long)d * N + e, w<R>(I) * rho0);
-    v[Q + I] = Store<S>::load(f + (long long)(Q + d) * N + e, w<R>(I) * rho0);
+    const unsigned idx = (unsigned)d * (unsigned)N + (unsigned)e;
+    v[I] = Store<S>::load(f + idx, w<R>(I) * rho0);
+    v[Q + I] = Store<S>::load(f + (size_t)Q * (size_t)N + idx, w<R>(I) * rho0);
 }
 
 template <int S, int I>
@@ -171,7 +180,8 @@ struct HaloRange {
         constexpr int a = QQ / Q, i = QQ % Q;
         int d;
         const int e = gather_elem<i>(pr, c, d);
-        v[k] = Store<S>::load(f + (long long)(a * Q + d) * N + e, w<R>(i) * rho0);
+        const unsigned idx = (unsigned)d * (unsigned)N + (unsigned)e;
+        v[k] = Store<S>::load(f + (size_t)a * Q * (size_t)N + idx, w<R>(i) * rho0);
         HaloRange<S, QQ + 1, Q1>::load(f, N, rho0, pr, c, v, k + 1);
     }
     __device__ __forceinline__ static void sum(const typename Store<S>::R (&v)[kPer], int k,
@@ -216,13 +226,17 @@ __device__ __forceinline__ void halo_sum(const typename Store<S>::R (&v)[kPer], 
 template <int S, bool REG>
 __device__ __forceinline__ void collide_cell(typename Store<S>::T *__restrict__ fout, const Phys<typename Store<S>::R> &p,
                                              const FusedSmem<typename Store<S>::R> &sm, int sl_m, int sl_c, int sl_p,
-                                             int st, long long cell)
+                                             int st, long long cell, typename Store<S>::R *__restrict__ rho_out)
 {
     using R = typename Store<S>::R;
     const int tid = threadIdx.x;
     const int lx = tid % kTX + 1, ly = tid / kTX + 1;
     const R r1 = sm.ring[sl_c][0][ly][lx];
     const R r2 = sm.ring[sl_c][1][ly][lx];
+    if (rho_out) {   // pre-collision densities of this step (reverse-mode replay)
+        rho_out[cell] = r1;
+        rho_out[p.N + cell] = r2;
+    }
     const R inv = R(1) / (r1 + r2);
     const R ux = sm.mom[st][0][tid] * inv, uy = sm.mom[st][1][tid] * inv, uz = sm.mom[st][2][tid] * inv;
     // S^b = sum_{i != 0} w_i c_i rho^b(x + c_i)  (Eq. 7; ghost planes carry Eq. 13's rho')
@@ -254,8 +268,9 @@ __device__ __forceinline__ void collide_cell(typename Store<S>::T *__restrict__ 
     const R keep1 = R(1) - p.omega[0], keep2 = R(1) - p.omega[1];
     const R *s0 = &sm.stash[st][0][tid];
     const R rq1 = r1 / R(36), rq2 = r2 / R(36);   // rho w_i = (rho / 36) k_i
-    typename Store<S>::T *o = fout + cell;
-    const long long N = p.N;
+    typename Store<S>::T *o = fout + cell;                     // component 1
+    typename Store<S>::T *o2 = fout + (size_t)Q * (size_t)p.N + cell;   // component 2
+    const unsigned N32 = (unsigned)p.N;
     const R ref0 = p.rho0;
 
     // Regularized: second moments of f - f^eq(u): Pi = sum c c f - rho (T0 I + u u)
@@ -286,16 +301,16 @@ __device__ __forceinline__ void collide_cell(typename Store<S>::T *__restrict__ 
     // rest population (k_0 = 12)
     {
         const R w0 = w<R>(0);
-        R o1, o2;
+        R o1, o2v;
         if (!REG) {
             o1 = rq1 * R(12) * (A1 - keep1 * Au) + keep1 * s0[0];
-            o2 = rq2 * R(12) * (A2 - keep2 * Au) + keep2 * s0[Q * kThreadsF];
+            o2v = rq2 * R(12) * (A2 - keep2 * Au) + keep2 * s0[Q * kThreadsF];
         } else {
             o1 = rq1 * R(12) * A1 - keep1 * R(1.5) * t1;
-            o2 = rq2 * R(12) * A2 - keep2 * R(1.5) * t2;
+            o2v = rq2 * R(12) * A2 - keep2 * R(1.5) * t2;
         }
         Store<S>::store(o, o1, w0 * ref0);
-        Store<S>::store(o + (long long)Q * N, o2, w0 * ref0);
+        Store<S>::store(o2, o2v, w0 * ref0);
     }
 #pragma unroll
     for (int i = 1; i < Q; i += 2) {
@@ -333,10 +348,11 @@ __device__ __forceinline__ void collide_cell(typename Store<S>::T *__restrict__ 
             o2m = rw2 * (E2 - O2) + n2;
         }
         const R ref = w<R>(i) * ref0;
-        Store<S>::store(o + (long long)i * N, o1p, ref);
-        Store<S>::store(o + (long long)(i + 1) * N, o1m, ref);
-        Store<S>::store(o + (long long)(Q + i) * N, o2p, ref);
-        Store<S>::store(o + (long long)(Q + i + 1) * N, o2m, ref);
+        const unsigned ip = (unsigned)i * N32, im = (unsigned)(i + 1) * N32;
+        Store<S>::store(o + ip, o1p, ref);
+        Store<S>::store(o + im, o1m, ref);
+        Store<S>::store(o2 + ip, o2p, ref);
+        Store<S>::store(o2 + im, o2m, ref);
     }
 }
 
@@ -387,11 +403,12 @@ __device__ __forceinline__ void halo_combine(const Phys<R> &p, FusedSmem<R> &sm,
     sm.ring[slot][1][hy][hx] = r2;
 }
 
-template <int S, bool REG>
+template <int S, bool REG, bool WALLZ, int LZ>
 __global__ void __launch_bounds__(kThreadsF, 2)
 k_step_fused(const typename Store<S>::T *__restrict__ fin, typename Store<S>::T *__restrict__ fout,
-             Phys<typename Store<S>::R> p, int ntx)
+             Phys<typename Store<S>::R> p, int ntx, typename Store<S>::R *__restrict__ rho_out)
 {
+    constexpr int lz = LZ;
     using R = typename Store<S>::R;
     static_assert(sizeof(R) == sizeof(float), "the fused step runs FP32 arithmetic");
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -399,8 +416,8 @@ k_step_fused(const typename Store<S>::T *__restrict__ fin, typename Store<S>::T 
     const int tid = threadIdx.x;
     const int tx0 = (blockIdx.x % ntx) * kTX;
     const int ty0 = (blockIdx.x / ntx) * kTY;
-    const int z0 = blockIdx.y * kLZ;
-    const int z1 = min(z0 + kLZ, p.nz);
+    const int z0 = blockIdx.y * lz;
+    const int z1 = min(z0 + lz, p.nz);
     const int lx = tid % kTX, ly = tid / kTX;
     const int x = tx0 + lx, y = ty0 + ly;
     const bool active = x < p.nx && y < p.ny;
@@ -421,11 +438,11 @@ k_step_fused(const typename Store<S>::T *__restrict__ fin, typename Store<S>::T 
     int hgy = (ty0 - 1 + hy) % p.ny; if (hgy < 0) hgy += p.ny;
     const Col ch = make_col(hgx, hgy, p.nx, p.ny);
 
-    // ring slot of plane q: (q - z0 + 1) % 3; stash, moment and halo-partial
+    // ring slot of plane q: (q - z0 + 1) & 3; stash, moment and halo-partial
     // slot of plane q: (q - z0) & 1.
     // prologue: planes z0-1 and z0 in full, halo partials of z0+1
     for (int q = z0 - 1; q <= z0; ++q) {
-        const PlaneRef pr = plane_ref(p, q);
+        const PlaneRef pr = plane_ref<WALLZ>(p, q);
         R v[Q2];
         if (!pr.constant) GatherAll<S, 0>::run(fin, p.N, p.rho0, pr, ci, v);
         interior_plane<S>(fin, p, sm, q - z0 + 1, q == z0 ? 0 : -1, pr, v);
@@ -443,7 +460,7 @@ k_step_fused(const typename Store<S>::T *__restrict__ fin, typename Store<S>::T 
         }
     }
     {
-        const PlaneRef pr = plane_ref(p, z0 + 1);
+        const PlaneRef pr = plane_ref<WALLZ>(p, z0 + 1);
         if (has_halo) {
             R hv[kPer];
             R s1 = 0, s2 = 0;
@@ -458,13 +475,13 @@ k_step_fused(const typename Store<S>::T *__restrict__ fin, typename Store<S>::T 
     __syncthreads();
 
     const long long cell_xy = (long long)y * p.nx + x;
-    int s_m = 0, s_c = 1, s_p = 2;
     for (int z = z0; z < z1; ++z) {
         const int k = z - z0;
+        const int s_m = k & 3, s_c = (k + 1) & 3, s_p = (k + 2) & 3;
         // ---- phase A: gathers of plane z+1 (interior) and z+2 (halo partials)
-        const PlaneRef pr1 = plane_ref(p, z + 1);
+        const PlaneRef pr1 = plane_ref<WALLZ>(p, z + 1);
         const bool need2 = z + 2 <= z1;           // rho(z+2) feeds the collision of z+1
-        const PlaneRef pr2 = plane_ref(p, z + 2);
+        const PlaneRef pr2 = plane_ref<WALLZ>(p, z + 2);
         R v[Q2];
         R hv[kPer];
         if (!pr1.constant) GatherAll<S, 0>::run(fin, p.N, p.rho0, pr1, ci, v);
@@ -480,12 +497,7 @@ k_step_fused(const typename Store<S>::T *__restrict__ fin, typename Store<S>::T 
         __syncthreads();
         // ---- phase B: collision of plane z
         if (active)
-            collide_cell<S, REG>(fout, p, sm, s_m, s_c, s_p, k & 1, (long long)z * p.nx * p.ny + cell_xy);
-        __syncthreads();
-        const int t = s_m;
-        s_m = s_c;
-        s_c = s_p;
-        s_p = t;
+            collide_cell<S, REG>(fout, p, sm, s_m, s_c, s_p, k & 1, (long long)z * p.nx * p.ny + cell_xy, rho_out);
     }
 }
 
@@ -508,29 +520,51 @@ Phys<R> make_phys_f(const HostPhys &h)
 constexpr size_t kSmemBytes = sizeof(FusedSmem<float>);
 
 template <int S>
-cudaError_t fused_t(const HostPhys &h, const void *fin, void *fout, cudaStream_t s, cudaEvent_t *ev)
+cudaError_t fused_t(const HostPhys &h, const void *fin, void *fout, cudaStream_t s, cudaEvent_t *ev, void *rho_out)
 {
     using T = typename Store<S>::T;
     using R = typename Store<S>::R;
     const Phys<R> p = make_phys_f<R>(h);
     const int ntx = (h.nx + kTX - 1) / kTX;
     const int nty = (h.ny + kTY - 1) / kTY;
-    const dim3 grid((unsigned)(ntx * nty), (unsigned)((h.nz + kLZ - 1) / kLZ));
+    // planes per CTA: 64, or 8 when 64 would leave fewer than two CTAs per SM
+    // (small lattices get shorter chunks and more CTAs)
+    static int sms = 0;
+    if (!sms) {
+        int dev = 0;
+        if (cudaGetDevice(&dev) != cudaSuccess ||
+            cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || sms <= 0)
+            sms = 152;
+    }
+    const bool small = (long long)ntx * nty * ((h.nz + kLZmax - 1) / kLZmax) < 2LL * sms;
+    const int lz = small ? kLZsmall : kLZmax;
+    const dim3 grid((unsigned)(ntx * nty), (unsigned)((h.nz + lz - 1) / lz));
     static bool attr_set = false;
     if (!attr_set) {
-        cudaError_t e = cudaFuncSetAttribute(k_step_fused<S, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             (int)kSmemBytes);
-        if (e == cudaSuccess)
-            e = cudaFuncSetAttribute(k_step_fused<S, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                     (int)kSmemBytes);
+        cudaError_t e = cudaSuccess;
+        const void *fns[8] = {
+            (const void *)k_step_fused<S, true, false, kLZmax>, (const void *)k_step_fused<S, false, false, kLZmax>,
+            (const void *)k_step_fused<S, true, false, kLZsmall>, (const void *)k_step_fused<S, false, false, kLZsmall>,
+            (const void *)k_step_fused<S, true, true, kLZmax>, (const void *)k_step_fused<S, false, true, kLZmax>,
+            (const void *)k_step_fused<S, true, true, kLZsmall>, (const void *)k_step_fused<S, false, true, kLZsmall>};
+        for (int q = 0; q < 8 && e == cudaSuccess; ++q)
+            e = cudaFuncSetAttribute(fns[q], cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemBytes);
         if (e != cudaSuccess) return e;
         attr_set = true;
     }
     if (ev) cudaEventRecord(ev[0], s);
-    if (h.collision == LBM_REGULARIZED)
-        k_step_fused<S, true><<<grid, kThreadsF, kSmemBytes, s>>>((const T *)fin, (T *)fout, p, ntx);
-    else
-        k_step_fused<S, false><<<grid, kThreadsF, kSmemBytes, s>>>((const T *)fin, (T *)fout, p, ntx);
+    const T *fi = (const T *)fin;
+    T *fo = (T *)fout;
+    const bool reg = h.collision == LBM_REGULARIZED;
+#define LBM_LAUNCH(REG_, WALL_, LZ_) k_step_fused<S, REG_, WALL_, LZ_><<<grid, kThreadsF, kSmemBytes, s>>>(fi, fo, p, ntx, (R *)rho_out)
+    if (h.wall_z) {
+        if (reg) { if (small) LBM_LAUNCH(true, true, kLZsmall); else LBM_LAUNCH(true, true, kLZmax); }
+        else { if (small) LBM_LAUNCH(false, true, kLZsmall); else LBM_LAUNCH(false, true, kLZmax); }
+    } else {
+        if (reg) { if (small) LBM_LAUNCH(true, false, kLZsmall); else LBM_LAUNCH(true, false, kLZmax); }
+        else { if (small) LBM_LAUNCH(false, false, kLZsmall); else LBM_LAUNCH(false, false, kLZmax); }
+    }
+#undef LBM_LAUNCH
     if (ev) cudaEventRecord(ev[1], s);
     return cudaGetLastError();
 }
@@ -539,18 +573,19 @@ cudaError_t fused_t(const HostPhys &h, const void *fin, void *fout, cudaStream_t
 
 bool fused_supported(const HostPhys &p)
 {
-    // 32-bit element offsets inside one population array
-    return p.storage != ST_F64 && p.N < (1LL << 31) &&
+    // 32-bit element offsets inside one component's 19 population arrays
+    return p.storage != ST_F64 && (long long)Q * p.N < (1LL << 32) &&
            (long long)((p.nx + kTX - 1) / kTX) * ((p.ny + kTY - 1) / kTY) < (1LL << 31) &&
-           (p.nz + kLZ - 1) / kLZ < 65536;
+           (p.nz + 7) / 8 < 65536;
 }
 
-cudaError_t launch_step_fused(const HostPhys &p, const void *f_in, void *f_out, cudaStream_t s, cudaEvent_t *ev)
+cudaError_t launch_step_fused(const HostPhys &p, const void *f_in, void *f_out, cudaStream_t s, cudaEvent_t *ev,
+                              void *rho_out)
 {
     switch (p.storage) {
-    case ST_F32: return fused_t<ST_F32>(p, f_in, f_out, s, ev);
-    case ST_F16_DEV: return fused_t<ST_F16_DEV>(p, f_in, f_out, s, ev);
-    case ST_BF16_DEV: return fused_t<ST_BF16_DEV>(p, f_in, f_out, s, ev);
+    case ST_F32: return fused_t<ST_F32>(p, f_in, f_out, s, ev, rho_out);
+    case ST_F16_DEV: return fused_t<ST_F16_DEV>(p, f_in, f_out, s, ev, rho_out);
+    case ST_BF16_DEV: return fused_t<ST_BF16_DEV>(p, f_in, f_out, s, ev, rho_out);
     default: return cudaErrorInvalidValue;
     }
 }

@@ -38,8 +38,10 @@ cudaError_t launch_step_split(const HostPhys &p, const void *f_in, void *f_out, 
 
 // One full time step with the fused single-pass kernel (no scratch).
 // ev (optional, 2 events): recorded before and after the launch.
+// rho_out (optional, 2*N FP32 values): receives the step's pre-collision
+// densities rho^1, rho^2 (the replay of the reverse pass uses them).
 cudaError_t launch_step_fused(const HostPhys &p, const void *f_in, void *f_out, cudaStream_t s,
-                              cudaEvent_t *ev = nullptr);
+                              cudaEvent_t *ev = nullptr, void *rho_out = nullptr);
 bool fused_supported(const HostPhys &p);
 
 // State set-up: populations from (rho1, rho2, u) via f^eq (u may be NULL),
@@ -65,18 +67,21 @@ cudaError_t launch_reduce(const HostPhys &p, const void *f, void *rho, double *p
 constexpr long long kNoallocMaxCells = 2097152;   // 128^3
 cudaError_t launch_step_split_noalloc(const HostPhys &p, const void *f_in, void *f_out, cudaStream_t s);
 
-// Reverse (adjoint) step: lambda^n from lambda^{n+1} and the forward state f^n
-// (raw state, its densities in rho).  lam_loc (2*19*N reals) and a (6*N
-// reals) are scratch; partials (adjoint_blocks() x 4 doubles: dG12, dG21,
-// dtau1, dtau2) accumulate.
+// Reverse (adjoint) step n: from lambda_loc^{n+1} (2*19*N reals) and D^{n+1}
+// (2*N reals) and the forward state f^n (raw state, its densities in rho),
+// writes lambda_loc^n, a^n (6*N reals, scratch) and D^n; partials
+// (adjoint_blocks() x 4 doubles: dG12, dG21, dtau1, dtau2) accumulate.
+// lambda^n = lambda_loc^n + D^n of the population's component.
 int adjoint_blocks();
 cudaError_t launch_adjoint_step(const HostPhys &p, const void *f, const void *rho, const void *lam_next,
-                                void *lam_loc, void *a, void *lam_out, double *partials, cudaStream_t s);
-// lambda^N_i = dL/drho^a of the component of i (g1/g2 may be NULL).
+                                const void *Dn, void *lam_loc, void *a, void *Dout, double *partials,
+                                cudaStream_t s);
+// lambda_loc^N_i = dL/drho^a of the component of i (g1/g2 may be NULL).
 cudaError_t launch_adjoint_seed(const HostPhys &p, const void *g1, const void *g2, int g_f64, void *lam,
                                 cudaStream_t s);
 // dL/drho^a_0 = sum_i w_i lambda^0_i for an initial state f^eq(rho_0, u = 0).
-cudaError_t launch_adjoint_rho0(const HostPhys &p, const void *lam, double *g1, double *g2, cudaStream_t s);
+cudaError_t launch_adjoint_rho0(const HostPhys &p, const void *lam, const void *D, double *g1, double *g2,
+                                cudaStream_t s);
 // density pass only (rho = sum_i f_i, pull-gathered) into rho
 cudaError_t launch_density(const HostPhys &p, const void *f, void *rho, cudaStream_t s);
 
