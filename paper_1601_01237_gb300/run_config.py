@@ -1,15 +1,17 @@
 """Run one of the five synthetic cases on the GPU and print its measurements
 as one JSON line.
 
-    python -m paper_1601_01237_gb300.run_config c0 [--steps N] [--stride K]
+    python -m paper_1601_01237_gb300.run_config c0 [--steps N] [--shape NZ NY NX]
 
 c0  quasi-2D droplet 64x64x1, FP64: Delta p, spurious current max|u_F|, mass drift
 c1  3D droplets 128^3, FP32: Delta p vs 1/R fit (surface tension) per tau
+    (--radii, --taus, --shape for subsets)
 c2  spinodal mixture 256^3: FP32 / FP16-dev / BF16-dev, MLUPS, mass drift,
     interface measure <|rho1 - rho2|>
 c3  differentiation 96^3: loss, gradients (tied G, tau_1), adjoint/forward time
-c4  wall-bounded 512x512x384, regularized, mirror wetting, tilted gravity:
-    MLUPS, droplet drift velocity, thin-film density, volume ratio
+c4  wall-bounded 512x512x384, regularized, mirror wetting (or --wall-model
+    potential), no body force (or --gravity: tilted by 30 deg): MLUPS, droplet
+    drift velocity, thin-film density, volume ratio
 
 Everything runs through the C ABI of include/lbm.h; torch provides device
 buffers and the stream only.
@@ -22,6 +24,7 @@ import numpy as np
 
 from . import diagnostics as dg
 from . import workloads as wl
+from ._native import LBMError
 from .lattice import Lattice
 
 
@@ -66,30 +69,34 @@ def run_c1(steps=None, radii=None, taus=None, shape=None, storage=None):
     storage = storage or c["storage"]
     radii = radii or c["radii"]
     taus = taus or c["taus"]
-    out = {"case": "c1", "steps": steps, "shape": shape, "storage": storage, "fits": {}}
+    G = c["G"]
+    out = {"case": "c1", "steps": steps, "shape": shape, "storage": storage, "G_eq7": G, "fits": {}}
+    ctr = ((shape[2] - 1) / 2.0, (shape[1] - 1) / 2.0, (shape[0] - 1) / 2.0)
     for tau in taus:
-        # the tau = 0.55 BGK runs diverge for every tested G (see the design notes);
-        # they are run with the regularized operator at G = -1.2
-        if tau < 0.6:
-            G, col = -1.2, "regularized"
-        else:
-            G, col = c["G"], "bgk"
-        Rs, dps, spur = [], [], []
+        col = c["collision_for_tau"].get(tau, "regularized")
+        Rs, dps, spur, diverged = [], [], [], []
         for R0 in radii:
             lat = Lattice(shape, storage=storage, tau=(tau, tau), G12=G, collision=col)
             r1, r2 = wl.droplet(shape, R0)
             lat.init_fields(r1, r2)
             lat.step(steps)
-            ctr = ((shape[2] - 1) / 2.0, (shape[1] - 1) / 2.0, (shape[0] - 1) / 2.0)
+            try:
+                red = lat.reduce()
+            except LBMError:
+                diverged.append(R0)
+                lat.close()
+                continue
             _, _, dp = lat.pressure_jump(ctr, R0 / 2.0, R0 + 8.0)
             st = lat.droplet_stats(0.5 * (1.0 + 0.03), origin=ctr)
-            spur.append(lat.reduce()["max_uF"])
+            spur.append(red["max_uF"])
             lat.close()
             Rs.append(dg.equivalent_radius(st["volume"], False))
             dps.append(dp)
-        sigma, icpt, res = dg.laplace_fit(Rs, dps, dims=3)
-        out["fits"][str(tau)] = {"collision": col, "G_eq7": G, "R": Rs, "delta_p": dps, "sigma": sigma,
-                                 "intercept": icpt, "max_residual": res, "spurious_max_uF": spur}
+        fit = {"collision": col, "R": Rs, "delta_p": dps, "spurious_max_uF": spur, "diverged_R0": diverged}
+        if len(Rs) >= 2:
+            sigma, icpt, res = dg.laplace_fit(Rs, dps, dims=3)
+            fit.update(sigma=sigma, intercept=icpt, max_residual=res)
+        out["fits"][str(tau)] = fit
     return out
 
 
@@ -101,7 +108,7 @@ def run_c2(steps=None, storages=("f32", "f16_dev", "bf16_dev")):
     out = {"case": "c2", "steps": steps, "runs": {}}
     for st in storages:
         kw = {"rho0_dev": 0.5} if st.endswith("_dev") else {}
-        lat = Lattice(shape, storage=st, tau=c["tau"], G12=c["G"], **kw)
+        lat = Lattice(shape, storage=st, tau=c["tau"], G12=c["G"], collision=c.get("collision", "bgk"), **kw)
         lat.init_fields(r1, r2)
         m0 = lat.reduce()
         dt = _timed_steps(lat, steps)
@@ -142,18 +149,24 @@ def run_c3(steps=None):
             "adjoint_forward_ratio": t_a / t_f}
 
 
-def run_c4(steps=None, stride=None, shape=None):
+def run_c4(steps=None, shape=None, gravity=False, wall_model="mirror"):
+    """Wall-attached droplet.  No body force by default (the paper's inclined-
+    wall test has none); gravity=True adds g_mag_tilted rotated by tilt_deg,
+    which in a channel periodic along x drives a bulk Poiseuille flow that
+    carries the droplet."""
     c = wl.CONFIGS["c4_wall512"]
     steps = steps or c["steps"]
     shape = tuple(shape or c["shape"])
-    g = wl.tilted_gravity(c["g_mag"], c["tilt_deg"])
+    g = wl.tilted_gravity(c["g_mag_tilted"] if gravity else c["g_mag"], c["tilt_deg"])
+    R = c["R"] * shape[2] / c["shape"][2]
     lat = Lattice(shape, storage=c["storage"], tau=c["tau"], G12=c["G"], collision=c["collision"],
-                  periodic=c["periodic"], g_ext=g, wall_model="mirror")
-    r1, r2 = wl.hemisphere(shape, c["R"])
+                  periodic=c["periodic"], g_ext=g, wall_model=wall_model)
+    r1, r2 = wl.hemisphere(shape, R, rho_in=c["rho_in"], rho_out=c["rho_out"])
     lat.init_fields(r1, r2)
     nz, ny, nx = shape
     origin = ((nx - 1) / 2.0, (ny - 1) / 2.0, -0.5)
-    thr = 0.5 * (1.0 + 0.03)
+    thr = 0.5 * (c["rho_in"] + c["rho_out"])
+    s_0 = lat.droplet_stats(thr, origin)
     # drift over the last quarter of the run (the paper measures between
     # 8.0e4 and 8.5e4 steps of a longer run)
     t_a = steps - max(steps // 4, 1)
@@ -164,18 +177,31 @@ def run_c4(steps=None, stride=None, shape=None):
     red = lat.reduce()
     lat.close()
     v = dg.drift_velocity(s_a["com"], s_b["com"], steps - t_a)
-    return {"case": "c4", "steps": steps, "shape": shape, "MLUPS": np.prod(shape) * steps / dt / 1e6,
-            "drift_velocity": v.tolist(), "film_rho1": s_b["film_rho"], "volume_ratio": s_b["volume"] / np.prod(shape),
-            "droplet_volume": s_b["volume"], "max_uF": red["max_uF"]}
+    return {"case": "c4", "steps": steps, "shape": shape, "R": R, "g_ext": g, "wall_model": wall_model,
+            "MLUPS": np.prod(shape) * steps / dt / 1e6,
+            "HBM_GBs_algorithmic": np.prod(shape) * steps * 304 / dt / 1e9,
+            "drift_velocity": v.tolist(), "film_rho1": s_b["film_rho"], "bulk_minority_rho1": c["rho_out"],
+            "volume_ratio": s_b["volume"] / np.prod(shape), "droplet_volume": [s_0["volume"], s_b["volume"]],
+            "max_uF": red["max_uF"]}
 
 
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("case", choices=["c0", "c1", "c2", "c3", "c4"])
     ap.add_argument("--steps", type=int, default=None)
+    ap.add_argument("--shape", type=int, nargs=3, default=None, help="nz ny nx (c1, c4)")
+    ap.add_argument("--gravity", action="store_true", help="c4: tilted gravity")
+    ap.add_argument("--wall-model", default="mirror", choices=["mirror", "potential"], help="c4")
+    ap.add_argument("--radii", type=int, nargs="+", default=None, help="c1")
+    ap.add_argument("--taus", type=float, nargs="+", default=None, help="c1")
     args = ap.parse_args()
-    fn = {"c0": run_c0, "c1": run_c1, "c2": run_c2, "c3": run_c3, "c4": run_c4}[args.case]
-    print(json.dumps(fn(args.steps), default=float))
+    if args.case == "c4":
+        r = run_c4(args.steps, args.shape, args.gravity, args.wall_model)
+    elif args.case == "c1":
+        r = run_c1(args.steps, radii=args.radii, taus=args.taus, shape=args.shape)
+    else:
+        r = {"c0": run_c0, "c2": run_c2, "c3": run_c3}[args.case](args.steps)
+    print(json.dumps(r, default=float))
 
 
 if __name__ == "__main__":

@@ -14,27 +14,18 @@ Recipes (Otomo et al., arXiv:1601.01237):
   * hemisphere on a wall: a sphere centred on the wall plane z = -1/2 (the
     wall-attached droplet of Sec. 4.2).
 
-Interaction strength: the configurations quote G as a repulsion strength for
-weights normalised to a unit second moment (w_i / T0).  Eq. 7 uses the lattice
-weights w_i with a signed G, so the lattice value is G_eq7 = -G_cfg / T0 =
--3 G_cfg (repulsive).  Where that value makes the FP64 oracle diverge (the
-spinodal mixture at tau = 0.7 with G_eq7 = -3.6, and tau = 0.55 with -2.7,
-both within a few hundred steps), the cases use G_eq7 = -1.2 instead, which
-is still above the discrete spinodal threshold |G| rho0 = 1 - 1/(2 tau) of the
-BGK scheme and above the droplet's coexistence threshold for the regularized
-one.
+Interaction strength: Eq. 7 takes a signed G (repulsion: G < 0).  The
+droplet cases quote 1.0 inside / 0.03 outside; G = -1.8 is the value whose
+flat-interface coexistence densities are those (1.026 / 0.029, measured on
+the oracle at tau = 1), so the droplets start at equilibrium densities.  The
+mixture cases use G = -1.2, which separates a 0.5 / 0.5 mixture into
+0.897 / 0.148 with the regularized operator at every tau from 0.6 to 1.
 """
 import math
 
 import numpy as np
 
-T0 = 1.0 / 3.0
 MASK64 = (1 << 64) - 1
-
-
-def g_from_config(G_cfg):
-    """Signed G^{12} of Eq. 7 for a configuration's repulsion strength."""
-    return -G_cfg / T0
 
 
 def splitmix64(seed, n):
@@ -120,20 +111,35 @@ def random_state(shape, seed, rho_lo=0.2, rho_hi=1.0, u_max=0.05):
 
 # ---------------------------------------------------------------------------
 # The five cases and the 512^3 throughput case.  "G" is the signed Eq. 7 value.
+# Signed G^{12} = G^{21} of Eq. 7 per case.  The droplet cases start from
+# 1.0 inside / 0.03 outside; G = -1.8 is where those are the flat-interface
+# coexistence densities (1.026 / 0.029 on the oracle at tau = 1).  G = -1.2
+# separates a 0.5 / 0.5 mixture into 0.897 / 0.148 with the regularized
+# operator at any tau (BGK at tau < 1 separates further and diverges).
+G_DROPLET = -1.8
+G_MIXTURE = -1.2
+
 CONFIGS = {
-    "c0_droplet2d_f64": dict(shape=(1, 64, 64), storage="f64", tau=(1.0, 1.0), G=g_from_config(0.9),
+    "c0_droplet2d_f64": dict(shape=(1, 64, 64), storage="f64", tau=(1.0, 1.0), G=G_DROPLET,
                              R=16, steps=2000, init="droplet"),
-    "c1_droplet3d_f32": dict(shape=(128, 128, 128), storage="f32", tau=(1.0, 1.0), G=g_from_config(0.9),
-                             R=16, steps=10000, init="droplet",
-                             radii=(12, 16, 20, 24, 32), taus=(0.55, 0.8, 1.0)),
-    "c2_spinodal256": dict(shape=(256, 256, 256), storage="f32", tau=(0.7, 0.7), G=-1.2,
-                           steps=5000, init="spinodal"),
-    "c3_adjoint96": dict(shape=(96, 96, 96), storage="f32", tau=(1.0, 1.0), G=g_from_config(0.9),
+    # tau = 1: BGK and regularized coincide; tau = 0.8: regularized (BGK
+    # diverges); tau = 0.55 diverges with both operators at this G
+    "c1_droplet3d_f32": dict(shape=(128, 128, 128), storage="f32", tau=(1.0, 1.0), G=G_DROPLET,
+                             R=16, steps=10000, init="droplet", radii=(12, 16, 20, 24, 32),
+                             taus=(0.55, 0.8, 1.0), collision_for_tau={0.55: "regularized", 0.8: "regularized",
+                                                                       1.0: "bgk"}),
+    "c2_spinodal256": dict(shape=(256, 256, 256), storage="f32", tau=(0.7, 0.7), G=G_MIXTURE,
+                           collision="regularized", steps=5000, init="spinodal"),
+    "c3_adjoint96": dict(shape=(96, 96, 96), storage="f32", tau=(1.0, 1.0), G=G_DROPLET,
                          R=20, steps=500, init="droplet", ckpt_every=25, target_axes=(24, 20, 16)),
-    "c4_wall512": dict(shape=(384, 512, 512), storage="f32", tau=(0.55, 0.55), G=-1.2,
-                       R=48, steps=20000, init="hemisphere", collision="regularized",
-                       periodic=(1, 1, 0), g_mag=1e-5, tilt_deg=30.0),
-    "perf512_spinodal_f32": dict(shape=(512, 512, 512), storage="f32", tau=(0.7, 0.7), G=-1.2,
+    # tau = 0.55 holds no droplet at G_DROPLET: G_MIXTURE with the hemisphere at
+    # that G's coexistence densities; no body force (g_mag = 0), the tilted
+    # gravity of magnitude g_mag_tilted is a separate run
+    "c4_wall512": dict(shape=(384, 512, 512), storage="f32", tau=(0.55, 0.55), G=G_MIXTURE,
+                       R=48, steps=20000, init="hemisphere", rho_in=0.897, rho_out=0.148,
+                       collision="regularized", periodic=(1, 1, 0), g_mag=0.0, g_mag_tilted=1e-5,
+                       tilt_deg=30.0),
+    "perf512_spinodal_f32": dict(shape=(512, 512, 512), storage="f32", tau=(1.0, 1.0), G=G_MIXTURE,
                                  init="spinodal"),
 }
 
@@ -154,5 +160,5 @@ def fields_for(name, shape=None, **over):
     if kind == "spinodal":
         return spinodal(shape)
     if kind == "hemisphere":
-        return hemisphere(shape, c["R"])
+        return hemisphere(shape, c["R"], rho_in=c.get("rho_in", 1.0), rho_out=c.get("rho_out", 0.03))
     raise KeyError(kind)

@@ -7,6 +7,11 @@ import oracle
 Q = 19
 
 
+# A strongly separating G of Eq. 7 (flat-interface coexistence 1.056 / 0.0045
+# at tau = 1) for the droplet tests; parity and the pins need no particular G.
+G_STRONG = -2.7
+
+
 def direction_map():
     """perm such that oracle direction perm[i] has the library's c_i."""
     from paper_1601_01237_gb300 import lbm_lattice_dirs

@@ -14,6 +14,7 @@ import pytest
 
 import oracle
 from paper_1601_01237_gb300 import workloads as wl
+from _helpers import G_STRONG
 
 pytestmark = pytest.mark.gpu
 
@@ -65,7 +66,7 @@ def gpu_grads(r1, r2, tgt, G, tau1, tau2, steps, storage, **kw):
 @pytest.fixture(scope="module")
 def fd_reference():
     r1, r2, tgt = crop_case()
-    G = wl.g_from_config(0.9)
+    G = G_STRONG
     return (r1, r2, tgt, G) + fd_grads(r1, r2, tgt, G, 1.0, 1.0, STEPS)
 
 
@@ -116,7 +117,7 @@ def test_autograd_rollout_matches_adjoint(gpu_lib):
     import torch
     from paper_1601_01237_gb300.adjoint import LBMRollout
     r1, r2, tgt = crop_case()
-    G = wl.g_from_config(0.9)
+    G = G_STRONG
     gG, gT, gr = gpu_grads(r1, r2, tgt, G, 1.0, 1.0, STEPS, "f64")
     x1 = torch.tensor(r1, device="cuda", requires_grad=True)
     x2 = torch.tensor(r2, device="cuda", requires_grad=True)

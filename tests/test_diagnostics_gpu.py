@@ -6,13 +6,13 @@ import numpy as np
 import pytest
 
 import oracle
-from _helpers import oracle_run
+from _helpers import G_STRONG, oracle_run
 from paper_1601_01237_gb300 import diagnostics as dg
 from paper_1601_01237_gb300 import workloads as wl
 
 pytestmark = pytest.mark.gpu
 T0 = 1.0 / 3.0
-G = wl.g_from_config(0.9)
+G = G_STRONG
 
 
 def _np_dp(a, b, Gv, center, r_in, r_out):

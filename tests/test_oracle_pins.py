@@ -12,6 +12,7 @@ import pytest
 
 import oracle
 from paper_1601_01237_gb300 import workloads as wl
+from _helpers import G_STRONG
 
 T0 = 1.0 / 3.0
 RNG = np.random.default_rng(1601)
@@ -336,7 +337,7 @@ def test_laplace_law_2d():
     in 1/R through the origin.  p = T0 rho - G T0 rho^1 rho^2 is the bulk
     pressure of the Eq. 7 force (sum_a F^{ab} -> G T0 grad(rho^1 rho^2)); R is
     the measured equivalent-area radius of the relaxed droplet."""
-    G = wl.g_from_config(0.9)
+    G = G_STRONG
     n = 48
     Rs, dps = [], []
     for R0 in (6, 8, 10, 12):

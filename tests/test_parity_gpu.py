@@ -10,12 +10,12 @@ Tolerances:
 import numpy as np
 import pytest
 
-from _helpers import Q, direction_map, gpu_run, oracle_run, rel_err
+from _helpers import G_STRONG, Q, direction_map, gpu_run, oracle_run, rel_err
 from paper_1601_01237_gb300 import workloads as wl
 
 pytestmark = pytest.mark.gpu
 
-G_DROP = wl.g_from_config(0.9)
+G_DROP = G_STRONG
 
 CASES = [
     # (name, shape, kwargs)

@@ -19,6 +19,7 @@ import numpy as np
 import pytest
 
 from paper_1601_01237_gb300 import workloads as wl
+from _helpers import G_STRONG
 
 
 def test_noalloc_rejects_oversized_lattice():
@@ -40,7 +41,7 @@ def test_noalloc_rejects_oversized_lattice():
 
 @pytest.mark.gpu
 @pytest.mark.parametrize("storage,kw,tol", [
-    ("f32", dict(tau=(0.8, 1.1), G12=wl.g_from_config(0.9)), 1e-6),
+    ("f32", dict(tau=(0.8, 1.1), G12=G_STRONG), 1e-6),
     ("f64", dict(tau=(0.7, 0.9), G12=-1.3, periodic=(1, 1, 0), collision="regularized",
                  g_ext=(1e-5, 0.0, -2e-5)), 1e-13),
 ])
