@@ -50,14 +50,17 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-adjoint", action="store_true")
+    ap.add_argument("--shape", type=int, nargs=3, default=None, metavar=("NZ", "NY", "NX"),
+                    help="run the workload's parameters on another lattice (small profiling captures)")
     return ap.parse_args()
 
 
 def workload_desc(name, cfg, storage):
     nz, ny, nx = cfg["shape"]
     return {
-        "workload": "%s: %dx%dx%d two-component D3Q19, %s populations, %s, tau=%s, G_eq7=%.3g, %s" % (
-            name, nx, ny, nz, storage, cfg.get("collision", "bgk"), cfg["tau"][0], cfg["G"],
+        "workload": "%s%s: %dx%dx%d two-component D3Q19, %s populations, %s, tau=%s, G_eq7=%.3g, %s" % (
+            name, " (lattice override)" if cfg.get("shape_override") else "", nx, ny, nz, storage,
+            cfg.get("collision", "bgk"), cfg["tau"][0], cfg["G"],
             "periodic" if all(cfg.get("periodic", (1, 1, 1))) else "z walls"),
         "shape_zyx": list(cfg["shape"]),
         "storage": storage,
@@ -302,6 +305,8 @@ def run_ours(args, rank, world, local_rank):
     dist = world > 1
     torch.cuda.set_device(local_rank)
     cfg = dict(wl.CONFIGS[args.workload])
+    if args.shape:
+        cfg["shape"], cfg["shape_override"] = tuple(args.shape), True
     storage = args.storage or cfg["storage"]
     shape = tuple(cfg["shape"])
     cells = int(np.prod(shape))
@@ -309,7 +314,7 @@ def run_ours(args, rank, world, local_rank):
     kw = dict(storage=storage, tau=cfg["tau"], G12=cfg["G"], periodic=cfg.get("periodic", (1, 1, 1)),
               collision=cfg.get("collision", "bgk"), g_ext=g_ext,
               rho0_dev=0.5 if storage.endswith("_dev") else 0.0)
-    r1, r2 = wl.fields_for(args.workload)
+    r1, r2 = wl.fields_for(args.workload, shape=shape)
     stream = torch.cuda.current_stream()
     lat = Lattice(shape, stream=stream.cuda_stream, **kw)
     d1 = torch.from_numpy(r1).cuda()

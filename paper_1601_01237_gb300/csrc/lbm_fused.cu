@@ -13,7 +13,10 @@
 //      shared-memory stash) and, for the halo ring of plane z+2, 12 or 13 of
 //      the 38 populations of one halo cell (84 halo cells x 3 groups), summed
 //      into fixed-order partial densities; the halo densities of plane z+1
-//      (partials gathered one iteration earlier) are completed in the ring;
+//      (partials gathered one iteration earlier) are completed in the ring.
+//      The side-column halo cells cost one scattered sector per load, so their
+//      tasks are spread evenly over the warps (6 per warp) next to runs of
+//      consecutive row-halo tasks;
 //   -- one barrier --
 //   B. every thread collides its column at plane z from its stash entries and
 //      stores the post-collision populations.
@@ -424,19 +427,48 @@ k_step_fused(const typename Store<S>::T *__restrict__ fin, typename Store<S>::T 
     // interior column (wrapped so that ragged tiles fill their ring slots
     // with the periodic images their active neighbours read)
     const Col ci = make_col((tx0 + lx) % p.nx, (ty0 + ly) % p.ny, p.nx, p.ny);
-    // halo cell h and population group g of this thread (tid < 3 * 84)
-    const bool has_halo = tid < kGroups * kHalo;
-    const int h = tid % kHalo, g = tid / kHalo;
     auto halo_pos = [](int hh, int &hx, int &hy) {
         if (hh < kTX + 2) { hx = hh; hy = 0; }
         else if (hh < 2 * (kTX + 2)) { hx = hh - (kTX + 2); hy = kTY + 1; }
         else { const int k = hh - 2 * (kTX + 2); hx = k < kTY ? 0 : kTX + 1; hy = 1 + (k % kTY); }
     };
+    auto halo_col = [&](int hx_, int hy_) {
+        int gx = (tx0 - 1 + hx_) % p.nx; if (gx < 0) gx += p.nx;
+        int gy = (ty0 - 1 + hy_) % p.ny; if (gy < 0) gy += p.ny;
+        return make_col(gx, gy, p.nx, p.ny);
+    };
+    // halo cell h = tid (< 84) of this thread for the full gathers of the
+    // prologue and for completing the halo densities
+    const int h = tid % kHalo;
     int hx, hy;
     halo_pos(h, hx, hy);
-    int hgx = (tx0 - 1 + hx) % p.nx; if (hgx < 0) hgx += p.nx;
-    int hgy = (ty0 - 1 + hy) % p.ny; if (hgy < 0) hgy += p.ny;
-    const Col ch = make_col(hgx, hgy, p.nx, p.ny);
+    const Col ch = halo_col(hx, hy);
+    // partial-gather task (cell ht, population group g): every warp takes 25-26
+    // consecutive row-halo tasks (coalesced) and 6 of the 48 side-column tasks
+    // (one scattered sector per load), so no warp carries the side columns alone
+    constexpr int kRowCells = 2 * (kTX + 2), kSideCells = 2 * kTY;
+    constexpr int kRowTasks = kGroups * kRowCells, kSideTasks = kGroups * kSideCells;
+    constexpr int kWarps = kThreadsF / 32;
+    static_assert(kSideTasks % kWarps == 0, "side tasks spread evenly over the warps");
+    constexpr int kSidePerWarp = kSideTasks / kWarps, kRowBase = kRowTasks / kWarps, kRowExtra = kRowTasks % kWarps;
+    static_assert(kRowBase + (kRowExtra ? 1 : 0) + kSidePerWarp <= 32, "halo tasks fit a warp");
+    int ht = 0, g = 0;
+    bool has_halo = false;
+    {
+        const int w = tid >> 5, lane = tid & 31;
+        const int nrow = kRowBase + (w < kRowExtra ? 1 : 0);
+        const int row0 = w * kRowBase + (w < kRowExtra ? w : kRowExtra);
+        if (lane < nrow) {
+            const int t = row0 + lane;
+            g = t / kRowCells; ht = t % kRowCells; has_halo = true;
+        } else if (lane - nrow < kSidePerWarp) {
+            const int t = w * kSidePerWarp + (lane - nrow);
+            g = t / kSideCells; ht = kRowCells + t % kSideCells; has_halo = true;
+        }
+    }
+    int htx, hty;
+    halo_pos(ht, htx, hty);
+    const Col cht = halo_col(htx, hty);
 
     // ring slot of plane q: (q - z0 + 1) & 3; stash, moment and halo-partial
     // slot of plane q: (q - z0) & 1.
@@ -465,11 +497,11 @@ k_step_fused(const typename Store<S>::T *__restrict__ fin, typename Store<S>::T 
             R hv[kPer];
             R s1 = 0, s2 = 0;
             if (!pr.constant) {
-                halo_load<S>(fin, p, pr, ch, g, hv);
+                halo_load<S>(fin, p, pr, cht, g, hv);
                 halo_sum<S>(hv, g, s1, s2);
             }
-            sm.hpart[1][g][0][h] = s1;
-            sm.hpart[1][g][1][h] = s2;
+            sm.hpart[1][g][0][ht] = s1;
+            sm.hpart[1][g][1][ht] = s2;
         }
     }
     __syncthreads();
@@ -485,14 +517,14 @@ k_step_fused(const typename Store<S>::T *__restrict__ fin, typename Store<S>::T 
         R v[Q2];
         R hv[kPer];
         if (!pr1.constant) GatherAll<S, 0>::run(fin, p.N, p.rho0, pr1, ci, v);
-        if (need2 && has_halo && !pr2.constant) halo_load<S>(fin, p, pr2, ch, g, hv);
+        if (need2 && has_halo && !pr2.constant) halo_load<S>(fin, p, pr2, cht, g, hv);
         if (tid < kHalo) halo_combine<R>(p, sm, s_p, (k + 1) & 1, pr1, h, hx, hy);
         interior_plane<S>(fin, p, sm, s_p, z + 1 < z1 ? ((k + 1) & 1) : -1, pr1, v);
         if (need2 && has_halo) {
             R s1 = 0, s2 = 0;
             if (!pr2.constant) halo_sum<S>(hv, g, s1, s2);
-            sm.hpart[k & 1][g][0][h] = s1;
-            sm.hpart[k & 1][g][1][h] = s2;
+            sm.hpart[k & 1][g][0][ht] = s1;
+            sm.hpart[k & 1][g][1][ht] = s2;
         }
         __syncthreads();
         // ---- phase B: collision of plane z
