@@ -195,11 +195,12 @@ lbm_status lbm_record(lbm_lattice *h, long n_steps, int ckpt_every);
  * dL/dG^{12}, dL/dG^{21}, dL/dtau_1, dL/dtau_2 (for a tied G^{12} = G^{21},
  * sum the first two).  All array pointers are host (on_device = 0) or device
  * (on_device = 1) memory.  The forward states of each checkpoint segment are
- * recomputed (time-checkpointing); working memory (adjoint fields and one
- * segment of states) is allocated for the call and released.  Leaves the
- * lattice state at the end of the recorded run.  Synchronizes.  Errors:
- * LBM_EINVAL (no recording), LBM_ENOTSUP (initial-density gradient requested
- * for a recording that did not start at rest from lbm_init_fields),
+ * recomputed (time-checkpointing); working memory (adjoint fields, one
+ * segment of states and their densities) is allocated for the call and
+ * released.  Leaves the lattice state at the end of the recorded run.
+ * Synchronizes.  Errors: LBM_EINVAL (no recording), LBM_ENOTSUP
+ * (initial-density gradient requested for a recording that did not start at
+ * rest from lbm_init_fields, or a lattice of more than 2^32 cells),
  * LBM_ENOMEM, LBM_ECUDA. */
 lbm_status lbm_adjoint(lbm_lattice *h, const double *dL_drho1, const double *dL_drho2, int on_device,
                        double *dL_drho1_0, double *dL_drho2_0, double dL_dparams[4]);

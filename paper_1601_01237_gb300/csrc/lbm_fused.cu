@@ -388,7 +388,8 @@ __device__ __forceinline__ void interior_plane(const typename Store<S>::T *__res
     sm.ring[slot][1][ly][lx] = r2;
 }
 
-// Halo densities of a plane in ring slot `slot` from the three partials.
+// Halo densities of a plane in ring slot `slot` from the partials of the
+// population groups.
 template <class R>
 __device__ __forceinline__ void halo_combine(const Phys<R> &p, FusedSmem<R> &sm, int slot, int hs,
                                              const PlaneRef &pr, int h, int hx, int hy)
