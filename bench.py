@@ -19,6 +19,7 @@ import argparse
 import hashlib
 import json
 import os
+import re
 import statistics
 import subprocess
 import sys
@@ -157,10 +158,15 @@ KERNEL_SOURCES = {"k_step_fused": ("d3q19.cuh", "lbm_fused.cu"),
 
 
 def kernel_source_hash(kernel):
+    """Hash of the kernel's sources with comments and blank lines removed
+    (editing a comment keeps the committed counters valid)."""
     h = hashlib.sha256()
     csrc = os.path.join(ROOT, "paper_1601_01237_gb300", "csrc")
     for f in KERNEL_SOURCES[kernel]:
-        h.update(open(os.path.join(csrc, f), "rb").read())
+        text = open(os.path.join(csrc, f)).read()
+        text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+        text = re.sub(r"//[^\n]*", "", text)
+        h.update("\n".join(l.rstrip() for l in text.splitlines() if l.strip()).encode())
     return h.hexdigest()[:16]
 
 
