@@ -83,10 +83,13 @@ def test_adjoint_matches_finite_differences(gpu_lib, fd_reference, storage):
     assert np.max(np.abs(gr - fr)[big] / np.abs(fr)[big]) <= 1e-3
 
 
+@pytest.mark.parametrize("storage", ["f64", "f32"])
 @pytest.mark.parametrize("collision", ["bgk", "regularized"])
-def test_adjoint_walls_and_forcing(gpu_lib, collision):
+def test_adjoint_walls_and_forcing(gpu_lib, collision, storage):
     """Reverse pass through mirror wetting walls, bounce-back, g_ext, unequal
-    tau and the regularized operator (FP64), on sampled cells."""
+    tau and the regularized operator, on sampled cells (FP64: 1e-5 of the
+    oracle's central differences; FP32, whose force-adjoint stencil runs in
+    the tiled kernel: 1e-4)."""
     shape = (6, 5, 7)
     r1, r2, _ = wl.random_state(shape, seed=17, u_max=0.0)
     tgt = np.roll(r1, 2, axis=2)
@@ -97,19 +100,20 @@ def test_adjoint_walls_and_forcing(gpu_lib, collision):
     cells += [(0, 2, 3), (5, 1, 1)]   # both wall layers
     fG, fT, fr = fd_grads(r1, r2, tgt, G, t1, t2, steps, cells=cells, **kw)
     from paper_1601_01237_gb300 import Lattice
-    lat = Lattice(shape, storage="f64", tau=(t1, t2), G12=G, G21=G, **kw)
+    lat = Lattice(shape, storage=storage, tau=(t1, t2), G12=G, G21=G, **kw)
     lat.init_fields(r1, r2)
     lat.record(steps, 4)
     a, _, _ = lat.moments()
     d1 = np.empty(shape)
     par = lat.adjoint(2 * (a - tgt), None, d1, None)
     lat.close()
-    print("%s walls: dG %.6g vs %.6g, dtau1 %.6g vs %.6g" % (collision, par[0] + par[1], fG, par[2], fT))
-    assert abs(par[0] + par[1] - fG) <= 1e-5 * abs(fG)
-    assert abs(par[2] - fT) <= 1e-5 * abs(fT)
+    tol = 1e-5 if storage == "f64" else 1e-4
+    print("%s %s walls: dG %.6g vs %.6g, dtau1 %.6g vs %.6g" % (storage, collision, par[0] + par[1], fG, par[2], fT))
+    assert abs(par[0] + par[1] - fG) <= tol * abs(fG)
+    assert abs(par[2] - fT) <= tol * abs(fT)
     scale = np.abs([fr[q] for q in cells]).max()
     for c in cells:
-        assert abs(d1[c] - fr[c]) <= 1e-5 * scale, (c, d1[c], fr[c])
+        assert abs(d1[c] - fr[c]) <= tol * scale, (c, d1[c], fr[c])
 
 
 def test_autograd_rollout_matches_adjoint(gpu_lib):
