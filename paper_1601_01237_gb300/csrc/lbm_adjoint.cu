@@ -70,10 +70,6 @@ __device__ __forceinline__ unsigned at(const Nb &n, int dx, int dy, int dz)
     return n.zo[1 + dz] + n.yo[1 + dy] + n.xo[1 + dx];
 }
 
-template <class R>
-__device__ __forceinline__ R gradP_alpha(R cv, R vsq) { return R(3) + R(9) * cv + R(13.5) * cv * cv - R(4.5) * vsq; }
-template <class R>
-__device__ __forceinline__ R P_of(R cv, R vsq) { return R(1) + R(3) * cv + R(4.5) * cv * cv - R(1.5) * vsq + R(4.5) * cv * cv * cv - R(4.5) * cv * vsq; }
 
 // Local reverse pass of one component a at one cell, run by a pair of lanes
 // (lane l: component 0, lane l ^ 16: component 1, same cell).  The two
@@ -179,37 +175,60 @@ __device__ __forceinline__ void adj_half(const typename Store<S>::T *__restrict_
     // BGK:         f* = E(rho, v) + keep (f - E(rho, u))
     // regularized: f* = E(rho, v) + keep (k_i / 8) (c c : Pi - tr(Pi) / 3)
     // with E_i(rho, x) = (rho / 36) k_i P(c_i . x, x . x)
+    // Opposite directions (i, i + 1) share k_i and |c_i . x|: with s = k (mu_i +
+    // mu_opp), d = k (mu_i - mu_opp) and P(+-c) = E +- O, grad P(+-c) = A +- B,
+    // the pair contributes E s + O d to the density sensitivity and (A d + B s)
+    // c_i to the velocity one.
     R Kbar = 0, rbar = 0;
     R vbx = 0, vby = 0, vbz = 0, vbv = 0, ubx = 0, uby = 0, ubz = 0, ubv = 0;
     R pb[6] = {0, 0, 0, 0, 0, 0};
-#pragma unroll
-    for (int i = 0; i < Q; ++i) {
-        const R m = mu[i];
-        const R ki = R(k36(i));
-        const R mk = m * ki;
-        const R cv = cdot<R>(i, v0, v1, v2);
-        rbar += mk * P_of(cv, vsq);
-        const R al = gradP_alpha(cv, vsq) * mk;
-        if (cx(i) == 1) vbx += al; else if (cx(i) == -1) vbx -= al;
-        if (cy(i) == 1) vby += al; else if (cy(i) == -1) vby -= al;
-        if (cz(i) == 1) vbz += al; else if (cz(i) == -1) vbz -= al;
-        vbv += mk * (R(3) + R(9) * cv);
+    {
+        // rest population: c = 0, k = 12
+        const R m = mu[0], mk = m * R(12);
+        rbar += mk * (R(1) - R(1.5) * vsq);
+        vbv += R(3) * mk;
         if (!REG) {
-            const R cu = cdot<R>(i, u0, u1, u2);
-            const R Pu = P_of(cu, usq);
-            Kbar += m * (fa[i] - rq * ki * Pu);
+            const R Pu = R(1) - R(1.5) * usq;
+            Kbar += m * (fa[0] - rq * R(12) * Pu);
             rbar -= keep * mk * Pu;
-            const R alu = gradP_alpha(cu, usq) * mk;
-            if (cx(i) == 1) ubx += alu; else if (cx(i) == -1) ubx -= alu;
-            if (cy(i) == 1) uby += alu; else if (cy(i) == -1) uby -= alu;
-            if (cz(i) == 1) ubz += alu; else if (cz(i) == -1) ubz -= alu;
-            ubv += mk * (R(3) + R(9) * cu);
+            ubv += R(3) * mk;
+        } else {
+            Kbar += mk * R(0.125) * (-tr / R(3));
+            const R nb = keep * mk * R(0.125);
+            pb[0] -= nb / R(3);
+            pb[1] -= nb / R(3);
+            pb[2] -= nb / R(3);
+        }
+    }
+#pragma unroll
+    for (int i = 1; i < Q; i += 2) {
+        const R ki = R(k36(i));
+        const R sg = (mu[i] + mu[i + 1]) * ki, df = (mu[i] - mu[i + 1]) * ki;
+        const R cv = cdot<R>(i, v0, v1, v2), cv2 = cv * cv;
+        const R E = R(1) + R(4.5) * cv2 - R(1.5) * vsq, O = cv * (R(3) + R(4.5) * cv2 - R(4.5) * vsq);
+        rbar += E * sg + O * df;
+        const R t = (R(3) + R(13.5) * cv2 - R(4.5) * vsq) * df + R(9) * cv * sg;
+        if (cx(i)) vbx += R(cx(i)) * t;
+        if (cy(i)) vby += R(cy(i)) * t;
+        if (cz(i)) vbz += R(cz(i)) * t;
+        vbv += R(3) * sg + R(9) * cv * df;
+        if (!REG) {
+            const R cu = cdot<R>(i, u0, u1, u2), cu2 = cu * cu;
+            const R Eu = R(1) + R(4.5) * cu2 - R(1.5) * usq, Ou = cu * (R(3) + R(4.5) * cu2 - R(4.5) * usq);
+            const R Pm = Eu * sg + Ou * df;
+            Kbar += mu[i] * fa[i] + mu[i + 1] * fa[i + 1] - rq * Pm;
+            rbar -= keep * Pm;
+            const R tu = (R(3) + R(13.5) * cu2 - R(4.5) * usq) * df + R(9) * cu * sg;
+            if (cx(i)) ubx += R(cx(i)) * tu;
+            if (cy(i)) uby += R(cy(i)) * tu;
+            if (cz(i)) ubz += R(cz(i)) * tu;
+            ubv += R(3) * sg + R(9) * cu * df;
         } else {
             const int c0 = cx(i), c1 = cy(i), c2 = cz(i);
             const R ccP = R(c0 * c0) * Pi[0] + R(c1 * c1) * Pi[1] + R(c2 * c2) * Pi[2] + R(2 * c0 * c1) * Pi[3] +
                           R(2 * c0 * c2) * Pi[4] + R(2 * c1 * c2) * Pi[5];
-            Kbar += mk * R(0.125) * (ccP - tr / R(3));
-            const R nb = keep * mk * R(0.125);
+            Kbar += sg * R(0.125) * (ccP - tr / R(3));
+            const R nb = keep * sg * R(0.125);
             pb[0] += nb * (R(c0 * c0) - R(1) / R(3));
             pb[1] += nb * (R(c1 * c1) - R(1) / R(3));
             pb[2] += nb * (R(c2 * c2) - R(1) / R(3));
