@@ -35,6 +35,10 @@ struct lbm_lattice {
     int rec_every;
     long rec_nck;
     int rec_at_rest;     // the recording started at rest right after lbm_init_fields
+    // CUDA graph of kGraphSteps steps from copy 0 (replayed by lbm_step)
+    cudaGraphExec_t graph;
+    int graph_state;     // 0 not built, 1 ready, -1 not available (plain launches)
+    int use_graphs;
 };
 
 namespace {
@@ -166,6 +170,7 @@ lbm_status lbm_create(const lbm_params *pp, lbm_lattice **out)
     ph.rho_s[0] = p.rho_s[0]; ph.rho_s[1] = p.rho_s[1];
     ph.rho0 = p.rho0_dev;
     h->use_fused = env_flag("LBM_FUSED", 1) && lbm::fused_supported(ph);
+    h->use_graphs = env_flag("LBM_GRAPHS", 1);
 
     cudaError_t e = cudaGetDevice(&h->device);
     if (e != cudaSuccess) { free(h); return cuda_fail(e, "lbm_create: cudaGetDevice"); }
@@ -214,6 +219,7 @@ void lbm_destroy(lbm_lattice *h)
     cudaFree(h->rho);
     cudaFree(h->ckpt);
     cudaFree(h->partials);
+    if (h->graph) cudaGraphExecDestroy(h->graph);
     if (h->partials_h) cudaFreeHost(h->partials_h);
     if (h->own_stream && h->stream) cudaStreamDestroy(h->stream);
     free(h);
@@ -250,22 +256,76 @@ lbm_status lbm_init_fields(lbm_lattice *h, const double *rho1, const double *rho
     return LBM_OK;
 }
 
+namespace {
+
+// Steps per graph launch; even, so that a replay leaves the state in copy 0.
+constexpr long kGraphSteps = 16;
+
+cudaError_t launch_one(lbm_lattice *h, int from, cudaStream_t s)
+{
+    return h->use_fused ? lbm::launch_step_fused(h->phys, h->f[from], h->f[from ^ 1], s)
+                        : lbm::launch_step_split(h->phys, h->f[from], h->f[from ^ 1], h->rho, s);
+}
+
+// Captures kGraphSteps ping-pong steps starting from copy 0 on a private
+// stream (the lattice's stream may be the legacy default stream, which cannot
+// be captured) and instantiates them.  On any failure the lattice keeps
+// plain launches.
+bool build_graph(lbm_lattice *h)
+{
+    cudaStream_t cs = nullptr;
+    if (cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    cudaGraph_t gr = nullptr;
+    bool ok = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal) == cudaSuccess;
+    if (ok) {
+        for (long t = 0; t < kGraphSteps && ok; ++t) ok = launch_one(h, (int)(t & 1), cs) == cudaSuccess;
+        const cudaError_t e = cudaStreamEndCapture(cs, &gr);
+        ok = ok && e == cudaSuccess && gr != nullptr;
+    }
+    if (ok) ok = cudaGraphInstantiate(&h->graph, gr, 0) == cudaSuccess;
+    if (gr) cudaGraphDestroy(gr);
+    cudaStreamDestroy(cs);
+    cudaGetLastError();
+    if (!ok) h->graph = nullptr;
+    return ok;
+}
+
+}  // namespace
+
 lbm_status lbm_step(lbm_lattice *h, long n_steps)
 {
     if (!h) return fail(LBM_EINVAL, "lbm_step: NULL handle");
     if (n_steps < 0) return fail(LBM_EINVAL, "lbm_step: n_steps = %ld < 0", n_steps);
     DeviceGuard g(h->device);
-    for (long t = 0; t < n_steps; ++t) {
-        cudaError_t e;
-        if (h->use_fused)
-            e = lbm::launch_step_fused(h->phys, h->f[h->cur], h->f[h->cur ^ 1], h->stream);
-        else
-            e = lbm::launch_step_split(h->phys, h->f[h->cur], h->f[h->cur ^ 1], h->rho, h->stream);
-        if (e != cudaSuccess) return cuda_fail(e, "lbm_step: launch");
-        h->cur ^= 1;
-        ++h->steps;
+    long t = 0;
+    auto plain = [&](long upto) -> lbm_status {
+        for (; t < upto; ++t) {
+            const cudaError_t e = launch_one(h, h->cur, h->stream);
+            if (e != cudaSuccess) return cuda_fail(e, "lbm_step: launch");
+            h->cur ^= 1;
+            ++h->steps;
+        }
+        return LBM_OK;
+    };
+    // long runs replay a captured graph of kGraphSteps steps (one launch per
+    // graph instead of one or two per step); the first steps run plainly, so
+    // that every kernel has been launched once before the capture
+    if (h->use_graphs && h->graph_state >= 0 && n_steps >= 2 * kGraphSteps + 2) {
+        lbm_status st = plain(h->cur == 1 ? 1 : 2);
+        if (st != LBM_OK) return st;
+        if (h->graph_state == 0) h->graph_state = build_graph(h) ? 1 : -1;
+        if (h->graph_state == 1) {
+            for (; n_steps - t >= kGraphSteps; t += kGraphSteps) {
+                const cudaError_t e = cudaGraphLaunch(h->graph, h->stream);
+                if (e != cudaSuccess) return cuda_fail(e, "lbm_step: graph launch");
+                h->steps += kGraphSteps;
+            }
+        }
     }
-    return LBM_OK;
+    return plain(n_steps);
 }
 
 lbm_status lbm_step_timed(lbm_lattice *h, long n_steps, double kernel_ms[4], long launches[4],

@@ -318,3 +318,20 @@ def test_fused_f32_against_oracle(gpu_lib, name, shape, kw):
     lat.close()
     assert np.max(np.abs(ga - a) / a) < 2e-6 and np.max(np.abs(gb - b) / b) < 2e-6
     assert np.max(np.abs(guF - uF)) < 2e-7
+
+
+@pytest.mark.parametrize("storage,shape", [("f32", (16, 12, 64)), ("f64", (6, 5, 7))])
+def test_graph_replay_is_bitwise(gpu_lib, monkeypatch, storage, shape):
+    """Long lbm_step runs replay a captured CUDA graph of the same launches;
+    the state equals plain launches bit for bit (odd step counts, a run that
+    starts from the second copy)."""
+    r1, r2, u = wl.random_state(shape, seed=21, u_max=0.02)
+    out = {}
+    for graphs in ("1", "0"):
+        monkeypatch.setenv("LBM_GRAPHS", graphs)
+        lat = gpu_run(shape, r1, r2, u, 1, storage=storage, tau=(0.9, 1.1), G12=-1.2)
+        lat.step(101)
+        lat.step(40)
+        out[graphs] = lat.get_populations()
+        lat.close()
+    assert np.array_equal(out["1"], out["0"])
