@@ -164,7 +164,10 @@ lbm_status lbm_set_populations(lbm_lattice *h, const double *in, int on_device);
 
 /* Raw state (the storage-format populations) for fast checkpoints:
  * lbm_state_bytes gives the size; get/set copy it to or from a
- * caller device buffer of at least that many bytes. */
+ * caller device buffer of at least that many bytes.  Layout: population i
+ * of component a at cell c (x fastest) is element 2 (i N + c) + a in the
+ * storage type (the two components of a direction side by side); the values
+ * are the post-collision populations at their origin cell. */
 lbm_status lbm_state_bytes(const lbm_lattice *h, size_t *bytes);
 lbm_status lbm_get_state(lbm_lattice *h, void *dev_buf, size_t bytes);
 lbm_status lbm_set_state(lbm_lattice *h, const void *dev_buf, size_t bytes);

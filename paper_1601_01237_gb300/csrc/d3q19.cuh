@@ -52,7 +52,17 @@ __host__ __device__ constexpr int k36(int i) { return i == 0 ? 12 : (i < 7 ? 2 :
 // ---------------------------------------------------------------------------
 // Storage formats.  R = arithmetic type, T = stored type.  The *_DEV formats
 // keep d_i = f_i - w_i rho0 in 16 bits.
+//
+// Population layout: direction-major, x fastest, with the two components of a
+// cell side by side: f^a_i(cell) is element 2 (i N + cell) + a.  A pull gather
+// fetches both components of a direction with one vector load (8 bytes in
+// FP32) and a collision stores them with one vector store.
 enum StorageKind { ST_F64 = 0, ST_F32 = 1, ST_F16_DEV = 2, ST_BF16_DEV = 3 };
+
+__host__ __device__ __forceinline__ long long pair_index(int i, long long cell, long long N)
+{
+    return 2 * ((long long)i * N + cell);
+}
 
 template <int S> struct Store;
 
@@ -61,24 +71,55 @@ template <> struct Store<ST_F64> {
     using R = double;
     __device__ static __forceinline__ R load(const T *p, R) { return __ldg(p); }
     __device__ static __forceinline__ void store(T *p, R v, R) { *p = v; }
+    __device__ static __forceinline__ void load2(const T *p, R, R &a, R &b)
+    {
+        const double2 v = __ldg(reinterpret_cast<const double2 *>(p));
+        a = v.x; b = v.y;
+    }
+    __device__ static __forceinline__ void store2(T *p, R a, R b, R) { *reinterpret_cast<double2 *>(p) = make_double2(a, b); }
 };
 template <> struct Store<ST_F32> {
     using T = float;
     using R = float;
     __device__ static __forceinline__ R load(const T *p, R) { return __ldg(p); }
     __device__ static __forceinline__ void store(T *p, R v, R) { *p = v; }
+    __device__ static __forceinline__ void load2(const T *p, R, R &a, R &b)
+    {
+        const float2 v = __ldg(reinterpret_cast<const float2 *>(p));
+        a = v.x; b = v.y;
+    }
+    __device__ static __forceinline__ void store2(T *p, R a, R b, R) { *reinterpret_cast<float2 *>(p) = make_float2(a, b); }
 };
 template <> struct Store<ST_F16_DEV> {
     using T = __half;
     using R = float;
     __device__ static __forceinline__ R load(const T *p, R ref) { return __half2float(__ldg(p)) + ref; }
     __device__ static __forceinline__ void store(T *p, R v, R ref) { *p = __float2half_rn(v - ref); }
+    __device__ static __forceinline__ void load2(const T *p, R ref, R &a, R &b)
+    {
+        const __half2 v = __ldg(reinterpret_cast<const __half2 *>(p));
+        a = __low2float(v) + ref; b = __high2float(v) + ref;
+    }
+    __device__ static __forceinline__ void store2(T *p, R a, R b, R ref)
+    {
+        *reinterpret_cast<__half2 *>(p) = __halves2half2(__float2half_rn(a - ref), __float2half_rn(b - ref));
+    }
 };
 template <> struct Store<ST_BF16_DEV> {
     using T = __nv_bfloat16;
     using R = float;
     __device__ static __forceinline__ R load(const T *p, R ref) { return __bfloat162float(__ldg(p)) + ref; }
     __device__ static __forceinline__ void store(T *p, R v, R ref) { *p = __float2bfloat16_rn(v - ref); }
+    __device__ static __forceinline__ void load2(const T *p, R ref, R &a, R &b)
+    {
+        const __nv_bfloat162 v = __ldg(reinterpret_cast<const __nv_bfloat162 *>(p));
+        a = __low2float(v) + ref; b = __high2float(v) + ref;
+    }
+    __device__ static __forceinline__ void store2(T *p, R a, R b, R ref)
+    {
+        *reinterpret_cast<__nv_bfloat162 *>(p) =
+            __halves2bfloat162(__float2bfloat16_rn(a - ref), __float2bfloat16_rn(b - ref));
+    }
 };
 
 // ---------------------------------------------------------------------------

@@ -96,8 +96,7 @@ __device__ __forceinline__ void adj_half(const typename Store<S>::T *__restrict_
 #pragma unroll
     for (int i = 0; i < Q; ++i) {
         const bool wall = (cz(i) == 1 && n.zlo) || (cz(i) == -1 && n.zhi);
-        const long long idx = wall ? (long long)(a * Q + opp(i)) * N + n.cell
-                                   : (long long)(a * Q + i) * N + at(n, -cx(i), -cy(i), -cz(i));
+        const long long idx = (wall ? pair_index(opp(i), n.cell, N) : pair_index(i, at(n, -cx(i), -cy(i), -cz(i)), N)) + a;
         fa[i] = Store<S>::load(f + idx, w<R>(i) * p.rho0);
     }
     R ra = 0, jx = 0, jy = 0, jz = 0;

@@ -64,18 +64,12 @@ __device__ __forceinline__ void gather(const typename Store<S>::T *__restrict__ 
 {
     using R = typename Store<S>::R;
 #pragma unroll
-    for (int a = 0; a < 2; ++a) {
-#pragma unroll
-        for (int i = 0; i < Q; ++i) {
-            const R ref = w<R>(i) * p.rho0;
-            const bool wall = (cz(i) == 1 && n.zlo_wall) || (cz(i) == -1 && n.zhi_wall);
-            long long idx;
-            if (wall)
-                idx = (long long)(a * Q + opp(i)) * p.N + n.cell;
-            else
-                idx = (long long)(a * Q + i) * p.N + n.zo[1 - cz(i)] + n.yo[1 - cy(i)] + n.xo[1 - cx(i)];
-            fa[a][i] = Store<S>::load(f + idx, ref);
-        }
+    for (int i = 0; i < Q; ++i) {
+        const R ref = w<R>(i) * p.rho0;
+        const bool wall = (cz(i) == 1 && n.zlo_wall) || (cz(i) == -1 && n.zhi_wall);
+        const long long idx = wall ? pair_index(opp(i), n.cell, p.N)
+                                   : pair_index(i, n.zo[1 - cz(i)] + n.yo[1 - cy(i)] + n.xo[1 - cx(i)], p.N);
+        Store<S>::load2(f + idx, ref, fa[0][i], fa[1][i]);
     }
 }
 
@@ -178,10 +172,7 @@ k_collide(const typename Store<S>::T *__restrict__ fin, typename Store<S>::T *__
     collide<R, REG>(fa[0], r1, ux, uy, uz, g1x, g1y, g1z, p.omega[0]);
     collide<R, REG>(fa[1], r2, ux, uy, uz, g2x, g2y, g2z, p.omega[1]);
 #pragma unroll
-    for (int a = 0; a < 2; ++a)
-#pragma unroll
-        for (int i = 0; i < Q; ++i)
-            Store<S>::store(fout + (long long)(a * Q + i) * p.N + n.cell, fa[a][i], w<R>(i) * p.rho0);
+    for (int i = 0; i < Q; ++i) Store<S>::store2(fout + pair_index(i, n.cell, p.N), fa[0][i], fa[1][i], w<R>(i) * p.rho0);
 }
 
 // Stored value s_j(y): the population that the gather of step 0 reads as
@@ -205,8 +196,8 @@ k_init_feq(const double *__restrict__ rho1, const double *__restrict__ rho2,
         const double usq = ux * ux + uy * uy + uz * uz;
         const double cu = cdot<double>(k, ux, uy, uz);
         const double P = 1.0 - 1.5 * usq + cu * (3.0 - 4.5 * usq) + 4.5 * cu * cu * (1.0 + cu);
-        Store<S>::store(f + (long long)j * p.N + n.cell, (R)(rho1[src] * wd(k) * P), w<R>(j) * p.rho0);
-        Store<S>::store(f + (long long)(Q + j) * p.N + n.cell, (R)(rho2[src] * wd(k) * P), w<R>(j) * p.rho0);
+        Store<S>::store2(f + pair_index(j, n.cell, p.N), (R)(rho1[src] * wd(k) * P), (R)(rho2[src] * wd(k) * P),
+                         w<R>(j) * p.rho0);
     }
 }
 
@@ -225,8 +216,8 @@ k_set_pop(const double *__restrict__ src, typename Store<S>::T *__restrict__ f,
             const bool wall = (cz(j) == -1 && n.zlo_wall) || (cz(j) == 1 && n.zhi_wall);
             const long long sc = wall ? n.cell : n.zo[1 + cz(j)] + n.yo[1 + cy(j)] + n.xo[1 + cx(j)];
             const int k = wall ? opp(j) : j;
-            Store<S>::store(f + (long long)(a * Q + j) * p.N + n.cell,
-                            (R)src[(long long)(a * Q + k) * p.N + sc], w<R>(j) * p.rho0);
+            Store<S>::store(f + pair_index(j, n.cell, p.N) + a, (R)src[(long long)(a * Q + k) * p.N + sc],
+                            w<R>(j) * p.rho0);
         }
 }
 

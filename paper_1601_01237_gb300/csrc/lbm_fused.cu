@@ -9,9 +9,10 @@
 // one-cell halo; those densities live in a ring of four shared-memory planes.
 // Iteration z:
 //   A. every thread pull-gathers its column's 38 populations at plane z+1
-//      (rho into the ring, momentum into a moment buffer, populations into a
-//      shared-memory stash) and, for the halo ring of plane z+2, 12 or 13 of
-//      the 38 populations of one halo cell (84 halo cells x 3 groups), summed
+//      (19 paired loads of both components; rho into the ring, momentum into
+//      a moment buffer, populations into a shared-memory stash) and, for the
+//      halo ring of plane z+2, 6 or 7 of the 19 directions of one halo cell
+//      (84 halo cells x 3 groups, both components per load), summed
 //      into fixed-order partial densities; the halo densities of plane z+1
 //      (partials gathered one iteration earlier) are completed in the ring.
 //      The side-column halo cells cost one scattered sector per load, so their
@@ -41,8 +42,8 @@ constexpr int kTX = 32;
 constexpr int kTY = 8;
 constexpr int kThreadsF = kTX * kTY;
 constexpr int kHalo = 2 * (kTX + 2) + 2 * kTY;   // perimeter cells of the (TX+2) x (TY+2) box
-constexpr int kGroups = 3;                        // halo populations split 13 + 13 + 12
-constexpr int kPer = 13;
+constexpr int kGroups = 3;                        // halo directions split 7 + 6 + 6 (both components each)
+constexpr int kPer = 14;
 constexpr int kLZmax = 64;                        // planes per CTA (large lattices)
 constexpr int kLZsmall = 8;                       // planes per CTA (small lattices)
 constexpr int Q2 = 2 * Q;
@@ -133,8 +134,7 @@ __device__ __forceinline__ void load_dir(const typename Store<S>::T *__restrict_
     int d;
     const int e = gather_elem<I>(pr, c, d);
     const unsigned idx = (unsigned)d * (unsigned)N + (unsigned)e;
-    v[I] = Store<S>::load(f + idx, w<R>(I) * rho0);
-    v[Q + I] = Store<S>::load(f + (size_t)Q * (size_t)N + idx, w<R>(I) * rho0);
+    Store<S>::load2(f + 2 * (size_t)idx, w<R>(I) * rho0, v[I], v[Q + I]);
 }
 
 template <int S, int I>
@@ -171,31 +171,31 @@ __device__ __forceinline__ void sums(const R (&v)[Q2], R &r1, R &r2, R &jx, R &j
     r1 = s1; r2 = s2; jx = ax; jy = ay; jz = az;
 }
 
-// Partial gather of one halo cell: the populations q in [Q0, Q1) of the 38
-// (component q / 19, direction q % 19), summed per component.
-template <int S, int QQ, int Q1>
+// Partial gather of one halo cell: directions [D, D1) of both components
+// (one paired load each), summed per component.
+template <int S, int D, int D1>
 struct HaloRange {
     __device__ __forceinline__ static void load(const typename Store<S>::T *__restrict__ f, long long N,
                                                 typename Store<S>::R rho0, const PlaneRef &pr, const Col &c,
                                                 typename Store<S>::R (&v)[kPer], int k)
     {
         using R = typename Store<S>::R;
-        constexpr int a = QQ / Q, i = QQ % Q;
         int d;
-        const int e = gather_elem<i>(pr, c, d);
+        const int e = gather_elem<D>(pr, c, d);
         const unsigned idx = (unsigned)d * (unsigned)N + (unsigned)e;
-        v[k] = Store<S>::load(f + (size_t)a * Q * (size_t)N + idx, w<R>(i) * rho0);
-        HaloRange<S, QQ + 1, Q1>::load(f, N, rho0, pr, c, v, k + 1);
+        Store<S>::load2(f + 2 * (size_t)idx, w<R>(D) * rho0, v[k], v[k + 1]);
+        HaloRange<S, D + 1, D1>::load(f, N, rho0, pr, c, v, k + 2);
     }
     __device__ __forceinline__ static void sum(const typename Store<S>::R (&v)[kPer], int k,
                                                typename Store<S>::R &s0, typename Store<S>::R &s1)
     {
-        if (QQ / Q == 0) s0 += v[k]; else s1 += v[k];
-        HaloRange<S, QQ + 1, Q1>::sum(v, k + 1, s0, s1);
+        s0 += v[k];
+        s1 += v[k + 1];
+        HaloRange<S, D + 1, D1>::sum(v, k + 2, s0, s1);
     }
 };
-template <int S, int Q1>
-struct HaloRange<S, Q1, Q1> {
+template <int S, int D1>
+struct HaloRange<S, D1, D1> {
     __device__ __forceinline__ static void load(const typename Store<S>::T *__restrict__, long long,
                                                 typename Store<S>::R, const PlaneRef &, const Col &,
                                                 typename Store<S>::R (&)[kPer], int) {}
@@ -207,9 +207,9 @@ template <int S>
 __device__ __forceinline__ void halo_load(const typename Store<S>::T *__restrict__ f, const Phys<typename Store<S>::R> &p,
                                           const PlaneRef &pr, const Col &c, int g, typename Store<S>::R (&v)[kPer])
 {
-    if (g == 0) HaloRange<S, 0, kPer>::load(f, p.N, p.rho0, pr, c, v, 0);
-    else if (g == 1) HaloRange<S, kPer, 2 * kPer>::load(f, p.N, p.rho0, pr, c, v, 0);
-    else HaloRange<S, 2 * kPer, Q2>::load(f, p.N, p.rho0, pr, c, v, 0);
+    if (g == 0) HaloRange<S, 0, 7>::load(f, p.N, p.rho0, pr, c, v, 0);
+    else if (g == 1) HaloRange<S, 7, 13>::load(f, p.N, p.rho0, pr, c, v, 0);
+    else HaloRange<S, 13, Q>::load(f, p.N, p.rho0, pr, c, v, 0);
 }
 
 template <int S>
@@ -218,9 +218,9 @@ __device__ __forceinline__ void halo_sum(const typename Store<S>::R (&v)[kPer], 
 {
     s0 = 0;
     s1 = 0;
-    if (g == 0) HaloRange<S, 0, kPer>::sum(v, 0, s0, s1);
-    else if (g == 1) HaloRange<S, kPer, 2 * kPer>::sum(v, 0, s0, s1);
-    else HaloRange<S, 2 * kPer, Q2>::sum(v, 0, s0, s1);
+    if (g == 0) HaloRange<S, 0, 7>::sum(v, 0, s0, s1);
+    else if (g == 1) HaloRange<S, 7, 13>::sum(v, 0, s0, s1);
+    else HaloRange<S, 13, Q>::sum(v, 0, s0, s1);
 }
 
 // Collision of both components at the thread's interior cell of plane z (the
@@ -271,8 +271,7 @@ __device__ __forceinline__ void collide_cell(typename Store<S>::T *__restrict__ 
     const R keep1 = R(1) - p.omega[0], keep2 = R(1) - p.omega[1];
     const R *s0 = &sm.stash[st][0][tid];
     const R rq1 = r1 / R(36), rq2 = r2 / R(36);   // rho w_i = (rho / 36) k_i
-    typename Store<S>::T *o = fout + cell;                     // component 1
-    typename Store<S>::T *o2 = fout + (size_t)Q * (size_t)p.N + cell;   // component 2
+    typename Store<S>::T *o = fout + 2 * cell;   // (component 1, component 2) of direction 0
     const unsigned N32 = (unsigned)p.N;
     const R ref0 = p.rho0;
 
@@ -312,8 +311,7 @@ __device__ __forceinline__ void collide_cell(typename Store<S>::T *__restrict__ 
             o1 = rq1 * R(12) * A1 - keep1 * R(1.5) * t1;
             o2v = rq2 * R(12) * A2 - keep2 * R(1.5) * t2;
         }
-        Store<S>::store(o, o1, w0 * ref0);
-        Store<S>::store(o2, o2v, w0 * ref0);
+        Store<S>::store2(o, o1, o2v, w0 * ref0);
     }
 #pragma unroll
     for (int i = 1; i < Q; i += 2) {
@@ -351,11 +349,9 @@ __device__ __forceinline__ void collide_cell(typename Store<S>::T *__restrict__ 
             o2m = rw2 * (E2 - O2) + n2;
         }
         const R ref = w<R>(i) * ref0;
-        const unsigned ip = (unsigned)i * N32, im = (unsigned)(i + 1) * N32;
-        Store<S>::store(o + ip, o1p, ref);
-        Store<S>::store(o + im, o1m, ref);
-        Store<S>::store(o2 + ip, o2p, ref);
-        Store<S>::store(o2 + im, o2m, ref);
+        const size_t ip = 2 * (size_t)((unsigned)i * N32), im = 2 * (size_t)((unsigned)(i + 1) * N32);
+        Store<S>::store2(o + ip, o1p, o2p, ref);
+        Store<S>::store2(o + im, o1m, o2m, ref);
     }
 }
 
@@ -606,7 +602,7 @@ cudaError_t fused_t(const HostPhys &h, const void *fin, void *fout, cudaStream_t
 
 bool fused_supported(const HostPhys &p)
 {
-    // 32-bit element offsets inside one component's 19 population arrays
+    // 32-bit offsets of the cell pairs inside the 19 direction arrays
     return p.storage != ST_F64 && (long long)Q * p.N < (1LL << 32) &&
            (long long)((p.nx + kTX - 1) / kTX) * ((p.ny + kTY - 1) / kTY) < (1LL << 31) &&
            (p.nz + 7) / 8 < 65536;
