@@ -278,7 +278,7 @@ k_moments(const typename Store<S>::T *__restrict__ f, const typename Store<S>::R
 constexpr int kReduceBlocks = 1216;   // 152 SMs x 8
 
 template <int S>
-__global__ void __launch_bounds__(kThreads)
+__global__ void __launch_bounds__(kThreads, 2)
 k_reduce(const typename Store<S>::T *__restrict__ f, const typename Store<S>::R *__restrict__ rho,
          double *__restrict__ partials, Phys<typename Store<S>::R> p)
 {

@@ -9,8 +9,9 @@
 // one-cell halo; those densities live in a ring of four shared-memory planes.
 // Iteration z:
 //   A. every thread pull-gathers its column's 38 populations at plane z+1
-//      (19 paired loads of both components; rho into the ring, momentum into
-//      a moment buffer, populations into a shared-memory stash) and, for the
+//      (19 paired loads of both components; the (rho^1, rho^2) pair into the
+//      ring, momentum into a moment buffer, the (f^1_i, f^2_i) pairs into a
+//      shared-memory stash: one 8-byte shared access per pair) and, for the
 //      halo ring of plane z+2, 6 or 7 of the 19 directions of one halo cell
 //      (84 halo cells x 3 groups, both components per load), summed
 //      into fixed-order partial densities; the halo densities of plane z+1
@@ -51,10 +52,10 @@ static_assert(kGroups * kHalo <= kThreadsF, "one halo group per thread");
 
 template <class R>
 struct FusedSmem {
-    R ring[4][2][kTY + 2][kTX + 2];        // rho^1, rho^2 of planes z-1 .. z+2 (+ halo)
+    float2 ring[4][kTY + 2][kTX + 2];      // (rho^1, rho^2) of planes z-1 .. z+2 (+ halo)
     R hpart[2][kGroups][2][kHalo];         // halo partial densities of the next two planes
     R mom[2][3][kThreadsF];                // sum_a sum_i c_i f_i of the stashed planes
-    R stash[2][Q2][kThreadsF];             // pre-collision populations of planes z, z+1
+    float2 stash[2][Q][kThreadsF];         // pre-collision (f^1_i, f^2_i) of planes z, z+1
 };
 
 // A lattice column (x, y) with its wrapped neighbour offsets.
@@ -234,8 +235,8 @@ __device__ __forceinline__ void collide_cell(typename Store<S>::T *__restrict__ 
     using R = typename Store<S>::R;
     const int tid = threadIdx.x;
     const int lx = tid % kTX + 1, ly = tid / kTX + 1;
-    const R r1 = sm.ring[sl_c][0][ly][lx];
-    const R r2 = sm.ring[sl_c][1][ly][lx];
+    const float2 rr = sm.ring[sl_c][ly][lx];
+    const R r1 = rr.x, r2 = rr.y;
     if (rho_out) {   // pre-collision densities of this step (reverse-mode replay)
         rho_out[cell] = r1;
         rho_out[p.N + cell] = r2;
@@ -243,19 +244,18 @@ __device__ __forceinline__ void collide_cell(typename Store<S>::T *__restrict__ 
     const R inv = R(1) / (r1 + r2);
     const R ux = sm.mom[st][0][tid] * inv, uy = sm.mom[st][1][tid] * inv, uz = sm.mom[st][2][tid] * inv;
     // S^b = sum_{i != 0} w_i c_i rho^b(x + c_i)  (Eq. 7; ghost planes carry Eq. 13's rho')
-    R Sb[2][3];
+    R Sb[2][3] = {{0, 0, 0}, {0, 0, 0}};
 #pragma unroll
-    for (int b = 0; b < 2; ++b) {
-        R sx = 0, sy = 0, sz = 0;
+    for (int i = 1; i < Q; ++i) {
+        const int sl = cz(i) == -1 ? sl_m : (cz(i) == 1 ? sl_p : sl_c);
+        const float2 rv = sm.ring[sl][ly + cy(i)][lx + cx(i)];
 #pragma unroll
-        for (int i = 1; i < Q; ++i) {
-            const int sl = cz(i) == -1 ? sl_m : (cz(i) == 1 ? sl_p : sl_c);
-            const R wr = w<R>(i) * sm.ring[sl][b][ly + cy(i)][lx + cx(i)];
-            if (cx(i) == 1) sx += wr; else if (cx(i) == -1) sx -= wr;
-            if (cy(i) == 1) sy += wr; else if (cy(i) == -1) sy -= wr;
-            if (cz(i) == 1) sz += wr; else if (cz(i) == -1) sz -= wr;
+        for (int b = 0; b < 2; ++b) {
+            const R wr = w<R>(i) * (b == 0 ? rv.x : rv.y);
+            if (cx(i) == 1) Sb[b][0] += wr; else if (cx(i) == -1) Sb[b][0] -= wr;
+            if (cy(i) == 1) Sb[b][1] += wr; else if (cy(i) == -1) Sb[b][1] -= wr;
+            if (cz(i) == 1) Sb[b][2] += wr; else if (cz(i) == -1) Sb[b][2] -= wr;
         }
-        Sb[b][0] = sx; Sb[b][1] = sy; Sb[b][2] = sz;
     }
     // g^a = sum_b F^{ab} / rho^a + g_ext = G^{ab} S^b + g_ext
     const R v1x = ux + p.G12 * Sb[1][0] + p.gext[0], v1y = uy + p.G12 * Sb[1][1] + p.gext[1],
@@ -269,7 +269,7 @@ __device__ __forceinline__ void collide_cell(typename Store<S>::T *__restrict__ 
     const R A1 = R(1) - R(1.5) * v1sq, B1 = R(3) - R(4.5) * v1sq;
     const R A2 = R(1) - R(1.5) * v2sq, B2 = R(3) - R(4.5) * v2sq;
     const R keep1 = R(1) - p.omega[0], keep2 = R(1) - p.omega[1];
-    const R *s0 = &sm.stash[st][0][tid];
+    const float2 *s0 = &sm.stash[st][0][tid];
     const R rq1 = r1 / R(36), rq2 = r2 / R(36);   // rho w_i = (rho / 36) k_i
     typename Store<S>::T *o = fout + 2 * cell;   // (component 1, component 2) of direction 0
     const unsigned N32 = (unsigned)p.N;
@@ -282,7 +282,8 @@ __device__ __forceinline__ void collide_cell(typename Store<S>::T *__restrict__ 
         for (int k = 0; k < 6; ++k) { P1[k] = 0; P2[k] = 0; }
 #pragma unroll
         for (int i = 1; i < Q; ++i) {
-            const R fa = s0[i * kThreadsF], fb = s0[(Q + i) * kThreadsF];
+            const float2 fp = s0[i * kThreadsF];
+            const R fa = fp.x, fb = fp.y;
             if (cx(i)) { P1[0] += fa; P2[0] += fb; }
             if (cy(i)) { P1[1] += fa; P2[1] += fb; }
             if (cz(i)) { P1[2] += fa; P2[2] += fb; }
@@ -305,8 +306,9 @@ __device__ __forceinline__ void collide_cell(typename Store<S>::T *__restrict__ 
         const R w0 = w<R>(0);
         R o1, o2v;
         if (!REG) {
-            o1 = rq1 * R(12) * (A1 - keep1 * Au) + keep1 * s0[0];
-            o2v = rq2 * R(12) * (A2 - keep2 * Au) + keep2 * s0[Q * kThreadsF];
+            const float2 f0 = s0[0];
+            o1 = rq1 * R(12) * (A1 - keep1 * Au) + keep1 * f0.x;
+            o2v = rq2 * R(12) * (A2 - keep2 * Au) + keep2 * f0.y;
         } else {
             o1 = rq1 * R(12) * A1 - keep1 * R(1.5) * t1;
             o2v = rq2 * R(12) * A2 - keep2 * R(1.5) * t2;
@@ -328,10 +330,11 @@ __device__ __forceinline__ void collide_cell(typename Store<S>::T *__restrict__ 
             const R Eu = Au + R(4.5) * cu * cu, Ou = cu * (Bu + R(4.5) * cu * cu);
             const R P1e = rw1 * (E1 - keep1 * Eu), M1 = rw1 * (O1 - keep1 * Ou);
             const R P2e = rw2 * (E2 - keep2 * Eu), M2 = rw2 * (O2 - keep2 * Ou);
-            o1p = P1e + M1 + keep1 * s0[i * kThreadsF];
-            o1m = P1e - M1 + keep1 * s0[(i + 1) * kThreadsF];
-            o2p = P2e + M2 + keep2 * s0[(Q + i) * kThreadsF];
-            o2m = P2e - M2 + keep2 * s0[(Q + i + 1) * kThreadsF];
+            const float2 fp = s0[i * kThreadsF], fm = s0[(i + 1) * kThreadsF];
+            o1p = P1e + M1 + keep1 * fp.x;
+            o1m = P1e - M1 + keep1 * fm.x;
+            o2p = P2e + M2 + keep2 * fp.y;
+            o2m = P2e - M2 + keep2 * fm.y;
         } else {
             // f* = f^eq(v) + keep (k_i / 8) (c c : Pi - tr(Pi) / 3)
             R cc1 = 0, cc2 = 0;
@@ -375,13 +378,12 @@ __device__ __forceinline__ void interior_plane(const typename Store<S>::T *__res
             r1 = a1; r2 = a2;
             if (st >= 0) {
 #pragma unroll
-                for (int k = 0; k < Q2; ++k) sm.stash[st][k][tid] = v[k];
+                for (int k = 0; k < Q; ++k) sm.stash[st][k][tid] = make_float2(v[k], v[Q + k]);
                 sm.mom[st][0][tid] = jx; sm.mom[st][1][tid] = jy; sm.mom[st][2][tid] = jz;
             }
         }
     }
-    sm.ring[slot][0][ly][lx] = r1;
-    sm.ring[slot][1][ly][lx] = r2;
+    sm.ring[slot][ly][lx] = make_float2(r1, r2);
 }
 
 // Halo densities of a plane in ring slot `slot` from the partials of the
@@ -399,8 +401,7 @@ __device__ __forceinline__ void halo_combine(const Phys<R> &p, FusedSmem<R> &sm,
         r2 = sm.hpart[hs][0][1][h] + sm.hpart[hs][1][1][h] + sm.hpart[hs][2][1][h];
         if (pr.ghost) { r1 += p.rho_s[0]; r2 += p.rho_s[1]; }
     }
-    sm.ring[slot][0][hy][hx] = r1;
-    sm.ring[slot][1][hy][hx] = r2;
+    sm.ring[slot][hy][hx] = make_float2(r1, r2);
 }
 
 template <int S, bool REG, bool WALLZ, int LZ>
@@ -484,8 +485,7 @@ k_step_fused(const typename Store<S>::T *__restrict__ fin, typename Store<S>::T 
                 sums(hv, a1, a2, jx, jy, jz);
                 if (pr.ghost) { r1 += a1; r2 += a2; } else { r1 = a1; r2 = a2; }
             }
-            sm.ring[q - z0 + 1][0][hy][hx] = r1;
-            sm.ring[q - z0 + 1][1][hy][hx] = r2;
+            sm.ring[q - z0 + 1][hy][hx] = make_float2(r1, r2);
         }
     }
     {
