@@ -9,6 +9,8 @@ c1  3D droplets 128^3, FP32: Delta p vs 1/R fit (surface tension) per tau
 c2  spinodal mixture 256^3: FP32 / FP16-dev / BF16-dev, MLUPS, mass drift,
     interface measure <|rho1 - rho2|>
 c3  differentiation 96^3: loss, gradients (tied G, tau_1), adjoint/forward time
+s1  the static-droplet study: quasi-2D droplets (R = 8-24, side 5 R) at
+    tau = 0.7-3, BGK and regularized: surface tension per tau, spurious current
 c4  wall-bounded 512x512x384, regularized, mirror wetting (or --wall-model
     potential), no body force (or --gravity: tilted by 30 deg): MLUPS, droplet
     drift velocity, thin-film density, volume ratio
@@ -185,9 +187,50 @@ def run_c4(steps=None, shape=None, gravity=False, wall_model="mirror"):
             "max_uF": red["max_uF"]}
 
 
+def run_s1(steps=None, radii=(8, 12, 16, 24), taus=(0.7, 0.8, 1.0, 1.5, 2.0, 3.0),
+           collisions=("bgk", "regularized"), storage="f32"):
+    """The paper's static-droplet study (Sec. 3): quasi-2D droplets on square
+    periodic domains of side 5 R, the surface tension from Delta p = sigma / R
+    (Eq. 12) per tau, for BGK and the regularized operator, and the largest
+    spurious velocity.  G = -1.8, 1.0 / 0.03 start (coexistence)."""
+    steps = steps or 20000
+    G = wl.G_DROPLET
+    out = {"case": "s1", "steps": steps, "G_eq7": G, "storage": storage, "runs": {}}
+    for col in collisions:
+        for tau in taus:
+            Rs, dps, spur, diverged = [], [], [], []
+            for R0 in radii:
+                n = 5 * R0
+                shape = (1, n, n)
+                lat = Lattice(shape, storage=storage, tau=(tau, tau), G12=G, collision=col)
+                r1, r2 = wl.droplet(shape, R0)
+                lat.init_fields(r1, r2)
+                lat.step(steps)
+                try:
+                    red = lat.reduce()
+                except LBMError:
+                    diverged.append(R0)
+                    lat.close()
+                    continue
+                ctr = ((n - 1) / 2.0, (n - 1) / 2.0, 0.0)
+                _, _, dp = lat.pressure_jump(ctr, R0 / 2.0, R0 + 0.5 * R0)
+                st = lat.droplet_stats(0.5 * (1.0 + 0.03), origin=ctr)
+                lat.close()
+                Rs.append(dg.equivalent_radius(st["volume"], True))
+                dps.append(dp)
+                spur.append(red["max_uF"])
+            run = {"R": Rs, "delta_p": dps, "sigma_per_R": [d * r for d, r in zip(dps, Rs)],
+                   "spurious_max_uF": spur, "diverged_R0": diverged}
+            if len(Rs) >= 2:
+                sigma, icpt, res = dg.laplace_fit(Rs, dps, dims=2)
+                run.update(sigma=sigma, intercept=icpt, max_residual=res)
+            out["runs"]["%s/%g" % (col, tau)] = run
+    return out
+
+
 def main():
     ap = argparse.ArgumentParser()
-    ap.add_argument("case", choices=["c0", "c1", "c2", "c3", "c4"])
+    ap.add_argument("case", choices=["c0", "c1", "c2", "c3", "c4", "s1"])
     ap.add_argument("--steps", type=int, default=None)
     ap.add_argument("--shape", type=int, nargs=3, default=None, help="nz ny nx (c1, c4)")
     ap.add_argument("--gravity", action="store_true", help="c4: tilted gravity")
@@ -200,7 +243,7 @@ def main():
     elif args.case == "c1":
         r = run_c1(args.steps, radii=args.radii, taus=args.taus, shape=args.shape)
     else:
-        r = {"c0": run_c0, "c2": run_c2, "c3": run_c3}[args.case](args.steps)
+        r = {"c0": run_c0, "c2": run_c2, "c3": run_c3, "s1": run_s1}[args.case](args.steps)
     print(json.dumps(r, default=float))
 
 
