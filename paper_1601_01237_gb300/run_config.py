@@ -198,7 +198,7 @@ def run_s1(steps=None, radii=(8, 12, 16, 24), taus=(0.7, 0.8, 1.0, 1.5, 2.0, 3.0
     out = {"case": "s1", "steps": steps, "G_eq7": G, "storage": storage, "runs": {}}
     for col in collisions:
         for tau in taus:
-            Rs, dps, spur, diverged = [], [], [], []
+            Rs, dps, spur, diverged, dissolved = [], [], [], [], []
             for R0 in radii:
                 n = 5 * R0
                 shape = (1, n, n)
@@ -213,15 +213,19 @@ def run_s1(steps=None, radii=(8, 12, 16, 24), taus=(0.7, 0.8, 1.0, 1.5, 2.0, 3.0
                     lat.close()
                     continue
                 ctr = ((n - 1) / 2.0, (n - 1) / 2.0, 0.0)
-                _, _, dp = lat.pressure_jump(ctr, R0 / 2.0, R0 + 0.5 * R0)
                 st = lat.droplet_stats(0.5 * (1.0 + 0.03), origin=ctr)
+                if st["volume"] < 4:   # the droplet dissolved
+                    dissolved.append(R0)
+                    lat.close()
+                    continue
+                _, _, dp = lat.pressure_jump(ctr, R0 / 2.0, R0 + 0.5 * R0)
                 lat.close()
                 Rs.append(dg.equivalent_radius(st["volume"], True))
                 dps.append(dp)
                 spur.append(red["max_uF"])
             run = {"R": Rs, "delta_p": dps, "sigma_per_R": [d * r for d, r in zip(dps, Rs)],
-                   "spurious_max_uF": spur, "diverged_R0": diverged}
-            if len(Rs) >= 2:
+                   "spurious_max_uF": spur, "diverged_R0": diverged, "dissolved_R0": dissolved}
+            if len(Rs) >= 2 and all(np.isfinite(dps)):
                 sigma, icpt, res = dg.laplace_fit(Rs, dps, dims=2)
                 run.update(sigma=sigma, intercept=icpt, max_residual=res)
             out["runs"]["%s/%g" % (col, tau)] = run
