@@ -186,7 +186,10 @@ lbm_status lbm_sync(lbm_lattice *h);
  *
  * lbm_record runs n_steps >= 1 forward exactly as lbm_step does and keeps the
  * raw state every ckpt_every >= 1 steps (a library-owned checkpoint store of
- * ceil(n_steps / ckpt_every) states, replaced by the next lbm_record).
+ * ceil(n_steps / ckpt_every) states), and reserves the working memory of the
+ * reverse pass (adjoint fields of 2 x 19 values per cell, one checkpoint
+ * segment of states and of their densities); both are held until the next
+ * lbm_record or lbm_destroy, so that lbm_adjoint allocates nothing.
  * Synchronizes.  Errors: LBM_EINVAL, LBM_ENOMEM, LBM_ECUDA. */
 lbm_status lbm_record(lbm_lattice *h, long n_steps, int ckpt_every);
 
@@ -198,9 +201,9 @@ lbm_status lbm_record(lbm_lattice *h, long n_steps, int ckpt_every);
  * dL/dG^{12}, dL/dG^{21}, dL/dtau_1, dL/dtau_2 (for a tied G^{12} = G^{21},
  * sum the first two).  All array pointers are host (on_device = 0) or device
  * (on_device = 1) memory.  The forward states of each checkpoint segment are
- * recomputed (time-checkpointing); working memory (adjoint fields, one
- * segment of states and their densities) is allocated for the call and
- * released.  Leaves the lattice state at the end of the recorded run.
+ * recomputed (time-checkpointing) in the working memory that lbm_record
+ * reserved; the call may be repeated with other loss gradients.  Leaves the
+ * lattice state at the end of the recorded run.
  * Synchronizes.  Errors: LBM_EINVAL (no recording), LBM_ENOTSUP
  * (initial-density gradient requested for a recording that did not start at
  * rest from lbm_init_fields, or a lattice of more than 2^32 cells),

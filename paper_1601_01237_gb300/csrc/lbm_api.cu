@@ -35,6 +35,11 @@ struct lbm_lattice {
     int rec_every;
     long rec_nck;
     int rec_at_rest;     // the recording started at rest right after lbm_init_fields
+    // working memory of the reverse pass, reserved by lbm_record: lambda_loc
+    // (two, ping-pong), a, D (two), one segment of states and of their
+    // densities, gradient staging, partials
+    void *ws_lam, *ws_lam_loc, *ws_a, *ws_d, *ws_seg, *ws_rseg, *ws_io;
+    double *ws_part;
     // CUDA graph of kGraphSteps steps from copy 0 (replayed by lbm_step)
     cudaGraphExec_t graph;
     int graph_state;     // 0 not built, 1 ready, -1 not available (plain launches)
@@ -209,6 +214,18 @@ lbm_status lbm_create(const lbm_params *pp, lbm_lattice **out)
     return LBM_OK;
 }
 
+namespace {
+
+void free_workspace(lbm_lattice *h)
+{
+    void *bufs[8] = {h->ws_lam, h->ws_lam_loc, h->ws_a, h->ws_d, h->ws_seg, h->ws_rseg, h->ws_io, h->ws_part};
+    for (void *b : bufs) cudaFree(b);
+    h->ws_lam = h->ws_lam_loc = h->ws_a = h->ws_d = h->ws_seg = h->ws_rseg = h->ws_io = nullptr;
+    h->ws_part = nullptr;
+}
+
+}  // namespace
+
 void lbm_destroy(lbm_lattice *h)
 {
     if (!h) return;
@@ -218,6 +235,7 @@ void lbm_destroy(lbm_lattice *h)
     cudaFree(h->f[1]);
     cudaFree(h->rho);
     cudaFree(h->ckpt);
+    free_workspace(h);
     cudaFree(h->partials);
     if (h->graph) cudaGraphExecDestroy(h->graph);
     if (h->partials_h) cudaFreeHost(h->partials_h);
@@ -579,7 +597,21 @@ lbm_status lbm_record(lbm_lattice *h, long n_steps, int ckpt_every)
     cudaFree(h->ckpt);
     h->ckpt = nullptr;
     h->rec_steps = 0;
+    free_workspace(h);
     CK(cudaMalloc(&h->ckpt, sb * (size_t)nck), "lbm_record: checkpoint store");
+    {
+        const size_t N = (size_t)h->phys.N;
+        const size_t rb = lbm::real_bytes(h->phys.storage);
+        const size_t E = (size_t)(ckpt_every < n_steps ? ckpt_every : n_steps);
+        CK(cudaMalloc(&h->ws_lam, rb * 2 * lbm::Q * N), "lbm_record: reverse-pass lambda");
+        CK(cudaMalloc(&h->ws_lam_loc, rb * 2 * lbm::Q * N), "lbm_record: reverse-pass lambda_loc");
+        CK(cudaMalloc(&h->ws_a, rb * 6 * N), "lbm_record: reverse-pass a");
+        CK(cudaMalloc(&h->ws_d, rb * 4 * N), "lbm_record: reverse-pass D");
+        CK(cudaMalloc(&h->ws_seg, sb * (E + 1)), "lbm_record: reverse-pass segment states");
+        CK(cudaMalloc(&h->ws_rseg, rb * 2 * N * E), "lbm_record: reverse-pass segment densities");
+        CK(cudaMalloc(&h->ws_io, sizeof(double) * 2 * N), "lbm_record: reverse-pass staging");
+        CK(cudaMalloc((void **)&h->ws_part, sizeof(double) * 4 * lbm::adjoint_blocks()), "lbm_record: partials");
+    }
     h->rec_at_rest = h->init_at_rest && h->steps == 0;
     for (long t = 0; t < n_steps; ++t) {
         if (t % ckpt_every == 0)
@@ -612,32 +644,22 @@ lbm_status lbm_adjoint(lbm_lattice *h, const double *dL_drho1, const double *dL_
     lbm_state_bytes(h, &sb);
     const long E = h->rec_every;
     const int nb = lbm::adjoint_blocks();
-    // working memory: lambda_loc (two, ping-pong), a, D (two), one segment of
-    // states and of their densities, gradient staging, partials
-    void *lam = nullptr, *lam_loc = nullptr, *abuf = nullptr, *seg = nullptr, *io = nullptr, *dbuf = nullptr;
-    void *rseg = nullptr;
-    double *part = nullptr;
+    // working memory reserved by lbm_record
+    void *lam = h->ws_lam, *lam_loc = h->ws_lam_loc, *abuf = h->ws_a, *seg = h->ws_seg, *io = h->ws_io;
+    void *dbuf = h->ws_d, *rseg = h->ws_rseg;
+    double *part = h->ws_part;
+    if (!lam || !lam_loc || !abuf || !seg || !io || !dbuf || !rseg || !part)
+        return fail(LBM_EINVAL, "lbm_adjoint: the reverse pass's working memory is missing (call lbm_record)");
     std::vector<double> parth((size_t)nb * 4);
     cudaError_t e;
     lbm_status st = LBM_OK;
-    auto cleanup = [&]() {
-        cudaFree(lam); cudaFree(lam_loc); cudaFree(abuf); cudaFree(seg); cudaFree(io); cudaFree(part); cudaFree(dbuf);
-        cudaFree(rseg);
-    };
+    auto cleanup = [&]() {};
 #define CKA(expr, where)                                  \
     do {                                                  \
         e = (expr);                                       \
         if (e != cudaSuccess) { st = cuda_fail(e, where); cleanup(); return st; } \
     } while (0)
-    CKA(cudaMalloc(&lam, rb * 2 * lbm::Q * N), "lbm_adjoint: lambda");
-    CKA(cudaMalloc(&lam_loc, rb * 2 * lbm::Q * N), "lbm_adjoint: lambda_loc");
-    CKA(cudaMalloc(&abuf, rb * 6 * N), "lbm_adjoint: a");
-    CKA(cudaMalloc(&dbuf, rb * 4 * N), "lbm_adjoint: D");
     CKA(cudaMemsetAsync(dbuf, 0, rb * 4 * N, h->stream), "lbm_adjoint: clear D");
-    CKA(cudaMalloc(&seg, sb * (size_t)(E + 1)), "lbm_adjoint: segment states");
-    CKA(cudaMalloc(&rseg, rb * 2 * N * (size_t)E), "lbm_adjoint: segment densities");
-    CKA(cudaMalloc((void **)&part, sizeof(double) * 4 * nb), "lbm_adjoint: partials");
-    CKA(cudaMalloc(&io, sizeof(double) * 2 * N), "lbm_adjoint: staging");
     CKA(cudaMemsetAsync(part, 0, sizeof(double) * 4 * nb, h->stream), "lbm_adjoint: clear");
     double *io1 = (double *)io, *io2 = (double *)io + N;
     const double *g1 = dL_drho1, *g2 = dL_drho2;

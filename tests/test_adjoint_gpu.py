@@ -148,3 +148,24 @@ def test_adjoint_errors(gpu_lib):
     par = lat.adjoint(np.zeros((4, 4, 4)))
     assert par == [0.0, 0.0, 0.0, 0.0]
     lat.close()
+
+
+def test_adjoint_repeated_calls_agree(gpu_lib):
+    """lbm_record reserves the reverse pass's working memory once; repeated
+    lbm_adjoint calls over the same recording reuse it and return the same
+    gradients bit for bit."""
+    from paper_1601_01237_gb300 import Lattice
+    shape = (8, 6, 10)
+    r1, r2, _ = wl.random_state(shape, seed=5, u_max=0.0)
+    lat = Lattice(shape, storage="f32", tau=(0.9, 1.1), G12=G_STRONG)
+    lat.init_fields(r1, r2)
+    lat.record(7, 3)
+    a, _, _ = lat.moments()
+    outs = []
+    for _ in range(2):
+        d1 = np.empty(shape)
+        par = lat.adjoint(2 * (a - r1), None, d1, None)
+        outs.append((d1, par))
+    lat.close()
+    assert np.array_equal(outs[0][0], outs[1][0])
+    assert list(outs[0][1]) == list(outs[1][1])
