@@ -8,28 +8,30 @@
 // The force at plane z needs rho^b at planes z-1, z, z+1 over the tile plus a
 // one-cell halo; those densities live in a ring of four shared-memory planes.
 // Iteration z:
-//   A. every thread pull-gathers its column's 38 populations at plane z+1
-//      (19 paired loads of both components; the (rho^1, rho^2) pair into the
-//      ring, momentum into a moment buffer, the (f^1_i, f^2_i) pairs into a
-//      shared-memory stash: one 8-byte shared access per pair) and, for the
-//      halo ring of plane z+2, 6 or 7 of the 19 directions of one halo cell
-//      (84 halo cells x 3 groups, both components per load), summed
-//      into fixed-order partial densities; the halo densities of plane z+1
-//      (partials gathered one iteration earlier) are completed in the ring.
-//      The side-column halo cells cost one scattered sector per load, so their
-//      tasks are spread evenly over the warps (6 per warp) next to runs of
-//      consecutive row-halo tasks;
+//   A. every thread takes its column's 38 populations of plane z+1 from
+//      registers (19 paired loads of both components issued one iteration
+//      earlier): the (rho^1, rho^2) pair into the ring, momentum into a moment
+//      buffer, the (f^1_i, f^2_i) pairs into a shared-memory stash (one 8-byte
+//      shared access per pair); for the halo ring of plane z+2 it gathers 6 or
+//      7 of the 19 directions of one halo cell (84 halo cells x 3 groups, both
+//      components per load), summed into fixed-order partial densities; the
+//      halo densities of plane z+1 (partials gathered one iteration earlier)
+//      are completed in the ring.  The side-column halo cells cost one
+//      scattered sector per load, so their tasks are spread evenly over the
+//      warps (6 per warp) next to runs of consecutive row-halo tasks;
 //   -- one barrier --
-//   B. every thread collides its column at plane z from its stash entries and
-//      stores the post-collision populations.
+//   B. every thread issues the interior gathers of plane z+2 into registers,
+//      then collides its column at plane z from its stash entries and stores
+//      the post-collision populations, so that the loads are in flight
+//      during the collision.
 // Phase A of iteration z+1 writes only the ring slot of plane z+2, the
 // thread's own stash and moment entries and the halo partials of plane z+3,
 // none of which phase B of iteration z reads, so one barrier per plane
-// suffices and fast warps start the next plane's loads while slow warps
-// finish their collisions.  Interior and halo loads are balanced over all
-// threads; every interior population is read from HBM once and written once,
-// and the halo re-reads neighbouring tiles' populations that the
-// neighbouring CTAs stream at about the same time (L2 hits).
+// suffices and fast warps start the next plane while slow warps finish their
+// collisions.  Interior and halo loads are balanced over all threads; every
+// interior population is read from HBM once and written once, and the halo
+// re-reads neighbouring tiles' populations that the neighbouring CTAs stream
+// at about the same time (L2 hits).
 #include <cuda_runtime.h>
 
 #include "d3q19.cuh"
@@ -501,19 +503,24 @@ k_step_fused(const typename Store<S>::T *__restrict__ fin, typename Store<S>::T 
             sm.hpart[1][g][1][ht] = s2;
         }
     }
+    // interior populations of plane z0+1, in registers until the first iteration
+    R v[Q2];
+    {
+        const PlaneRef pr = plane_ref<WALLZ>(p, z0 + 1);
+        if (!pr.constant) GatherAll<S, 0>::run(fin, p.N, p.rho0, pr, ci, v);
+    }
     __syncthreads();
 
     const long long cell_xy = (long long)y * p.nx + x;
     for (int z = z0; z < z1; ++z) {
         const int k = z - z0;
         const int s_m = k & 3, s_c = (k + 1) & 3, s_p = (k + 2) & 3;
-        // ---- phase A: gathers of plane z+1 (interior) and z+2 (halo partials)
+        // ---- phase A: plane z+1 from the registers filled during the previous
+        //      collision; halo partial gathers of plane z+2
         const PlaneRef pr1 = plane_ref<WALLZ>(p, z + 1);
         const bool need2 = z + 2 <= z1;           // rho(z+2) feeds the collision of z+1
         const PlaneRef pr2 = plane_ref<WALLZ>(p, z + 2);
-        R v[Q2];
         R hv[kPer];
-        if (!pr1.constant) GatherAll<S, 0>::run(fin, p.N, p.rho0, pr1, ci, v);
         if (need2 && has_halo && !pr2.constant) halo_load<S>(fin, p, pr2, cht, g, hv);
         if (tid < kHalo) halo_combine<R>(p, sm, s_p, (k + 1) & 1, pr1, h, hx, hy);
         interior_plane<S>(fin, p, sm, s_p, z + 1 < z1 ? ((k + 1) & 1) : -1, pr1, v);
@@ -524,7 +531,9 @@ k_step_fused(const typename Store<S>::T *__restrict__ fin, typename Store<S>::T 
             sm.hpart[k & 1][g][1][ht] = s2;
         }
         __syncthreads();
-        // ---- phase B: collision of plane z
+        // ---- phase B: the interior gathers of plane z+2 are issued first and
+        //      stay in flight (in registers) during the collision of plane z
+        if (z + 1 < z1 && !pr2.constant) GatherAll<S, 0>::run(fin, p.N, p.rho0, pr2, ci, v);
         if (active)
             collide_cell<S, REG>(fout, p, sm, s_m, s_c, s_p, k & 1, (long long)z * p.nx * p.ny + cell_xy, rho_out);
     }
