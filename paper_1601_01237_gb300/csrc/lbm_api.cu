@@ -40,6 +40,10 @@ struct lbm_lattice {
     // densities, gradient staging, partials
     void *ws_lam, *ws_lam_loc, *ws_a, *ws_d, *ws_seg, *ws_rseg, *ws_io;
     double *ws_part;
+    // CUDA graphs of one full checkpoint segment of the reverse pass, one per
+    // ping-pong parity of the adjoint fields (0 not built, -1 not available)
+    cudaGraphExec_t seg_graph[2];
+    int seg_graph_state[2];
     // CUDA graph of kGraphSteps steps from copy 0 (replayed by lbm_step)
     cudaGraphExec_t graph;
     int graph_state;     // 0 not built, 1 ready, -1 not available (plain launches)
@@ -220,6 +224,11 @@ void free_workspace(lbm_lattice *h)
 {
     void *bufs[8] = {h->ws_lam, h->ws_lam_loc, h->ws_a, h->ws_d, h->ws_seg, h->ws_rseg, h->ws_io, h->ws_part};
     for (void *b : bufs) cudaFree(b);
+    for (int q = 0; q < 2; ++q) {
+        if (h->seg_graph[q]) cudaGraphExecDestroy(h->seg_graph[q]);
+        h->seg_graph[q] = nullptr;
+        h->seg_graph_state[q] = 0;
+    }
     h->ws_lam = h->ws_lam_loc = h->ws_a = h->ws_d = h->ws_seg = h->ws_rseg = h->ws_io = nullptr;
     h->ws_part = nullptr;
 }
@@ -672,29 +681,65 @@ lbm_status lbm_adjoint(lbm_lattice *h, const double *dL_drho1, const double *dL_
     CKA(lbm::launch_adjoint_seed(h->phys, g1, g2, 1, lam, h->stream), "lbm_adjoint: seed");
     void *d_cur = dbuf, *d_nxt = (char *)dbuf + rb * 2 * N;   // D^N = 0 (cleared above)
     const bool use_fused = h->use_fused;
+    // One checkpoint segment of len steps on stream st: recompute its forward
+    // states and their densities, then len reverse steps with the adjoint
+    // fields ping-ponging from (la, da).
+    auto enqueue_segment = [&](cudaStream_t st, long len, void *la, void *lb, void *da, void *db) -> cudaError_t {
+        cudaError_t er = cudaSuccess;
+        for (long t = 0; t + 1 < len && er == cudaSuccess; ++t) {
+            const void *fi = (char *)seg + sb * (size_t)t;
+            void *fo = (char *)seg + sb * (size_t)(t + 1);
+            void *rt = (char *)rseg + rb * 2 * N * (size_t)t;
+            er = use_fused ? lbm::launch_step_fused(h->phys, fi, fo, st, nullptr, rt)
+                           : lbm::launch_step_split(h->phys, fi, fo, rt, st);
+        }
+        if (er == cudaSuccess)
+            er = lbm::launch_density(h->phys, (char *)seg + sb * (size_t)(len - 1),
+                                     (char *)rseg + rb * 2 * N * (size_t)(len - 1), st);
+        for (long t = len - 1; t >= 0 && er == cudaSuccess; --t) {
+            const void *fn = (char *)seg + sb * (size_t)t;
+            const void *rn = (char *)rseg + rb * 2 * N * (size_t)t;
+            // step t reads (la, da) and writes (lb, db)
+            er = lbm::launch_adjoint_step(h->phys, fn, rn, la, da, lb, abuf, db, part, st);
+            std::swap(la, lb);
+            std::swap(da, db);
+        }
+        return er;
+    };
+    // A full segment replays a captured graph (one per ping-pong parity): the
+    // same launches with one launch instead of about 3E.
+    auto segment_graph = [&](int par) -> cudaGraphExec_t {
+        if (h->seg_graph_state[par] == 0) {
+            h->seg_graph_state[par] = -1;
+            cudaStream_t cs = nullptr;
+            if (cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking) == cudaSuccess) {
+                cudaGraph_t gr = nullptr;
+                if (cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal) == cudaSuccess) {
+                    const cudaError_t er = enqueue_segment(cs, E, lam, lam_loc, d_cur, d_nxt);
+                    const cudaError_t ee = cudaStreamEndCapture(cs, &gr);
+                    if (er == cudaSuccess && ee == cudaSuccess && gr &&
+                        cudaGraphInstantiate(&h->seg_graph[par], gr, 0) == cudaSuccess)
+                        h->seg_graph_state[par] = 1;
+                    else
+                        h->seg_graph[par] = nullptr;
+                }
+                if (gr) cudaGraphDestroy(gr);
+                cudaStreamDestroy(cs);
+            }
+            cudaGetLastError();
+        }
+        return h->seg_graph_state[par] == 1 ? h->seg_graph[par] : nullptr;
+    };
     for (long k = h->rec_nck - 1; k >= 0; --k) {
         const long t0 = k * E;
         const long t1 = (t0 + E < h->rec_steps) ? t0 + E : h->rec_steps;
-        // recompute the segment's forward states f^{t0} .. f^{t1-1} and their
-        // densities rho^{t0} .. rho^{t1-1} (the last from a density pass)
+        const long len = t1 - t0;
         CKA(cudaMemcpyAsync(seg, (char *)h->ckpt + sb * (size_t)k, sb, cudaMemcpyDeviceToDevice, h->stream),
             "lbm_adjoint: restore");
-        for (long t = t0; t + 1 < t1; ++t) {
-            const void *fi = (char *)seg + sb * (size_t)(t - t0);
-            void *fo = (char *)seg + sb * (size_t)(t - t0 + 1);
-            void *rt = (char *)rseg + rb * 2 * N * (size_t)(t - t0);
-            if (use_fused) CKA(lbm::launch_step_fused(h->phys, fi, fo, h->stream, nullptr, rt), "lbm_adjoint: recompute");
-            else CKA(lbm::launch_step_split(h->phys, fi, fo, rt, h->stream), "lbm_adjoint: recompute");
-        }
-        CKA(lbm::launch_density(h->phys, (char *)seg + sb * (size_t)(t1 - 1 - t0),
-                                (char *)rseg + rb * 2 * N * (size_t)(t1 - 1 - t0), h->stream),
-            "lbm_adjoint: density");
-        for (long t = t1 - 1; t >= t0; --t) {
-            const void *fn = (char *)seg + sb * (size_t)(t - t0);
-            const void *rn = (char *)rseg + rb * 2 * N * (size_t)(t - t0);
-            // (lambda_loc, D) ping-pong: step t reads (lam, d_cur) and writes (lam_loc, d_nxt)
-            CKA(lbm::launch_adjoint_step(h->phys, fn, rn, lam, d_cur, lam_loc, abuf, d_nxt, part, h->stream),
-                "lbm_adjoint: step");
+        cudaGraphExec_t gx = (len == E && h->use_graphs) ? segment_graph(lam == h->ws_lam ? 0 : 1) : nullptr;
+        if (gx) CKA(cudaGraphLaunch(gx, h->stream), "lbm_adjoint: segment graph");
+        else CKA(enqueue_segment(h->stream, len, lam, lam_loc, d_cur, d_nxt), "lbm_adjoint: segment");
+        if (len & 1) {
             std::swap(lam, lam_loc);
             std::swap(d_cur, d_nxt);
         }

@@ -169,3 +169,25 @@ def test_adjoint_repeated_calls_agree(gpu_lib):
     lat.close()
     assert np.array_equal(outs[0][0], outs[1][0])
     assert list(outs[0][1]) == list(outs[1][1])
+
+
+def test_adjoint_graph_replay_is_bitwise(gpu_lib, monkeypatch):
+    """Full checkpoint segments of the reverse pass replay captured CUDA
+    graphs; the gradients equal plain launches bit for bit (odd segment
+    length, so both ping-pong parities are used, and a ragged segment)."""
+    from paper_1601_01237_gb300 import Lattice
+    shape = (8, 6, 10)
+    r1, r2, _ = wl.random_state(shape, seed=8, u_max=0.0)
+    out = {}
+    for graphs in ("1", "0"):
+        monkeypatch.setenv("LBM_GRAPHS", graphs)
+        lat = Lattice(shape, storage="f32", tau=(0.9, 1.1), G12=G_STRONG)
+        lat.init_fields(r1, r2)
+        lat.record(17, 5)
+        a, _, _ = lat.moments()
+        d1 = np.empty(shape)
+        par = lat.adjoint(2 * (a - r1), None, d1, None)
+        lat.close()
+        out[graphs] = (d1, list(par))
+    assert np.array_equal(out["1"][0], out["0"][0])
+    assert out["1"][1] == out["0"][1]
