@@ -79,7 +79,7 @@ __device__ __forceinline__ unsigned at(const Nb &n, int dx, int dy, int dz)
 //   mu_i(y) = lambda^{n+1}_i(y + c_i) = lambda_loc^{n+1}_i(y + c_i) + D^{n+1}_a(y + c_i)
 // (or lambda^{n+1}_opp(i)(y) at a wall), and writes lambda_loc^n_i(y) of its
 // component and a^n_b(y) of the other component b = 1 - a.
-template <int S, bool REG>
+template <int S, bool REG, bool SIN>
 __device__ __forceinline__ void adj_half(const typename Store<S>::T *__restrict__ f,
                                          const typename Store<S>::R *__restrict__ rho,
                                          const typename Store<S>::R *__restrict__ lam_next,
@@ -113,10 +113,16 @@ __device__ __forceinline__ void adj_half(const typename Store<S>::T *__restrict_
     const R u1 = (jy + __shfl_xor_sync(full, jy, 16)) / rt;
     const R u2 = (jz + __shfl_xor_sync(full, jz, 16)) / rt;
     const R usq = u0 * u0 + u1 * u1 + u2 * u2;
-    // S^b of the other component b (Eq. 7; wall sites carry Eq. 13's rho')
+    // S^b of the other component b (Eq. 7; wall sites carry Eq. 13's rho'):
+    // stored by the replayed forward step (SIN, rho = the sums [3 b + d][cell])
+    // or formed from the densities
     const int b = 1 - a;
     R Sb0 = 0, Sb1 = 0, Sb2 = 0;
-    {
+    if (SIN) {
+        Sb0 = rho[(long long)(3 * b + 0) * N + n.cell];
+        Sb1 = rho[(long long)(3 * b + 1) * N + n.cell];
+        Sb2 = rho[(long long)(3 * b + 2) * N + n.cell];
+    } else {
         const R *rbp = rho + (long long)b * N;
 #pragma unroll
         for (int i = 1; i < Q; ++i) {
@@ -286,7 +292,7 @@ __device__ __forceinline__ void adj_half(const typename Store<S>::T *__restrict_
 // Grid-stride over groups of 16 cells per warp; lanes 0-15 take component 0
 // and lanes 16-31 component 1 of the same 16 cells.  Per-block FP64 partials
 // of dL/dG^{12}, dL/dG^{21}, dL/dtau_1, dL/dtau_2 accumulate over the steps.
-template <int S, bool REG>
+template <int S, bool REG, bool SIN>
 __global__ void __launch_bounds__(kThreadsA, 2)
 k_adj_local(const typename Store<S>::T *__restrict__ f, const typename Store<S>::R *__restrict__ rho,
             const typename Store<S>::R *__restrict__ lam_next, const typename Store<S>::R *__restrict__ Dn,
@@ -303,7 +309,7 @@ k_adj_local(const typename Store<S>::T *__restrict__ f, const typename Store<S>:
         const bool valid = c < p.N;
         Nb n;
         nb_of(p, (unsigned)(valid ? c : p.N - 1), n);
-        adj_half<S, REG>(f, rho, lam_next, Dn, lam_loc, aout, p, n, a, valid, pg, pt);
+        adj_half<S, REG, SIN>(f, rho, lam_next, Dn, lam_loc, aout, p, n, a, valid, pg, pt);
     }
     // lanes of component a hold parts of par[a] and par[2 + a]
     __shared__ double sh[4][kThreadsA];
@@ -413,18 +419,20 @@ Phys<R> make_phys_a(const HostPhys &h)
 inline unsigned gridA(long long N) { return (unsigned)((N + kThreadsA - 1) / kThreadsA); }
 
 template <int S>
-cudaError_t adj_step_t(const HostPhys &h, const void *f, const void *rho, const void *lam_next, const void *Dn,
-                       void *lam_loc, void *a, void *Dout, double *partials, cudaStream_t s)
+cudaError_t adj_step_t(const HostPhys &h, const void *f, const void *rho, int rho_is_sums, const void *lam_next,
+                       const void *Dn, void *lam_loc, void *a, void *Dout, double *partials, cudaStream_t s)
 {
     using T = typename Store<S>::T;
     using R = typename Store<S>::R;
     const Phys<R> p = make_phys_a<R>(h);
-    if (h.collision == LBM_REGULARIZED)
-        k_adj_local<S, true><<<adjoint_blocks(), kThreadsA, 0, s>>>((const T *)f, (const R *)rho, (const R *)lam_next,
-                                                              (const R *)Dn, (R *)lam_loc, (R *)a, partials, p);
-    else
-        k_adj_local<S, false><<<adjoint_blocks(), kThreadsA, 0, s>>>((const T *)f, (const R *)rho, (const R *)lam_next,
-                                                               (const R *)Dn, (R *)lam_loc, (R *)a, partials, p);
+#define LBM_ADJ(REG_, SIN_)                                                                                  \
+    k_adj_local<S, REG_, SIN_><<<adjoint_blocks(), kThreadsA, 0, s>>>((const T *)f, (const R *)rho,         \
+                                                                      (const R *)lam_next, (const R *)Dn,  \
+                                                                      (R *)lam_loc, (R *)a, partials, p)
+    const bool reg = h.collision == LBM_REGULARIZED;
+    if (rho_is_sums) { if (reg) LBM_ADJ(true, true); else LBM_ADJ(false, true); }
+    else { if (reg) LBM_ADJ(true, false); else LBM_ADJ(false, false); }
+#undef LBM_ADJ
     k_adj_D<R><<<gridA(h.N), kThreadsA, 0, s>>>((const R *)a, (R *)Dout, p);
     return cudaGetLastError();
 }
@@ -445,14 +453,14 @@ int adjoint_blocks()
     return blocks;
 }
 
-cudaError_t launch_adjoint_step(const HostPhys &p, const void *f, const void *rho, const void *lam_next,
+cudaError_t launch_adjoint_step(const HostPhys &p, const void *f, const void *rho, int rho_is_sums, const void *lam_next,
                                 const void *Dn, void *lam_loc, void *a, void *Dout, double *partials, cudaStream_t s)
 {
     switch (p.storage) {
-    case ST_F64: return adj_step_t<ST_F64>(p, f, rho, lam_next, Dn, lam_loc, a, Dout, partials, s);
-    case ST_F32: return adj_step_t<ST_F32>(p, f, rho, lam_next, Dn, lam_loc, a, Dout, partials, s);
-    case ST_F16_DEV: return adj_step_t<ST_F16_DEV>(p, f, rho, lam_next, Dn, lam_loc, a, Dout, partials, s);
-    case ST_BF16_DEV: return adj_step_t<ST_BF16_DEV>(p, f, rho, lam_next, Dn, lam_loc, a, Dout, partials, s);
+    case ST_F64: return adj_step_t<ST_F64>(p, f, rho, rho_is_sums, lam_next, Dn, lam_loc, a, Dout, partials, s);
+    case ST_F32: return adj_step_t<ST_F32>(p, f, rho, rho_is_sums, lam_next, Dn, lam_loc, a, Dout, partials, s);
+    case ST_F16_DEV: return adj_step_t<ST_F16_DEV>(p, f, rho, rho_is_sums, lam_next, Dn, lam_loc, a, Dout, partials, s);
+    case ST_BF16_DEV: return adj_step_t<ST_BF16_DEV>(p, f, rho, rho_is_sums, lam_next, Dn, lam_loc, a, Dout, partials, s);
     default: return cudaErrorInvalidValue;
     }
 }

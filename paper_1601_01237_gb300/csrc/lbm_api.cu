@@ -617,7 +617,9 @@ lbm_status lbm_record(lbm_lattice *h, long n_steps, int ckpt_every)
         CK(cudaMalloc(&h->ws_a, rb * 6 * N), "lbm_record: reverse-pass a");
         CK(cudaMalloc(&h->ws_d, rb * 4 * N), "lbm_record: reverse-pass D");
         CK(cudaMalloc(&h->ws_seg, sb * (E + 1)), "lbm_record: reverse-pass segment states");
-        CK(cudaMalloc(&h->ws_rseg, rb * 2 * N * E), "lbm_record: reverse-pass segment densities");
+        // per replayed step: the interaction sums (fused step, 6 N) or the
+        // densities (two-kernel step, 2 N)
+        CK(cudaMalloc(&h->ws_rseg, rb * (h->use_fused ? 6 : 2) * N * E), "lbm_record: reverse-pass segment sums");
         CK(cudaMalloc(&h->ws_io, sizeof(double) * 2 * N), "lbm_record: reverse-pass staging");
         CK(cudaMalloc((void **)&h->ws_part, sizeof(double) * 4 * lbm::adjoint_blocks()), "lbm_record: partials");
     }
@@ -684,23 +686,32 @@ lbm_status lbm_adjoint(lbm_lattice *h, const double *dL_drho1, const double *dL_
     // One checkpoint segment of len steps on stream st: recompute its forward
     // states and their densities, then len reverse steps with the adjoint
     // fields ping-ponging from (la, da).
+    // The fused replay keeps each step's interaction sums (6 N reals; the
+    // last state of a segment is stepped once more into the spare state slot
+    // for them); the two-kernel replay keeps each step's densities (2 N reals;
+    // the last state's from a density pass).
+    const size_t rstride = rb * (use_fused ? 6 : 2) * N;
+    // One checkpoint segment of len steps on stream st: recompute its forward
+    // states, then len reverse steps with the adjoint fields ping-ponging from
+    // (la, da).
     auto enqueue_segment = [&](cudaStream_t st, long len, void *la, void *lb, void *da, void *db) -> cudaError_t {
         cudaError_t er = cudaSuccess;
-        for (long t = 0; t + 1 < len && er == cudaSuccess; ++t) {
+        const long nrec = use_fused ? len : len - 1;
+        for (long t = 0; t < nrec && er == cudaSuccess; ++t) {
             const void *fi = (char *)seg + sb * (size_t)t;
             void *fo = (char *)seg + sb * (size_t)(t + 1);
-            void *rt = (char *)rseg + rb * 2 * N * (size_t)t;
+            void *rt = (char *)rseg + rstride * (size_t)t;
             er = use_fused ? lbm::launch_step_fused(h->phys, fi, fo, st, nullptr, rt)
                            : lbm::launch_step_split(h->phys, fi, fo, rt, st);
         }
-        if (er == cudaSuccess)
+        if (er == cudaSuccess && !use_fused)
             er = lbm::launch_density(h->phys, (char *)seg + sb * (size_t)(len - 1),
-                                     (char *)rseg + rb * 2 * N * (size_t)(len - 1), st);
+                                     (char *)rseg + rstride * (size_t)(len - 1), st);
         for (long t = len - 1; t >= 0 && er == cudaSuccess; --t) {
             const void *fn = (char *)seg + sb * (size_t)t;
-            const void *rn = (char *)rseg + rb * 2 * N * (size_t)t;
+            const void *rn = (char *)rseg + rstride * (size_t)t;
             // step t reads (la, da) and writes (lb, db)
-            er = lbm::launch_adjoint_step(h->phys, fn, rn, la, da, lb, abuf, db, part, st);
+            er = lbm::launch_adjoint_step(h->phys, fn, rn, use_fused ? 1 : 0, la, da, lb, abuf, db, part, st);
             std::swap(la, lb);
             std::swap(da, db);
         }

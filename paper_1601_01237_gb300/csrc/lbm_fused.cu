@@ -232,17 +232,13 @@ __device__ __forceinline__ void halo_sum(const typename Store<S>::R (&v)[kPer], 
 template <int S, bool REG>
 __device__ __forceinline__ void collide_cell(typename Store<S>::T *__restrict__ fout, const Phys<typename Store<S>::R> &p,
                                              const FusedSmem<typename Store<S>::R> &sm, int sl_m, int sl_c, int sl_p,
-                                             int st, long long cell, typename Store<S>::R *__restrict__ rho_out)
+                                             int st, long long cell, typename Store<S>::R *__restrict__ s_out)
 {
     using R = typename Store<S>::R;
     const int tid = threadIdx.x;
     const int lx = tid % kTX + 1, ly = tid / kTX + 1;
     const float2 rr = sm.ring[sl_c][ly][lx];
     const R r1 = rr.x, r2 = rr.y;
-    if (rho_out) {   // pre-collision densities of this step (reverse-mode replay)
-        rho_out[cell] = r1;
-        rho_out[p.N + cell] = r2;
-    }
     const R inv = R(1) / (r1 + r2);
     const R ux = sm.mom[st][0][tid] * inv, uy = sm.mom[st][1][tid] * inv, uz = sm.mom[st][2][tid] * inv;
     // S^b = sum_{i != 0} w_i c_i rho^b(x + c_i)  (Eq. 7; ghost planes carry Eq. 13's rho')
@@ -258,6 +254,12 @@ __device__ __forceinline__ void collide_cell(typename Store<S>::T *__restrict__ 
             if (cy(i) == 1) Sb[b][1] += wr; else if (cy(i) == -1) Sb[b][1] -= wr;
             if (cz(i) == 1) Sb[b][2] += wr; else if (cz(i) == -1) Sb[b][2] -= wr;
         }
+    }
+    if (s_out) {   // interaction sums of this step (reverse-mode replay)
+#pragma unroll
+        for (int b = 0; b < 2; ++b)
+#pragma unroll
+            for (int d = 0; d < 3; ++d) s_out[(long long)(3 * b + d) * p.N + cell] = Sb[b][d];
     }
     // g^a = sum_b F^{ab} / rho^a + g_ext = G^{ab} S^b + g_ext
     const R v1x = ux + p.G12 * Sb[1][0] + p.gext[0], v1y = uy + p.G12 * Sb[1][1] + p.gext[1],
@@ -409,7 +411,7 @@ __device__ __forceinline__ void halo_combine(const Phys<R> &p, FusedSmem<R> &sm,
 template <int S, bool REG, bool WALLZ, int LZ>
 __global__ void __launch_bounds__(kThreadsF, 2)
 k_step_fused(const typename Store<S>::T *__restrict__ fin, typename Store<S>::T *__restrict__ fout,
-             Phys<typename Store<S>::R> p, int ntx, typename Store<S>::R *__restrict__ rho_out)
+             Phys<typename Store<S>::R> p, int ntx, typename Store<S>::R *__restrict__ s_out)
 {
     constexpr int lz = LZ;
     using R = typename Store<S>::R;
@@ -535,7 +537,7 @@ k_step_fused(const typename Store<S>::T *__restrict__ fin, typename Store<S>::T 
         //      stay in flight (in registers) during the collision of plane z
         if (z + 1 < z1 && !pr2.constant) GatherAll<S, 0>::run(fin, p.N, p.rho0, pr2, ci, v);
         if (active)
-            collide_cell<S, REG>(fout, p, sm, s_m, s_c, s_p, k & 1, (long long)z * p.nx * p.ny + cell_xy, rho_out);
+            collide_cell<S, REG>(fout, p, sm, s_m, s_c, s_p, k & 1, (long long)z * p.nx * p.ny + cell_xy, s_out);
     }
 }
 
@@ -558,7 +560,7 @@ Phys<R> make_phys_f(const HostPhys &h)
 constexpr size_t kSmemBytes = sizeof(FusedSmem<float>);
 
 template <int S>
-cudaError_t fused_t(const HostPhys &h, const void *fin, void *fout, cudaStream_t s, cudaEvent_t *ev, void *rho_out)
+cudaError_t fused_t(const HostPhys &h, const void *fin, void *fout, cudaStream_t s, cudaEvent_t *ev, void *s_out)
 {
     using T = typename Store<S>::T;
     using R = typename Store<S>::R;
@@ -594,7 +596,7 @@ cudaError_t fused_t(const HostPhys &h, const void *fin, void *fout, cudaStream_t
     const T *fi = (const T *)fin;
     T *fo = (T *)fout;
     const bool reg = h.collision == LBM_REGULARIZED;
-#define LBM_LAUNCH(REG_, WALL_, LZ_) k_step_fused<S, REG_, WALL_, LZ_><<<grid, kThreadsF, kSmemBytes, s>>>(fi, fo, p, ntx, (R *)rho_out)
+#define LBM_LAUNCH(REG_, WALL_, LZ_) k_step_fused<S, REG_, WALL_, LZ_><<<grid, kThreadsF, kSmemBytes, s>>>(fi, fo, p, ntx, (R *)s_out)
     if (h.wall_z) {
         if (reg) { if (small) LBM_LAUNCH(true, true, kLZsmall); else LBM_LAUNCH(true, true, kLZmax); }
         else { if (small) LBM_LAUNCH(false, true, kLZsmall); else LBM_LAUNCH(false, true, kLZmax); }
@@ -618,12 +620,12 @@ bool fused_supported(const HostPhys &p)
 }
 
 cudaError_t launch_step_fused(const HostPhys &p, const void *f_in, void *f_out, cudaStream_t s, cudaEvent_t *ev,
-                              void *rho_out)
+                              void *s_out)
 {
     switch (p.storage) {
-    case ST_F32: return fused_t<ST_F32>(p, f_in, f_out, s, ev, rho_out);
-    case ST_F16_DEV: return fused_t<ST_F16_DEV>(p, f_in, f_out, s, ev, rho_out);
-    case ST_BF16_DEV: return fused_t<ST_BF16_DEV>(p, f_in, f_out, s, ev, rho_out);
+    case ST_F32: return fused_t<ST_F32>(p, f_in, f_out, s, ev, s_out);
+    case ST_F16_DEV: return fused_t<ST_F16_DEV>(p, f_in, f_out, s, ev, s_out);
+    case ST_BF16_DEV: return fused_t<ST_BF16_DEV>(p, f_in, f_out, s, ev, s_out);
     default: return cudaErrorInvalidValue;
     }
 }

@@ -38,10 +38,10 @@ cudaError_t launch_step_split(const HostPhys &p, const void *f_in, void *f_out, 
 
 // One full time step with the fused single-pass kernel (no scratch).
 // ev (optional, 2 events): recorded before and after the launch.
-// rho_out (optional, 2*N FP32 values): receives the step's pre-collision
-// densities rho^1, rho^2 (the replay of the reverse pass uses them).
+// s_out (optional, 6*N FP32 values, [3 b + d][cell]): receives the step's
+// interaction sums S^b_d of Eq. 7 (the replay of the reverse pass uses them).
 cudaError_t launch_step_fused(const HostPhys &p, const void *f_in, void *f_out, cudaStream_t s,
-                              cudaEvent_t *ev = nullptr, void *rho_out = nullptr);
+                              cudaEvent_t *ev = nullptr, void *s_out = nullptr);
 bool fused_supported(const HostPhys &p);
 
 // State set-up: populations from (rho1, rho2, u) via f^eq (u may be NULL),
@@ -68,14 +68,16 @@ constexpr long long kNoallocMaxCells = 2097152;   // 128^3
 cudaError_t launch_step_split_noalloc(const HostPhys &p, const void *f_in, void *f_out, cudaStream_t s);
 
 // Reverse (adjoint) step n: from lambda_loc^{n+1} (2*19*N reals) and D^{n+1}
-// (2*N reals) and the forward state f^n (raw state, its densities in rho),
-// writes lambda_loc^n, a^n (6*N reals, scratch) and D^n; partials
+// (2*N reals) and the forward state f^n (raw state) with either its densities
+// (rho, 2*N reals) or, when rho_is_sums, its interaction sums (rho, 6*N reals
+// [3 b + d][cell], as written by launch_step_fused's s_out), writes
+// lambda_loc^n, a^n (6*N reals, scratch) and D^n; partials
 // (adjoint_blocks() x 4 doubles: dG12, dG21, dtau1, dtau2) accumulate.
 // lambda^n = lambda_loc^n + D^n of the population's component.
 int adjoint_blocks();
-cudaError_t launch_adjoint_step(const HostPhys &p, const void *f, const void *rho, const void *lam_next,
-                                const void *Dn, void *lam_loc, void *a, void *Dout, double *partials,
-                                cudaStream_t s);
+cudaError_t launch_adjoint_step(const HostPhys &p, const void *f, const void *rho, int rho_is_sums,
+                                const void *lam_next, const void *Dn, void *lam_loc, void *a, void *Dout,
+                                double *partials, cudaStream_t s);
 // lambda_loc^N_i = dL/drho^a of the component of i (g1/g2 may be NULL).
 cudaError_t launch_adjoint_seed(const HostPhys &p, const void *g1, const void *g2, int g_f64, void *lam,
                                 cudaStream_t s);
