@@ -3,7 +3,7 @@
 
 One "step" is one full time step (moments, Eq. 7 interaction, collision with
 forcing, streaming) over the whole lattice.  Default workload: the 512^3
-periodic spinodal mixture, FP32 populations, BGK, tau = 0.7.  The metric is
+periodic spinodal mixture, FP32 populations, BGK, tau = 1.0.  The metric is
 MLUPS (million two-component cell updates per second) for the whole job.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
@@ -304,9 +304,11 @@ def cpu_baseline(args, cfg):
 
 def adjoint_ratio(stream):
     """Adjoint/forward time ratio on the differentiation case: 96^3 droplet
-    (R = 20), FP32, 500 steps, checkpoints every 25.  Forward = lbm_step(500);
-    reverse = lbm_adjoint over an lbm_record of the same 500 steps, including
-    its recomputation of every checkpoint segment."""
+    (R = 20), FP32, 500 steps, checkpoints every 25.  Forward = lbm_step(500)
+    after a warm-up lbm_step(100); reverse = lbm_adjoint over an lbm_record of
+    the same 500 steps, including its recomputation of every checkpoint
+    segment, after one warm-up lbm_adjoint call over the same recording (both
+    warm-ups build the CUDA graphs that the timed calls replay)."""
     import torch
     from paper_1601_01237_gb300 import Lattice
     c = wl.CONFIGS["c3_adjoint96"]
@@ -316,7 +318,7 @@ def adjoint_ratio(stream):
     lat = Lattice(shape, storage=c["storage"], tau=c["tau"], G12=c["G"], stream=stream.cuda_stream)
     d1, d2 = torch.from_numpy(r1).cuda(), torch.from_numpy(r2).cuda()
     lat.init_fields(d1, d2)
-    lat.step(20)
+    lat.step(100)
     torch.cuda.synchronize()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e0.record(stream)
@@ -330,6 +332,7 @@ def adjoint_ratio(stream):
     lat.moments_device(rho1=out1, out_f64=True)
     g = 2.0 * (out1 - torch.from_numpy(tgt).cuda())
     gr0 = torch.empty(shape, dtype=torch.float64, device="cuda")
+    lat.adjoint(g, None, gr0, None)
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     par = lat.adjoint(g, None, gr0, None)
