@@ -11,6 +11,8 @@ c2  spinodal mixture 256^3: FP32 / FP16-dev / BF16-dev, MLUPS, mass drift,
 c3  differentiation 96^3: loss, gradients (tied G, tau_1), adjoint/forward time
 s1  the static-droplet study: quasi-2D droplets (R = 8-24, side 5 R) at
     tau = 0.7-3, BGK and regularized: surface tension per tau, spurious current
+s2  the wetting study: a quasi-2D droplet on a wall, wall potentials from
+    alpha = -0.4 .. 0.4, modified vs original wall model: contact angle, film
 c4  wall-bounded 512x512x384, regularized, mirror wetting (or --wall-model
     potential), no body force (or --gravity: tilted by 30 deg): MLUPS, droplet
     drift velocity, thin-film density, volume ratio
@@ -232,9 +234,78 @@ def run_s1(steps=None, radii=(8, 12, 16, 24), taus=(0.7, 0.8, 1.0, 1.5, 2.0, 3.0
     return out
 
 
+def _cap_angle(a, thr):
+    """Contact angle of a quasi-2D droplet of component 1 on the wall z = -1/2
+    from its height h at the centre column and its half-width b on the first
+    fluid layer (both with linear interpolation of rho^1 across the
+    threshold), for a circular cap."""
+    col = a[:, 0, :]
+    nz, nx = col.shape
+    inside = col > thr
+    xs = np.nonzero(inside[0])[0]
+    if xs.size == 0:
+        return None, 0.0, 0.0
+    xc = int(round(xs.mean()))
+    # height: last cell above the threshold in the centre column, interpolated
+    zc = col[:, xc]
+    k = int(np.nonzero(zc > thr)[0].max())
+    h = k + 0.5 + (zc[k] - thr) / (zc[k] - zc[k + 1]) if k + 1 < nz else float(nz)
+    row = col[0]
+    lo, hi = int(xs.min()), int(xs.max())
+    left = lo - 0.5 + (row[lo] - thr) / (row[lo] - row[lo - 1]) - 0.5 if lo > 0 else float(lo)
+    right = hi + 0.5 - (row[hi] - thr) / (row[hi] - row[(hi + 1) % nx]) + 0.5
+    b = 0.5 * (right - left)
+    # circle through the top (z = h - 1/2) and the chord 2 b on the first layer
+    # (z = 0); the angle between it and the wall z = -1/2, measured inside the
+    # droplet
+    zt = h - 0.5
+    Rc = (b * b + zt * zt) / (2.0 * zt)
+    zc = zt - Rc
+    theta = np.degrees(np.arccos(np.clip(-(zc + 0.5) / Rc, -1.0, 1.0)))
+    return float(theta), float(h), float(b)
+
+
+def run_s2(steps=None, alphas=(-0.4, -0.2, 0.0, 0.2, 0.4), shape=(64, 1, 160), R=24,
+           models=("mirror", "potential")):
+    """The wetting study of Sec. 4.2: a quasi-2D droplet on the wall z = -1/2
+    with wall potentials rho_s^1 = -rho0 alpha (alpha < 0) and
+    rho_s^2 = rho0 alpha (alpha > 0), rho0 = 0.22, tau = 1, for the modified
+    (mirror) and the original (point-wise potential) wall model: the static
+    contact angle and the density of component 1 on the wall outside the
+    droplet (thin film)."""
+    steps = steps or 20000
+    G = wl.G_DROPLET
+    rho0 = 0.22
+    thr = 0.5 * (1.0 + 0.03)
+    out = {"case": "s2", "steps": steps, "shape": shape, "R": R, "G_eq7": G, "runs": {}}
+    nz, ny, nx = shape
+    for model in models:
+        for al in alphas:
+            rs = (-rho0 * al if al < 0 else 0.0, rho0 * al if al > 0 else 0.0)
+            lat = Lattice(shape, storage="f32", tau=(1.0, 1.0), G12=G, periodic=(1, 1, 0), rho_s=rs,
+                          wall_model=model)
+            r1, r2 = wl.hemisphere(shape, R)
+            lat.init_fields(r1, r2)
+            lat.step(steps)
+            try:
+                red = lat.reduce()
+            except LBMError:
+                out["runs"]["%s/%g" % (model, al)] = {"diverged": True}
+                lat.close()
+                continue
+            a, _, _ = lat.moments()
+            st = lat.droplet_stats(thr, origin=((nx - 1) / 2.0, 0.0, -0.5))
+            lat.close()
+            theta, h, b = _cap_angle(a, thr)
+            out["runs"]["%s/%g" % (model, al)] = {
+                "rho_s": rs, "contact_angle_deg": theta, "height": h, "half_width": b,
+                "film_rho1": st["film_rho"], "droplet_area": st["volume"], "max_uF": red["max_uF"]}
+    return out
+
+
 def main():
     ap = argparse.ArgumentParser()
-    ap.add_argument("case", choices=["c0", "c1", "c2", "c3", "c4", "s1"])
+    ap.add_argument("case", choices=["c0", "c1", "c2", "c3", "c4", "s1", "s2"])
     ap.add_argument("--steps", type=int, default=None)
     ap.add_argument("--shape", type=int, nargs=3, default=None, help="nz ny nx (c1, c4)")
     ap.add_argument("--gravity", action="store_true", help="c4: tilted gravity")
@@ -247,7 +318,7 @@ def main():
     elif args.case == "c1":
         r = run_c1(args.steps, radii=args.radii, taus=args.taus, shape=args.shape)
     else:
-        r = {"c0": run_c0, "c2": run_c2, "c3": run_c3, "s1": run_s1}[args.case](args.steps)
+        r = {"c0": run_c0, "c2": run_c2, "c3": run_c3, "s1": run_s1, "s2": run_s2}[args.case](args.steps)
     print(json.dumps(r, default=float))
 
 
