@@ -125,3 +125,25 @@ def test_laplace_3d_f32_within_1pct_of_f64(gpu_lib):
     err = abs(fits["f32"][0] - fits["f64"][0]) / abs(fits["f64"][0])
     print("3D sigma FP32 %.6f FP64 %.6f (%.3g), intercept %.3g" % (fits["f32"][0], fits["f64"][0], err, fits["f64"][1]))
     assert err <= 0.01
+
+
+def test_neutral_wetting_keeps_90_degrees(gpu_lib):
+    """Modified wall model (mirrored densities, rho_s = 0, Eq. 13): a quasi-2D
+    droplet on the wall keeps a 90 degree contact angle within 2 degrees, and
+    the wall layer outside it stays near the bulk minority density (no thin
+    film)."""
+    from paper_1601_01237_gb300 import Lattice
+    from paper_1601_01237_gb300.run_config import _cap_angle
+    shape, R = (40, 1, 96), 14
+    lat = Lattice(shape, storage="f32", tau=(1.0, 1.0), G12=wl.G_DROPLET, periodic=(1, 1, 0),
+                  wall_model="mirror")
+    r1, r2 = wl.hemisphere(shape, R)
+    lat.init_fields(r1, r2)
+    lat.step(6000)
+    a, _, _ = lat.moments()
+    st = lat.droplet_stats(0.515, origin=(47.5, 0.0, -0.5))
+    lat.close()
+    theta, h, b = _cap_angle(a, 0.515)
+    print("neutral wetting: theta %.2f deg (h %.2f, b %.2f), film %.4f" % (theta, h, b, st["film_rho"]))
+    assert abs(theta - 90.0) <= 2.0
+    assert st["film_rho"] < 0.06
