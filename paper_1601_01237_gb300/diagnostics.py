@@ -1,5 +1,6 @@
 """Host-side helpers for the paper's measurements (Sec. 3-4): Young-Laplace fit
-(Eq. 12), equivalent radius of a droplet from its volume, drift velocity.
+(Eq. 12), equivalent radius of a droplet from its volume, drift velocity,
+contact angles of a sessile droplet and of a slug between plates (Sec. 4.2).
 The field reductions themselves run on the GPU (lbm_pressure_jump,
 lbm_droplet_stats, lbm_reduce)."""
 import math
@@ -31,3 +32,98 @@ def drift_velocity(com_a, com_b, steps):
     """Centre-of-mass displacement per step between two measurements."""
     d = np.asarray(com_b, dtype=float) - np.asarray(com_a, dtype=float)
     return d / float(steps)
+
+
+def _crossing(v, thr, k):
+    """Position where the profile v crosses thr between cells k and k + 1
+    (linear interpolation)."""
+    return k + (thr - v[k]) / (v[k + 1] - v[k])
+
+
+def cap_contact_angle(rho, thr):
+    """Contact angle of a quasi-2D droplet (fields (nz, 1, nx)) on the wall
+    z = -1/2, measured inside the droplet, for a circular cap: from its height
+    h at the centre column and its half-width b on the first fluid layer (both
+    where rho crosses thr, interpolated linearly), the circle through the top
+    and the chord on z = 0.  Returns (theta in degrees, h, b); theta is None
+    when no cell of the first layer exceeds thr."""
+    col = np.asarray(rho)[:, 0, :]
+    nz, nx = col.shape
+    xs = np.nonzero(col[0] > thr)[0]
+    if xs.size == 0:
+        return None, 0.0, 0.0
+    xc = int(round(xs.mean()))
+    zc = col[:, xc]
+    k = int(np.nonzero(zc > thr)[0].max())
+    h = (_crossing(zc, thr, k) + 0.5) if k + 1 < nz else float(nz)
+    row = col[0]
+    lo, hi = int(xs.min()), int(xs.max())
+    left = _crossing(row, thr, lo - 1) if lo > 0 else float(lo)
+    right = _crossing(row, thr, hi) if hi + 1 < nx else float(hi)
+    b = 0.5 * (right - left)
+    # circle through the top (z = h - 1/2) and the chord 2 b on z = 0; the
+    # angle between it and the wall z = -1/2 inside the droplet
+    zt = h - 0.5
+    Rc = (b * b + zt * zt) / (2.0 * zt)
+    zcen = zt - Rc
+    theta = np.degrees(np.arccos(np.clip(-(zcen + 0.5) / Rc, -1.0, 1.0)))
+    return float(theta), float(h), float(b)
+
+
+def fit_circle(x, z):
+    """Algebraic least-squares circle x^2 + z^2 + D x + E z + F = 0 through
+    the points (Kasa's fit).  Returns (xc, zc, R)."""
+    x = np.asarray(x, dtype=float)
+    z = np.asarray(z, dtype=float)
+    A = np.vstack([x, z, np.ones_like(x)]).T
+    (D, E, F), *_ = np.linalg.lstsq(A, -(x * x + z * z), rcond=None)
+    xc, zc = -0.5 * D, -0.5 * E
+    return xc, zc, math.sqrt(max(xc * xc + zc * zc - F, 0.0))
+
+
+def slug_contact_angle(rho, thr, skip=2):
+    """Contact angle of a quasi-2D slug (fields (nz, 1, nx)) spanning the
+    channel between the walls z = -1/2 and z = nz - 1/2, measured inside the
+    slug (the component whose density rho is given, rho > thr inside, centred
+    in x).  Each meniscus is the set of per-row crossings of thr (rows skip ..
+    nz - 1 - skip); a circle fitted to them meets both walls at the angle
+    returned (the mean over the two menisci and two walls, degrees), with the
+    per-meniscus angles."""
+    col = np.asarray(rho)[:, 0, :]
+    nz, nx = col.shape
+    mid = nx // 2
+    out = []
+    for side in (-1, 1):
+        xs, zs = [], []
+        for z in range(skip, nz - skip):
+            row = col[z]
+            if side < 0:
+                ks = np.nonzero((row[:mid] <= thr) & (row[1:mid + 1] > thr))[0]
+                if ks.size:
+                    xs.append(_crossing(row, thr, int(ks.max())))
+                    zs.append(z)
+            else:
+                ks = np.nonzero((row[mid:-1] > thr) & (row[mid + 1:] <= thr))[0]
+                if ks.size:
+                    xs.append(_crossing(row, thr, int(ks.min()) + mid))
+                    zs.append(z)
+        if len(xs) < 3:
+            return None, []
+        if np.ptp(xs) < 1e-9:   # a straight meniscus
+            out += [90.0, 90.0]
+            continue
+        xc, zc, R = fit_circle(xs, zs)
+        # the slug wets (angle < 90) when the centre lies on the other
+        # component's side of the meniscus
+        s = 1.0 if (xc - np.mean(xs)) * side > 0 else -1.0
+        # distance of the centre from each wall over R is the cosine
+        for h in (zc + 0.5, nz - 0.5 - zc):
+            out.append(float(np.degrees(np.arccos(np.clip(s * h / R, -1.0, 1.0)))))
+    return float(np.mean(out)), out
+
+
+def wall_layer_density(rho, x_lo, x_hi):
+    """Mean density on the first fluid layers next to the walls (z = 0 and
+    z = nz - 1) over x_lo <= x < x_hi, y = 0 (the thin-film measure)."""
+    r = np.asarray(rho)
+    return float(0.5 * (r[0, 0, x_lo:x_hi].mean() + r[-1, 0, x_lo:x_hi].mean()))

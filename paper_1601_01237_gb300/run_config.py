@@ -13,6 +13,8 @@ s1  the static-droplet study: quasi-2D droplets (R = 8-24, side 5 R) at
     tau = 0.7-3, BGK and regularized: surface tension per tau, spurious current
 s2  the wetting study: a quasi-2D droplet on a wall, wall potentials from
     alpha = -0.4 .. 0.4, modified vs original wall model: contact angle, film
+s3  the static slug between plates (channel height 32): contact angle inside
+    the slug and wall film, modified vs original wall model
 c4  wall-bounded 512x512x384, regularized, mirror wetting (or --wall-model
     potential), no body force (or --gravity: tilted by 30 deg): MLUPS, droplet
     drift velocity, thin-film density, volume ratio
@@ -234,78 +236,91 @@ def run_s1(steps=None, radii=(8, 12, 16, 24), taus=(0.7, 0.8, 1.0, 1.5, 2.0, 3.0
     return out
 
 
-def _cap_angle(a, thr):
-    """Contact angle of a quasi-2D droplet of component 1 on the wall z = -1/2
-    from its height h at the centre column and its half-width b on the first
-    fluid layer (both with linear interpolation of rho^1 across the
-    threshold), for a circular cap."""
-    col = a[:, 0, :]
-    nz, nx = col.shape
-    inside = col > thr
-    xs = np.nonzero(inside[0])[0]
-    if xs.size == 0:
-        return None, 0.0, 0.0
-    xc = int(round(xs.mean()))
-    # height: last cell above the threshold in the centre column, interpolated
-    zc = col[:, xc]
-    k = int(np.nonzero(zc > thr)[0].max())
-    h = k + 0.5 + (zc[k] - thr) / (zc[k] - zc[k + 1]) if k + 1 < nz else float(nz)
-    row = col[0]
-    lo, hi = int(xs.min()), int(xs.max())
-    left = lo - 0.5 + (row[lo] - thr) / (row[lo] - row[lo - 1]) - 0.5 if lo > 0 else float(lo)
-    right = hi + 0.5 - (row[hi] - thr) / (row[hi] - row[(hi + 1) % nx]) + 0.5
-    b = 0.5 * (right - left)
-    # circle through the top (z = h - 1/2) and the chord 2 b on the first layer
-    # (z = 0); the angle between it and the wall z = -1/2, measured inside the
-    # droplet
-    zt = h - 0.5
-    Rc = (b * b + zt * zt) / (2.0 * zt)
-    zc = zt - Rc
-    theta = np.degrees(np.arccos(np.clip(-(zc + 0.5) / Rc, -1.0, 1.0)))
-    return float(theta), float(h), float(b)
-
-
 def run_s2(steps=None, alphas=(-0.4, -0.2, 0.0, 0.2, 0.4), shape=(64, 1, 160), R=24,
-           models=("mirror", "potential")):
+           models=("mirror", "potential"), rho0s=(0.22, 1.0)):
     """The wetting study of Sec. 4.2: a quasi-2D droplet on the wall z = -1/2
     with wall potentials rho_s^1 = -rho0 alpha (alpha < 0) and
-    rho_s^2 = rho0 alpha (alpha > 0), rho0 = 0.22, tau = 1, for the modified
-    (mirror) and the original (point-wise potential) wall model: the static
-    contact angle and the density of component 1 on the wall outside the
-    droplet (thin film)."""
+    rho_s^2 = rho0 alpha (alpha > 0), tau = 1, for the modified (mirror) and
+    the original (point-wise potential) wall model: the static contact angle
+    and the density of component 1 on the wall outside the droplet (thin
+    film).  rho0 = 0.22 as printed, and rho0 = 1, the liquid density of these
+    droplets (the printed value is in the paper's own density scale)."""
     steps = steps or 20000
     G = wl.G_DROPLET
-    rho0 = 0.22
     thr = 0.5 * (1.0 + 0.03)
     out = {"case": "s2", "steps": steps, "shape": shape, "R": R, "G_eq7": G, "runs": {}}
     nz, ny, nx = shape
+    for rho0 in rho0s:
+        for model in models:
+            for al in alphas:
+                key = "%s/rho0=%g/%g" % (model, rho0, al)
+                rs = (-rho0 * al if al < 0 else 0.0, rho0 * al if al > 0 else 0.0)
+                lat = Lattice(shape, storage="f32", tau=(1.0, 1.0), G12=G, periodic=(1, 1, 0), rho_s=rs,
+                              wall_model=model)
+                r1, r2 = wl.hemisphere(shape, R)
+                lat.init_fields(r1, r2)
+                lat.step(steps)
+                try:
+                    red = lat.reduce()
+                except LBMError:
+                    out["runs"][key] = {"diverged": True}
+                    lat.close()
+                    continue
+                a, _, _ = lat.moments()
+                st = lat.droplet_stats(thr, origin=((nx - 1) / 2.0, 0.0, -0.5))
+                lat.close()
+                theta, h, b = dg.cap_contact_angle(a, thr)
+                out["runs"][key] = {
+                    "rho_s": rs, "contact_angle_deg": theta, "height": h, "half_width": b,
+                    "film_rho1": st["film_rho"], "droplet_area": st["volume"], "max_uF": red["max_uF"]}
+    return out
+
+
+def run_s3(steps=None, shape=(32, 1, 192), width=96, rho_s2=(0.0, 0.088, 0.4),
+           models=("mirror", "potential")):
+    """The static slug between flat plates of Sec. 4.2: channel height 32,
+    tau = 1, component 2 filling the middle section, rho_s^1 = 0 and
+    rho_s^2 = 0.088 (the printed value), 0.4 (the same alpha with the liquid
+    density of these slugs as rho0) and 0 (neutral), for the modified and the
+    original wall model: the contact angle inside the slug from circles fitted
+    to both menisci, and the density of component 2 on the first layer next
+    to the walls in the middle of the component-1 section (thin film) against
+    its bulk value there."""
+    steps = steps or 30000
+    G = wl.G_DROPLET
+    thr = 0.5 * (1.0 + 0.03)
+    nz, ny, nx = shape
+    out = {"case": "s3", "steps": steps, "shape": shape, "slug_width": width, "G_eq7": G, "runs": {}}
+    x0 = (nx - width) / 2.0
+    far = (0, max(1, (nx - width) // 6))     # cells next to x = 0, farthest from the slug
     for model in models:
-        for al in alphas:
-            rs = (-rho0 * al if al < 0 else 0.0, rho0 * al if al > 0 else 0.0)
-            lat = Lattice(shape, storage="f32", tau=(1.0, 1.0), G12=G, periodic=(1, 1, 0), rho_s=rs,
-                          wall_model=model)
-            r1, r2 = wl.hemisphere(shape, R)
+        for r2s in rho_s2:
+            key = "%s/%g" % (model, r2s)
+            lat = Lattice(shape, storage="f32", tau=(1.0, 1.0), G12=G, periodic=(1, 1, 0),
+                          rho_s=(0.0, r2s), wall_model=model)
+            r1, r2 = wl.slug(shape, x0, x0 + width)
             lat.init_fields(r1, r2)
             lat.step(steps)
             try:
                 red = lat.reduce()
             except LBMError:
-                out["runs"]["%s/%g" % (model, al)] = {"diverged": True}
+                out["runs"][key] = {"diverged": True}
                 lat.close()
                 continue
-            a, _, _ = lat.moments()
-            st = lat.droplet_stats(thr, origin=((nx - 1) / 2.0, 0.0, -0.5))
+            _, b, _ = lat.moments()
             lat.close()
-            theta, h, b = _cap_angle(a, thr)
-            out["runs"]["%s/%g" % (model, al)] = {
-                "rho_s": rs, "contact_angle_deg": theta, "height": h, "half_width": b,
-                "film_rho1": st["film_rho"], "droplet_area": st["volume"], "max_uF": red["max_uF"]}
+            theta, each = dg.slug_contact_angle(b, thr)
+            out["runs"][key] = {
+                "contact_angle_deg": theta, "per_meniscus_wall": each,
+                "film_rho2": dg.wall_layer_density(b, *far),
+                "bulk_rho2_outside": float(b[nz // 2, 0, far[0]:far[1]].mean()),
+                "max_uF": red["max_uF"]}
     return out
 
 
 def main():
     ap = argparse.ArgumentParser()
-    ap.add_argument("case", choices=["c0", "c1", "c2", "c3", "c4", "s1", "s2"])
+    ap.add_argument("case", choices=["c0", "c1", "c2", "c3", "c4", "s1", "s2", "s3"])
     ap.add_argument("--steps", type=int, default=None)
     ap.add_argument("--shape", type=int, nargs=3, default=None, help="nz ny nx (c1, c4)")
     ap.add_argument("--gravity", action="store_true", help="c4: tilted gravity")
@@ -318,7 +333,8 @@ def main():
     elif args.case == "c1":
         r = run_c1(args.steps, radii=args.radii, taus=args.taus, shape=args.shape)
     else:
-        r = {"c0": run_c0, "c2": run_c2, "c3": run_c3, "s1": run_s1, "s2": run_s2}[args.case](args.steps)
+        r = {"c0": run_c0, "c2": run_c2, "c3": run_c3, "s1": run_s1, "s2": run_s2,
+             "s3": run_s3}[args.case](args.steps)
     print(json.dumps(r, default=float))
 
 

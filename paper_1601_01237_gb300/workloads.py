@@ -12,7 +12,9 @@ Recipes (Otomo et al., arXiv:1601.01237):
   * spinodal mixture: rho^a = rho0 (1 + amp * U(-1, 1)), U from SplitMix64 over
     the linear cell index with seed + a;
   * hemisphere on a wall: a sphere centred on the wall plane z = -1/2 (the
-    wall-attached droplet of Sec. 4.2).
+    wall-attached droplet of Sec. 4.2);
+  * slug: component 2 filling a channel section between two flat interfaces
+    (the slug between plates of Sec. 4.2).
 
 Interaction strength: Eq. 7 takes a signed G (repulsion: G < 0).  The
 droplet cases quote 1.0 inside / 0.03 outside; G = -1.8 is the value whose
@@ -89,6 +91,17 @@ def hemisphere(shape, R, rho_in=1.0, rho_out=0.03, width=2.0):
     nz, ny, nx = shape
     r = _radius(shape, (-0.5, (ny - 1) / 2.0, (nx - 1) / 2.0))
     return tanh_profile(r, R, rho_in, rho_out, width)
+
+
+def slug(shape, x_left, x_right, rho_in=1.0, rho_out=0.03, width=2.0):
+    """Slug of component 2 filling the channel between x_left and x_right
+    (flat interfaces; the static slug between plates of Sec. 4.2); returns
+    (rho1, rho2)."""
+    nz, ny, nx = shape
+    x = np.broadcast_to(np.arange(nx, dtype=np.float64), shape)
+    d = np.minimum(x - x_left, x_right - x)
+    rho2, rho1 = tanh_profile(-d, 0.0, rho_in, rho_out, width)
+    return rho1, rho2
 
 
 def spinodal(shape, rho0=0.5, amp=0.01, seed=20160105):

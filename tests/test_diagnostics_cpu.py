@@ -1,0 +1,93 @@
+"""Host-side measurement helpers against fields whose answer is known by
+construction: circular caps and slug menisci of a given contact angle, drawn
+as tanh profiles around exact circles (the contact-angle measurement of
+Sec. 4.2 fits a circle to the interface)."""
+import math
+
+import numpy as np
+import pytest
+
+from paper_1601_01237_gb300 import diagnostics as dg
+
+W = 2.0
+HI, LO = 1.0, 0.03
+THR = 0.5 * (HI + LO)
+
+
+def _profile(d):
+    """Density rising from LO to HI across d = 0 (tanh, width W)."""
+    return LO + 0.5 * (HI - LO) * (1.0 + np.tanh(d / W))
+
+
+def _cap(theta_deg, Rc, shape=(64, 1, 160)):
+    """Droplet whose boundary is the circle of radius Rc meeting the wall
+    z = -1/2 at theta (inside the droplet): centre height -1/2 - Rc cos theta."""
+    nz, _, nx = shape
+    zc = -0.5 - Rc * math.cos(math.radians(theta_deg))
+    z, x = np.meshgrid(np.arange(nz, dtype=float), np.arange(nx, dtype=float), indexing="ij")
+    r = np.hypot(x - (nx - 1) / 2.0, z - zc)
+    return _profile(Rc - r)[:, None, :]
+
+
+def _slug(theta_deg, nz=32, nx=160, x_mid=50.0):
+    """Slug centred in x spanning the channel between the walls z = -1/2 and
+    nz - 1/2; each meniscus is a circular arc meeting both walls at theta
+    (inside the slug).  The profile runs across the arc along x."""
+    zc = (nz - 1) / 2.0
+    a = nz / 2.0
+    z = np.arange(nz, dtype=float)[:, None]
+    x = np.arange(nx, dtype=float)[None, :]
+    c = math.cos(math.radians(theta_deg))
+    if abs(c) < 1e-12:
+        xa = np.full_like(z, x_mid)
+    else:
+        R = a / abs(c)
+        # wetting slug: centre on the other component's side
+        xa = x_mid - math.copysign(1.0, c) * (R - np.sqrt(R * R - (z - zc) ** 2))
+    # left half: slug to the right of the arc; right half mirrored
+    d = np.where(x < nx / 2.0, x - xa, (nx - 1 - x) - xa)
+    return _profile(d)[:, None, :]
+
+
+@pytest.mark.parametrize("theta", [35.0, 60.0, 90.0, 115.0, 140.0])
+@pytest.mark.parametrize("Rc", [18.3, 24.0, 29.7])
+def test_cap_contact_angle_on_exact_caps(theta, Rc):
+    got, h, b = dg.cap_contact_angle(_cap(theta, Rc), THR)
+    zc = -0.5 - Rc * math.cos(math.radians(theta))
+    assert abs(h - (zc + Rc + 0.5)) < 0.05
+    assert abs(b - math.sqrt(Rc * Rc - zc * zc)) < 0.05
+    assert abs(got - theta) < 0.5
+
+
+@pytest.mark.parametrize("theta", [20.0, 40.0, 65.0, 90.0, 110.0, 140.0, 160.0])
+def test_slug_contact_angle_on_exact_menisci(theta):
+    got, each = dg.slug_contact_angle(_slug(theta), THR)
+    assert len(each) == 4
+    assert abs(got - theta) < 0.5
+    assert max(each) - min(each) < 0.5
+
+
+def test_slug_angle_is_the_supplement_for_the_other_component():
+    rho2 = _slug(40.0)
+    rho1 = HI + LO - rho2
+    # component 1 occupies the ends: roll it so that it sits in the middle
+    rho1 = np.roll(rho1, rho1.shape[2] // 2, axis=2)
+    t2, _ = dg.slug_contact_angle(rho2, THR)
+    t1, _ = dg.slug_contact_angle(rho1, THR)
+    assert abs(t1 + t2 - 180.0) < 1.0
+
+
+def test_fit_circle_recovers_centre_and_radius():
+    t = np.linspace(0.3, 1.4, 40)
+    x = 3.0 + 17.0 * np.cos(t)
+    z = -2.0 + 17.0 * np.sin(t)
+    xc, zc, R = dg.fit_circle(x, z)
+    assert abs(xc - 3.0) < 1e-9 and abs(zc + 2.0) < 1e-9 and abs(R - 17.0) < 1e-9
+
+
+def test_wall_layer_density():
+    r = np.zeros((8, 1, 20))
+    r[0, 0, :] = 0.1
+    r[-1, 0, :] = 0.3
+    r[0, 0, 5:10] = 9.0
+    assert abs(dg.wall_layer_density(r, 10, 20) - 0.2) < 1e-15

@@ -133,7 +133,6 @@ def test_neutral_wetting_keeps_90_degrees(gpu_lib):
     the wall layer outside it stays near the bulk minority density (no thin
     film)."""
     from paper_1601_01237_gb300 import Lattice
-    from paper_1601_01237_gb300.run_config import _cap_angle
     shape, R = (40, 1, 96), 14
     lat = Lattice(shape, storage="f32", tau=(1.0, 1.0), G12=wl.G_DROPLET, periodic=(1, 1, 0),
                   wall_model="mirror")
@@ -143,7 +142,7 @@ def test_neutral_wetting_keeps_90_degrees(gpu_lib):
     a, _, _ = lat.moments()
     st = lat.droplet_stats(0.515, origin=(47.5, 0.0, -0.5))
     lat.close()
-    theta, h, b = _cap_angle(a, 0.515)
+    theta, h, b = dg.cap_contact_angle(a, 0.515)
     print("neutral wetting: theta %.2f deg (h %.2f, b %.2f), film %.4f" % (theta, h, b, st["film_rho"]))
     assert abs(theta - 90.0) <= 2.0
     assert st["film_rho"] < 0.06
