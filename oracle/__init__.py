@@ -71,7 +71,7 @@ def make_params(shape, tau=(1.0, 1.0), G12=0.0, G21=None, g_ext=(0.0, 0.0, 0.0),
     p.G[0][1] = float(G12)
     p.G[1][0] = float(G12 if G21 is None else G21)
     p.rho_s[0], p.rho_s[1] = float(rho_s[0]), float(rho_s[1])
-    p.collision = {"bgk": 0, "regularized": 1}[collision]
+    p.collision = {"bgk": 0, "regularized": 1, "regularized3": 2}[collision]
     p.wall_model = {"potential": 0, "mirror": 1}[wall_model]
     return p
 

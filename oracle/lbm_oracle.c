@@ -27,7 +27,12 @@
  *    u + g/2 as Eq. 8 states.
  *  - The regularized non-equilibrium part (Eq. 11) is the second-order Hermite
  *    projection w_i/(2 T0^2) Q_i : Pi^neq, Q_i = c_i c_i - T0 I, with Pi^neq
- *    from the pre-collision populations and f^eq(rho^a, u).
+ *    from the pre-collision populations and f^eq(rho^a, u).  Sec. 2 also
+ *    keeps third-order non-equilibrium moments ("the energy flux"); the
+ *    collision = 2 variant adds the orthogonal projection (weighted by w_i)
+ *    of (f - f^eq) / w_i onto the span of the third-order Hermite polynomials
+ *    H_abc(c_i) = c_a c_b c_c - T0 (c_a d_bc + c_b d_ac + c_c d_ab) evaluated
+ *    on the lattice (every third-order moment the lattice can carry).
  *  - Walls (Sec. 4.1): half-way bounce-back; a solid site's density in
  *    Eq. 13 is rho'_b = rho_b(mirror cell) + rho_s^b for the modified model
  *    (zero normal derivative) or rho'_b = rho_s^b for the original
@@ -51,7 +56,8 @@ typedef struct {
     double G[2][2];
     double g_ext[3];   /* body acceleration added to every component */
     double rho_s[2];   /* wall potential of each component */
-    int collision;     /* 0 = BGK (Eq. 2), 1 = regularized filter (Eqs. 10-11) */
+    int collision;     /* 0 = BGK (Eq. 2), 1 = regularized filter (Eqs. 10-11),
+                          2 = the same with third-order moments kept */
     int wall_model;    /* 0 = point-wise wall potential, 1 = mirrored rho' + rho_s */
 } oracle_params;
 
@@ -59,6 +65,10 @@ static int C[Q][3];
 static double W[Q];
 static int OPP[Q];
 static int lattice_ready = 0;
+/* Orthonormal basis (inner product sum_i w_i g_i h_i) of the span of the
+ * third-order Hermite polynomials on the lattice, N3 vectors. */
+static double E3[10][Q];
+static int N3 = 0;
 
 /* D3Q19 (Sec. 2): enumerate every c in {-1,0,1}^3 with |c|^2 <= 2. */
 static void build_lattice(void)
@@ -78,6 +88,27 @@ static void build_lattice(void)
         for (int j = 0; j < Q; ++j)
             if (C[j][0] == -C[i][0] && C[j][1] == -C[i][1] && C[j][2] == -C[i][2])
                 OPP[i] = j;
+    /* Gram-Schmidt over H_abc, a <= b <= c; vectors that vanish on the
+     * lattice or depend on earlier ones are dropped */
+    N3 = 0;
+    for (int a = 0; a < 3; ++a)
+        for (int b = a; b < 3; ++b)
+            for (int c = b; c < 3; ++c) {
+                double v[Q];
+                for (int i = 0; i < Q; ++i)
+                    v[i] = C[i][a] * C[i][b] * C[i][c] -
+                           T0 * (C[i][a] * (b == c) + C[i][b] * (a == c) + C[i][c] * (a == b));
+                for (int k = 0; k < N3; ++k) {
+                    double d = 0.0;
+                    for (int i = 0; i < Q; ++i) d += W[i] * v[i] * E3[k][i];
+                    for (int i = 0; i < Q; ++i) v[i] -= d * E3[k][i];
+                }
+                double nn = 0.0;
+                for (int i = 0; i < Q; ++i) nn += W[i] * v[i] * v[i];
+                if (nn < 1e-24) continue;
+                for (int i = 0; i < Q; ++i) E3[N3][i] = v[i] / sqrt(nn);
+                ++N3;
+            }
     lattice_ready = 1;
 }
 
@@ -261,6 +292,14 @@ static void collide_cell(const oracle_params *p, int a, const double fin[Q], dou
                 }
             double fneq = W[i] / (2.0 * T0 * T0) * contr;
             fpost[i] = feq[i] + (1.0 - 1.0 / tau) * fneq + Fi[i];
+        }
+        if (p->collision == 2) {
+            /* third-order part: w_i sum_k E3_k(c_i) <E3_k, (f - f^eq) / w> */
+            for (int k = 0; k < N3; ++k) {
+                double coef = 0.0;
+                for (int i = 0; i < Q; ++i) coef += E3[k][i] * (fin[i] - feq[i]);
+                for (int i = 0; i < Q; ++i) fpost[i] += (1.0 - 1.0 / tau) * W[i] * E3[k][i] * coef;
+            }
         }
     }
 }

@@ -113,6 +113,69 @@ def test_collision_moments(collision):
             assert np.allclose(Pp, ref, atol=1e-14)
 
 
+def _hermite_basis(c, w, order):
+    """Values on the lattice of the Hermite polynomials of one order (all
+    index tuples a <= b <= ...), as rows."""
+    import itertools
+    d = np.eye(3)
+    rows = []
+    for idx in itertools.combinations_with_replacement(range(3), order):
+        if order == 0:
+            rows.append(np.ones(len(w)))
+        elif order == 1:
+            rows.append(c[:, idx[0]].astype(float))
+        elif order == 2:
+            a, b = idx
+            rows.append(c[:, a] * c[:, b] - T0 * d[a, b])
+        else:
+            a, b, e = idx
+            rows.append(c[:, a] * c[:, b] * c[:, e] - T0 * (c[:, a] * d[b, e] + c[:, b] * d[a, e] + c[:, e] * d[a, b]))
+    return np.array(rows, dtype=float)
+
+
+def test_regularized3_keeps_moments_to_third_order_and_drops_the_rest():
+    """Sec. 2: the filter keeps the non-equilibrium moments up to the chosen
+    order (second: momentum flux; third: energy flux) and removes the rest.
+    On D3Q19 the 19 populations split, in the w-weighted inner product, into
+    orders 0 (1), 1 (3), 2 (6), 3 (6: H_xxx, H_yyy, H_zzz and H_xyz vanish on
+    the lattice) and a 3-dimensional remainder.  So d = f* - f^eq(u + g) is
+    fixed by: no mass or momentum; second and third Hermite moments equal to
+    (1 - 1/tau) times those of f - f^eq(u); nothing in the remainder (computed
+    here as the w-orthogonal complement of orders 0-3 with an SVD)."""
+    c, w = oracle.lattice()
+    c = c.astype(float)
+    H = [_hermite_basis(c, w, k) for k in range(4)]
+    low = np.vstack(H)                                   # 1 + 3 + 6 + 10 rows (4 vanish)
+    # complement: h with sum_i w_i h_i H_k(c_i) = 0 for every k
+    _, sv, vt = np.linalg.svd(low * w[None, :])
+    rank = int((sv > 1e-12).sum())
+    assert rank == 16
+    comp = vt[rank:]
+    assert comp.shape[0] == 3
+    tau = 0.73
+    p = oracle.make_params((1, 1, 1), tau=(tau, tau), collision="regularized3")
+    for _ in range(4):
+        u = RNG.uniform(-0.08, 0.08, 3)
+        g = RNG.uniform(-0.01, 0.01, 3)
+        fin = oracle.feq(RNG.uniform(0.2, 1.5), RNG.uniform(-0.08, 0.08, 3)) * (1 + 0.05 * RNG.uniform(-1, 1, 19))
+        rho = fin.sum()
+        fp = oracle.collide_cell(p, 0, fin, rho, u, g)
+        d = fp - oracle.feq(rho, u + g)
+        neq = fin - oracle.feq(rho, u)
+        assert abs(d.sum()) < 1e-15
+        assert np.allclose(c.T @ d, 0.0, atol=1e-15)
+        assert np.allclose(H[2] @ d, (1 - 1 / tau) * (H[2] @ neq), atol=1e-15)
+        assert np.allclose(H[3] @ d, (1 - 1 / tau) * (H[3] @ neq), atol=1e-15)
+        assert np.allclose(comp @ d, 0.0, atol=1e-15)
+        # the remainder of the input is not zero: the test has something to drop
+        assert np.abs(comp @ neq).max() > 1e-5
+        # and the third-order part is really kept: the second-order filter differs
+        p2 = oracle.make_params((1, 1, 1), tau=(tau, tau), collision="regularized")
+        d2 = oracle.collide_cell(p2, 0, fin, rho, u, g) - oracle.feq(rho, u + g)
+        assert np.allclose(H[3] @ d2, 0.0, atol=1e-15)
+        assert np.abs(H[3] @ neq).max() > 1e-5
+
+
 def test_regularized_equals_bgk_at_tau_one_and_for_hermite_states():
     """At tau = 1 both operators return f^eq(u + g); for a population whose
     non-equilibrium part is a pure second-order Hermite term they agree at any tau."""
@@ -134,6 +197,17 @@ def test_regularized_equals_bgk_at_tau_one_and_for_hermite_states():
     pr = oracle.make_params((1, 1, 1), tau=(0.7, 0.7), collision="regularized")
     assert np.allclose(oracle.collide_cell(pb, 0, fin, rho, u, g), oracle.collide_cell(pr, 0, fin, rho, u, g),
                        atol=1e-15)
+    # third order: tau = 1 gives f^eq(u + g); a non-equilibrium part made of
+    # second- and third-order Hermite terms passes the filter unchanged
+    p3 = oracle.make_params((1, 1, 1), tau=(1.0, 1.0), collision="regularized3")
+    assert np.allclose(oracle.collide_cell(p3, 0, fin, rho, u, g), oracle.feq(rho, u + g), atol=1e-16)
+    H3 = _hermite_basis(c.astype(float), w, 3)
+    fin3 = fin + w * (np.array([2e-3, -1e-3, 5e-4, 1e-3, 0, -2e-3, 7e-4, 3e-4, -6e-4, 1e-3]) @ H3)
+    p3 = oracle.make_params((1, 1, 1), tau=(0.7, 0.7), collision="regularized3")
+    assert np.allclose(oracle.collide_cell(pb, 0, fin3, rho, u, g), oracle.collide_cell(p3, 0, fin3, rho, u, g),
+                       atol=1e-15)
+    assert not np.allclose(oracle.collide_cell(pr, 0, fin3, rho, u, g), oracle.collide_cell(p3, 0, fin3, rho, u, g),
+                           atol=1e-6)
 
 
 def test_sc_sum_sinusoid_closed_form():
@@ -236,7 +310,8 @@ def test_uniform_flow_is_galilean():
     assert np.allclose(a, 0.6, atol=1e-14) and np.allclose(b, 0.4, atol=1e-14)
 
 
-@pytest.mark.parametrize("collision,tau", [("bgk", (0.8, 0.8)), ("regularized", (0.6, 1.3))])
+@pytest.mark.parametrize("collision,tau", [("bgk", (0.8, 0.8)), ("regularized", (0.6, 1.3)),
+                                           ("regularized3", (0.6, 1.3))])
 def test_mass_and_momentum_conservation(collision, tau):
     """Periodic lattice, symmetric G: each component's mass is conserved and so
     is the total momentum sum_x sum_a j^a, since the pairwise Shan-Chen forces
