@@ -59,7 +59,13 @@ typedef enum {
 
 typedef enum {
     LBM_BGK = 0,          /* Eq. 2 */
-    LBM_REGULARIZED = 1   /* Eqs. 10-11, second-order Hermite projection */
+    LBM_REGULARIZED = 1,  /* Eqs. 10-11, second-order Hermite projection */
+    LBM_REGULARIZED3 = 2  /* Eqs. 10-11 keeping also the third-order
+                             non-equilibrium moments ("energy flux", Sec. 2):
+                             f^neq is the w-weighted projection of
+                             (f - f^eq) / w_i onto the second- and
+                             third-order Hermite polynomials that D3Q19
+                             carries (6 + 6 of them); forward only */
 } lbm_collision;
 
 /* Density a solid site presents to the interaction sum of Eq. 13. */
@@ -190,7 +196,8 @@ lbm_status lbm_sync(lbm_lattice *h);
  * reverse pass (adjoint fields of 2 x 19 values per cell, one checkpoint
  * segment of states and of their densities); both are held until the next
  * lbm_record or lbm_destroy, so that lbm_adjoint allocates nothing.
- * Synchronizes.  Errors: LBM_EINVAL, LBM_ENOMEM, LBM_ECUDA. */
+ * Synchronizes.  Errors: LBM_EINVAL, LBM_ENOMEM, LBM_ECUDA, LBM_ENOTSUP
+ * (collision LBM_REGULARIZED3, which has no reverse pass). */
 lbm_status lbm_record(lbm_lattice *h, long n_steps, int ckpt_every);
 
 /* Reverse pass over the last lbm_record.  Inputs dL_drho1, dL_drho2: N values

@@ -17,7 +17,7 @@ STATUS_NAMES = {0: "LBM_OK", 1: "LBM_EINVAL", 2: "LBM_ENOMEM", 3: "LBM_ECUDA",
                 4: "LBM_ENOTSUP", 5: "LBM_ENUMERIC"}
 # lbm_storage, lbm_collision, lbm_wall_model
 STORAGE = {"f64": 0, "f32": 1, "f16_dev": 2, "bf16_dev": 3}
-COLLISION = {"bgk": 0, "regularized": 1}
+COLLISION = {"bgk": 0, "regularized": 1, "regularized3": 2}
 WALL_MODEL = {"potential": 0, "mirror": 1}
 
 

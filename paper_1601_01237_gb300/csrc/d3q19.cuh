@@ -48,6 +48,75 @@ __host__ __device__ constexpr R w(int i) { return (R)wd(i); }
 // rounded FP32 values of 1/3, 1/18, 1/36 sum to 1 + 1.5e-8, which would add
 // that fraction of mass times 1/tau at every BGK collision.
 __host__ __device__ constexpr int k36(int i) { return i == 0 ? 12 : (i < 7 ? 2 : 1); }
+__host__ __device__ constexpr int ca(int i, int a) { return a == 0 ? cx(i) : (a == 1 ? cy(i) : cz(i)); }
+
+// Third-order Hermite polynomials on D3Q19.  Of the ten H_abc, four vanish on
+// the lattice (H_xxx, H_yyy, H_zzz because c^3 = c and 3 T0 = 1; H_xyz because
+// no direction has three non-zero components).  The other six pair up along
+// the axis a of the odd index, with b < c the two other axes:
+//   H_abb + H_acc = c_a (c_b^2 + c_c^2 - 2 T0)   (the energy flux along a)
+//   H_abb - H_acc = c_a (c_b^2 - c_c^2)
+// which are w-orthogonal on the lattice with norms 2/27 and 6/27.  h3s3 is
+// 3 (H_abb + H_acc) and h3d is H_abb - H_acc, both integers.
+__host__ __device__ constexpr int h3s3(int i, int a)
+{
+    return ca(i, a) * (3 * (ca(i, (a + 1) % 3) * ca(i, (a + 1) % 3) + ca(i, (a + 2) % 3) * ca(i, (a + 2) % 3)) - 2);
+}
+__host__ __device__ constexpr int h3d(int i, int a)
+{
+    // b < c: (y, z) for a = x, (x, z) for a = y, (x, y) for a = z
+    return ca(i, a) * (a == 0 ? cy(i) * cy(i) - cz(i) * cz(i)
+                              : (a == 1 ? cx(i) * cx(i) - cz(i) * cz(i) : cx(i) * cx(i) - cy(i) * cy(i)));
+}
+
+// Third-order part of the regularized filter for one component: accumulate
+// the sums of h3s3 f_i and h3d f_i over the directions (add3), then subtract
+// the same moments of f^eq(rho, u) (the third-order equilibrium of Eq. 3 on
+// D3Q19 has sum_i (H_abb + H_acc) f^eq_i = rho u_a (u_b^2 + u_c^2) / 2 and
+// sum_i (H_abb - H_acc) f^eq_i = 3 rho u_a (u_b^2 - u_c^2) / 2) to get
+//   S_a = sum_i (H_abb + H_acc)(f_i - f^eq_i),  D_a = sum_i (H_abb - H_acc)(f_i - f^eq_i).
+// The projection of (f - f^eq)/w onto the six polynomials then gives
+//   f^neq3_i = (k_i / 8) sum_a (S_a h3s3(i, a) + D_a h3d(i, a))
+// (w_i = k_i / 36; coefficients 1/(2/27) and 1/(6/27) on the pair basis).
+template <class R>
+struct Third {
+    R s[3], d[3];
+    __device__ __forceinline__ void zero()
+    {
+#pragma unroll
+        for (int a = 0; a < 3; ++a) { s[a] = R(0); d[a] = R(0); }
+    }
+    __device__ __forceinline__ void add(int i, R f)
+    {
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+            if (h3s3(i, a)) s[a] += R(h3s3(i, a)) * f;
+            if (h3d(i, a)) d[a] += R(h3d(i, a)) * f;
+        }
+    }
+    __device__ __forceinline__ void finish(R rho, R ux, R uy, R uz)
+    {
+        const R u[3] = {ux, uy, uz};
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+            const R ub = u[a == 0 ? 1 : 0], uc = u[a == 2 ? 1 : 2];
+            const R ra = rho * u[a];
+            s[a] = s[a] * (R(1) / R(3)) - R(0.5) * ra * (ub * ub + uc * uc);
+            d[a] = d[a] - R(1.5) * ra * (ub * ub - uc * uc);
+        }
+    }
+    // f^neq3 of direction i (the opposite direction takes the negative)
+    __device__ __forceinline__ R odd(int i) const
+    {
+        R r = R(0);
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+            if (h3s3(i, a)) r += R(h3s3(i, a)) * s[a];
+            if (h3d(i, a)) r += R(h3d(i, a)) * d[a];
+        }
+        return R(k36(i)) * R(0.125) * r;
+    }
+};
 
 // ---------------------------------------------------------------------------
 // Storage formats.  R = arithmetic type, T = stored type.  The *_DEV formats
@@ -164,11 +233,12 @@ __device__ __forceinline__ R cdot(int i, R ux, R uy, R uz)
 // Collision of one component in place: f[] holds the pre-collision f_i^a and
 // receives the post-collision f*_i^a (Eq. 1 with Eq. 2, or Eq. 10), including
 // the forcing term F_i = f^eq_i(rho, u + g) - f^eq_i(rho, u).
-//   BGK:          f* = f^eq(u + g) + (1 - 1/tau) (f - f^eq(u))
-//   regularized:  f* = f^eq(u + g) + (1 - 1/tau) w_i/(2 T0^2) Q_i : Pi^neq,
+//   BGK (REG = 0):         f* = f^eq(u + g) + (1 - 1/tau) (f - f^eq(u))
+//   regularized (REG = 1): f* = f^eq(u + g) + (1 - 1/tau) w_i/(2 T0^2) Q_i : Pi^neq,
 //                 Pi^neq = sum_i c_i c_i f_i - rho (T0 I + u u);
 //                 w_i/(2 T0^2) = k_i / 8 and Q_i : Pi = c_i c_i : Pi - tr(Pi)/3.
-template <class R, bool REG>
+//   REG = 2: the regularized f^neq plus its third-order part (struct Third).
+template <class R, int REG>
 __device__ __forceinline__ void collide(R (&f)[Q], R rho, R ux, R uy, R uz,
                                         R gx, R gy, R gz, R omega)
 {
@@ -213,6 +283,13 @@ __device__ __forceinline__ void collide(R (&f)[Q], R rho, R ux, R uy, R uz,
         pxz -= rho * ux * uz;
         pyz -= rho * uy * uz;
         const R t = (pxx + pyy + pzz) / R(3);
+        Third<R> th;
+        if (REG == 2) {
+            th.zero();
+#pragma unroll
+            for (int i = 1; i < Q; ++i) th.add(i, f[i]);
+            th.finish(rho, ux, uy, uz);
+        }
         // f^neq_i = (k_i / 8) (c_i c_i : Pi - tr(Pi) / 3)
         {
             const R s0 = rq * R(12) * (R(1) - R(1.5) * vsq);
@@ -228,10 +305,11 @@ __device__ __forceinline__ void collide(R (&f)[Q], R rho, R ux, R uy, R uz,
             if (cx(i) && cz(i)) cc += (cx(i) == cz(i) ? R(2) : R(-2)) * pxz;
             if (cy(i) && cz(i)) cc += (cy(i) == cz(i) ? R(2) : R(-2)) * pyz;
             const R fneq = R(k36(i)) * R(0.125) * (cc - t);   // same for i and opp(i)
+            const R f3 = REG == 2 ? th.odd(i) : R(0);          // odd: -f3 for opp(i)
             R sp, sm;
             feq_pair<R>(rq * R(k36(i)), cdot<R>(i, vx, vy, vz), vsq, sp, sm);
-            f[i] = sp + keep * fneq;
-            f[i + 1] = sm + keep * fneq;
+            f[i] = sp + keep * (fneq + f3);
+            f[i + 1] = sm + keep * (fneq - f3);
         }
     }
 }

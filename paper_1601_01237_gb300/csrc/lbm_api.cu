@@ -154,7 +154,7 @@ lbm_status lbm_create(const lbm_params *pp, lbm_lattice **out)
         return fail(LBM_EINVAL, "lbm_create: rho0_dev applies to the 16-bit deviation formats only");
     if (p.storage == LBM_F32 && p.rho0_dev != 0.0)
         return fail(LBM_EINVAL, "lbm_create: rho0_dev applies to the 16-bit deviation formats only");
-    if (p.collision != LBM_BGK && p.collision != LBM_REGULARIZED)
+    if (p.collision != LBM_BGK && p.collision != LBM_REGULARIZED && p.collision != LBM_REGULARIZED3)
         return fail(LBM_EINVAL, "lbm_create: unknown collision %d", p.collision);
     if (p.wall_model != LBM_WALL_POTENTIAL && p.wall_model != LBM_WALL_MIRROR)
         return fail(LBM_EINVAL, "lbm_create: unknown wall model %d", p.wall_model);
@@ -599,6 +599,8 @@ lbm_status lbm_record(lbm_lattice *h, long n_steps, int ckpt_every)
     if (!h) return fail(LBM_EINVAL, "lbm_record: NULL handle");
     if (n_steps < 1 || ckpt_every < 1)
         return fail(LBM_EINVAL, "lbm_record: n_steps = %ld and ckpt_every = %d must be >= 1", n_steps, ckpt_every);
+    if (h->phys.collision == LBM_REGULARIZED3)
+        return fail(LBM_ENOTSUP, "lbm_record: the third-order regularized collision has no reverse pass");
     DeviceGuard g(h->device);
     size_t sb = 0;
     lbm_state_bytes(h, &sb);
@@ -805,7 +807,7 @@ lbm_status lbm_step_noalloc(const lbm_params *pp, const void *f_in, void *f_out)
         return fail(LBM_EINVAL, "lbm_step_noalloc: unknown storage %d", p.storage);
     if ((p.storage == LBM_F64 || p.storage == LBM_F32) && p.rho0_dev != 0.0)
         return fail(LBM_EINVAL, "lbm_step_noalloc: rho0_dev applies to the 16-bit deviation formats only");
-    if (p.collision != LBM_BGK && p.collision != LBM_REGULARIZED)
+    if (p.collision != LBM_BGK && p.collision != LBM_REGULARIZED && p.collision != LBM_REGULARIZED3)
         return fail(LBM_EINVAL, "lbm_step_noalloc: unknown collision %d", p.collision);
     if (p.wall_model != LBM_WALL_POTENTIAL && p.wall_model != LBM_WALL_MIRROR)
         return fail(LBM_EINVAL, "lbm_step_noalloc: unknown wall model %d", p.wall_model);

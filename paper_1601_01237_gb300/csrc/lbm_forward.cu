@@ -150,7 +150,7 @@ k_density(const typename Store<S>::T *__restrict__ f, typename Store<S>::R *__re
     }
 }
 
-template <int S, bool REG>
+template <int S, int REG>
 __global__ void __launch_bounds__(kThreads)
 k_collide(const typename Store<S>::T *__restrict__ fin, typename Store<S>::T *__restrict__ fout,
           const typename Store<S>::R *__restrict__ rho, Phys<typename Store<S>::R> p)
@@ -357,9 +357,11 @@ cudaError_t step_split_t(const HostPhys &h, const void *fin, void *fout, void *r
     k_density<S><<<g, kThreads, 0, s>>>((const T *)fin, (R *)rho, p);
     if (ev) cudaEventRecord(ev[1], s);
     if (h.collision == LBM_REGULARIZED)
-        k_collide<S, true><<<g, kThreads, 0, s>>>((const T *)fin, (T *)fout, (const R *)rho, p);
+        k_collide<S, 1><<<g, kThreads, 0, s>>>((const T *)fin, (T *)fout, (const R *)rho, p);
+    else if (h.collision == LBM_REGULARIZED3)
+        k_collide<S, 2><<<g, kThreads, 0, s>>>((const T *)fin, (T *)fout, (const R *)rho, p);
     else
-        k_collide<S, false><<<g, kThreads, 0, s>>>((const T *)fin, (T *)fout, (const R *)rho, p);
+        k_collide<S, 0><<<g, kThreads, 0, s>>>((const T *)fin, (T *)fout, (const R *)rho, p);
     if (ev) cudaEventRecord(ev[2], s);
     return cudaGetLastError();
 }

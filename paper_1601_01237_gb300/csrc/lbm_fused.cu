@@ -229,7 +229,7 @@ __device__ __forceinline__ void halo_sum(const typename Store<S>::R (&v)[kPer], 
 // Collision of both components at the thread's interior cell of plane z (the
 // populations come from the stash, densities from the ring, momentum from the
 // moment buffer), forcing term included, result stored at the cell.
-template <int S, bool REG>
+template <int S, int REG>
 __device__ __forceinline__ void collide_cell(typename Store<S>::T *__restrict__ fout, const Phys<typename Store<S>::R> &p,
                                              const FusedSmem<typename Store<S>::R> &sm, int sl_m, int sl_c, int sl_p,
                                              int st, long long cell, typename Store<S>::R *__restrict__ s_out)
@@ -281,13 +281,16 @@ __device__ __forceinline__ void collide_cell(typename Store<S>::T *__restrict__ 
 
     // Regularized: second moments of f - f^eq(u): Pi = sum c c f - rho (T0 I + u u)
     R P1[6], P2[6], t1 = 0, t2 = 0;
+    Third<R> th1, th2;   // REG = 2: third-order moments of f - f^eq(u)
     if (REG) {
 #pragma unroll
         for (int k = 0; k < 6; ++k) { P1[k] = 0; P2[k] = 0; }
+        if (REG == 2) { th1.zero(); th2.zero(); }
 #pragma unroll
         for (int i = 1; i < Q; ++i) {
             const float2 fp = s0[i * kThreadsF];
             const R fa = fp.x, fb = fp.y;
+            if (REG == 2) { th1.add(i, fa); th2.add(i, fb); }
             if (cx(i)) { P1[0] += fa; P2[0] += fb; }
             if (cy(i)) { P1[1] += fa; P2[1] += fb; }
             if (cz(i)) { P1[2] += fa; P2[2] += fb; }
@@ -304,6 +307,7 @@ __device__ __forceinline__ void collide_cell(typename Store<S>::T *__restrict__ 
         P1[5] -= r1 * uy * uz; P2[5] -= r2 * uy * uz;
         t1 = (P1[0] + P1[1] + P1[2]) / R(3);
         t2 = (P2[0] + P2[1] + P2[2]) / R(3);
+        if (REG == 2) { th1.finish(r1, ux, uy, uz); th2.finish(r2, ux, uy, uz); }
     }
     // rest population (k_0 = 12)
     {
@@ -350,10 +354,13 @@ __device__ __forceinline__ void collide_cell(typename Store<S>::T *__restrict__ 
             if (cy(i) && cz(i)) { const R sg = cy(i) == cz(i) ? R(2) : R(-2); cc1 += sg * P1[5]; cc2 += sg * P2[5]; }
             const R n1 = keep1 * (R(k36(i)) * R(0.125)) * (cc1 - t1);
             const R n2 = keep2 * (R(k36(i)) * R(0.125)) * (cc2 - t2);
-            o1p = rw1 * (E1 + O1) + n1;
-            o1m = rw1 * (E1 - O1) + n1;
-            o2p = rw2 * (E2 + O2) + n2;
-            o2m = rw2 * (E2 - O2) + n2;
+            // third-order part, odd in c_i: + for i, - for opp(i)
+            const R m1 = REG == 2 ? keep1 * th1.odd(i) : R(0);
+            const R m2 = REG == 2 ? keep2 * th2.odd(i) : R(0);
+            o1p = rw1 * (E1 + O1) + n1 + m1;
+            o1m = rw1 * (E1 - O1) + n1 - m1;
+            o2p = rw2 * (E2 + O2) + n2 + m2;
+            o2m = rw2 * (E2 - O2) + n2 - m2;
         }
         const R ref = w<R>(i) * ref0;
         const size_t ip = 2 * (size_t)((unsigned)i * N32), im = 2 * (size_t)((unsigned)(i + 1) * N32);
@@ -408,7 +415,7 @@ __device__ __forceinline__ void halo_combine(const Phys<R> &p, FusedSmem<R> &sm,
     sm.ring[slot][hy][hx] = make_float2(r1, r2);
 }
 
-template <int S, bool REG, bool WALLZ, int LZ>
+template <int S, int REG, bool WALLZ, int LZ>
 __global__ void __launch_bounds__(kThreadsF, 2)
 k_step_fused(const typename Store<S>::T *__restrict__ fin, typename Store<S>::T *__restrict__ fout,
              Phys<typename Store<S>::R> p, int ntx, typename Store<S>::R *__restrict__ s_out)
@@ -582,12 +589,14 @@ cudaError_t fused_t(const HostPhys &h, const void *fin, void *fout, cudaStream_t
     static bool attr_set = false;
     if (!attr_set) {
         cudaError_t e = cudaSuccess;
-        const void *fns[8] = {
-            (const void *)k_step_fused<S, true, false, kLZmax>, (const void *)k_step_fused<S, false, false, kLZmax>,
-            (const void *)k_step_fused<S, true, false, kLZsmall>, (const void *)k_step_fused<S, false, false, kLZsmall>,
-            (const void *)k_step_fused<S, true, true, kLZmax>, (const void *)k_step_fused<S, false, true, kLZmax>,
-            (const void *)k_step_fused<S, true, true, kLZsmall>, (const void *)k_step_fused<S, false, true, kLZsmall>};
-        for (int q = 0; q < 8 && e == cudaSuccess; ++q)
+        const void *fns[12] = {
+            (const void *)k_step_fused<S, 1, false, kLZmax>, (const void *)k_step_fused<S, 0, false, kLZmax>,
+            (const void *)k_step_fused<S, 1, false, kLZsmall>, (const void *)k_step_fused<S, 0, false, kLZsmall>,
+            (const void *)k_step_fused<S, 1, true, kLZmax>, (const void *)k_step_fused<S, 0, true, kLZmax>,
+            (const void *)k_step_fused<S, 1, true, kLZsmall>, (const void *)k_step_fused<S, 0, true, kLZsmall>,
+            (const void *)k_step_fused<S, 2, false, kLZmax>, (const void *)k_step_fused<S, 2, false, kLZsmall>,
+            (const void *)k_step_fused<S, 2, true, kLZmax>, (const void *)k_step_fused<S, 2, true, kLZsmall>};
+        for (int q = 0; q < 12 && e == cudaSuccess; ++q)
             e = cudaFuncSetAttribute(fns[q], cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemBytes);
         if (e != cudaSuccess) return e;
         attr_set = true;
@@ -595,15 +604,18 @@ cudaError_t fused_t(const HostPhys &h, const void *fin, void *fout, cudaStream_t
     if (ev) cudaEventRecord(ev[0], s);
     const T *fi = (const T *)fin;
     T *fo = (T *)fout;
-    const bool reg = h.collision == LBM_REGULARIZED;
 #define LBM_LAUNCH(REG_, WALL_, LZ_) k_step_fused<S, REG_, WALL_, LZ_><<<grid, kThreadsF, kSmemBytes, s>>>(fi, fo, p, ntx, (R *)s_out)
-    if (h.wall_z) {
-        if (reg) { if (small) LBM_LAUNCH(true, true, kLZsmall); else LBM_LAUNCH(true, true, kLZmax); }
-        else { if (small) LBM_LAUNCH(false, true, kLZsmall); else LBM_LAUNCH(false, true, kLZmax); }
-    } else {
-        if (reg) { if (small) LBM_LAUNCH(true, false, kLZsmall); else LBM_LAUNCH(true, false, kLZmax); }
-        else { if (small) LBM_LAUNCH(false, false, kLZsmall); else LBM_LAUNCH(false, false, kLZmax); }
+#define LBM_LAUNCH_W(REG_)                                                                   \
+    do {                                                                                     \
+        if (h.wall_z) { if (small) LBM_LAUNCH(REG_, true, kLZsmall); else LBM_LAUNCH(REG_, true, kLZmax); }   \
+        else { if (small) LBM_LAUNCH(REG_, false, kLZsmall); else LBM_LAUNCH(REG_, false, kLZmax); }          \
+    } while (0)
+    switch (h.collision) {
+    case LBM_REGULARIZED: LBM_LAUNCH_W(1); break;
+    case LBM_REGULARIZED3: LBM_LAUNCH_W(2); break;
+    default: LBM_LAUNCH_W(0); break;
     }
+#undef LBM_LAUNCH_W
 #undef LBM_LAUNCH
     if (ev) cudaEventRecord(ev[1], s);
     return cudaGetLastError();

@@ -10,7 +10,9 @@ c2  spinodal mixture 256^3: FP32 / FP16-dev / BF16-dev, MLUPS, mass drift,
     interface measure <|rho1 - rho2|>
 c3  differentiation 96^3: loss, gradients (tied G, tau_1), adjoint/forward time
 s1  the static-droplet study: quasi-2D droplets (R = 8-24, side 5 R) at
-    tau = 0.7-3, BGK and regularized: surface tension per tau, spurious current
+    tau = 0.7-3, BGK and regularized (--collisions, --taus for subsets; the
+    third-order filter is "regularized3"): surface tension per tau, spurious
+    current
 s2  the wetting study: a quasi-2D droplet on a wall, wall potentials from
     alpha = -0.4 .. 0.4, modified vs original wall model: contact angle, film
 s3  the static slug between plates (channel height 32): contact angle inside
@@ -326,10 +328,15 @@ def main():
     ap.add_argument("--gravity", action="store_true", help="c4: tilted gravity")
     ap.add_argument("--wall-model", default="mirror", choices=["mirror", "potential"], help="c4")
     ap.add_argument("--radii", type=int, nargs="+", default=None, help="c1")
-    ap.add_argument("--taus", type=float, nargs="+", default=None, help="c1")
+    ap.add_argument("--taus", type=float, nargs="+", default=None, help="c1, s1")
+    ap.add_argument("--collisions", nargs="+", default=None, choices=["bgk", "regularized", "regularized3"],
+                    help="s1")
     args = ap.parse_args()
     if args.case == "c4":
         r = run_c4(args.steps, args.shape, args.gravity, args.wall_model)
+    elif args.case == "s1":
+        kw = {k: v for k, v in (("taus", args.taus), ("collisions", args.collisions)) if v}
+        r = run_s1(args.steps, **kw)
     elif args.case == "c1":
         r = run_c1(args.steps, radii=args.radii, taus=args.taus, shape=args.shape)
     else:

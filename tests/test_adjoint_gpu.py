@@ -148,6 +148,12 @@ def test_adjoint_errors(gpu_lib):
     par = lat.adjoint(np.zeros((4, 4, 4)))
     assert par == [0.0, 0.0, 0.0, 0.0]
     lat.close()
+    # the third-order regularized collision has no reverse pass
+    lat = Lattice((4, 4, 4), storage="f32", collision="regularized3")
+    lat.init_fields(np.full((4, 4, 4), 0.5), np.full((4, 4, 4), 0.5))
+    with pytest.raises(LBMError, match="ENOTSUP"):
+        lat.record(3, 1)
+    lat.close()
 
 
 def test_adjoint_repeated_calls_agree(gpu_lib):

@@ -30,6 +30,9 @@ CASES = [
     ("single_layer_walls", (1, 6, 5), dict(tau=(0.9, 0.9), G12=-1.0, periodic=(1, 1, 0))),
     ("nx1_ny1", (7, 1, 1), dict(tau=(0.8, 0.8), G12=-1.2)),
     ("quasi2d", (1, 9, 11), dict(tau=(1.0, 1.0), G12=G_DROP)),
+    ("periodic_reg3", (5, 4, 6), dict(tau=(0.6, 1.1), G12=-1.4, g_ext=(1e-4, 0, -5e-5), collision="regularized3")),
+    ("wall_mirror_rhos_reg3", (5, 6, 4), dict(tau=(0.7, 1.2), G12=-1.3, periodic=(1, 1, 0), rho_s=(0.05, 0.1),
+                                              collision="regularized3")),
 ]
 
 
@@ -277,6 +280,9 @@ FUSED_CASES = [
                                             rho_s=(0.02, 0.01))),
     ("cluster_walls_potential", (6, 5, 256), dict(tau=(1.0, 0.8), G12=-1.1, periodic=(1, 1, 0),
                                                  wall_model="potential", rho_s=(0.05, 0.0))),
+    ("ragged_reg3", (37, 19, 45), dict(tau=(0.6, 1.3), G12=-1.3, g_ext=(1e-5, -2e-5, 1e-5), collision="regularized3")),
+    ("walls_reg3", (20, 9, 128), dict(tau=(0.7, 0.9), G12=-1.2, periodic=(1, 1, 0), collision="regularized3",
+                                      rho_s=(0.0, 0.05))),
 ]
 
 
