@@ -37,6 +37,11 @@
  *    Eq. 13 is rho'_b = rho_b(mirror cell) + rho_s^b for the modified model
  *    (zero normal derivative) or rho'_b = rho_s^b for the original
  *    point-wise wall potential.
+ *  - Staircase walls of any shape (the inclined walls of Sec. 4.2) are a mask
+ *    of solid sites: half-way bounce-back on every link into a solid site,
+ *    and a solid site's density in Eq. 13 is the w-weighted mean of its
+ *    fluid neighbours' densities (plus rho_s) for the modified model, rho_s
+ *    for the original one.
  *  - G is taken literally as printed in Eq. 7 (signed; a repulsive
  *    interaction has G < 0).  The wall force of Eq. 13 uses the same G^{ab}.
  *
@@ -59,6 +64,8 @@ typedef struct {
     int collision;     /* 0 = BGK (Eq. 2), 1 = regularized filter (Eqs. 10-11),
                           2 = the same with third-order moments kept */
     int wall_model;    /* 0 = point-wise wall potential, 1 = mirrored rho' + rho_s */
+    const unsigned char *solid;  /* N flags, 1 = solid site inside the lattice
+                                    (staircase walls of any shape); NULL = none */
 } oracle_params;
 
 static int C[Q][3];
@@ -148,13 +155,20 @@ static int wrap(int v, int n)
     return v < 0 ? v + n : v;
 }
 
-/* Is lattice site (x,y,z) (possibly out of range) a solid wall site? */
+/* Is lattice site (x,y,z), inside the lattice, flagged solid in the mask? */
+static int mask_solid(const oracle_params *p, int x, int y, int z)
+{
+    return p->solid && p->solid[cell_index(p, x, y, z)];
+}
+
+/* Is lattice site (x,y,z) (possibly out of range) a solid wall site: beyond a
+ * non-periodic end, or (after periodic wrap) flagged in the mask? */
 static int is_solid(const oracle_params *p, int x, int y, int z)
 {
     if (!p->periodic[0] && (x < 0 || x >= p->nx)) return 1;
     if (!p->periodic[1] && (y < 0 || y >= p->ny)) return 1;
     if (!p->periodic[2] && (z < 0 || z >= p->nz)) return 1;
-    return 0;
+    return mask_solid(p, wrap(x, p->nx), wrap(y, p->ny), wrap(z, p->nz));
 }
 
 /* Eqs. 4-6: rho^a = sum_i f_i^a; rho = sum_a rho^a;
@@ -165,6 +179,11 @@ void oracle_moments_raw(const oracle_params *p, const double *f,
     build_lattice();
     long N = (long)p->nx * p->ny * p->nz;
     for (long s = 0; s < N; ++s) {
+        if (p->solid && p->solid[s]) {   /* no fluid at a solid site */
+            rho1[s] = rho2[s] = 0.0;
+            u[3 * s] = u[3 * s + 1] = u[3 * s + 2] = 0.0;
+            continue;
+        }
         double r[2] = {0.0, 0.0}, j[3] = {0.0, 0.0, 0.0};
         for (int a = 0; a < 2; ++a)
             for (int i = 0; i < Q; ++i) {
@@ -185,11 +204,29 @@ void oracle_moments_raw(const oracle_params *p, const double *f,
 
 /* Density a solid site presents to the interaction sum (Eq. 13): the
  * modified model mirrors the adjacent fluid cell across the wall (zero
- * normal derivative) and adds rho_s; the original model uses rho_s alone. */
+ * normal derivative) and adds rho_s; the original model uses rho_s alone.
+ * A solid site of the mask has no single mirror cell: its density is the
+ * mean of rho_b over its fluid neighbours, weighted by w_i (a volumetric
+ * construction whose normal derivative vanishes for fields that vary along
+ * the wall normal only), plus rho_s. */
 static double wall_density(const oracle_params *p, const double *rho_b, double rho_s,
                            int x, int y, int z)
 {
     if (p->wall_model == 0) return rho_s;
+    {
+        int in = (p->periodic[0] || (x >= 0 && x < p->nx)) && (p->periodic[1] || (y >= 0 && y < p->ny)) &&
+                 (p->periodic[2] || (z >= 0 && z < p->nz));
+        if (in && mask_solid(p, wrap(x, p->nx), wrap(y, p->ny), wrap(z, p->nz))) {
+            double num = 0.0, den = 0.0;
+            for (int i = 1; i < Q; ++i) {
+                int X = x + C[i][0], Y = y + C[i][1], Z = z + C[i][2];
+                if (is_solid(p, X, Y, Z)) continue;
+                num += W[i] * rho_b[cell_index(p, wrap(X, p->nx), wrap(Y, p->ny), wrap(Z, p->nz))];
+                den += W[i];
+            }
+            return (den > 0.0 ? num / den : 0.0) + rho_s;
+        }
+    }
     int mx = x, my = y, mz = z;
     if (!p->periodic[0]) { if (mx < 0) mx = -1 - mx; else if (mx >= p->nx) mx = 2 * p->nx - 1 - mx; }
     else mx = wrap(mx, p->nx);
@@ -197,6 +234,8 @@ static double wall_density(const oracle_params *p, const double *rho_b, double r
     else my = wrap(my, p->ny);
     if (!p->periodic[2]) { if (mz < 0) mz = -1 - mz; else if (mz >= p->nz) mz = 2 * p->nz - 1 - mz; }
     else mz = wrap(mz, p->nz);
+    /* a mirror cell that is itself solid presents its own wall density */
+    if (mask_solid(p, mx, my, mz)) return wall_density(p, rho_b, rho_s, mx, my, mz);
     return rho_b[cell_index(p, mx, my, mz)] + rho_s;
 }
 
@@ -249,6 +288,7 @@ void oracle_accelerations(const oracle_params *p, const double *rho1, const doub
     for (long s = 0; s < N; ++s)
         for (int a = 0; a < 2; ++a)
             for (int d = 0; d < 3; ++d) {
+                if (p->solid && p->solid[s]) { g[a][3 * s + d] = 0.0; continue; }
                 double Fsum = 0.0;
                 for (int b = 0; b < 2; ++b) {
                     double F = p->G[a][b] * rho[a][s] * Sf[b][3 * s + d];
@@ -316,6 +356,7 @@ static void stream(const oracle_params *p, const double *fpost, double *fnew)
                 for (int y = 0; y < p->ny; ++y)
                     for (int x = 0; x < p->nx; ++x) {
                         long s = cell_index(p, x, y, z);
+                        if (p->solid && p->solid[s]) continue;   /* nothing leaves a solid site */
                         int X = x + C[i][0], Y = y + C[i][1], Z = z + C[i][2];
                         double v = fpost[((long)a * Q + i) * N + s];
                         if (is_solid(p, X, Y, Z))
@@ -343,6 +384,10 @@ void oracle_step(const oracle_params *p, double *f, double *work, long nsteps)
         for (long s = 0; s < N; ++s)
             for (int a = 0; a < 2; ++a) {
                 double fin[Q], fpost[Q];
+                if (p->solid && p->solid[s]) {   /* solid sites hold no populations */
+                    for (int i = 0; i < Q; ++i) work[((long)a * Q + i) * N + s] = 0.0;
+                    continue;
+                }
                 for (int i = 0; i < Q; ++i) fin[i] = f[((long)a * Q + i) * N + s];
                 collide_cell(p, a, fin, a == 0 ? rho1[s] : rho2[s], &u[3 * s],
                              a == 0 ? &g1[3 * s] : &g2[3 * s], fpost);
@@ -365,7 +410,7 @@ void oracle_init(const oracle_params *p, const double *rho1, const double *rho2,
         double feq[Q];
         for (int a = 0; a < 2; ++a) {
             oracle_feq(a == 0 ? rho1[s] : rho2[s], us, feq);
-            for (int i = 0; i < Q; ++i) f[((long)a * Q + i) * N + s] = feq[i];
+            for (int i = 0; i < Q; ++i) f[((long)a * Q + i) * N + s] = (p->solid && p->solid[s]) ? 0.0 : feq[i];
         }
     }
 }
@@ -383,6 +428,7 @@ void oracle_moments(const oracle_params *p, const double *f,
     oracle_accelerations(p, rho1, rho2, g1, g2);
     for (long s = 0; s < N; ++s) {
         double rho = rho1[s] + rho2[s];
+        if (p->solid && p->solid[s]) { uF[3 * s] = uF[3 * s + 1] = uF[3 * s + 2] = 0.0; continue; }
         for (int d = 0; d < 3; ++d) {
             double g = (g1[3 * s + d] * rho1[s] + g2[3 * s + d] * rho2[s]) / rho;
             uF[3 * s + d] = u[3 * s + d] + g / 2.0;

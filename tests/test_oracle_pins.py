@@ -434,3 +434,122 @@ def test_laplace_law_2d():
     (sigma, icpt), *_ = np.linalg.lstsq(A, dp, rcond=None)
     assert sigma > 0
     assert abs(icpt) < 0.05 * dp.min()
+
+
+# ---------------------------------------------------------------------------
+# Staircase walls (a mask of solid sites; the inclined walls of Sec. 4.2)
+
+def _layered_state(nz_fluid, ny, nx, seed):
+    """Densities and velocities that vary along z only."""
+    rng = np.random.default_rng(seed)
+    r1 = np.broadcast_to(rng.uniform(0.2, 1.0, nz_fluid)[:, None, None], (nz_fluid, ny, nx)).copy()
+    r2 = np.broadcast_to(rng.uniform(0.2, 1.0, nz_fluid)[:, None, None], (nz_fluid, ny, nx)).copy()
+    u = np.zeros((nz_fluid, ny, nx, 3))
+    u[..., 0] = rng.uniform(-0.03, 0.03, nz_fluid)[:, None, None]
+    u[..., 2] = rng.uniform(-0.02, 0.02, nz_fluid)[:, None, None]
+    u[0, ..., 2] = 0.0
+    u[-1, ..., 2] = 0.0
+    return r1, r2, u
+
+
+@pytest.mark.parametrize("wall_model,rho_s", [("mirror", (0.0, 0.0)), ("mirror", (0.04, 0.1)),
+                                              ("potential", (0.0, 0.15))])
+def test_mask_planes_equal_flat_walls_for_layered_states(wall_model, rho_s):
+    """Two solid planes of the mask around nz fluid layers (periodic lattice of
+    nz + 2 layers) against the flat half-way walls of the non-periodic
+    lattice: the same bounce-back links, and for fields that vary along the
+    wall normal only the w-weighted mean over a solid site's fluid neighbours
+    equals the mirrored density, so every fluid population agrees over 40
+    steps (forces, walls, wetting potential)."""
+    nz, ny, nx = 5, 3, 4
+    r1, r2, u = _layered_state(nz, ny, nx, seed=7)
+    kw = dict(tau=(0.8, 1.1), G12=-1.4, rho_s=rho_s, wall_model=wall_model, g_ext=(2e-4, 0.0, -1e-4))
+    pf = oracle.make_params((nz, ny, nx), periodic=(1, 1, 0), **kw)
+    ff = oracle.init(pf, r1, r2, u)
+    oracle.step(pf, ff, 40)
+    solid = np.zeros((nz + 2, ny, nx), np.uint8)
+    solid[0] = solid[-1] = 1
+    pad = lambda a, v: np.concatenate([np.full((1,) + a.shape[1:], v), a, np.full((1,) + a.shape[1:], v)])
+    pm = oracle.make_params((nz + 2, ny, nx), periodic=(1, 1, 1), solid=solid, **kw)
+    fm = oracle.init(pm, pad(r1, 1.0), pad(r2, 1.0), pad(u, 0.0))
+    assert np.all(fm[:, :, 0] == 0) and np.all(fm[:, :, -1] == 0)
+    oracle.step(pm, fm, 40)
+    assert np.all(fm[:, :, 0] == 0) and np.all(fm[:, :, -1] == 0)
+    assert np.max(np.abs(fm[:, :, 1:-1] - ff)) < 1e-13
+    # and the same walls across x instead of z (transposed lattice)
+    pfx = oracle.make_params((ny, nx, nz), periodic=(0, 1, 1), **dict(kw, g_ext=(-1e-4, 0.0, 2e-4)))
+    tr = lambda a: np.ascontiguousarray(np.moveaxis(a, 0, 2))
+    ux = np.ascontiguousarray(tr(u)[..., ::-1])
+    ffx = oracle.init(pfx, tr(r1), tr(r2), ux)
+    oracle.step(pfx, ffx, 40)
+    a_f, b_f, _ = oracle.moments_raw(pf, ff)
+    a_x, b_x, _ = oracle.moments_raw(pfx, ffx)
+    assert np.max(np.abs(tr(a_f) - a_x)) < 1e-13 and np.max(np.abs(tr(b_f) - b_x)) < 1e-13
+
+
+def _staircase(shape, seed):
+    """A blob-and-step mask: a staircase wall along the bottom and a few
+    solid sites scattered inside."""
+    nz, ny, nx = shape
+    m = np.zeros(shape, np.uint8)
+    for x in range(nx):
+        m[: 1 + (x * 3) // nx, :, x] = 1
+    rng = np.random.default_rng(seed)
+    for _ in range(3):
+        m[rng.integers(2, nz), rng.integers(0, ny), rng.integers(0, nx)] = 1
+    return m
+
+
+@pytest.mark.parametrize("collision", ["bgk", "regularized"])
+def test_mask_conserves_mass(collision):
+    """Half-way bounce-back returns every population that meets a solid site
+    to its cell: each component's mass is conserved, and solid sites stay
+    empty."""
+    shape = (7, 4, 9)
+    solid = _staircase(shape, seed=2)
+    r1, r2, u = wl.random_state(shape, seed=8, u_max=0.03)
+    p = oracle.make_params(shape, tau=(0.7, 1.2), G12=-1.3, collision=collision, solid=solid, rho_s=(0.0, 0.05))
+    f = oracle.init(p, r1, r2, u)
+    a0, b0, _ = oracle.moments_raw(p, f)
+    oracle.step(p, f, 150)
+    a, b, uu = oracle.moments_raw(p, f)
+    assert abs(a.sum() - a0.sum()) < 1e-12 * a0.sum() and abs(b.sum() - b0.sum()) < 1e-12 * b0.sum()
+    assert np.all(a[solid == 1] == 0) and np.all(f[:, :, solid == 1] == 0)
+    assert np.all(np.isfinite(uu))
+
+
+def test_mask_uniform_rest_state_is_fixed_point():
+    """Modified model, rho_s = 0: next to walls of any shape a uniform fluid at
+    rest feels no wall force (each solid site presents the fluid's own
+    density, so the interaction sums cancel) and bounce-back returns the rest
+    equilibrium: the state does not change."""
+    shape = (6, 3, 8)
+    solid = _staircase(shape, seed=5)
+    r1 = np.full(shape, 0.7)
+    r2 = np.full(shape, 0.3)
+    p = oracle.make_params(shape, tau=(0.9, 0.9), G12=-1.5, solid=solid, periodic=(1, 1, 0))
+    f = oracle.init(p, r1, r2)
+    f0 = f.copy()
+    oracle.step(p, f, 30)
+    assert np.max(np.abs(f - f0)) < 1e-15
+
+
+def test_mask_mirror_symmetry():
+    """A mask and state symmetric under x -> nx - 1 - x stay symmetric (with
+    mirrored x velocities): checks the direction bookkeeping of bounce-back
+    and of the solid-site densities on a staircase."""
+    nz, ny, nx = 8, 1, 10
+    m = np.zeros((nz, ny, nx), np.uint8)
+    for x in range(nx // 2):
+        m[: 1 + x // 2, :, x] = 1
+        m[: 1 + x // 2, :, nx - 1 - x] = 1
+    r1, r2 = wl.droplet((nz, ny, nx), 3.0, center=(4.0, 0.0, (nx - 1) / 2.0))
+    p = oracle.make_params((nz, ny, nx), tau=(0.8, 0.8), G12=G_STRONG, solid=m, periodic=(1, 1, 0),
+                           rho_s=(0.0, 0.08))
+    f = oracle.init(p, r1, r2)
+    oracle.step(p, f, 60)
+    a, b, uu = oracle.moments_raw(p, f)
+    assert np.max(np.abs(a - a[..., ::-1])) < 1e-13
+    assert np.max(np.abs(uu[..., 0] + uu[..., ::-1, 0])) < 1e-13
+    assert np.max(np.abs(uu[..., 2] - uu[..., ::-1, 2])) < 1e-13
+    assert np.abs(uu).max() > 1e-5
