@@ -218,7 +218,7 @@ static double wall_density(const oracle_params *p, const double *rho_b, double r
                  (p->periodic[2] || (z >= 0 && z < p->nz));
         if (in && mask_solid(p, wrap(x, p->nx), wrap(y, p->ny), wrap(z, p->nz))) {
             double num = 0.0, den = 0.0;
-            for (int i = 1; i < Q; ++i) {
+            for (int i = 0; i < Q; ++i) {   /* the rest direction is the site itself: solid */
                 int X = x + C[i][0], Y = y + C[i][1], Z = z + C[i][2];
                 if (is_solid(p, X, Y, Z)) continue;
                 num += W[i] * rho_b[cell_index(p, wrap(X, p->nx), wrap(Y, p->ny), wrap(Z, p->nz))];

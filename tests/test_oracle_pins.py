@@ -553,3 +553,30 @@ def test_mask_mirror_symmetry():
     assert np.max(np.abs(uu[..., 0] + uu[..., ::-1, 0])) < 1e-13
     assert np.max(np.abs(uu[..., 2] - uu[..., ::-1, 2])) < 1e-13
     assert np.abs(uu).max() > 1e-5
+
+
+def test_isolated_solid_site_presents_the_linear_field():
+    """A solid site with only fluid neighbours, in a density field linear in
+    x, y, z: the w-weighted mean over all 18 neighbours is the field's value
+    at the site (the weights are symmetric), so next to it the interaction
+    sum is that of the unbroken linear field, T0 grad(rho), and the wall part
+    is w_i c_i rho(site).  A neighbour dropped from the mean or a wrong
+    direction breaks both."""
+    c, w = oracle.lattice()
+    n = 9
+    shape = (n, n, n)
+    z, y, x = np.meshgrid(np.arange(n), np.arange(n), np.arange(n), indexing="ij")
+    grad = np.array([0.01, -0.02, 0.03])
+    rho = 0.5 + grad[0] * x + grad[1] * y + grad[2] * z
+    solid = np.zeros(shape, np.uint8)
+    s = (4, 4, 4)                      # (z, y, x)
+    solid[s] = 1
+    p = oracle.make_params(shape, solid=solid)
+    Sf, Sw = oracle.interaction_sums(p, rho)
+    for i in range(19):
+        if not c[i].any():
+            continue
+        xz = (s[0] - c[i][2], s[1] - c[i][1], s[2] - c[i][0])    # the fluid cell that sees s along c_i
+        tot = Sf[xz] + Sw[xz]
+        assert np.allclose(tot, T0 * grad, atol=1e-15)
+        assert np.allclose(Sw[xz], w[i] * c[i] * rho[s], atol=1e-15)
