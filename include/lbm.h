@@ -161,6 +161,21 @@ lbm_status lbm_pressure_jump(lbm_lattice *h, const double center[3], double r_in
  * LBM_EINVAL, LBM_ECUDA. */
 lbm_status lbm_droplet_stats(lbm_lattice *h, double threshold, const double origin[3], double out[7]);
 
+/* Staircase walls of any shape (the inclined walls of Sec. 4.2): solid[cell]
+ * != 0 marks a solid site, N bytes in [z][y][x] order, host (on_device = 0)
+ * or device memory, copied.  Every link into a solid site is a half-way
+ * bounce-back link; solid sites hold no fluid (their populations, densities
+ * and velocities read as 0); in Eq. 13 a solid site presents the w-weighted
+ * mean of rho^b over its fluid neighbours plus rho_s^b (LBM_WALL_MIRROR) or
+ * rho_s^b alone (LBM_WALL_POTENTIAL).  NULL removes the mask.  A lattice
+ * with a mask steps with the two-kernel step; lbm_record,
+ * lbm_pressure_jump and lbm_droplet_stats return LBM_ENOTSUP for it.  Set
+ * the mask before lbm_init_fields (a state set earlier keeps the populations
+ * of the new solid sites, which are never read).  Drops the lattice's
+ * recording.  Synchronizes.  Errors: LBM_EINVAL (NULL handle), LBM_ENOTSUP
+ * (lattice with walls along z), LBM_ENOMEM, LBM_ECUDA. */
+lbm_status lbm_set_solid(lbm_lattice *h, const unsigned char *solid, int on_device);
+
 /* Copy the populations f_i^a(x, t) of the current state, as doubles laid out
  * [a][i][z][y][x] in the lbm_lattice_dirs order (2*19*N values), to or from a
  * caller buffer (host or device).  Used for checkpoints and for population-level

@@ -10,4 +10,4 @@ from .lattice import (Lattice, make_params, lbm_lattice_dirs, lbm_create, lbm_in
                       lbm_step, lbm_step_timed, lbm_moments, lbm_reduce, lbm_get_populations, lbm_set_populations,
                       lbm_state_bytes, lbm_get_state, lbm_set_state, lbm_step_count, lbm_sync,
                       lbm_destroy, lbm_step_noalloc, NOALLOC_MAX_CELLS, lbm_record, lbm_adjoint,
-                      lbm_pressure_jump, lbm_droplet_stats)
+                      lbm_pressure_jump, lbm_droplet_stats, lbm_set_solid)

@@ -50,6 +50,7 @@ SIGNATURES = [
     ("lbm_reduce", _I, [_VP, _DP]),
     ("lbm_pressure_jump", _I, [_VP, _DP, ctypes.c_double, ctypes.c_double, _DP]),
     ("lbm_droplet_stats", _I, [_VP, ctypes.c_double, _DP, _DP]),
+    ("lbm_set_solid", _I, [_VP, _VP, _I]),
     ("lbm_get_populations", _I, [_VP, _VP, _I]),
     ("lbm_set_populations", _I, [_VP, _VP, _I]),
     ("lbm_state_bytes", _I, [_VP, ctypes.POINTER(_SZ)]),

@@ -204,6 +204,7 @@ struct Phys {
     R gext[3];
     R rho_s[2];
     R rho0;                 // reference density of deviation storage (0 otherwise)
+    const unsigned char *solid = nullptr;   // N flags, 1 = solid site (two-kernel step only)
 };
 
 // Third-order equilibrium of Eq. 3 with T0 = 1/3, for direction i and its

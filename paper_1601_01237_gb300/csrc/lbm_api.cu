@@ -48,6 +48,7 @@ struct lbm_lattice {
     cudaGraphExec_t graph;
     int graph_state;     // 0 not built, 1 ready, -1 not available (plain launches)
     int use_graphs;
+    unsigned char *solid;   // device mask of solid sites (N bytes) or nullptr
 };
 
 namespace {
@@ -245,6 +246,7 @@ void lbm_destroy(lbm_lattice *h)
     cudaFree(h->rho);
     cudaFree(h->ckpt);
     free_workspace(h);
+    cudaFree(h->solid);
     cudaFree(h->partials);
     if (h->graph) cudaGraphExecDestroy(h->graph);
     if (h->partials_h) cudaFreeHost(h->partials_h);
@@ -480,6 +482,7 @@ lbm_status diag_run(lbm_lattice *h, int which, const double *vec3, double a0, do
 lbm_status lbm_pressure_jump(lbm_lattice *h, const double center[3], double r_in, double r_out, double out[3])
 {
     if (!h || !center || !out) return fail(LBM_EINVAL, "lbm_pressure_jump: NULL argument");
+    if (h->solid) return fail(LBM_ENOTSUP, "lbm_pressure_jump: not available with a solid mask");
     if (!(r_in > 0) || !(r_out >= r_in)) return fail(LBM_EINVAL, "lbm_pressure_jump: need 0 < r_in <= r_out");
     DeviceGuard g(h->device);
     double s[4];
@@ -495,6 +498,7 @@ lbm_status lbm_pressure_jump(lbm_lattice *h, const double center[3], double r_in
 lbm_status lbm_droplet_stats(lbm_lattice *h, double threshold, const double origin[3], double out[7])
 {
     if (!h || !origin || !out) return fail(LBM_EINVAL, "lbm_droplet_stats: NULL argument");
+    if (h->solid) return fail(LBM_ENOTSUP, "lbm_droplet_stats: not available with a solid mask");
     DeviceGuard g(h->device);
     double s[7];
     lbm_status st = diag_run(h, 1, origin, threshold, 0.0, s, 7);
@@ -504,6 +508,39 @@ lbm_status lbm_droplet_stats(lbm_lattice *h, double threshold, const double orig
     out[4] = s[4];
     out[5] = s[6] > 0 ? s[5] / s[6] : 0.0;
     out[6] = s[6];
+    return LBM_OK;
+}
+
+lbm_status lbm_set_solid(lbm_lattice *h, const unsigned char *solid, int on_device)
+{
+    if (!h) return fail(LBM_EINVAL, "lbm_set_solid: NULL handle");
+    if (solid && h->phys.wall_z)
+        return fail(LBM_ENOTSUP, "lbm_set_solid: a mask needs a lattice periodic along z (walls are given "
+                                 "either as z walls or as a mask)");
+    DeviceGuard g(h->device);
+    CK(cudaStreamSynchronize(h->stream), "lbm_set_solid: sync");
+    // the captured step graph and any recording belong to the old geometry
+    if (h->graph) cudaGraphExecDestroy(h->graph);
+    h->graph = nullptr;
+    h->graph_state = 0;
+    cudaFree(h->ckpt);
+    h->ckpt = nullptr;
+    h->rec_steps = 0;
+    free_workspace(h);
+    if (!solid) {
+        cudaFree(h->solid);
+        h->solid = nullptr;
+        h->phys.solid = nullptr;
+        h->use_fused = env_flag("LBM_FUSED", 1) && lbm::fused_supported(h->phys);
+        return LBM_OK;
+    }
+    const size_t N = (size_t)h->phys.N;
+    if (!h->solid) CK(cudaMalloc((void **)&h->solid, N), "lbm_set_solid: mask");
+    CK(cudaMemcpyAsync(h->solid, solid, N, on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice,
+                       h->stream), "lbm_set_solid: copy");
+    CK(cudaStreamSynchronize(h->stream), "lbm_set_solid: sync");
+    h->phys.solid = h->solid;
+    h->use_fused = 0;   // the fused kernel takes no mask
     return LBM_OK;
 }
 
@@ -601,6 +638,7 @@ lbm_status lbm_record(lbm_lattice *h, long n_steps, int ckpt_every)
         return fail(LBM_EINVAL, "lbm_record: n_steps = %ld and ckpt_every = %d must be >= 1", n_steps, ckpt_every);
     if (h->phys.collision == LBM_REGULARIZED3)
         return fail(LBM_ENOTSUP, "lbm_record: the third-order regularized collision has no reverse pass");
+    if (h->solid) return fail(LBM_ENOTSUP, "lbm_record: lattices with a solid mask have no reverse pass");
     DeviceGuard g(h->device);
     size_t sb = 0;
     lbm_state_bytes(h, &sb);

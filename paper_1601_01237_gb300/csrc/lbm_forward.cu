@@ -9,6 +9,11 @@
 // pre-collision population f_i(x, t) is gathered from x - c_i (streaming is
 // the gather), or is the reversed population of x itself when x - c_i lies
 // behind a half-way bounce-back wall.
+//
+// Staircase walls (the inclined walls of Sec. 4.2) are a mask of solid sites
+// (Phys::solid): links into a solid site bounce back, solid sites hold zero
+// populations, and the density pass is followed by k_wall_rho, which gives
+// each solid site the density it presents to Eq. 13.
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -66,9 +71,10 @@ __device__ __forceinline__ void gather(const typename Store<S>::T *__restrict__ 
 #pragma unroll
     for (int i = 0; i < Q; ++i) {
         const R ref = w<R>(i) * p.rho0;
-        const bool wall = (cz(i) == 1 && n.zlo_wall) || (cz(i) == -1 && n.zhi_wall);
-        const long long idx = wall ? pair_index(opp(i), n.cell, p.N)
-                                   : pair_index(i, n.zo[1 - cz(i)] + n.yo[1 - cy(i)] + n.xo[1 - cx(i)], p.N);
+        const long long src = n.zo[1 - cz(i)] + n.yo[1 - cy(i)] + n.xo[1 - cx(i)];
+        const bool wall = (cz(i) == 1 && n.zlo_wall) || (cz(i) == -1 && n.zhi_wall) ||
+                          (i != 0 && p.solid && __ldg(p.solid + src));
+        const long long idx = wall ? pair_index(opp(i), n.cell, p.N) : pair_index(i, src, p.N);
         Store<S>::load2(f + idx, ref, fa[0][i], fa[1][i]);
     }
 }
@@ -139,6 +145,7 @@ k_density(const typename Store<S>::T *__restrict__ f, typename Store<S>::R *__re
     using R = typename Store<S>::R;
     Nbr n;
     if (!decode_cell(p, (long long)blockIdx.x * kThreads + threadIdx.x, n)) return;
+    if (p.solid && p.solid[n.cell]) return;   // k_wall_rho writes solid sites
     R fa[2][Q];
     gather<S>(f, p, n, fa);
 #pragma unroll
@@ -150,6 +157,36 @@ k_density(const typename Store<S>::T *__restrict__ f, typename Store<S>::R *__re
     }
 }
 
+// Density that a solid site of the mask presents to the interaction sum of
+// Eq. 13, written into rho after the density pass: the modified model takes
+// the mean of rho^b over the site's fluid neighbours weighted by w_i (zero
+// normal derivative for fields that vary along the wall normal) plus rho_s^b;
+// the original model takes rho_s^b.  A site with no fluid neighbour is never
+// read by a fluid cell and gets rho_s^b.
+template <class R>
+__global__ void __launch_bounds__(kThreads)
+k_wall_rho(R *__restrict__ rho, Phys<R> p)
+{
+    Nbr n;
+    if (!decode_cell(p, (long long)blockIdx.x * kThreads + threadIdx.x, n)) return;
+    if (!p.solid[n.cell]) return;
+    R num1 = 0, num2 = 0;
+    int den36 = 0;   // sum of w_i over fluid neighbours, in units of 1/36
+    if (p.wall_mirror) {
+#pragma unroll
+        for (int i = 1; i < Q; ++i) {
+            const long long nb = n.zo[1 + cz(i)] + n.yo[1 + cy(i)] + n.xo[1 + cx(i)];
+            if (__ldg(p.solid + nb)) continue;
+            const R k = R(k36(i));
+            num1 += k * rho[nb];
+            num2 += k * rho[p.N + nb];
+            den36 += k36(i);
+        }
+    }
+    rho[n.cell] = (den36 ? num1 / R(den36) : R(0)) + p.rho_s[0];
+    rho[p.N + n.cell] = (den36 ? num2 / R(den36) : R(0)) + p.rho_s[1];
+}
+
 template <int S, int REG>
 __global__ void __launch_bounds__(kThreads)
 k_collide(const typename Store<S>::T *__restrict__ fin, typename Store<S>::T *__restrict__ fout,
@@ -158,6 +195,11 @@ k_collide(const typename Store<S>::T *__restrict__ fin, typename Store<S>::T *__
     using R = typename Store<S>::R;
     Nbr n;
     if (!decode_cell(p, (long long)blockIdx.x * kThreads + threadIdx.x, n)) return;
+    if (p.solid && p.solid[n.cell]) {   // solid sites hold no populations
+#pragma unroll
+        for (int i = 0; i < Q; ++i) Store<S>::store2(fout + pair_index(i, n.cell, p.N), R(0), R(0), w<R>(i) * p.rho0);
+        return;
+    }
     R fa[2][Q];
     gather<S>(fin, p, n, fa);
     R r1, r2, ux, uy, uz;
@@ -186,18 +228,22 @@ k_init_feq(const double *__restrict__ rho1, const double *__restrict__ rho2,
     using R = typename Store<S>::R;
     Nbr n;
     if (!decode_cell(p, (long long)blockIdx.x * kThreads + threadIdx.x, n)) return;
+    const bool here_solid = p.solid && p.solid[n.cell];
 #pragma unroll
     for (int j = 0; j < Q; ++j) {
-        const bool wall = (cz(j) == -1 && n.zlo_wall) || (cz(j) == 1 && n.zhi_wall);
-        const long long src = wall ? n.cell : n.zo[1 + cz(j)] + n.yo[1 + cy(j)] + n.xo[1 + cx(j)];
+        const long long dst = n.zo[1 + cz(j)] + n.yo[1 + cy(j)] + n.xo[1 + cx(j)];
+        const bool wall = (cz(j) == -1 && n.zlo_wall) || (cz(j) == 1 && n.zhi_wall) ||
+                          (j != 0 && p.solid && p.solid[dst]);
+        const long long src = wall ? n.cell : dst;
         const int k = wall ? opp(j) : j;
         double ux = 0, uy = 0, uz = 0;
         if (u) { ux = u[3 * src]; uy = u[3 * src + 1]; uz = u[3 * src + 2]; }
         const double usq = ux * ux + uy * uy + uz * uz;
         const double cu = cdot<double>(k, ux, uy, uz);
         const double P = 1.0 - 1.5 * usq + cu * (3.0 - 4.5 * usq) + 4.5 * cu * cu * (1.0 + cu);
-        Store<S>::store2(f + pair_index(j, n.cell, p.N), (R)(rho1[src] * wd(k) * P), (R)(rho2[src] * wd(k) * P),
-                         w<R>(j) * p.rho0);
+        const R v1 = here_solid ? R(0) : (R)(rho1[src] * wd(k) * P);
+        const R v2 = here_solid ? R(0) : (R)(rho2[src] * wd(k) * P);
+        Store<S>::store2(f + pair_index(j, n.cell, p.N), v1, v2, w<R>(j) * p.rho0);
     }
 }
 
@@ -209,15 +255,18 @@ k_set_pop(const double *__restrict__ src, typename Store<S>::T *__restrict__ f,
     using R = typename Store<S>::R;
     Nbr n;
     if (!decode_cell(p, (long long)blockIdx.x * kThreads + threadIdx.x, n)) return;
+    const bool here_solid = p.solid && p.solid[n.cell];
 #pragma unroll
     for (int a = 0; a < 2; ++a)
 #pragma unroll
         for (int j = 0; j < Q; ++j) {
-            const bool wall = (cz(j) == -1 && n.zlo_wall) || (cz(j) == 1 && n.zhi_wall);
-            const long long sc = wall ? n.cell : n.zo[1 + cz(j)] + n.yo[1 + cy(j)] + n.xo[1 + cx(j)];
+            const long long dst = n.zo[1 + cz(j)] + n.yo[1 + cy(j)] + n.xo[1 + cx(j)];
+            const bool wall = (cz(j) == -1 && n.zlo_wall) || (cz(j) == 1 && n.zhi_wall) ||
+                              (j != 0 && p.solid && p.solid[dst]);
+            const long long sc = wall ? n.cell : dst;
             const int k = wall ? opp(j) : j;
-            Store<S>::store(f + pair_index(j, n.cell, p.N) + a, (R)src[(long long)(a * Q + k) * p.N + sc],
-                            w<R>(j) * p.rho0);
+            Store<S>::store(f + pair_index(j, n.cell, p.N) + a,
+                            here_solid ? R(0) : (R)src[(long long)(a * Q + k) * p.N + sc], w<R>(j) * p.rho0);
         }
 }
 
@@ -229,12 +278,13 @@ k_get_pop(const typename Store<S>::T *__restrict__ f, double *__restrict__ dst,
     using R = typename Store<S>::R;
     Nbr n;
     if (!decode_cell(p, (long long)blockIdx.x * kThreads + threadIdx.x, n)) return;
+    const bool here_solid = p.solid && p.solid[n.cell];
     R fa[2][Q];
     gather<S>(f, p, n, fa);
 #pragma unroll
     for (int a = 0; a < 2; ++a)
 #pragma unroll
-        for (int i = 0; i < Q; ++i) dst[(long long)(a * Q + i) * p.N + n.cell] = (double)fa[a][i];
+        for (int i = 0; i < Q; ++i) dst[(long long)(a * Q + i) * p.N + n.cell] = here_solid ? 0.0 : (double)fa[a][i];
 }
 
 // Velocity of Eq. 8: u_F = u + g/2 with g = sum_a g^a rho^a / rho (Eq. 9).
@@ -258,6 +308,12 @@ k_moments(const typename Store<S>::T *__restrict__ f, const typename Store<S>::R
     using R = typename Store<S>::R;
     Nbr n;
     if (!decode_cell(p, (long long)blockIdx.x * kThreads + threadIdx.x, n)) return;
+    if (p.solid && p.solid[n.cell]) {   // no fluid at a solid site
+        if (o1) o1[n.cell] = (O)0;
+        if (o2) o2[n.cell] = (O)0;
+        if (ouF) { ouF[3 * n.cell] = (O)0; ouF[3 * n.cell + 1] = (O)0; ouF[3 * n.cell + 2] = (O)0; }
+        return;
+    }
     R fa[2][Q];
     gather<S>(f, p, n, fa);
     R r1, r2, ux, uy, uz;
@@ -289,6 +345,7 @@ k_reduce(const typename Store<S>::T *__restrict__ f, const typename Store<S>::R 
          c += (long long)gridDim.x * kThreads) {
         Nbr n;
         decode_cell(p, c, n);
+        if (p.solid && p.solid[c]) continue;   // solid sites hold no fluid
         R fa[2][Q];
         gather<S>(f, p, n, fa);
         R r1, r2, ux, uy, uz;
@@ -340,10 +397,22 @@ Phys<R> make_phys(const HostPhys &h)
     for (int d = 0; d < 3; ++d) p.gext[d] = (R)h.gext[d];
     p.rho_s[0] = (R)h.rho_s[0]; p.rho_s[1] = (R)h.rho_s[1];
     p.rho0 = (R)h.rho0;
+    p.solid = h.solid;
     return p;
 }
 
 inline unsigned grid_for(long long N) { return (unsigned)((N + kThreads - 1) / kThreads); }
+
+// Density pass: rho^a of every fluid cell, then (with a mask) the densities
+// the solid sites present to Eq. 13.
+template <int S>
+void density_pass(const HostPhys &h, const typename Store<S>::T *f, typename Store<S>::R *rho, cudaStream_t s)
+{
+    using R = typename Store<S>::R;
+    const Phys<R> p = make_phys<R>(h);
+    k_density<S><<<grid_for(h.N), kThreads, 0, s>>>(f, rho, p);
+    if (h.solid) k_wall_rho<R><<<grid_for(h.N), kThreads, 0, s>>>(rho, p);
+}
 
 template <int S>
 cudaError_t step_split_t(const HostPhys &h, const void *fin, void *fout, void *rho, cudaStream_t s,
@@ -354,7 +423,7 @@ cudaError_t step_split_t(const HostPhys &h, const void *fin, void *fout, void *r
     const Phys<R> p = make_phys<R>(h);
     const unsigned g = grid_for(h.N);
     if (ev) cudaEventRecord(ev[0], s);
-    k_density<S><<<g, kThreads, 0, s>>>((const T *)fin, (R *)rho, p);
+    density_pass<S>(h, (const T *)fin, (R *)rho, s);
     if (ev) cudaEventRecord(ev[1], s);
     if (h.collision == LBM_REGULARIZED)
         k_collide<S, 1><<<g, kThreads, 0, s>>>((const T *)fin, (T *)fout, (const R *)rho, p);
@@ -402,7 +471,7 @@ cudaError_t moments_t(const HostPhys &h, const void *f, void *rho, int out_f64, 
     using R = typename Store<S>::R;
     const Phys<R> p = make_phys<R>(h);
     const unsigned g = grid_for(h.N);
-    if (ouF) k_density<S><<<g, kThreads, 0, s>>>((const T *)f, (R *)rho, p);
+    if (ouF) density_pass<S>(h, (const T *)f, (R *)rho, s);
     if (out_f64)
         k_moments<S, double><<<g, kThreads, 0, s>>>((const T *)f, (const R *)rho, (double *)o1,
                                                     (double *)o2, (double *)ouF, p);
@@ -418,7 +487,7 @@ cudaError_t reduce_t(const HostPhys &h, const void *f, void *rho, double *partia
     using T = typename Store<S>::T;
     using R = typename Store<S>::R;
     const Phys<R> p = make_phys<R>(h);
-    k_density<S><<<grid_for(h.N), kThreads, 0, s>>>((const T *)f, (R *)rho, p);
+    density_pass<S>(h, (const T *)f, (R *)rho, s);
     k_reduce<S><<<kReduceBlocks, kThreads, 0, s>>>((const T *)f, (const R *)rho, partials, p);
     return cudaGetLastError();
 }
@@ -488,19 +557,10 @@ int reduce_blocks() { return kReduceBlocks; }
 cudaError_t launch_density(const HostPhys &h, const void *f, void *rho, cudaStream_t s)
 {
     switch (h.storage) {
-    case ST_F64:
-        k_density<ST_F64><<<grid_for(h.N), kThreads, 0, s>>>((const double *)f, (double *)rho, make_phys<double>(h));
-        break;
-    case ST_F32:
-        k_density<ST_F32><<<grid_for(h.N), kThreads, 0, s>>>((const float *)f, (float *)rho, make_phys<float>(h));
-        break;
-    case ST_F16_DEV:
-        k_density<ST_F16_DEV><<<grid_for(h.N), kThreads, 0, s>>>((const __half *)f, (float *)rho, make_phys<float>(h));
-        break;
-    case ST_BF16_DEV:
-        k_density<ST_BF16_DEV><<<grid_for(h.N), kThreads, 0, s>>>((const __nv_bfloat16 *)f, (float *)rho,
-                                                                  make_phys<float>(h));
-        break;
+    case ST_F64: density_pass<ST_F64>(h, (const double *)f, (double *)rho, s); break;
+    case ST_F32: density_pass<ST_F32>(h, (const float *)f, (float *)rho, s); break;
+    case ST_F16_DEV: density_pass<ST_F16_DEV>(h, (const __half *)f, (float *)rho, s); break;
+    case ST_BF16_DEV: density_pass<ST_BF16_DEV>(h, (const __nv_bfloat16 *)f, (float *)rho, s); break;
     default: return cudaErrorInvalidValue;
     }
     return cudaGetLastError();

@@ -21,6 +21,10 @@ struct HostPhys {
     double gext[3];
     double rho_s[2];
     double rho0;
+    // N flags on the device, 1 = solid site (staircase walls); nullptr = none.
+    // Only the two-kernel step and its density, output and reduction kernels
+    // take a mask.
+    const unsigned char *solid = nullptr;
 };
 
 // Populations are stored as 2*19*N values of the storage type, laid out

@@ -1,6 +1,7 @@
 """Host-side helpers for the paper's measurements (Sec. 3-4): Young-Laplace fit
 (Eq. 12), equivalent radius of a droplet from its volume, drift velocity,
-contact angles of a sessile droplet and of a slug between plates (Sec. 4.2).
+contact angles of a sessile droplet and of a slug between plates, and the
+position and size of a droplet in an inclined channel (Sec. 4.2).
 The field reductions themselves run on the GPU (lbm_pressure_jump,
 lbm_droplet_stats, lbm_reduce)."""
 import math
@@ -127,3 +128,26 @@ def wall_layer_density(rho, x_lo, x_hi):
     z = nz - 1) over x_lo <= x < x_hi, y = 0 (the thin-film measure)."""
     r = np.asarray(rho)
     return float(0.5 * (r[0, 0, x_lo:x_hi].mean() + r[-1, 0, x_lo:x_hi].mean()))
+
+
+def channel_droplet_stats(b, solid, info, thr):
+    """Droplet of component 2 in an inclined channel: number of fluid cells
+    with rho^2 > thr, their rho^2-weighted centre along the channel (circular
+    mean over the channel length L, each cell taken in the periodic copy of
+    the channel that holds the lattice centre), and the fluid cell count."""
+    nz, _, nx = b.shape
+    es, en, P, L = info["along"], info["across"], info["P"], info["L"]
+    z, x = np.meshgrid(np.arange(nz, dtype=np.float64), np.arange(nx, dtype=np.float64), indexing="ij")
+    X = x - (nx - 1) / 2.0
+    Z = z - (nz - 1) / 2.0
+    s = X * es[0] + Z * es[1]
+    n = X * en[0] + Z * en[1]
+    k = np.round(n / P)
+    s = s + k * nx * es[0]            # translate by k (nx, 0): n -> n - k P
+    rho = b[:, 0, :]
+    fl = solid[:, 0, :] == 0
+    drop = fl & (rho > thr)
+    m = rho[drop]
+    ph = 2.0 * np.pi * s[drop] / L
+    com = L / (2.0 * np.pi) * np.arctan2((m * np.sin(ph)).sum(), (m * np.cos(ph)).sum()) if m.size else float("nan")
+    return int(drop.sum()), float(com), int(fl.sum())

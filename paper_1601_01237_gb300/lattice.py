@@ -99,6 +99,18 @@ def lbm_droplet_stats(h, threshold, origin=(0.0, 0.0, 0.0)):
             "film_cells": out[6]}
 
 
+def lbm_set_solid(h, solid):
+    """solid: (nz, ny, nx) flags (numpy uint8 on the host, or a torch uint8
+    tensor on the device), non-zero = solid site; None removes the mask."""
+    if solid is None:
+        check(lib().lbm_set_solid(h, None, 0), h)
+        return
+    if isinstance(solid, np.ndarray):
+        solid = np.ascontiguousarray(solid != 0, dtype=np.uint8)
+    p, d = _ptr(solid)
+    check(lib().lbm_set_solid(h, p, d), h)
+
+
 def lbm_get_populations(h, out):
     p, d = _ptr(out)
     check(lib().lbm_get_populations(h, p, d), h)
@@ -271,6 +283,12 @@ class Lattice:
 
     def droplet_stats(self, threshold, origin=(0.0, 0.0, 0.0)):
         return lbm_droplet_stats(self.h, threshold, origin)
+
+    def set_solid(self, solid):
+        """Staircase walls: solid (nz, ny, nx) flags, non-zero = solid site."""
+        if isinstance(solid, np.ndarray):
+            assert solid.shape == self.shape
+        lbm_set_solid(self.h, solid)
 
     def get_populations(self):
         """Host copy of f_i^a(x, t), shape (2, 19, nz, ny, nx), library direction order."""

@@ -17,6 +17,9 @@ s2  the wetting study: a quasi-2D droplet on a wall, wall potentials from
     alpha = -0.4 .. 0.4, modified vs original wall model: contact angle, film
 s3  the static slug between plates (channel height 32): contact angle inside
     the slug and wall film, modified vs original wall model
+s4  the droplet on an inclined wall: channels of height 16 at 10-70 degrees
+    with staircase walls, three tau pairs, modified vs original wall model:
+    droplet velocity and droplet volume ratio
 c4  wall-bounded 512x512x384, regularized, mirror wetting (or --wall-model
     potential), no body force (or --gravity: tilted by 30 deg): MLUPS, droplet
     drift velocity, thin-film density, volume ratio
@@ -320,9 +323,58 @@ def run_s3(steps=None, shape=(32, 1, 192), width=96, rho_s2=(0.0, 0.088, 0.4),
     return out
 
 
+def run_s4(steps=None, angles=(10, 30, 50, 70), taus=((0.55, 1.5), (1.0, 1.0), (1.5, 0.55)),
+           models=("mirror", "potential"), rho_s2=0.4, R=8.0, collision="regularized", window=5000):
+    """The inclined-wall case of Sec. 4.2: a quasi-2D droplet of component 2
+    on the lower wall of a channel of height 16 inclined by 10-70 degrees
+    (staircase solid sites, periodic along the channel), no driving force,
+    wall potential rho_s^2 = 0.4 (0.088 in the paper's density scale, R12):
+    the droplet's velocity along the channel from its centre of mass over the
+    last `window` steps, and the droplet volume (rho^2 above 0.18 / 0.22 of
+    the liquid density) over the fluid volume, for the modified (mirror) and
+    the original (point-wise potential) wall model."""
+    steps = steps or 85000
+    G = wl.G_DROPLET
+    thr = 0.18 / 0.22
+    out = {"case": "s4", "steps": steps, "window": window, "G_eq7": G, "rho_s2": rho_s2, "R": R,
+           "collision": collision, "runs": {}}
+    for ang in angles:
+        shape, solid, info = wl.inclined_channel(ang)
+        r1, r2 = wl.channel_droplet(shape, info, R)
+        for tau in taus:
+            for model in models:
+                key = "%s/%g-%g/%g" % (model, tau[0], tau[1], ang)
+                lat = Lattice(shape, storage="f32", tau=tau, G12=G, rho_s=(0.0, rho_s2), wall_model=model,
+                              collision=collision)
+                lat.set_solid(solid)
+                lat.init_fields(r1, r2)
+                vol0, _, nfl = dg.channel_droplet_stats(r2, solid, info, thr)
+                lat.step(steps - window)
+                try:
+                    lat.reduce()
+                    _, b0, _ = lat.moments()
+                    lat.step(window)
+                    red = lat.reduce()
+                    _, b1, _ = lat.moments()
+                except LBMError:
+                    out["runs"][key] = {"diverged": True}
+                    lat.close()
+                    continue
+                lat.close()
+                v0, c0, _ = dg.channel_droplet_stats(b0, solid, info, thr)
+                v1, c1, _ = dg.channel_droplet_stats(b1, solid, info, thr)
+                ds = c1 - c0
+                ds -= info["L"] * np.round(ds / info["L"])
+                out["runs"][key] = {
+                    "shape": shape, "angle_deg": info["theta_deg"], "velocity": ds / window,
+                    "volume_ratio": v1 / nfl, "volume_ratio_start": vol0 / nfl, "droplet_cells": v1,
+                    "max_uF": red["max_uF"]}
+    return out
+
+
 def main():
     ap = argparse.ArgumentParser()
-    ap.add_argument("case", choices=["c0", "c1", "c2", "c3", "c4", "s1", "s2", "s3"])
+    ap.add_argument("case", choices=["c0", "c1", "c2", "c3", "c4", "s1", "s2", "s3", "s4"])
     ap.add_argument("--steps", type=int, default=None)
     ap.add_argument("--shape", type=int, nargs=3, default=None, help="nz ny nx (c1, c4)")
     ap.add_argument("--gravity", action="store_true", help="c4: tilted gravity")
@@ -341,7 +393,7 @@ def main():
         r = run_c1(args.steps, radii=args.radii, taus=args.taus, shape=args.shape)
     else:
         r = {"c0": run_c0, "c2": run_c2, "c3": run_c3, "s1": run_s1, "s2": run_s2,
-             "s3": run_s3}[args.case](args.steps)
+             "s3": run_s3, "s4": run_s4}[args.case](args.steps)
     print(json.dumps(r, default=float))
 
 

@@ -14,7 +14,10 @@ Recipes (Otomo et al., arXiv:1601.01237):
   * hemisphere on a wall: a sphere centred on the wall plane z = -1/2 (the
     wall-attached droplet of Sec. 4.2);
   * slug: component 2 filling a channel section between two flat interfaces
-    (the slug between plates of Sec. 4.2).
+    (the slug between plates of Sec. 4.2);
+  * inclined channel: staircase solid sites around a channel of height H at
+    an angle to the lattice, periodic along its length, with a droplet of
+    component 2 on its lower wall (the inclined-wall case of Sec. 4.2).
 
 Interaction strength: Eq. 7 takes a signed G (repulsion: G < 0).  The
 droplet cases quote 1.0 inside / 0.03 outside; G = -1.8 is the value whose
@@ -102,6 +105,62 @@ def slug(shape, x_left, x_right, rho_in=1.0, rho_out=0.03, width=2.0):
     d = np.minimum(x - x_left, x_right - x)
     rho2, rho1 = tanh_profile(-d, 0.0, rho_in, rho_out, width)
     return rho1, rho2
+
+
+def inclined_channel(theta_deg, H=16, min_len=96, min_gap=4, max_side=400):
+    """Quasi-2D channel of perpendicular height H whose walls are inclined by
+    theta_deg to the x axis, as staircase solid sites on a lattice periodic
+    in x and z (the inclined-wall case of Sec. 4.2): the channel's centre
+    line runs along (nx, nz) through the lattice centre and closes on itself
+    after its length L = |(nx, nz)|; its periodic copies lie P = nx nz / L
+    apart, and the cells farther than H/2 from the nearest copy are solid.
+    (nx, nz) is the smallest lattice whose angle atan(nz/nx) is within 0.3
+    degrees of theta_deg with L >= min_len and P >= H + min_gap.
+    Returns (shape (nz, 1, nx), solid (nz, 1, nx) uint8, info dict with the
+    angle, L, P and the unit vectors along and across the channel)."""
+    t = math.radians(theta_deg)
+    best = None
+    for nx in range(1, max_side + 1):
+        nz = int(round(nx * math.tan(t)))
+        for cz in (nz, nz + 1):
+            if cz < 1 or cz > max_side:
+                continue
+            L = math.hypot(nx, cz)
+            P = nx * cz / L
+            ang = math.degrees(math.atan2(cz, nx))
+            if abs(ang - theta_deg) <= 0.3 and L >= min_len and P >= H + min_gap:
+                if best is None or nx * cz < best[0] * best[1]:
+                    best = (nx, cz)
+    if best is None:
+        raise ValueError("no lattice up to %d for %g degrees" % (max_side, theta_deg))
+    nx, nz = best
+    L = math.hypot(nx, nz)
+    P = nx * nz / L
+    es = np.array([nx, nz], dtype=np.float64) / L          # along the channel (x, z)
+    en = np.array([-nz, nx], dtype=np.float64) / L         # across, towards the upper wall
+    z, x = np.meshgrid(np.arange(nz, dtype=np.float64), np.arange(nx, dtype=np.float64), indexing="ij")
+    d = (x - (nx - 1) / 2.0) * en[0] + (z - (nz - 1) / 2.0) * en[1]
+    d = d - P * np.round(d / P)                             # distance to the nearest copy
+    solid = (np.abs(d) >= H / 2.0).astype(np.uint8)[:, None, :]
+    info = {"theta_deg": math.degrees(math.atan2(nz, nx)), "L": L, "P": P, "H": H, "along": es, "across": en}
+    return (nz, 1, nx), solid, info
+
+
+def channel_droplet(shape, info, R, s0=0.0, rho_in=1.0, rho_out=0.03, width=2.0):
+    """Droplet of component 2 in an inclined_channel: a disc of radius R
+    centred on the lower wall, s0 along the centre line from the lattice
+    centre (distances by minimum image on the periodic lattice; the part of
+    the disc inside the wall is solid).  Returns (rho1, rho2)."""
+    nz, _, nx = shape
+    c = (np.array([(nx - 1) / 2.0, (nz - 1) / 2.0]) + s0 * info["along"] - (info["H"] / 2.0) * info["across"])
+    z, x = np.meshgrid(np.arange(nz, dtype=np.float64), np.arange(nx, dtype=np.float64), indexing="ij")
+    dx = x - c[0]
+    dz = z - c[1]
+    dx = dx - nx * np.round(dx / nx)
+    dz = dz - nz * np.round(dz / nz)
+    r = np.sqrt(dx * dx + dz * dz)
+    rho2, rho1 = tanh_profile(r, R, rho_in, rho_out, width)
+    return rho1[:, None, :], rho2[:, None, :]
 
 
 def spinodal(shape, rho0=0.5, amp=0.01, seed=20160105):

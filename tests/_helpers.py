@@ -23,18 +23,21 @@ def direction_map():
 
 
 def oracle_run(shape, rho1, rho2, u, nsteps, tau=(1.0, 1.0), G12=0.0, G21=None, g_ext=(0, 0, 0),
-               periodic=(1, 1, 1), rho_s=(0.0, 0.0), collision="bgk", wall_model="mirror", rho0_dev=None):
+               periodic=(1, 1, 1), rho_s=(0.0, 0.0), collision="bgk", wall_model="mirror", rho0_dev=None,
+               solid=None):
     p = oracle.make_params(shape, tau=tau, G12=G12, G21=G21, g_ext=g_ext, periodic=periodic, rho_s=rho_s,
-                           collision=collision, wall_model=wall_model)
+                           collision=collision, wall_model=wall_model, solid=solid)
     f = oracle.init(p, rho1, rho2, u)
     if nsteps:
         oracle.step(p, f, nsteps)
     return p, f
 
 
-def gpu_run(shape, rho1, rho2, u, nsteps, storage="f64", **kw):
+def gpu_run(shape, rho1, rho2, u, nsteps, storage="f64", solid=None, **kw):
     from paper_1601_01237_gb300 import Lattice
     lat = Lattice(shape, storage=storage, **kw)
+    if solid is not None:
+        lat.set_solid(solid)
     lat.init_fields(rho1, rho2, u)
     if nsteps:
         lat.step(nsteps)

@@ -91,3 +91,25 @@ def test_wall_layer_density():
     r[-1, 0, :] = 0.3
     r[0, 0, 5:10] = 9.0
     assert abs(dg.wall_layer_density(r, 10, 20) - 0.2) < 1e-15
+
+
+@pytest.mark.parametrize("angle", [10, 30, 50, 70])
+def test_channel_droplet_centre_tracks_displacement(angle):
+    """Droplets drawn at known distances along an inclined channel (staircase
+    walls, periodic copies): the centre found by channel_droplet_stats moves
+    by the drawn displacement, across the periodic end of the channel too,
+    and the droplet keeps its size."""
+    from paper_1601_01237_gb300 import workloads as wl
+    shape, solid, info = wl.inclined_channel(angle)
+    L = info["L"]
+    res = {}
+    for s0 in (0.0, 17.0, L / 2 - 3.0, -L / 2 + 3.0):
+        _, r2 = wl.channel_droplet(shape, info, 8.0, s0=s0)
+        res[s0] = dg.channel_droplet_stats(r2, solid, info, 0.818)
+    v0, c0, nfl = res[0.0]
+    assert nfl == int((solid == 0).sum())
+    assert abs((res[17.0][1] - c0) - 17.0) < 0.25
+    d = res[-L / 2 + 3.0][1] - res[L / 2 - 3.0][1]
+    d -= L * np.round(d / L)
+    assert abs(d - 6.0) < 0.5          # 6 cells forward through the periodic end
+    assert all(abs(r[0] - v0) <= 0.15 * v0 for r in res.values())
