@@ -20,6 +20,8 @@ s3  the static slug between plates (channel height 32): contact angle inside
 s4  the droplet on an inclined wall: channels of height 16 at 10-70 degrees
     with staircase walls, three tau pairs, modified vs original wall model:
     droplet velocity and droplet volume ratio
+s5  single-component flow through the simple-cubic array of touching spheres
+    (34^3 cell): absolute permeability against viscosity per collision operator
 c4  wall-bounded 512x512x384, regularized, mirror wetting (or --wall-model
     potential), no body force (or --gravity: tilted by 30 deg): MLUPS, droplet
     drift velocity, thin-film density, volume ratio
@@ -372,9 +374,52 @@ def run_s4(steps=None, angles=(10, 30, 50, 70), taus=((0.55, 1.5), (1.0, 1.0), (
     return out
 
 
+def run_s5(steps=None, taus=(0.505, 0.51, 0.55, 0.6, 1.0, 1.5, 2.5),
+           collisions=("bgk", "regularized", "regularized3"), L=34):
+    """The single-component flow through the simple-cubic array of touching
+    spheres of Sec. 4.2: a periodic L^3 cell with one sphere, a body force g
+    along x with g = 1e-4 at nu = 1/6 and g / nu^2 fixed (constant Reynolds
+    number), half-way bounce-back on the staircase sphere; the absolute
+    permeability K = phi nu U / g with U the mean velocity over the pore
+    space, per tau and collision operator.  A single component is two
+    identical components (rho = 0.5 each, G = 0, equal tau).  Runs until U
+    changes by less than 1e-7 relative over 1000 steps (FP64)."""
+    shape, solid, phi = wl.sphere_array_cell(L)
+    fl = solid == 0
+    out = {"case": "s5", "L": L, "porosity": phi, "runs": {}}
+    for col in collisions:
+        for tau in taus:
+            nu = (tau - 0.5) / 3.0
+            g = 1e-4 * (nu / (1.0 / 6.0)) ** 2
+            lat = Lattice(shape, storage="f64", tau=(tau, tau), G12=0.0, g_ext=(g, 0.0, 0.0), collision=col)
+            lat.set_solid(solid)
+            lat.init_fields(np.full(shape, 0.5), np.full(shape, 0.5))
+            cap = steps or int(60 * (L / (2 * np.pi)) ** 2 / nu) + 5000
+            U_prev, done, U = None, 0, float("nan")
+            try:
+                while done < cap:
+                    lat.step(1000)
+                    done += 1000
+                    _, _, uF = lat.moments()
+                    U = float(uF[..., 0][fl].mean())
+                    if U_prev is not None and abs(U - U_prev) <= 1e-7 * abs(U):
+                        break
+                    U_prev = U
+                red = lat.reduce()
+            except LBMError:
+                out["runs"]["%s/%g" % (col, tau)] = {"diverged": True, "steps": done}
+                lat.close()
+                continue
+            lat.close()
+            out["runs"]["%s/%g" % (col, tau)] = {
+                "nu": nu, "g": g, "steps": done, "converged": done < cap, "U_pore": U,
+                "K": phi * nu * U / g, "Re": U * L / nu, "max_uF": red["max_uF"]}
+    return out
+
+
 def main():
     ap = argparse.ArgumentParser()
-    ap.add_argument("case", choices=["c0", "c1", "c2", "c3", "c4", "s1", "s2", "s3", "s4"])
+    ap.add_argument("case", choices=["c0", "c1", "c2", "c3", "c4", "s1", "s2", "s3", "s4", "s5"])
     ap.add_argument("--steps", type=int, default=None)
     ap.add_argument("--shape", type=int, nargs=3, default=None, help="nz ny nx (c1, c4)")
     ap.add_argument("--gravity", action="store_true", help="c4: tilted gravity")
@@ -393,7 +438,7 @@ def main():
         r = run_c1(args.steps, radii=args.radii, taus=args.taus, shape=args.shape)
     else:
         r = {"c0": run_c0, "c2": run_c2, "c3": run_c3, "s1": run_s1, "s2": run_s2,
-             "s3": run_s3, "s4": run_s4}[args.case](args.steps)
+             "s3": run_s3, "s4": run_s4, "s5": run_s5}[args.case](args.steps)
     print(json.dumps(r, default=float))
 
 

@@ -163,6 +163,17 @@ def channel_droplet(shape, info, R, s0=0.0, rho_in=1.0, rho_out=0.03, width=2.0)
     return rho1[:, None, :], rho2[:, None, :]
 
 
+def sphere_array_cell(L=34, chi=1.0):
+    """One cell of the simple-cubic array of spheres (Sec. 4.2): an L^3
+    periodic lattice with a sphere of radius chi L / 2 centred in it (chi = 1:
+    neighbouring spheres touch); solid sites are the cells whose centres lie
+    inside.  Returns (shape, solid uint8, porosity)."""
+    shape = (L, L, L)
+    r = _radius(shape, ((L - 1) / 2.0,) * 3)
+    solid = (r < chi * L / 2.0).astype(np.uint8)
+    return shape, solid, float((solid == 0).mean())
+
+
 def spinodal(shape, rho0=0.5, amp=0.01, seed=20160105):
     """Uniform mixture with +-amp relative seeded noise per component."""
     n = int(np.prod(shape))
