@@ -113,3 +113,17 @@ def test_channel_droplet_centre_tracks_displacement(angle):
     d -= L * np.round(d / L)
     assert abs(d - 6.0) < 0.5          # 6 cells forward through the periodic end
     assert all(abs(r[0] - v0) <= 0.15 * v0 for r in res.values())
+
+
+def test_sphere_array_cell_geometry():
+    """The simple-cubic cell of touching spheres: porosity within 1 % of
+    1 - pi/6, neighbouring spheres meet at the face centres, and the solid is
+    symmetric under the cube's reflections."""
+    from paper_1601_01237_gb300 import workloads as wl
+    shape, solid, phi = wl.sphere_array_cell(34)
+    assert shape == (34, 34, 34)
+    assert abs(phi - (1 - np.pi / 6)) < 0.01 * (1 - np.pi / 6)
+    assert solid[0, 16, 16] and solid[16, 0, 16] and solid[16, 16, 0] and not solid[0, 0, 0]
+    for ax in range(3):
+        assert np.array_equal(solid, np.flip(solid, axis=ax))
+    assert np.array_equal(solid, solid.transpose(1, 0, 2)) and np.array_equal(solid, solid.transpose(2, 1, 0))
