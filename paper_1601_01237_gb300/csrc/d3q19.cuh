@@ -123,8 +123,9 @@ struct Third {
 // size: a warp's row of 32 pulled pairs (256 bytes) spans one or two 256-byte
 // blocks, and fetching whole blocks into L2 on a miss serves the neighbouring
 // rows and tiles that pull from the same blocks (8.45 -> 8.25 ms per 512^3
-// step).  The 16-bit rows are 128 bytes; there the hint cost 10 % (a 256^3
-// mixture), so they keep the default load.
+// step).  The 16-bit storage formats keep the default load: their rows are
+// 128 bytes, and the hint changed their step time by under 1 % (a 256^3
+// mixture).
 __device__ __forceinline__ float2 ldg_pair_f32(const float *p)
 {
     float2 v;
