@@ -119,17 +119,20 @@ struct Third {
 };
 
 // ---------------------------------------------------------------------------
-// Read-only load of one FP32 population pair with a 256-byte L2 prefetch
-// size: a warp's row of 32 pulled pairs (256 bytes) spans one or two 256-byte
-// blocks, and fetching whole blocks into L2 on a miss serves the neighbouring
-// rows and tiles that pull from the same blocks (8.45 -> 8.25 ms per 512^3
-// step).  The 16-bit storage formats keep the default load: their rows are
-// 128 bytes, and the hint changed their step time by under 1 % (a 256^3
-// mixture).
-__device__ __forceinline__ float2 ldg_pair_f32(const float *p)
+// Load of one FP32 population pair (the input copy, never written during a
+// launch) with two cache hints: a 256-byte L2 prefetch size, since a warp's
+// row of 32 pulled pairs (256 bytes) spans one or two 256-byte blocks that the
+// neighbouring rows and tiles pull from too, and evict-last priority in L1,
+// where the halo gathers re-read the rows of the tile's own planes.  At 512^3
+// (ms per step): 8.33 with a plain load, 8.25 with the read-only path and the
+// L2 hint, 8.14 with a coherent load and the L2 hint, 8.08 with both hints;
+// L1 no-allocate or evict-first: 11.5-12.2.  The 16-bit storage formats keep
+// the default load: their rows are 128 bytes, and the L2 hint changed their
+// step time by under 1 % (a 256^3 mixture).
+__device__ __forceinline__ float2 ld_pair_f32(const float *p)
 {
     float2 v;
-    asm("ld.global.nc.L2::256B.v2.f32 {%0, %1}, [%2];" : "=f"(v.x), "=f"(v.y) : "l"(p));
+    asm("ld.global.L1::evict_last.L2::256B.v2.f32 {%0, %1}, [%2];" : "=f"(v.x), "=f"(v.y) : "l"(p));
     return v;
 }
 
@@ -169,7 +172,7 @@ template <> struct Store<ST_F32> {
     __device__ static __forceinline__ void store(T *p, R v, R) { *p = v; }
     __device__ static __forceinline__ void load2(const T *p, R, R &a, R &b)
     {
-        const float2 v = ldg_pair_f32(p);
+        const float2 v = ld_pair_f32(p);
         a = v.x; b = v.y;
     }
     __device__ static __forceinline__ void store2(T *p, R a, R b, R) { *reinterpret_cast<float2 *>(p) = make_float2(a, b); }
