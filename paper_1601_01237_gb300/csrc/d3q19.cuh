@@ -120,15 +120,16 @@ struct Third {
 
 // ---------------------------------------------------------------------------
 // Load of one FP32 population pair (the input copy, never written during a
-// launch) with two cache hints: a 256-byte L2 prefetch size, since a warp's
-// row of 32 pulled pairs (256 bytes) spans one or two 256-byte blocks that the
-// neighbouring rows and tiles pull from too, and evict-last priority in L1,
-// where the halo gathers re-read the rows of the tile's own planes.  At 512^3
-// (ms per step): 8.33 with a plain load, 8.25 with the read-only path and the
-// L2 hint, 8.14 with a coherent load and the L2 hint, 8.08 with both hints;
-// L1 no-allocate or evict-first: 11.5-12.2.  The 16-bit storage formats keep
-// the default load: their rows are 128 bytes, and the L2 hint changed their
-// step time by under 1 % (a 256^3 mixture).
+// launch) with two cache hints: a 256-byte L2 prefetch size (a warp's row of
+// 32 pulled pairs is 256 bytes and spans one or two 256-byte blocks that the
+// neighbouring rows and tiles pull from too) and evict-last priority in L1.
+// Chosen by measurement at 512^3 (ms per step): 8.33 with a plain load, 8.25
+// with the read-only path and the L2 hint, 8.14 with a coherent load and the
+// L2 hint, 8.08 with both hints; L1 no-allocate or evict-first: 11.5-12.2.
+// The L1 hit rate stays near 1 % with every variant, so the L1 hint's gain
+// does not come from reuse in L1.  The 16-bit storage formats keep the
+// default load: their rows are 128 bytes, and the L2 hint changed their step
+// time by under 1 % (a 256^3 mixture).
 __device__ __forceinline__ float2 ld_pair_f32(const float *p)
 {
     float2 v;
