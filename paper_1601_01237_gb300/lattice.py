@@ -100,8 +100,10 @@ def lbm_droplet_stats(h, threshold, origin=(0.0, 0.0, 0.0)):
 
 
 def lbm_set_solid(h, solid):
-    """solid: (nz, ny, nx) flags (numpy uint8 on the host, or a torch uint8
-    tensor on the device), non-zero = solid site; None removes the mask."""
+    """solid: N = nx ny nz flags (numpy array on the host, or a contiguous
+    torch uint8/bool tensor), non-zero = solid site; None removes the mask.
+    The library copies N bytes: the caller guarantees the size
+    (Lattice.set_solid checks it)."""
     if solid is None:
         check(lib().lbm_set_solid(h, None, 0), h)
         return
@@ -285,9 +287,17 @@ class Lattice:
         return lbm_droplet_stats(self.h, threshold, origin)
 
     def set_solid(self, solid):
-        """Staircase walls: solid (nz, ny, nx) flags, non-zero = solid site."""
-        if isinstance(solid, np.ndarray):
-            assert solid.shape == self.shape
+        """Staircase walls: solid (nz, ny, nx) flags, non-zero = solid site (a
+        numpy array, or a torch uint8/bool tensor of that shape); None removes
+        the mask."""
+        if solid is not None:
+            if isinstance(solid, np.ndarray):
+                if solid.shape != self.shape:
+                    raise ValueError("mask shape %s != lattice shape %s" % (solid.shape, self.shape))
+            else:
+                import torch
+                if tuple(solid.shape) != self.shape or solid.dtype not in (torch.uint8, torch.bool):
+                    raise ValueError("mask must be a uint8 or bool tensor of shape %s" % (self.shape,))
         lbm_set_solid(self.h, solid)
 
     def get_populations(self):
