@@ -271,9 +271,10 @@ FUSED_CASES = [
                                      rho_s=(0.02, 0.0))),
     ("walls_potential", (5, 9, 34), dict(tau=(1.0, 1.0), G12=-1.1, periodic=(1, 1, 0), wall_model="potential",
                                          rho_s=(0.0, 0.1))),
-    # x extents of whole 32-wide tiles: tiles of a thread-block cluster along x
-    # exchange their edge-column densities (two tiles: the cluster is the whole
-    # row and wraps; 24 tiles: clusters of 8 with gathered halo at their ends)
+    # x extents of whole 32-wide tiles: two tiles (each tile's x halo is the
+    # other tile, across the periodic wrap) and 24 tiles; the names come from
+    # a thread-block-cluster variant of the kernel that was measured and
+    # dropped, and the cases stay as tile-row edge cases
     ("cluster_wrap", (20, 11, 64), dict(tau=(0.8, 1.0), G12=-1.3, g_ext=(2e-5, -1e-5, 1e-5))),
     ("cluster_of_8", (9, 8, 768), dict(tau=(0.9, 0.7), G12=-1.2)),
     ("cluster_walls_reg", (12, 9, 128), dict(tau=(0.7, 0.9), G12=-1.2, periodic=(1, 1, 0), collision="regularized",
