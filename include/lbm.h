@@ -156,8 +156,9 @@ lbm_status lbm_pressure_jump(lbm_lattice *h, const double center[3], double r_in
  * the GPU.  Droplet = cells with rho^1 > threshold.  out[0] = droplet volume
  * (cells), out[1..3] = its centre of mass (mean x, y, z relative to origin[3],
  * minimum image along periodic axes), out[4] = mass of component 1 inside it,
- * out[5] = mean rho^1 of the wall layer z = 0 outside the droplet (thin-film
- * density), out[6] = number of those cells.  Synchronizes.  Errors:
+ * out[5] = mean rho^1 of the wall layer z = 0 (with a solid mask: the fluid
+ * cells next to a solid site) outside the droplet (thin-film density),
+ * out[6] = number of those cells.  Synchronizes.  Errors:
  * LBM_EINVAL, LBM_ECUDA. */
 lbm_status lbm_droplet_stats(lbm_lattice *h, double threshold, const double origin[3], double out[7]);
 
@@ -168,8 +169,10 @@ lbm_status lbm_droplet_stats(lbm_lattice *h, double threshold, const double orig
  * and velocities read as 0); in Eq. 13 a solid site presents the w-weighted
  * mean of rho^b over its fluid neighbours plus rho_s^b (LBM_WALL_MIRROR) or
  * rho_s^b alone (LBM_WALL_POTENTIAL).  NULL removes the mask.  A lattice
- * with a mask steps with the two-kernel step; lbm_record,
- * lbm_pressure_jump and lbm_droplet_stats return LBM_ENOTSUP for it.  Set
+ * with a mask steps with the two-kernel step; lbm_record returns
+ * LBM_ENOTSUP for it; lbm_pressure_jump and lbm_droplet_stats leave solid
+ * sites out, and the thin-film layer of lbm_droplet_stats is then the fluid
+ * cells next to a solid site.  Set
  * the mask before lbm_init_fields (a state set earlier keeps the populations
  * of the new solid sites, which are never read).  Drops the lattice's
  * recording.  Synchronizes.  Errors: LBM_EINVAL (NULL handle), LBM_ENOTSUP

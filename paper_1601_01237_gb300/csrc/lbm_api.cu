@@ -482,7 +482,6 @@ lbm_status diag_run(lbm_lattice *h, int which, const double *vec3, double a0, do
 lbm_status lbm_pressure_jump(lbm_lattice *h, const double center[3], double r_in, double r_out, double out[3])
 {
     if (!h || !center || !out) return fail(LBM_EINVAL, "lbm_pressure_jump: NULL argument");
-    if (h->solid) return fail(LBM_ENOTSUP, "lbm_pressure_jump: not available with a solid mask");
     if (!(r_in > 0) || !(r_out >= r_in)) return fail(LBM_EINVAL, "lbm_pressure_jump: need 0 < r_in <= r_out");
     DeviceGuard g(h->device);
     double s[4];
@@ -498,7 +497,6 @@ lbm_status lbm_pressure_jump(lbm_lattice *h, const double center[3], double r_in
 lbm_status lbm_droplet_stats(lbm_lattice *h, double threshold, const double origin[3], double out[7])
 {
     if (!h || !origin || !out) return fail(LBM_EINVAL, "lbm_droplet_stats: NULL argument");
-    if (h->solid) return fail(LBM_ENOTSUP, "lbm_droplet_stats: not available with a solid mask");
     DeviceGuard g(h->device);
     double s[7];
     lbm_status st = diag_run(h, 1, origin, threshold, 0.0, s, 7);

@@ -22,7 +22,24 @@ struct Geo {
     int nx, ny, nz;
     long long N;
     int per[3];
+    const unsigned char *solid;   // mask of solid sites or nullptr
 };
+
+// Does fluid cell (x, y, z) of a masked (fully periodic) lattice have a solid
+// site among its 18 neighbours?
+template <class R>
+__device__ __forceinline__ bool next_to_solid(const Geo<R> &g, int x, int y, int z)
+{
+    for (int dz = -1; dz <= 1; ++dz)
+        for (int dy = -1; dy <= 1; ++dy)
+            for (int dx = -1; dx <= 1; ++dx) {
+                const int m = dx * dx + dy * dy + dz * dz;
+                if (m == 0 || m > 2) continue;
+                const int X = (x + dx + g.nx) % g.nx, Y = (y + dy + g.ny) % g.ny, Z = (z + dz + g.nz) % g.nz;
+                if (g.solid[((long long)Z * g.ny + Y) * g.nx + X]) return true;
+            }
+    return false;
+}
 
 __device__ __forceinline__ double min_image(double d, int n, int periodic)
 {
@@ -63,6 +80,7 @@ k_pressure(const R *__restrict__ rho, Geo<R> g, double G12, double cx, double cy
         const long long rem = c - (long long)z * plane;
         const int y = (int)(rem / g.nx);
         const int x = (int)(rem - (long long)y * g.nx);
+        if (g.solid && g.solid[c]) continue;   // no fluid at a solid site
         const double dx = min_image(x - cx, g.nx, g.per[0]);
         const double dy = min_image(y - cy, g.ny, g.per[1]);
         const double dz = min_image(z - cz, g.nz, g.per[2]);
@@ -77,8 +95,10 @@ k_pressure(const R *__restrict__ rho, Geo<R> g, double G12, double cx, double cy
 
 // Droplet of component 1: cells with rho^1 > threshold.  Partials: volume,
 // sum x, sum y, sum z (coordinates relative to `origin`, minimum image along
-// periodic axes), sum rho^1 over the droplet, and over the wall layer z = 0
-// outside the droplet: sum rho^1 and cell count (thin film).
+// periodic axes), sum rho^1 over the droplet, and over the wall layer outside
+// the droplet: sum rho^1 and cell count (thin film).  The wall layer is z = 0,
+// or with a mask the fluid cells next to a solid site; solid sites count for
+// nothing.
 template <class R>
 __global__ void __launch_bounds__(kThreadsD)
 k_droplet(const R *__restrict__ rho, Geo<R> g, double threshold, double ox, double oy, double oz,
@@ -91,6 +111,7 @@ k_droplet(const R *__restrict__ rho, Geo<R> g, double threshold, double ox, doub
         const long long rem = c - (long long)z * plane;
         const int y = (int)(rem / g.nx);
         const int x = (int)(rem - (long long)y * g.nx);
+        if (g.solid && g.solid[c]) continue;
         const double r1 = (double)rho[c];
         if (r1 > threshold) {
             acc[0] += 1.0;
@@ -98,7 +119,7 @@ k_droplet(const R *__restrict__ rho, Geo<R> g, double threshold, double ox, doub
             acc[2] += min_image(y - oy, g.ny, g.per[1]);
             acc[3] += min_image(z - oz, g.nz, g.per[2]);
             acc[4] += r1;
-        } else if (z == 0) {
+        } else if (g.solid ? next_to_solid(g, x, y, z) : z == 0) {
             acc[5] += r1;
             acc[6] += 1.0;
         }
@@ -112,6 +133,7 @@ Geo<R> geo_of(const HostPhys &h)
     Geo<R> g;
     g.nx = h.nx; g.ny = h.ny; g.nz = h.nz; g.N = h.N;
     g.per[0] = 1; g.per[1] = 1; g.per[2] = h.wall_z ? 0 : 1;
+    g.solid = h.solid;
     return g;
 }
 

@@ -138,10 +138,50 @@ def test_mask_refusals(gpu_lib):
     lat = Lattice(shape, storage="f32", G12=-1.2)
     lat.set_solid(solid)
     lat.init_fields(np.full(shape, 0.5), np.full(shape, 0.5))
-    for call in (lambda: lat.record(2, 1), lambda: lat.droplet_stats(0.5),
-                 lambda: lat.pressure_jump((2.0, 2.0, 2.0), 1.0, 2.0)):
-        with pytest.raises(LBMError, match="ENOTSUP"):
-            call()
-    lat.set_solid(None)       # without the mask the calls work again
+    with pytest.raises(LBMError, match="ENOTSUP"):
+        lat.record(2, 1)
+    with pytest.raises(ValueError):
+        lat.set_solid(solid[:, :, :-1])
+    lat.set_solid(None)       # without the mask the recording works again
     lat.record(2, 1)
     lat.close()
+
+
+def test_mask_droplet_stats_and_pressure(gpu_lib):
+    """Droplet statistics and the pressure jump on a masked lattice (inclined
+    channel, droplet on the wall, FP64, 200 steps) against the same sums over
+    the oracle's fields: solid sites left out, and the thin-film layer is the
+    fluid cells next to a solid site."""
+    shape, solid, info = wl.inclined_channel(30)
+    r1, r2 = wl.channel_droplet(shape, info, 7.0)
+    # component 1 as the droplet: swap the roles
+    r1, r2 = r2, r1
+    kw = dict(tau=(1.0, 1.0), G12=wl.G_DROPLET, rho_s=(0.3, 0.0))
+    p, f_or = oracle_run(shape, r1, r2, None, 200, solid=solid, **kw)
+    a, b, _ = oracle.moments(p, f_or)
+    lat = gpu_run(shape, r1, r2, None, 200, storage="f64", solid=solid, **kw)
+    nz, _, nx = shape
+    thr = 0.5
+    origin = ((nx - 1) / 2.0, 0.0, (nz - 1) / 2.0)
+    st = lat.droplet_stats(thr, origin=origin)
+    pin, pout, dp = lat.pressure_jump(origin, 3.0, 12.0)
+    lat.close()
+    fl = solid == 0
+    z, y, x = np.meshgrid(np.arange(nz), np.arange(1), np.arange(nx), indexing="ij")
+    drop = fl & (a > thr)
+    mi = lambda d, n: d - n * np.round(d / n)
+    assert st["volume"] == drop.sum()
+    assert abs(st["mass"] - a[drop].sum()) < 1e-10 * a[drop].sum()
+    assert abs(st["com"][0] - mi(x - origin[0], nx)[drop].mean()) < 1e-9
+    assert abs(st["com"][2] - mi(z - origin[2], nz)[drop].mean()) < 1e-9
+    near = np.zeros_like(fl)
+    for dz in (-1, 0, 1):
+        for dx in (-1, 0, 1):
+            if dz or dx:
+                near |= np.roll(np.roll(solid == 1, -dz, axis=0), -dx, axis=2)
+    # quasi-2D: links along y land on the cell's own column
+    film = fl & ~drop & near
+    assert film.sum() > 0 and abs(st["film_rho"] - a[film].mean()) < 1e-10
+    pr = (a + b) / 3.0 - wl.G_DROPLET / 3.0 * a * b
+    r = np.sqrt(mi(x - origin[0], nx) ** 2 + mi(z - origin[2], nz) ** 2)
+    assert abs(pin - pr[fl & (r < 3.0)].mean()) < 1e-12 and abs(pout - pr[fl & (r > 12.0)].mean()) < 1e-12
