@@ -65,7 +65,7 @@ typedef enum {
                              f^neq is the w-weighted projection of
                              (f - f^eq) / w_i onto the second- and
                              third-order Hermite polynomials that D3Q19
-                             carries (6 + 6 of them); forward only */
+                             carries (6 + 6 of them) */
 } lbm_collision;
 
 /* Density a solid site presents to the interaction sum of Eq. 13. */
@@ -215,7 +215,7 @@ lbm_status lbm_sync(lbm_lattice *h);
  * segment of states and of their densities); both are held until the next
  * lbm_record or lbm_destroy, so that lbm_adjoint allocates nothing.
  * Synchronizes.  Errors: LBM_EINVAL, LBM_ENOMEM, LBM_ECUDA, LBM_ENOTSUP
- * (collision LBM_REGULARIZED3, which has no reverse pass). */
+ * (a lattice with a solid mask, which has no reverse pass). */
 lbm_status lbm_record(lbm_lattice *h, long n_steps, int ckpt_every);
 
 /* Reverse pass over the last lbm_record.  Inputs dL_drho1, dL_drho2: N values

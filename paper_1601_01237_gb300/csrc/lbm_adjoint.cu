@@ -79,7 +79,7 @@ __device__ __forceinline__ unsigned at(const Nb &n, int dx, int dy, int dz)
 //   mu_i(y) = lambda^{n+1}_i(y + c_i) = lambda_loc^{n+1}_i(y + c_i) + D^{n+1}_a(y + c_i)
 // (or lambda^{n+1}_opp(i)(y) at a wall), and writes lambda_loc^n_i(y) of its
 // component and a^n_b(y) of the other component b = 1 - a.
-template <int S, bool REG, bool SIN>
+template <int S, int REG, bool SIN>
 __device__ __forceinline__ void adj_half(const typename Store<S>::T *__restrict__ f,
                                          const typename Store<S>::R *__restrict__ rho,
                                          const typename Store<S>::R *__restrict__ lam_next,
@@ -167,6 +167,14 @@ __device__ __forceinline__ void adj_half(const typename Store<S>::T *__restrict_
         Pi[5] -= ra * u1 * u2;
         tr = Pi[0] + Pi[1] + Pi[2];
     }
+    // third-order part (REG = 2): S_a, D_a of struct Third for this component
+    Third<R> th;
+    if (REG == 2) {
+        th.zero();
+#pragma unroll
+        for (int i = 1; i < Q; ++i) th.add(i, fa[i]);
+        th.finish(ra, u0, u1, u2);
+    }
     // ---- incoming sensitivities ---------------------------------------------
     R mu[Q];
 #pragma unroll
@@ -187,6 +195,7 @@ __device__ __forceinline__ void adj_half(const typename Store<S>::T *__restrict_
     R Kbar = 0, rbar = 0;
     R vbx = 0, vby = 0, vbz = 0, vbv = 0, ubx = 0, uby = 0, ubz = 0, ubv = 0;
     R pb[6] = {0, 0, 0, 0, 0, 0};
+    R sb[3] = {0, 0, 0}, db[3] = {0, 0, 0};   // dL/dS_a, dL/dD_a (REG = 2)
     {
         // rest population: c = 0, k = 12
         const R m = mu[0], mk = m * R(12);
@@ -240,6 +249,16 @@ __device__ __forceinline__ void adj_half(const typename Store<S>::T *__restrict_
             if (c0 && c1) pb[3] += nb * R(c0 * c1);
             if (c0 && c2) pb[4] += nb * R(c0 * c2);
             if (c1 && c2) pb[5] += nb * R(c1 * c2);
+            if (REG == 2) {
+                // f*_i +- keep (k_i / 8) sum_a (S_a h3s3(i, a) + D_a h3d(i, a)) for i, opp(i)
+                Kbar += df * R(0.125) * (th.odd(i) / (R(k36(i)) * R(0.125)));
+                const R nd = keep * df * R(0.125);
+#pragma unroll
+                for (int q = 0; q < 3; ++q) {
+                    if (h3s3(i, q)) sb[q] += nd * R(h3s3(i, q));
+                    if (h3d(i, q)) db[q] += nd * R(h3d(i, q));
+                }
+            }
         }
     }
     rbar /= R(36);
@@ -258,6 +277,24 @@ __device__ __forceinline__ void adj_half(const typename Store<S>::T *__restrict_
         ub0 -= R(2) * ra * (pb[0] * u0 + pb[3] * u1 + pb[4] * u2);
         ub1 -= R(2) * ra * (pb[3] * u0 + pb[1] * u1 + pb[5] * u2);
         ub2 -= R(2) * ra * (pb[4] * u0 + pb[5] * u1 + pb[2] * u2);
+        if (REG == 2) {
+            // S_a = (1/3) sum h3s3 f - rho u_a (u_b^2 + u_c^2) / 2,
+            // D_a = sum h3d f - 3/2 rho u_a (u_b^2 - u_c^2)   (b < c the other axes)
+            const R u[3] = {u0, u1, u2};
+            R ubq[3] = {0, 0, 0};
+#pragma unroll
+            for (int q = 0; q < 3; ++q) {
+                const int qb = q == 0 ? 1 : 0, qc = q == 2 ? 1 : 2;
+                const R ua = u[q], ubb = u[qb], ucc = u[qc];
+                rbar -= sb[q] * R(0.5) * ua * (ubb * ubb + ucc * ucc) + db[q] * R(1.5) * ua * (ubb * ubb - ucc * ucc);
+                ubq[q] -= ra * (sb[q] * R(0.5) * (ubb * ubb + ucc * ucc) + db[q] * R(1.5) * (ubb * ubb - ucc * ucc));
+                ubq[qb] -= ra * ua * ubb * (sb[q] + R(3) * db[q]);
+                ubq[qc] -= ra * ua * ucc * (sb[q] - R(3) * db[q]);
+            }
+            ub0 += ubq[0];
+            ub1 += ubq[1];
+            ub2 += ubq[2];
+        }
     }
     // u = j / rho over both components: dL/dj = ubar / rho, dL/drho += -(ubar . u) / rho
     const R U0 = ub0 + __shfl_xor_sync(full, ub0, 16);
@@ -276,6 +313,13 @@ __device__ __forceinline__ void adj_half(const typename Store<S>::T *__restrict_
                 const int c0 = cx(i), c1 = cy(i), c2 = cz(i);
                 l += R(c0 * c0) * pb[0] + R(c1 * c1) * pb[1] + R(c2 * c2) * pb[2] + R(2 * c0 * c1) * pb[3] +
                      R(2 * c0 * c2) * pb[4] + R(2 * c1 * c2) * pb[5];
+                if (REG == 2) {
+#pragma unroll
+                    for (int q = 0; q < 3; ++q) {
+                        if (h3s3(i, q)) l += sb[q] * (R(h3s3(i, q)) / R(3));
+                        if (h3d(i, q)) l += db[q] * R(h3d(i, q));
+                    }
+                }
             }
             lo[(long long)i * N] = l;
         }
@@ -292,7 +336,7 @@ __device__ __forceinline__ void adj_half(const typename Store<S>::T *__restrict_
 // Grid-stride over groups of 16 cells per warp; lanes 0-15 take component 0
 // and lanes 16-31 component 1 of the same 16 cells.  Per-block FP64 partials
 // of dL/dG^{12}, dL/dG^{21}, dL/dtau_1, dL/dtau_2 accumulate over the steps.
-template <int S, bool REG, bool SIN>
+template <int S, int REG, bool SIN>
 __global__ void __launch_bounds__(kThreadsA, 2)
 k_adj_local(const typename Store<S>::T *__restrict__ f, const typename Store<S>::R *__restrict__ rho,
             const typename Store<S>::R *__restrict__ lam_next, const typename Store<S>::R *__restrict__ Dn,
@@ -429,9 +473,9 @@ cudaError_t adj_step_t(const HostPhys &h, const void *f, const void *rho, int rh
     k_adj_local<S, REG_, SIN_><<<adjoint_blocks(), kThreadsA, 0, s>>>((const T *)f, (const R *)rho,         \
                                                                       (const R *)lam_next, (const R *)Dn,  \
                                                                       (R *)lam_loc, (R *)a, partials, p)
-    const bool reg = h.collision == LBM_REGULARIZED;
-    if (rho_is_sums) { if (reg) LBM_ADJ(true, true); else LBM_ADJ(false, true); }
-    else { if (reg) LBM_ADJ(true, false); else LBM_ADJ(false, false); }
+    const int reg = h.collision == LBM_REGULARIZED ? 1 : (h.collision == LBM_REGULARIZED3 ? 2 : 0);
+    if (rho_is_sums) { if (reg == 1) LBM_ADJ(1, true); else if (reg == 2) LBM_ADJ(2, true); else LBM_ADJ(0, true); }
+    else { if (reg == 1) LBM_ADJ(1, false); else if (reg == 2) LBM_ADJ(2, false); else LBM_ADJ(0, false); }
 #undef LBM_ADJ
     k_adj_D<R><<<gridA(h.N), kThreadsA, 0, s>>>((const R *)a, (R *)Dout, p);
     return cudaGetLastError();

@@ -634,8 +634,6 @@ lbm_status lbm_record(lbm_lattice *h, long n_steps, int ckpt_every)
     if (!h) return fail(LBM_EINVAL, "lbm_record: NULL handle");
     if (n_steps < 1 || ckpt_every < 1)
         return fail(LBM_EINVAL, "lbm_record: n_steps = %ld and ckpt_every = %d must be >= 1", n_steps, ckpt_every);
-    if (h->phys.collision == LBM_REGULARIZED3)
-        return fail(LBM_ENOTSUP, "lbm_record: the third-order regularized collision has no reverse pass");
     if (h->solid) return fail(LBM_ENOTSUP, "lbm_record: lattices with a solid mask have no reverse pass");
     DeviceGuard g(h->device);
     size_t sb = 0;
