@@ -127,3 +127,38 @@ def test_sphere_array_cell_geometry():
     for ax in range(3):
         assert np.array_equal(solid, np.flip(solid, axis=ax))
     assert np.array_equal(solid, solid.transpose(1, 0, 2)) and np.array_equal(solid, solid.transpose(2, 1, 0))
+
+
+@pytest.mark.parametrize("angle", [10, 30, 50, 70])
+def test_inclined_channel_geometry(angle):
+    """The inclined channel: its angle within 0.3 degrees, length >= 96, the
+    fluid band H = 16 wide across the channel (fluid fraction H / P of the
+    lattice), at least 4 solid layers between periodic copies, and a single
+    connected channel through the periodic ends."""
+    from paper_1601_01237_gb300 import workloads as wl
+    shape, solid, info = wl.inclined_channel(angle)
+    nz, _, nx = shape
+    assert abs(info["theta_deg"] - angle) <= 0.3 and info["L"] >= 96 and info["P"] >= 20
+    fl = solid[:, 0, :] == 0
+    assert abs(fl.mean() - 16.0 / info["P"]) < 0.03
+    # cells on a line across the channel: fluid run of about H cells
+    en = info["across"]
+    c = np.array([(nx - 1) / 2.0, (nz - 1) / 2.0])
+    run = [fl[int(round(c[1] + t * en[1])) % nz, int(round(c[0] + t * en[0])) % nx]
+           for t in np.arange(-info["P"] / 2 + 0.25, info["P"] / 2, 0.5)]
+    assert abs(0.5 * sum(run) - 16.0) <= 1.5
+    # one channel: the fluid cells form a single region on the periodic
+    # lattice (flood fill through the D2Q9 links, wrapping at the ends)
+    seen = np.zeros_like(fl)
+    start = tuple(np.argwhere(fl)[0])
+    stack = [start]
+    seen[start] = True
+    while stack:
+        z, x = stack.pop()
+        for dz in (-1, 0, 1):
+            for dx in (-1, 0, 1):
+                q = ((z + dz) % nz, (x + dx) % nx)
+                if fl[q] and not seen[q]:
+                    seen[q] = True
+                    stack.append(q)
+    assert seen.sum() == fl.sum()
