@@ -51,3 +51,23 @@ def test_reference_arm_other_ranks_do_nothing():
         gpus = 2
         storage = None
     assert bench.run_reference(A(), rank=1, world=2) is None
+
+
+def test_reference_arm_line_on_cpu():
+    """The reference arm runs without a GPU: the oracle on every host core,
+    one JSON line with the contract's keys, its value the aggregate over the
+    processes."""
+    import json
+    import subprocess
+    import sys
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    r = subprocess.run([sys.executable, os.path.join(root, "bench.py"), "--impl", "reference", "--steps", "1",
+                        "--warmup", "0"], capture_output=True, text=True, timeout=600, cwd=root)
+    assert r.returncode == 0, r.stderr[-2000:]
+    line = json.loads(r.stdout.strip().splitlines()[-1])
+    for k in ("metric", "value", "unit", "n_gpus", "steps", "warmup", "ms_per_step", "higher_is_better",
+              "config", "cpu_baseline", "e2e"):
+        assert k in line, k
+    assert line["impl"] == "reference" and line["value"] > 0
+    assert line["cpu_baseline"]["cores"] == (os.cpu_count() or 1)
+    assert line["e2e"]["h2d_bytes_per_step"] == 0
