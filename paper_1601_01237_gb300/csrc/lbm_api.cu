@@ -49,6 +49,7 @@ struct lbm_lattice {
     int graph_state;     // 0 not built, 1 ready, -1 not available (plain launches)
     int use_graphs;
     unsigned char *solid;   // device mask of solid sites (N bytes) or nullptr
+    unsigned *links;        // its link flags (N words) or nullptr
 };
 
 namespace {
@@ -247,6 +248,7 @@ void lbm_destroy(lbm_lattice *h)
     cudaFree(h->ckpt);
     free_workspace(h);
     cudaFree(h->solid);
+    cudaFree(h->links);
     cudaFree(h->partials);
     if (h->graph) cudaGraphExecDestroy(h->graph);
     if (h->partials_h) cudaFreeHost(h->partials_h);
@@ -527,17 +529,23 @@ lbm_status lbm_set_solid(lbm_lattice *h, const unsigned char *solid, int on_devi
     free_workspace(h);
     if (!solid) {
         cudaFree(h->solid);
+        cudaFree(h->links);
         h->solid = nullptr;
+        h->links = nullptr;
         h->phys.solid = nullptr;
+        h->phys.links = nullptr;
         h->use_fused = env_flag("LBM_FUSED", 1) && lbm::fused_supported(h->phys);
         return LBM_OK;
     }
     const size_t N = (size_t)h->phys.N;
     if (!h->solid) CK(cudaMalloc((void **)&h->solid, N), "lbm_set_solid: mask");
+    if (!h->links) CK(cudaMalloc((void **)&h->links, N * sizeof(unsigned)), "lbm_set_solid: link flags");
     CK(cudaMemcpyAsync(h->solid, solid, N, on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice,
                        h->stream), "lbm_set_solid: copy");
+    CK(lbm::launch_link_flags(h->phys, h->solid, h->links, h->stream), "lbm_set_solid: link flags");
     CK(cudaStreamSynchronize(h->stream), "lbm_set_solid: sync");
     h->phys.solid = h->solid;
+    h->phys.links = h->links;
     h->use_fused = 0;   // the fused kernel takes no mask
     return LBM_OK;
 }

@@ -68,12 +68,12 @@ __device__ __forceinline__ void gather(const typename Store<S>::T *__restrict__ 
                                        typename Store<S>::R (&fa)[2][Q])
 {
     using R = typename Store<S>::R;
+    const unsigned lf = p.links ? __ldg(p.links + n.cell) : 0u;   // bit i: x - c_i is solid
 #pragma unroll
     for (int i = 0; i < Q; ++i) {
         const R ref = w<R>(i) * p.rho0;
         const long long src = n.zo[1 - cz(i)] + n.yo[1 - cy(i)] + n.xo[1 - cx(i)];
-        const bool wall = (cz(i) == 1 && n.zlo_wall) || (cz(i) == -1 && n.zhi_wall) ||
-                          (i != 0 && p.solid && __ldg(p.solid + src));
+        const bool wall = (cz(i) == 1 && n.zlo_wall) || (cz(i) == -1 && n.zhi_wall) || ((lf >> i) & 1u);
         const long long idx = wall ? pair_index(opp(i), n.cell, p.N) : pair_index(i, src, p.N);
         Store<S>::load2(f + idx, ref, fa[0][i], fa[1][i]);
     }
@@ -185,6 +185,20 @@ k_wall_rho(R *__restrict__ rho, Phys<R> p)
     }
     rho[n.cell] = (den36 ? num1 / R(den36) : R(0)) + p.rho_s[0];
     rho[p.N + n.cell] = (den36 ? num2 / R(den36) : R(0)) + p.rho_s[1];
+}
+
+// Link flags of a mask: bit i of cell x set when x - c_i is a solid site, so
+// that the gather tests one word per cell instead of one byte per link.
+__global__ void __launch_bounds__(kThreads)
+k_link_flags(const unsigned char *__restrict__ solid, unsigned *__restrict__ links, Phys<float> p)
+{
+    Nbr n;
+    if (!decode_cell(p, (long long)blockIdx.x * kThreads + threadIdx.x, n)) return;
+    unsigned f = 0;
+#pragma unroll
+    for (int i = 1; i < Q; ++i)
+        if (solid[n.zo[1 - cz(i)] + n.yo[1 - cy(i)] + n.xo[1 - cx(i)]]) f |= 1u << i;
+    links[n.cell] = f;
 }
 
 template <int S, int REG>
@@ -398,6 +412,7 @@ Phys<R> make_phys(const HostPhys &h)
     p.rho_s[0] = (R)h.rho_s[0]; p.rho_s[1] = (R)h.rho_s[1];
     p.rho0 = (R)h.rho0;
     p.solid = h.solid;
+    p.links = h.links;
     return p;
 }
 
@@ -553,6 +568,12 @@ cudaError_t launch_moments(const HostPhys &p, const void *f, void *rho, int out_
 }
 
 int reduce_blocks() { return kReduceBlocks; }
+
+cudaError_t launch_link_flags(const HostPhys &h, const unsigned char *solid, unsigned *links, cudaStream_t s)
+{
+    k_link_flags<<<grid_for(h.N), kThreads, 0, s>>>(solid, links, make_phys<float>(h));
+    return cudaGetLastError();
+}
 
 cudaError_t launch_density(const HostPhys &h, const void *f, void *rho, cudaStream_t s)
 {

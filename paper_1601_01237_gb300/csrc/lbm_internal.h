@@ -25,6 +25,9 @@ struct HostPhys {
     // Only the two-kernel step and its density, output and reduction kernels
     // take a mask.
     const unsigned char *solid = nullptr;
+    // N words of link flags derived from the mask: bit i set when the pull
+    // source x - c_i of cell x is a solid site (launch_link_flags)
+    const unsigned *links = nullptr;
 };
 
 // Populations are stored as 2*19*N values of the storage type, laid out
@@ -99,6 +102,9 @@ cudaError_t launch_pressure(const HostPhys &h, const void *rho, const double cen
                             double *partials, cudaStream_t s);
 cudaError_t launch_droplet(const HostPhys &h, const void *rho, double threshold, const double origin[3],
                            double *partials, cudaStream_t s);
+
+// Link flags of a solid mask (N words, see HostPhys::links).
+cudaError_t launch_link_flags(const HostPhys &p, const unsigned char *solid, unsigned *links, cudaStream_t s);
 
 size_t storage_bytes(int storage);   // bytes per stored population value
 size_t real_bytes(int storage);      // bytes per arithmetic value
