@@ -237,7 +237,6 @@ struct Phys {
     R rho_s[2];
     R rho0;                 // reference density of deviation storage (0 otherwise)
     const unsigned char *solid = nullptr;   // N flags, 1 = solid site (two-kernel step only)
-    const unsigned *links = nullptr;        // N words: bit i set when x - c_i is a solid site
 };
 
 // Third-order equilibrium of Eq. 3 with T0 = 1/3, for direction i and its

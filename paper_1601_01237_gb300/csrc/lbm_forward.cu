@@ -26,6 +26,14 @@ namespace {
 
 constexpr int kThreads = 256;
 
+// Kernel parameters of the two-kernel step: the lattice's Phys plus the link
+// flags of a solid mask (N words, bit i set when x - c_i is a solid site;
+// nullptr without a mask).
+template <class R>
+struct PhysF : Phys<R> {
+    const unsigned *links = nullptr;
+};
+
 // Neighbourhood of one cell: offsets of x-1, x, x+1 (and likewise y, z) as
 // linear cell offsets with periodic wrap.  Index k = d + 1 for neighbour x + d.
 struct Nbr {
@@ -64,7 +72,7 @@ __device__ __forceinline__ bool decode_cell(const Phys<R> &p, long long cell, Nb
 // gather, with half-way bounce-back at z walls).
 template <int S>
 __device__ __forceinline__ void gather(const typename Store<S>::T *__restrict__ f,
-                                       const Phys<typename Store<S>::R> &p, const Nbr &n,
+                                       const PhysF<typename Store<S>::R> &p, const Nbr &n,
                                        typename Store<S>::R (&fa)[2][Q])
 {
     using R = typename Store<S>::R;
@@ -140,7 +148,7 @@ __device__ __forceinline__ void local_moments(const R (&fa)[2][Q], R &r1, R &r2,
 template <int S>
 __global__ void __launch_bounds__(kThreads)
 k_density(const typename Store<S>::T *__restrict__ f, typename Store<S>::R *__restrict__ rho,
-          Phys<typename Store<S>::R> p)
+          PhysF<typename Store<S>::R> p)
 {
     using R = typename Store<S>::R;
     Nbr n;
@@ -165,7 +173,7 @@ k_density(const typename Store<S>::T *__restrict__ f, typename Store<S>::R *__re
 // read by a fluid cell and gets rho_s^b.
 template <class R>
 __global__ void __launch_bounds__(kThreads)
-k_wall_rho(R *__restrict__ rho, Phys<R> p)
+k_wall_rho(R *__restrict__ rho, PhysF<R> p)
 {
     Nbr n;
     if (!decode_cell(p, (long long)blockIdx.x * kThreads + threadIdx.x, n)) return;
@@ -190,7 +198,7 @@ k_wall_rho(R *__restrict__ rho, Phys<R> p)
 // Link flags of a mask: bit i of cell x set when x - c_i is a solid site, so
 // that the gather tests one word per cell instead of one byte per link.
 __global__ void __launch_bounds__(kThreads)
-k_link_flags(const unsigned char *__restrict__ solid, unsigned *__restrict__ links, Phys<float> p)
+k_link_flags(const unsigned char *__restrict__ solid, unsigned *__restrict__ links, PhysF<float> p)
 {
     Nbr n;
     if (!decode_cell(p, (long long)blockIdx.x * kThreads + threadIdx.x, n)) return;
@@ -204,7 +212,7 @@ k_link_flags(const unsigned char *__restrict__ solid, unsigned *__restrict__ lin
 template <int S, int REG>
 __global__ void __launch_bounds__(kThreads)
 k_collide(const typename Store<S>::T *__restrict__ fin, typename Store<S>::T *__restrict__ fout,
-          const typename Store<S>::R *__restrict__ rho, Phys<typename Store<S>::R> p)
+          const typename Store<S>::R *__restrict__ rho, PhysF<typename Store<S>::R> p)
 {
     using R = typename Store<S>::R;
     Nbr n;
@@ -237,7 +245,7 @@ template <int S>
 __global__ void __launch_bounds__(kThreads)
 k_init_feq(const double *__restrict__ rho1, const double *__restrict__ rho2,
            const double *__restrict__ u, typename Store<S>::T *__restrict__ f,
-           Phys<typename Store<S>::R> p)
+           PhysF<typename Store<S>::R> p)
 {
     using R = typename Store<S>::R;
     Nbr n;
@@ -264,7 +272,7 @@ k_init_feq(const double *__restrict__ rho1, const double *__restrict__ rho2,
 template <int S>
 __global__ void __launch_bounds__(kThreads)
 k_set_pop(const double *__restrict__ src, typename Store<S>::T *__restrict__ f,
-          Phys<typename Store<S>::R> p)
+          PhysF<typename Store<S>::R> p)
 {
     using R = typename Store<S>::R;
     Nbr n;
@@ -287,7 +295,7 @@ k_set_pop(const double *__restrict__ src, typename Store<S>::T *__restrict__ f,
 template <int S>
 __global__ void __launch_bounds__(kThreads)
 k_get_pop(const typename Store<S>::T *__restrict__ f, double *__restrict__ dst,
-          Phys<typename Store<S>::R> p)
+          PhysF<typename Store<S>::R> p)
 {
     using R = typename Store<S>::R;
     Nbr n;
@@ -317,7 +325,7 @@ __device__ __forceinline__ void velocity_uF(const Phys<R> &p, R r1, R r2, R ux, 
 template <int S, class O>
 __global__ void __launch_bounds__(kThreads)
 k_moments(const typename Store<S>::T *__restrict__ f, const typename Store<S>::R *__restrict__ rho,
-          O *__restrict__ o1, O *__restrict__ o2, O *__restrict__ ouF, Phys<typename Store<S>::R> p)
+          O *__restrict__ o1, O *__restrict__ o2, O *__restrict__ ouF, PhysF<typename Store<S>::R> p)
 {
     using R = typename Store<S>::R;
     Nbr n;
@@ -350,7 +358,7 @@ constexpr int kReduceBlocks = 1216;   // 152 SMs x 8
 template <int S>
 __global__ void __launch_bounds__(kThreads, 2)
 k_reduce(const typename Store<S>::T *__restrict__ f, const typename Store<S>::R *__restrict__ rho,
-         double *__restrict__ partials, Phys<typename Store<S>::R> p)
+         double *__restrict__ partials, PhysF<typename Store<S>::R> p)
 {
     using R = typename Store<S>::R;
     double acc[6] = {0, 0, 0, 0, 0, 0};
@@ -399,9 +407,9 @@ k_reduce(const typename Store<S>::T *__restrict__ f, const typename Store<S>::R 
 }
 
 template <class R>
-Phys<R> make_phys(const HostPhys &h)
+PhysF<R> make_phys(const HostPhys &h)
 {
-    Phys<R> p;
+    PhysF<R> p;
     p.nx = h.nx; p.ny = h.ny; p.nz = h.nz; p.N = h.N;
     p.wall_z = h.wall_z;
     p.wall_mirror = h.wall_mirror;
@@ -424,7 +432,7 @@ template <int S>
 void density_pass(const HostPhys &h, const typename Store<S>::T *f, typename Store<S>::R *rho, cudaStream_t s)
 {
     using R = typename Store<S>::R;
-    const Phys<R> p = make_phys<R>(h);
+    const PhysF<R> p = make_phys<R>(h);
     k_density<S><<<grid_for(h.N), kThreads, 0, s>>>(f, rho, p);
     if (h.solid) k_wall_rho<R><<<grid_for(h.N), kThreads, 0, s>>>(rho, p);
 }
@@ -435,7 +443,7 @@ cudaError_t step_split_t(const HostPhys &h, const void *fin, void *fout, void *r
 {
     using T = typename Store<S>::T;
     using R = typename Store<S>::R;
-    const Phys<R> p = make_phys<R>(h);
+    const PhysF<R> p = make_phys<R>(h);
     const unsigned g = grid_for(h.N);
     if (ev) cudaEventRecord(ev[0], s);
     density_pass<S>(h, (const T *)fin, (R *)rho, s);
@@ -484,7 +492,7 @@ cudaError_t moments_t(const HostPhys &h, const void *f, void *rho, int out_f64, 
 {
     using T = typename Store<S>::T;
     using R = typename Store<S>::R;
-    const Phys<R> p = make_phys<R>(h);
+    const PhysF<R> p = make_phys<R>(h);
     const unsigned g = grid_for(h.N);
     if (ouF) density_pass<S>(h, (const T *)f, (R *)rho, s);
     if (out_f64)
@@ -501,7 +509,7 @@ cudaError_t reduce_t(const HostPhys &h, const void *f, void *rho, double *partia
 {
     using T = typename Store<S>::T;
     using R = typename Store<S>::R;
-    const Phys<R> p = make_phys<R>(h);
+    const PhysF<R> p = make_phys<R>(h);
     density_pass<S>(h, (const T *)f, (R *)rho, s);
     k_reduce<S><<<kReduceBlocks, kThreads, 0, s>>>((const T *)f, (const R *)rho, partials, p);
     return cudaGetLastError();
