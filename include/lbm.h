@@ -174,9 +174,11 @@ lbm_status lbm_droplet_stats(lbm_lattice *h, double threshold, const double orig
  * sites out, and the thin-film layer of lbm_droplet_stats is then the fluid
  * cells next to a solid site.  Set
  * the mask before lbm_init_fields (a state set earlier keeps the populations
- * of the new solid sites, which are never read).  Drops the lattice's
- * recording.  Synchronizes.  Errors: LBM_EINVAL (NULL handle), LBM_ENOTSUP
- * (lattice with walls along z), LBM_ENOMEM, LBM_ECUDA. */
+ * of the new solid sites, which are never read).  The library keeps the
+ * mask and one 32-bit word of link flags per cell on the device (5 bytes per
+ * cell) until the mask is removed or the lattice destroyed.  Drops the
+ * lattice's recording.  Synchronizes.  Errors: LBM_EINVAL (NULL handle),
+ * LBM_ENOTSUP (lattice with walls along z), LBM_ENOMEM, LBM_ECUDA. */
 lbm_status lbm_set_solid(lbm_lattice *h, const unsigned char *solid, int on_device);
 
 /* Copy the populations f_i^a(x, t) of the current state, as doubles laid out
