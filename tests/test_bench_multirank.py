@@ -71,3 +71,21 @@ def test_reference_arm_line_on_cpu():
     assert line["impl"] == "reference" and line["value"] > 0
     assert line["cpu_baseline"]["cores"] == (os.cpu_count() or 1)
     assert line["e2e"]["h2d_bytes_per_step"] == 0
+
+
+def test_kernel_hash_ignores_comments_only(tmp_path, monkeypatch):
+    """The committed DRAM-traffic figure stays valid across comment edits of
+    the kernel's sources and is dropped after any code edit."""
+    import sys
+    sys.path.insert(0, os.path.dirname(os.path.dirname(os.path.abspath(__file__))))
+    import bench
+    csrc = tmp_path / "paper_1601_01237_gb300" / "csrc"
+    csrc.mkdir(parents=True)
+    monkeypatch.setattr(bench, "ROOT", str(tmp_path))
+    monkeypatch.setitem(bench.KERNEL_SOURCES, "k_probe", ("a.cu",))
+    (csrc / "a.cu").write_text("// one\nint f() { return 1; }  /* x */\n")
+    h0 = bench.kernel_source_hash("k_probe")
+    (csrc / "a.cu").write_text("// two, longer\n\nint f() { return 1; }  /* y\n z */\n")
+    assert bench.kernel_source_hash("k_probe") == h0
+    (csrc / "a.cu").write_text("// one\nint f() { return 2; }\n")
+    assert bench.kernel_source_hash("k_probe") != h0
