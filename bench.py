@@ -256,6 +256,7 @@ def _oracle_sample(job):
     workload, shape, cfg, nsteps, t_start = job[:5]
     warmup = job[5] if len(job) > 5 else 1
     import oracle
+    oracle.set_threads(1)   # one single-threaded process per core
     r1, r2 = wl.fields_for(workload, shape=shape)
     p = oracle.make_params(shape, tau=cfg["tau"], G12=cfg["G"], periodic=cfg.get("periodic", (1, 1, 1)),
                            collision=cfg.get("collision", "bgk"))

@@ -49,7 +49,15 @@ def _L():
         _lib.oracle_interaction_sums.argtypes = [pp, dp, ctypes.c_double, dp, dp]
         _lib.oracle_accelerations.argtypes = [pp, dp, dp, dp, dp]
         _lib.oracle_collide_cell.argtypes = [pp, ctypes.c_int, dp, ctypes.c_double, dp, dp, dp]
+        _lib.oracle_set_threads.argtypes = [ctypes.c_int]
+        _lib.oracle_set_threads.restype = ctypes.c_int
     return _lib
+
+
+def set_threads(n):
+    """Threads of the oracle's cell loops (1 = serial); returns the count in
+    use (1 without OpenMP).  The results do not depend on it."""
+    return int(_L().oracle_set_threads(int(n)))
 
 
 def _dp(a):

@@ -14,9 +14,11 @@
  * wall interaction (Eq. 13) -> collision toward the third-order equilibrium
  * (Eq. 3) with BGK (Eq. 2) or the regularized filter (Eqs. 10-11) plus the
  * forcing term -> streaming (left-hand side of Eq. 1).  No tiling, fusion or
- * reordering.
+ * reordering.  With OpenMP, each pass runs its outer loop over cells (or z
+ * planes) on several threads; no pass reduces across cells, so the result
+ * does not depend on the thread count.
  *
- * Readings of passages the paper leaves open (each also listed in the design doc):
+ * Readings of passages the paper leaves open:
  *  - D3Q19 velocities and weights are not printed (Sec. 2 only names the
  *    set): the textbook set, rest 1/3, six axis links 1/18, twelve face
  *    diagonals 1/36.  Here they are generated from their definition
@@ -50,6 +52,9 @@
 #include <math.h>
 #include <stdlib.h>
 #include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
 
 #define Q 19
 #define T0 (1.0 / 3.0)
@@ -178,6 +183,7 @@ void oracle_moments_raw(const oracle_params *p, const double *f,
 {
     build_lattice();
     long N = (long)p->nx * p->ny * p->nz;
+#pragma omp parallel for schedule(static)
     for (long s = 0; s < N; ++s) {
         if (p->solid && p->solid[s]) {   /* no fluid at a solid site */
             rho1[s] = rho2[s] = 0.0;
@@ -247,6 +253,7 @@ void oracle_interaction_sums(const oracle_params *p, const double *rho_b, double
                              double *S_fluid, double *S_wall)
 {
     build_lattice();
+#pragma omp parallel for schedule(static)
     for (int z = 0; z < p->nz; ++z)
         for (int y = 0; y < p->ny; ++y)
             for (int x = 0; x < p->nx; ++x) {
@@ -285,6 +292,7 @@ void oracle_accelerations(const oracle_params *p, const double *rho1, const doub
         Sw[b] = (double *)malloc(sizeof(double) * 3 * N);
         oracle_interaction_sums(p, rho[b], p->rho_s[b], Sf[b], Sw[b]);
     }
+#pragma omp parallel for schedule(static)
     for (long s = 0; s < N; ++s)
         for (int a = 0; a < 2; ++a)
             for (int d = 0; d < 3; ++d) {
@@ -352,6 +360,7 @@ static void stream(const oracle_params *p, const double *fpost, double *fnew)
     long N = (long)p->nx * p->ny * p->nz;
     for (int a = 0; a < 2; ++a)
         for (int i = 0; i < Q; ++i)
+#pragma omp parallel for schedule(static)
             for (int z = 0; z < p->nz; ++z)
                 for (int y = 0; y < p->ny; ++y)
                     for (int x = 0; x < p->nx; ++x) {
@@ -381,6 +390,7 @@ void oracle_step(const oracle_params *p, double *f, double *work, long nsteps)
     for (long t = 0; t < nsteps; ++t) {
         oracle_moments_raw(p, f, rho1, rho2, u);
         oracle_accelerations(p, rho1, rho2, g1, g2);
+#pragma omp parallel for schedule(static)
         for (long s = 0; s < N; ++s)
             for (int a = 0; a < 2; ++a) {
                 double fin[Q], fpost[Q];
@@ -404,6 +414,7 @@ void oracle_init(const oracle_params *p, const double *rho1, const double *rho2,
 {
     build_lattice();
     long N = (long)p->nx * p->ny * p->nz;
+#pragma omp parallel for schedule(static)
     for (long s = 0; s < N; ++s) {
         double uz[3] = {0, 0, 0};
         const double *us = u ? &u[3 * s] : uz;
@@ -426,6 +437,7 @@ void oracle_moments(const oracle_params *p, const double *f,
     double *g2 = (double *)malloc(sizeof(double) * 3 * N);
     oracle_moments_raw(p, f, rho1, rho2, u);
     oracle_accelerations(p, rho1, rho2, g1, g2);
+#pragma omp parallel for schedule(static)
     for (long s = 0; s < N; ++s) {
         double rho = rho1[s] + rho2[s];
         if (p->solid && p->solid[s]) { uF[3 * s] = uF[3 * s + 1] = uF[3 * s + 2] = 0.0; continue; }
@@ -444,4 +456,17 @@ void oracle_collide_cell(const oracle_params *p, int a, const double fin[Q], dou
 {
     build_lattice();
     collide_cell(p, a, fin, rho_a, u, g_a, fpost);
+}
+
+/* Number of threads of the passes above (1 = plain serial loops); returns the
+ * count in use, or 1 when the library was built without OpenMP. */
+int oracle_set_threads(int n)
+{
+#ifdef _OPENMP
+    if (n > 0) omp_set_num_threads(n);
+    return omp_get_max_threads();
+#else
+    (void)n;
+    return 1;
+#endif
 }
