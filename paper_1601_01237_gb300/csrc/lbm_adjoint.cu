@@ -483,19 +483,9 @@ cudaError_t adj_step_t(const HostPhys &h, const void *f, const void *rho, int rh
 
 }  // namespace
 
-// One resident wave of k_adj_local: kAdjBlocksPerSM CTAs on every SM.
-int adjoint_blocks()
-{
-    static int blocks = 0;
-    if (!blocks) {
-        int dev = 0, sms = 0;
-        if (cudaGetDevice(&dev) != cudaSuccess ||
-            cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || sms <= 0)
-            sms = 152;
-        blocks = kAdjBlocksPerSM * sms;
-    }
-    return blocks;
-}
+// One resident wave of k_adj_local on the current device: kAdjBlocksPerSM
+// CTAs on every SM.
+int adjoint_blocks() { return kAdjBlocksPerSM * current_device_sms(); }
 
 cudaError_t launch_adjoint_step(const HostPhys &p, const void *f, const void *rho, int rho_is_sums, const void *lam_next,
                                 const void *Dn, void *lam_loc, void *a, void *Dout, double *partials, cudaStream_t s)

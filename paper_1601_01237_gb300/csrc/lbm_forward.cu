@@ -17,6 +17,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <atomic>
+
 #include "d3q19.cuh"
 #include "lbm_internal.h"
 
@@ -616,6 +618,26 @@ size_t storage_bytes(int storage)
 }
 
 size_t real_bytes(int storage) { return storage == ST_F64 ? 8 : 4; }
+
+namespace {
+constexpr int kMaxSmDevices = 64;
+std::atomic<int> g_device_sms[kMaxSmDevices];   // 0 = not looked up yet
+}  // namespace
+
+int current_device_sms()
+{
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return 152;
+    if (dev < 0 || dev >= kMaxSmDevices) {   // beyond the table: look it up every time
+        int n = 0;
+        return cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) == cudaSuccess && n > 0 ? n : 152;
+    }
+    int n = g_device_sms[dev].load(std::memory_order_acquire);
+    if (n > 0) return n;
+    if (cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || n <= 0) n = 152;
+    g_device_sms[dev].store(n, std::memory_order_release);
+    return n;
+}
 
 // ---------------------------------------------------------------------------
 // Allocation-free variant of the two-kernel step.  Its density scratch is a

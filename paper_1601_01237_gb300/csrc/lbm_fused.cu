@@ -34,6 +34,8 @@
 // at about the same time (L2 hits).
 #include <cuda_runtime.h>
 
+#include <atomic>
+
 #include "d3q19.cuh"
 #include "lbm_internal.h"
 
@@ -565,6 +567,7 @@ Phys<R> make_phys_f(const HostPhys &h)
 }
 
 constexpr size_t kSmemBytes = sizeof(FusedSmem<float>);
+constexpr int kMaxAttrDevices = 64;
 
 template <int S>
 cudaError_t fused_t(const HostPhys &h, const void *fin, void *fout, cudaStream_t s, cudaEvent_t *ev, void *s_out)
@@ -576,18 +579,19 @@ cudaError_t fused_t(const HostPhys &h, const void *fin, void *fout, cudaStream_t
     const int nty = (h.ny + kTY - 1) / kTY;
     // planes per CTA: 64, or 8 when 64 would leave fewer than two CTAs per SM
     // (small lattices get shorter chunks and more CTAs)
-    static int sms = 0;
-    if (!sms) {
-        int dev = 0;
-        if (cudaGetDevice(&dev) != cudaSuccess ||
-            cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || sms <= 0)
-            sms = 152;
-    }
+    const int sms = current_device_sms();
     const bool small = (long long)ntx * nty * ((h.nz + kLZmax - 1) / kLZmax) < 2LL * sms;
     const int lz = small ? kLZsmall : kLZmax;
     const dim3 grid((unsigned)(ntx * nty), (unsigned)((h.nz + lz - 1) / lz));
-    static bool attr_set = false;
-    if (!attr_set) {
+    // The shared-memory size attribute belongs to the device context: set it
+    // once per device (several host threads may race to set the same value,
+    // which is harmless).
+    static std::atomic<int> attr_set[kMaxAttrDevices];
+    int dev = 0;
+    cudaError_t ed = cudaGetDevice(&dev);
+    if (ed != cudaSuccess) return ed;
+    const bool cached = dev >= 0 && dev < kMaxAttrDevices;
+    if (!cached || !attr_set[dev].load(std::memory_order_acquire)) {
         cudaError_t e = cudaSuccess;
         const void *fns[12] = {
             (const void *)k_step_fused<S, 1, false, kLZmax>, (const void *)k_step_fused<S, 0, false, kLZmax>,
@@ -599,7 +603,7 @@ cudaError_t fused_t(const HostPhys &h, const void *fin, void *fout, cudaStream_t
         for (int q = 0; q < 12 && e == cudaSuccess; ++q)
             e = cudaFuncSetAttribute(fns[q], cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemBytes);
         if (e != cudaSuccess) return e;
-        attr_set = true;
+        if (cached) attr_set[dev].store(1, std::memory_order_release);
     }
     if (ev) cudaEventRecord(ev[0], s);
     const T *fi = (const T *)fin;

@@ -106,6 +106,11 @@ cudaError_t launch_droplet(const HostPhys &h, const void *rho, double threshold,
 // Link flags of a solid mask (N words, see HostPhys::links).
 cudaError_t launch_link_flags(const HostPhys &p, const unsigned char *solid, unsigned *links, cudaStream_t s);
 
+// Number of SMs of the current device, looked up once per device (every
+// device of the process has its own entry; safe to call from several host
+// threads).
+int current_device_sms();
+
 size_t storage_bytes(int storage);   // bytes per stored population value
 size_t real_bytes(int storage);      // bytes per arithmetic value
 
