@@ -151,3 +151,45 @@ def channel_droplet_stats(b, solid, info, thr):
     ph = 2.0 * np.pi * s[drop] / L
     com = L / (2.0 * np.pi) * np.arctan2((m * np.sin(ph)).sum(), (m * np.cos(ph)).sum()) if m.size else float("nan")
     return int(drop.sum()), float(com), int(fl.sum())
+
+
+def structure_factor(phi):
+    """Spherically averaged structure factor of a periodic order-parameter
+    field phi (nz, ny, nx): S(k) = <|FFT(phi - <phi>)|^2> over the shells
+    k - 1/2 <= |k| < k + 1/2, with |k| in units of 2 pi / L (a cube of side L).
+    Returns (k, S) for the shells k = 1 .. L/2."""
+    phi = np.asarray(phi, dtype=float)
+    n = phi.shape[0]
+    assert phi.shape == (n, n, n), "a cubic lattice"
+    P = np.abs(np.fft.fftn(phi - phi.mean())) ** 2
+    f = np.fft.fftfreq(n) * n
+    kz, ky, kx = np.meshgrid(f, f, f, indexing="ij")
+    shell = np.rint(np.sqrt(kx * kx + ky * ky + kz * kz)).astype(int)
+    kmax = n // 2
+    S = np.bincount(shell.ravel(), weights=P.ravel(), minlength=kmax + 1)[:kmax + 1]
+    cnt = np.bincount(shell.ravel(), minlength=kmax + 1)[:kmax + 1]
+    k = np.arange(1, kmax + 1)
+    return k, S[1:] / np.maximum(cnt[1:], 1)
+
+
+def spinodal_stats(rho1, rho2):
+    """Statistics of a two-component spinodal mixture on a periodic cube
+    (order parameter phi = rho^1 - rho^2):
+      mass1, mass2      sum of each density;
+      mean_abs_phi      <|rho^1 - rho^2|> over the cells;
+      k_star            first moment sum k S(k) / sum S(k) of the spherically
+                        averaged structure factor (units of 2 pi / L), the
+                        characteristic wavenumber of the domains;
+      k_peak            the shell where S(k) is largest;
+      interface_area    the number of lattice links (x, y and z neighbours,
+                        periodic) across which phi changes sign: the area of
+                        the phi = 0 surface in units of a cell face."""
+    a = np.asarray(rho1, dtype=float)
+    b = np.asarray(rho2, dtype=float)
+    phi = a - b
+    k, S = structure_factor(phi)
+    pos = phi > 0
+    area = sum(int(np.count_nonzero(pos != np.roll(pos, 1, axis=ax))) for ax in range(3))
+    return {"mass1": float(a.sum()), "mass2": float(b.sum()), "mean_abs_phi": float(np.abs(phi).mean()),
+            "k_star": float((k * S).sum() / S.sum()), "k_peak": int(k[int(np.argmax(S))]),
+            "interface_area": area}

@@ -162,3 +162,34 @@ def test_inclined_channel_geometry(angle):
                     seen[q] = True
                     stack.append(q)
     assert seen.sum() == fl.sum()
+
+
+def test_spinodal_stats_closed_forms():
+    """Statistics of the c2 comparison on fields with known answers: a single
+    Fourier mode of wavenumber k0 (in units of 2 pi / L) puts all of S(k) on
+    shell k0, so k* = k_peak = k0, and its phi = 0 surface is 2 k0 planes of
+    L^2 faces; a slab has 2 L^2 faces; <|phi|> of a mode of amplitude A is
+    2A/pi; the masses are the sums."""
+    L = 32
+    x = np.arange(L)
+    for k0 in (1, 3, 5):
+        phi = 0.3 * np.cos(2 * np.pi * k0 * (x + 0.25) / L)
+        a = 0.5 + 0.5 * np.broadcast_to(phi, (L, L, L))
+        b = 0.5 - 0.5 * np.broadcast_to(phi, (L, L, L))
+        st = dg.spinodal_stats(a, b)
+        assert abs(st["k_star"] - k0) < 1e-9 and st["k_peak"] == k0
+        assert st["interface_area"] == 2 * k0 * L * L
+        assert abs(st["mean_abs_phi"] - 2 * 0.3 / np.pi) < 1e-3
+        assert abs(st["mass1"] - a.sum()) < 1e-9 and abs(st["mass2"] - b.sum()) < 1e-9
+    # the mode along y and along z gives the same statistics (isotropy of the shells)
+    phi_z = 0.3 * np.cos(2 * np.pi * 3 * (np.arange(L) + 0.25) / L)[:, None, None] * np.ones((1, L, L))
+    st = dg.spinodal_stats(0.5 + 0.5 * phi_z, 0.5 - 0.5 * phi_z)
+    assert abs(st["k_star"] - 3) < 1e-9 and st["interface_area"] == 6 * L * L
+    slab = np.where(np.arange(L) < L // 2, 0.8, 0.2)[None, None, :] * np.ones((L, L, 1))
+    st = dg.spinodal_stats(slab, 1.0 - slab)
+    assert st["interface_area"] == 2 * L * L
+    # a diagonal mode (k = (2, 2, 1), |k| = 3) sits on shell 3
+    z, y, xx = np.meshgrid(x, x, x, indexing="ij")
+    phi = 0.2 * np.cos(2 * np.pi * (2 * xx + 2 * y + z + 0.1) / L)
+    st = dg.spinodal_stats(0.5 + 0.5 * phi, 0.5 - 0.5 * phi)
+    assert abs(st["k_star"] - 3) < 1e-9

@@ -73,13 +73,15 @@ def test_fields_many_steps_f64(gpu_lib, name, shape, kw):
 
 
 def test_droplet_c0_f64(gpu_lib):
-    """The quasi-2D droplet case (64x64x1, R = 16, tau = 1, FP64), 300 steps."""
+    """The c0 case in full: quasi-2D droplet (64x64x1, R = 16, tau = 1, FP64),
+    2000 steps; fields, masses and max |u_F| against the oracle."""
     import oracle
-    shape = (1, 64, 64)
-    r1, r2 = wl.droplet(shape, 16)
-    p, f_or = oracle_run(shape, r1, r2, None, 300, G12=G_DROP)
+    c = wl.CONFIGS["c0_droplet2d_f64"]
+    shape = c["shape"]
+    r1, r2 = wl.droplet(shape, c["R"])
+    p, f_or = oracle_run(shape, r1, r2, None, c["steps"], tau=c["tau"], G12=c["G"])
     a, b, uF = oracle.moments(p, f_or)
-    lat = gpu_run(shape, r1, r2, None, 300, storage="f64", G12=G_DROP)
+    lat = gpu_run(shape, r1, r2, None, c["steps"], storage="f64", tau=c["tau"], G12=c["G"])
     ga, gb, guF = lat.moments()
     red = lat.reduce()
     lat.close()
@@ -90,13 +92,43 @@ def test_droplet_c0_f64(gpu_lib):
     assert abs(red["max_uF"] - np.sqrt((uF ** 2).sum(-1)).max()) < 1e-10
 
 
+def _interface_split(gpu, ref, centre, periodic, W=2.0, hemisphere=False, thr=None):
+    """Per-cell relative error |gpu - ref| / ref split by the distance from
+    the interface of a (hemi)spherical droplet in the reference field: the
+    interface is the sphere of the reference's equivalent radius (cells above
+    the mid density); cells farther than 3 W from it are "far".  Also the
+    near-interface error expressed as an interface displacement,
+    max |gpu - ref| / |grad ref| over the near cells (in cells)."""
+    nz, ny, nx = ref.shape
+    mid = 0.5 * (ref.max() + ref.min()) if thr is None else thr
+    vol = float((ref > mid).sum()) if ref[tuple(int(round(c)) for c in centre)] > mid else float((ref < mid).sum())
+    Req = (3.0 * vol / (2.0 if hemisphere else 4.0) / np.pi) ** (1.0 / 3.0)
+    z, y, x = np.meshgrid(np.arange(nz), np.arange(ny), np.arange(nx), indexing="ij")
+    d = []
+    for v, c, n, per in zip((z, y, x), centre, (nz, ny, nx), periodic[::-1]):
+        dv = v - c
+        if per:
+            dv = dv - n * np.round(dv / n)
+        d.append(dv)
+    r = np.sqrt(d[0] ** 2 + d[1] ** 2 + d[2] ** 2)
+    far = np.abs(r - Req) > 3.0 * W
+    err = np.abs(gpu - ref) / ref
+    grad = np.sqrt(sum(g ** 2 for g in np.gradient(ref)))
+    near = ~far
+    disp = float(np.max(np.abs(gpu - ref)[near] / np.maximum(grad[near], 1e-12)))
+    return float(err[far].max()), int(far.sum()), float(err[near].max()), disp, Req
+
+
 def test_f32_droplet_1000_steps(gpu_lib):
-    """FP32 storage and arithmetic, 3D droplet on 24^3 (tau = 1, coexisting
-    densities about 1.1 / 0.006), 1000 steps.  FP32 storage rounds each
-    population by up to w_i rho_max 2^-24, which is ~5e-6 of the minority
-    density per step, so the per-cell relative error of the minority phase
-    is bounded by rounding growth (~sqrt(steps) x 5e-6), not by 1e-5.
-    Checked: max |d rho| / max rho <= 1e-5, and per cell <= 2e-4."""
+    """FP32 storage and arithmetic, 3D droplet on 24^3 (tau = 1, relaxing to
+    coexisting densities about 1.06 / 0.005), 1000 steps, against the FP64
+    oracle.  The stated FP32 bar, max |d rho| / rho <= 1e-5 per cell, holds for
+    every cell farther than 3 W from the interface (both phases, both
+    components).  Next to the interface FP32 rounding shifts the interface by
+    a tiny displacement delta; there |d rho| = delta |grad rho|, which relative
+    to the minority density of a cell in the interface's tail is far larger
+    than delta.  Near the interface the test bounds the displacement
+    (|d rho| / |grad rho| <= 1e-4 cells) and the per-cell error (2e-4)."""
     import oracle
     shape = (24, 24, 24)
     r1, r2 = wl.droplet(shape, 7)
@@ -105,13 +137,18 @@ def test_f32_droplet_1000_steps(gpu_lib):
     lat = gpu_run(shape, r1, r2, None, 1000, storage="f32", G12=G_DROP)
     ga, gb, guF = lat.moments()
     lat.close()
+    c = (11.5, 11.5, 11.5)
+    res = [_interface_split(g, o, c, (1, 1, 1)) for g, o in ((ga, a), (gb, b))]
+    for k, (far, nfar, near, disp, Req) in enumerate(res):
+        print("FP32 droplet 1000 steps, component %d: R_eq %.2f; far from the interface (%d cells) "
+              "max|drho|/rho = %.3g; near it %.3g, displacement %.3g cells" % (k + 1, Req, nfar, far, near, disp))
     g1 = np.max(np.abs(ga - a)) / a.max()
     g2 = np.max(np.abs(gb - b)) / b.max()
-    e1 = np.max(np.abs(ga - a) / a)
-    e2 = np.max(np.abs(gb - b) / b)
-    print("FP32 droplet 1000 steps: max|drho|/max rho = %.3g, %.3g; per cell %.3g, %.3g" % (g1, g2, e1, e2))
     assert g1 <= 1e-5 and g2 <= 1e-5
-    assert e1 <= 2e-4 and e2 <= 2e-4
+    for far, nfar, near, disp, _ in res:
+        assert nfar > 1000
+        assert far <= 1e-5
+        assert near <= 2e-4 and disp <= 1e-4
 
 
 def test_f32_mixture_1000_steps_per_cell(gpu_lib):
@@ -133,7 +170,9 @@ def test_f32_mixture_1000_steps_per_cell(gpu_lib):
 
 
 def test_f32_regularized_wall(gpu_lib):
-    """FP32, regularized collision, mirror wetting walls, tilted gravity: 300 steps."""
+    """FP32, regularized collision, mirror wetting walls, tilted gravity: 300
+    steps.  As for the droplet: 1e-5 per cell farther than 3 W from the
+    interface, the displacement bound near it."""
     import oracle
     shape = (12, 16, 16)
     r1, r2 = wl.hemisphere(shape, 6)
@@ -145,9 +184,16 @@ def test_f32_regularized_wall(gpu_lib):
     ga, gb, guF = lat.moments()
     lat.close()
     g = max(np.max(np.abs(ga - a)) / a.max(), np.max(np.abs(gb - b)) / b.max())
-    e = max(np.max(np.abs(ga - a) / a), np.max(np.abs(gb - b) / b))
-    print("FP32 regularized wall 300 steps: max|drho|/max rho = %.3g, per cell %.3g" % (g, e))
-    assert g < 1e-5 and e < 1e-4
+    c = (-0.5, 7.5, 7.5)
+    res = [_interface_split(gg, o, c, (1, 1, 0), hemisphere=True) for gg, o in ((ga, a), (gb, b))]
+    for k, (far, nfar, near, disp, Req) in enumerate(res):
+        print("FP32 regularized wall 300 steps, component %d: R_eq %.2f; far (%d cells) %.3g; near %.3g, "
+              "displacement %.3g cells" % (k + 1, Req, nfar, far, near, disp))
+    assert g < 1e-5
+    for far, nfar, near, disp, _ in res:
+        assert nfar > 300
+        assert far <= 1e-5
+        assert near <= 1e-4 and disp <= 1e-4
     assert np.max(np.abs(guF - uF)) < 2e-7
 
 
