@@ -36,7 +36,13 @@ from paper_1601_01237_gb300 import workloads as wl  # noqa: E402
 METRIC = "MLUPS (2-comp D3Q19)"
 UNIT = "MLUPS"
 FALLBACK_HBM_GBS = 6800.0
-BYTES_PER_VALUE = {"f64": 8, "f32": 4, "f16_dev": 2, "bf16_dev": 2}
+BYTES_PER_VALUE = {"f64": 8, "f32": 4, "f16_dev": 2, "bf16_dev": 2, "f16_rel": 2, "bf16_rel": 2}
+
+
+def state_bytes_per_cell(storage):
+    """Bytes of one state per cell: 2 components x 19 populations, plus the
+    two FP32 reference densities of the relative 16-bit formats."""
+    return 2 * 19 * BYTES_PER_VALUE[storage] + (8 if storage.endswith("_rel") else 0)
 ORACLE_SAMPLE_SHAPE = (64, 64, 64)
 
 
@@ -186,16 +192,17 @@ def ncu_traffic(kernel, storage, cells):
 
 def algorithmic_bytes_per_cell(kernel, storage):
     """Minimum HBM bytes per cell of one launch: every population read once
-    and written once (2 components x 19 values x s bytes x 2); the density
-    pass of the two-kernel step reads the populations and writes 2 densities;
-    the collision pass also reads the 2 densities."""
-    s = BYTES_PER_VALUE[storage]
+    and written once (2 components x 19 values x s bytes x 2, and for the
+    relative 16-bit formats the cell's two FP32 reference densities read and
+    written); the density pass of the two-kernel step reads the state and
+    writes 2 densities; the collision pass also reads the 2 densities."""
+    b = state_bytes_per_cell(storage)
     r = 8 if storage == "f64" else 4
     if kernel == "k_density":
-        return 2 * 19 * s + 2 * r
+        return b + 2 * r
     if kernel == "k_collide":
-        return 2 * 19 * s * 2 + 2 * r
-    return 2 * 19 * s * 2
+        return b * 2 + 2 * r
+    return b * 2
 
 
 def max_over_ranks(x, device="cpu"):
@@ -406,7 +413,7 @@ def run_ours(args, rank, world, local_rank):
                 "peak_source": peak_src,
                 "kernels": {k: {"ms_per_launch": v[0] / v[1], "launches": v[1],
                                 "share": v[0] / sum(x[0] for x in kern.values())} for k, v in kern.items()}}
-    step_bytes = 2 * 19 * BYTES_PER_VALUE[storage] * 2 * cells
+    step_bytes = state_bytes_per_cell(storage) * 2 * cells
     roofline["step_frac_of_peak"] = step_bytes / (ms_max / args.steps / 1e3) / 1e9 / peak
 
     # ---- end to end through the public API with host buffers -------------
@@ -439,7 +446,7 @@ def run_ours(args, rank, world, local_rank):
         "data": "synthetic",
         "config": dict(workload_desc(args.workload, cfg, storage),
                        l2="inputs larger than L2: %.1f GB of populations per copy" % (
-                           2 * 19 * BYTES_PER_VALUE[storage] * cells / 1e9),
+                           state_bytes_per_cell(storage) * cells / 1e9),
                        parallelism="replicas" if world > 1 else "single GPU"),
         "roofline": roofline,
         "gpu_launches": sum(v[1] for v in kern.values()),

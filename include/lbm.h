@@ -49,12 +49,21 @@ typedef enum {
 } lbm_status;
 
 /* Population storage.  Arithmetic is FP64 for LBM_F64 and FP32 otherwise.
- * The *_DEV formats store the deviation f_i - w_i * rho0_dev in 16 bits. */
+ * The *_DEV formats store the deviation f_i - w_i * rho0_dev in 16 bits.
+ * The *_REL formats store the relative deviation f_i / (w_i rho~) - 1 in 16
+ * bits, where rho~ is the density (of the population's own component), at
+ * the step that produced the population, of the cell that reads it next;
+ * every cell keeps its own pair (rho~1, rho~2) in FP32 beside the
+ * populations (8 more bytes per cell), so that both phases of a
+ * phase-separated state keep the full 16-bit precision (rho0_dev must be 0).
+ * None of the 16-bit codecs comes from the paper. */
 typedef enum {
     LBM_F64 = 0,
     LBM_F32 = 1,
     LBM_F16_DEV = 2,
-    LBM_BF16_DEV = 3
+    LBM_BF16_DEV = 3,
+    LBM_F16_REL = 4,
+    LBM_BF16_REL = 5
 } lbm_storage;
 
 typedef enum {
@@ -193,7 +202,9 @@ lbm_status lbm_set_populations(lbm_lattice *h, const double *in, int on_device);
  * caller device buffer of at least that many bytes.  Layout: population i
  * of component a at cell c (x fastest) is element 2 (i N + c) + a in the
  * storage type (the two components of a direction side by side); the values
- * are the post-collision populations at their origin cell. */
+ * are the post-collision populations at their origin cell.  The *_REL
+ * formats follow them, at the population bytes rounded up to a multiple of
+ * 256, with the N reference pairs (rho~1, rho~2) as FP32 (cell c at pair c). */
 lbm_status lbm_state_bytes(const lbm_lattice *h, size_t *bytes);
 lbm_status lbm_get_state(lbm_lattice *h, void *dev_buf, size_t bytes);
 lbm_status lbm_set_state(lbm_lattice *h, const void *dev_buf, size_t bytes);

@@ -16,7 +16,7 @@ LBM_OK, LBM_EINVAL, LBM_ENOMEM, LBM_ECUDA, LBM_ENOTSUP, LBM_ENUMERIC = range(6)
 STATUS_NAMES = {0: "LBM_OK", 1: "LBM_EINVAL", 2: "LBM_ENOMEM", 3: "LBM_ECUDA",
                 4: "LBM_ENOTSUP", 5: "LBM_ENUMERIC"}
 # lbm_storage, lbm_collision, lbm_wall_model
-STORAGE = {"f64": 0, "f32": 1, "f16_dev": 2, "bf16_dev": 3}
+STORAGE = {"f64": 0, "f32": 1, "f16_dev": 2, "bf16_dev": 3, "f16_rel": 4, "bf16_rel": 5}
 COLLISION = {"bgk": 0, "regularized": 1, "regularized3": 2}
 WALL_MODEL = {"potential": 0, "mirror": 1}
 

@@ -147,14 +147,28 @@ __device__ __forceinline__ unsigned ld_pair_b16(const void *p)
 }
 
 // ---------------------------------------------------------------------------
-// Storage formats.  R = arithmetic type, T = stored type.  The *_DEV formats
-// keep d_i = f_i - w_i rho0 in 16 bits.
+// Storage formats.  R = arithmetic type, T = stored type.
 //
 // Population layout: direction-major, x fastest, with the two components of a
 // cell side by side: f^a_i(cell) is element 2 (i N + cell) + a.  A pull gather
 // fetches both components of a direction with one vector load (8 bytes in
 // FP32) and a collision stores them with one vector store.
-enum StorageKind { ST_F64 = 0, ST_F32 = 1, ST_F16_DEV = 2, ST_BF16_DEV = 3 };
+//
+// Every format codes a population with one parameter per component, derived
+// from a reference density rho_ref:
+//   load:  f = dec(s, d) with d = w_i rho_ref (Store::load, load2),
+//   store: s = enc(f, e) with e = Store::enc(w_i rho_ref) (Store::store, store2).
+// FP64 / FP32 store f itself and ignore the parameters.  The *_DEV formats
+// keep d_i = f_i - w_i rho0 in 16 bits (rho_ref = rho0 of the lattice).  The
+// *_REL formats keep the relative deviation s_i = f_i / (w_i rho~) - 1 in 16
+// bits, where rho~ is the density, at the step that produced it, of the cell
+// that reads the population next (its destination): the writer knows it from
+// the interaction stencil, and every cell stores its own rho~ (FP32, both
+// components) beside the populations, so the reader decodes the 19
+// populations it gathers with its own one reference.  A population at rest in
+// a stationary bulk codes to 0 exactly, and both phases of a droplet keep the
+// full 16-bit precision of s.
+enum StorageKind { ST_F64 = 0, ST_F32 = 1, ST_F16_DEV = 2, ST_BF16_DEV = 3, ST_F16_REL = 4, ST_BF16_REL = 5 };
 
 __host__ __device__ __forceinline__ long long pair_index(int i, long long cell, long long N)
 {
@@ -166,62 +180,102 @@ template <int S> struct Store;
 template <> struct Store<ST_F64> {
     using T = double;
     using R = double;
+    static constexpr bool kRel = false;
+    __device__ static __forceinline__ R enc(R wr) { return wr; }
     __device__ static __forceinline__ R load(const T *p, R) { return __ldg(p); }
     __device__ static __forceinline__ void store(T *p, R v, R) { *p = v; }
-    __device__ static __forceinline__ void load2(const T *p, R, R &a, R &b)
+    __device__ static __forceinline__ void load2(const T *p, R, R, R &a, R &b)
     {
         const double2 v = __ldg(reinterpret_cast<const double2 *>(p));
         a = v.x; b = v.y;
     }
-    __device__ static __forceinline__ void store2(T *p, R a, R b, R) { *reinterpret_cast<double2 *>(p) = make_double2(a, b); }
+    __device__ static __forceinline__ void store2(T *p, R a, R b, R, R) { *reinterpret_cast<double2 *>(p) = make_double2(a, b); }
 };
 template <> struct Store<ST_F32> {
     using T = float;
     using R = float;
+    static constexpr bool kRel = false;
+    __device__ static __forceinline__ R enc(R wr) { return wr; }
     __device__ static __forceinline__ R load(const T *p, R) { return __ldg(p); }
     __device__ static __forceinline__ void store(T *p, R v, R) { *p = v; }
-    __device__ static __forceinline__ void load2(const T *p, R, R &a, R &b)
+    __device__ static __forceinline__ void load2(const T *p, R, R, R &a, R &b)
     {
         const float2 v = ld_pair_f32(p);
         a = v.x; b = v.y;
     }
-    __device__ static __forceinline__ void store2(T *p, R a, R b, R) { *reinterpret_cast<float2 *>(p) = make_float2(a, b); }
+    __device__ static __forceinline__ void store2(T *p, R a, R b, R, R) { *reinterpret_cast<float2 *>(p) = make_float2(a, b); }
 };
-template <> struct Store<ST_F16_DEV> {
+
+// 16-bit conversions of the two formats.
+struct H16 {
     using T = __half;
-    using R = float;
-    __device__ static __forceinline__ R load(const T *p, R ref) { return __half2float(__ldg(p)) + ref; }
-    __device__ static __forceinline__ void store(T *p, R v, R ref) { *p = __float2half_rn(v - ref); }
-    __device__ static __forceinline__ void load2(const T *p, R ref, R &a, R &b)
+    using T2 = __half2;
+    __device__ static __forceinline__ float to_f(T v) { return __half2float(v); }
+    __device__ static __forceinline__ T from_f(float v) { return __float2half_rn(v); }
+    __device__ static __forceinline__ void unpack(unsigned u, float &a, float &b)
     {
-        const unsigned u = ld_pair_b16(p);
         __half2 v;
         memcpy(&v, &u, sizeof v);
-        a = __low2float(v) + ref; b = __high2float(v) + ref;
+        a = __low2float(v); b = __high2float(v);
     }
-    __device__ static __forceinline__ void store2(T *p, R a, R b, R ref)
-    {
-        *reinterpret_cast<__half2 *>(p) = __halves2half2(__float2half_rn(a - ref), __float2half_rn(b - ref));
-    }
+    __device__ static __forceinline__ T2 pack(float a, float b) { return __halves2half2(from_f(a), from_f(b)); }
 };
-template <> struct Store<ST_BF16_DEV> {
+struct B16 {
     using T = __nv_bfloat16;
-    using R = float;
-    __device__ static __forceinline__ R load(const T *p, R ref) { return __bfloat162float(__ldg(p)) + ref; }
-    __device__ static __forceinline__ void store(T *p, R v, R ref) { *p = __float2bfloat16_rn(v - ref); }
-    __device__ static __forceinline__ void load2(const T *p, R ref, R &a, R &b)
+    using T2 = __nv_bfloat162;
+    __device__ static __forceinline__ float to_f(T v) { return __bfloat162float(v); }
+    __device__ static __forceinline__ T from_f(float v) { return __float2bfloat16_rn(v); }
+    __device__ static __forceinline__ void unpack(unsigned u, float &a, float &b)
     {
-        const unsigned u = ld_pair_b16(p);
         __nv_bfloat162 v;
         memcpy(&v, &u, sizeof v);
-        a = __low2float(v) + ref; b = __high2float(v) + ref;
+        a = __low2float(v); b = __high2float(v);
     }
-    __device__ static __forceinline__ void store2(T *p, R a, R b, R ref)
+    __device__ static __forceinline__ T2 pack(float a, float b) { return __halves2bfloat162(from_f(a), from_f(b)); }
+};
+
+// Deviation d = f - w rho0 (parameters: w rho0 for both directions).
+template <class C> struct StoreDev {
+    using T = typename C::T;
+    using R = float;
+    static constexpr bool kRel = false;
+    __device__ static __forceinline__ R enc(R wr) { return wr; }
+    __device__ static __forceinline__ R load(const T *p, R d) { return C::to_f(__ldg(p)) + d; }
+    __device__ static __forceinline__ void store(T *p, R v, R e) { *p = C::from_f(v - e); }
+    __device__ static __forceinline__ void load2(const T *p, R da, R db, R &a, R &b)
     {
-        *reinterpret_cast<__nv_bfloat162 *>(p) =
-            __halves2bfloat162(__float2bfloat16_rn(a - ref), __float2bfloat16_rn(b - ref));
+        C::unpack(ld_pair_b16(p), a, b);
+        a += da; b += db;
+    }
+    __device__ static __forceinline__ void store2(T *p, R a, R b, R ea, R eb)
+    {
+        *reinterpret_cast<typename C::T2 *>(p) = C::pack(a - ea, b - eb);
     }
 };
+// Relative deviation s = f / (w rho~) - 1 (load parameter d = w rho~, store
+// parameter e = 1 / (w rho~)).
+template <class C> struct StoreRel {
+    using T = typename C::T;
+    using R = float;
+    static constexpr bool kRel = true;
+    __device__ static __forceinline__ R enc(R wr) { return __frcp_rn(wr); }
+    __device__ static __forceinline__ R load(const T *p, R d) { return fmaf(d, C::to_f(__ldg(p)), d); }
+    __device__ static __forceinline__ void store(T *p, R v, R e) { *p = C::from_f(fmaf(v, e, -1.0f)); }
+    __device__ static __forceinline__ void load2(const T *p, R da, R db, R &a, R &b)
+    {
+        float sa, sb;
+        C::unpack(ld_pair_b16(p), sa, sb);
+        a = fmaf(da, sa, da); b = fmaf(db, sb, db);
+    }
+    __device__ static __forceinline__ void store2(T *p, R a, R b, R ea, R eb)
+    {
+        *reinterpret_cast<typename C::T2 *>(p) = C::pack(fmaf(a, ea, -1.0f), fmaf(b, eb, -1.0f));
+    }
+};
+template <> struct Store<ST_F16_DEV> : StoreDev<H16> {};
+template <> struct Store<ST_BF16_DEV> : StoreDev<B16> {};
+template <> struct Store<ST_F16_REL> : StoreRel<H16> {};
+template <> struct Store<ST_BF16_REL> : StoreRel<B16> {};
 
 // ---------------------------------------------------------------------------
 // Kernel-side parameters (by value).
@@ -237,7 +291,22 @@ struct Phys {
     R rho_s[2];
     R rho0;                 // reference density of deviation storage (0 otherwise)
     const unsigned char *solid = nullptr;   // N flags, 1 = solid site (two-kernel step only)
+    long long ref_off = 0;  // *_REL formats: byte offset of the per-cell reference
+                            // densities (float2 per cell) from the state's base
 };
+
+// Reference densities of a *_REL state (N pairs (rho~1, rho~2) behind the
+// populations, at byte offset ref_off).
+template <class T>
+__device__ __forceinline__ const float2 *state_ref(const T *state, long long ref_off)
+{
+    return reinterpret_cast<const float2 *>(reinterpret_cast<const char *>(state) + ref_off);
+}
+template <class T>
+__device__ __forceinline__ float2 *state_ref(T *state, long long ref_off)
+{
+    return reinterpret_cast<float2 *>(reinterpret_cast<char *>(state) + ref_off);
+}
 
 // Third-order equilibrium of Eq. 3 with T0 = 1/3, for direction i and its
 // opposite at once: f^eq_i = rho w_i (E + O), f^eq_opp(i) = rho w_i (E - O) with

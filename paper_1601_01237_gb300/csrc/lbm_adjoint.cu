@@ -93,11 +93,16 @@ __device__ __forceinline__ void adj_half(const typename Store<S>::T *__restrict_
     const unsigned full = 0xffffffffu;
     // ---- forward recomputation ------------------------------------------
     R fa[Q];
+    R rref = p.rho0;   // *_REL formats: the cell's own reference density of component a
+    if constexpr (Store<S>::kRel) {
+        const float2 rr = state_ref(f, p.ref_off)[n.cell];
+        rref = a == 0 ? rr.x : rr.y;
+    }
 #pragma unroll
     for (int i = 0; i < Q; ++i) {
         const bool wall = (cz(i) == 1 && n.zlo) || (cz(i) == -1 && n.zhi);
         const long long idx = (wall ? pair_index(opp(i), n.cell, N) : pair_index(i, at(n, -cx(i), -cy(i), -cz(i)), N)) + a;
-        fa[i] = Store<S>::load(f + idx, w<R>(i) * p.rho0);
+        fa[i] = Store<S>::load(f + idx, w<R>(i) * rref);
     }
     R ra = 0, jx = 0, jy = 0, jz = 0;
 #pragma unroll
@@ -457,6 +462,7 @@ Phys<R> make_phys_a(const HostPhys &h)
     for (int d = 0; d < 3; ++d) p.gext[d] = (R)h.gext[d];
     p.rho_s[0] = (R)h.rho_s[0]; p.rho_s[1] = (R)h.rho_s[1];
     p.rho0 = (R)h.rho0;
+    p.ref_off = h.ref_off;
     return p;
 }
 
@@ -495,6 +501,8 @@ cudaError_t launch_adjoint_step(const HostPhys &p, const void *f, const void *rh
     case ST_F32: return adj_step_t<ST_F32>(p, f, rho, rho_is_sums, lam_next, Dn, lam_loc, a, Dout, partials, s);
     case ST_F16_DEV: return adj_step_t<ST_F16_DEV>(p, f, rho, rho_is_sums, lam_next, Dn, lam_loc, a, Dout, partials, s);
     case ST_BF16_DEV: return adj_step_t<ST_BF16_DEV>(p, f, rho, rho_is_sums, lam_next, Dn, lam_loc, a, Dout, partials, s);
+    case ST_F16_REL: return adj_step_t<ST_F16_REL>(p, f, rho, rho_is_sums, lam_next, Dn, lam_loc, a, Dout, partials, s);
+    case ST_BF16_REL: return adj_step_t<ST_BF16_REL>(p, f, rho, rho_is_sums, lam_next, Dn, lam_loc, a, Dout, partials, s);
     default: return cudaErrorInvalidValue;
     }
 }

@@ -150,11 +150,9 @@ lbm_status lbm_create(const lbm_params *pp, lbm_lattice **out)
         if (!isfinite(p.g_ext[d])) return fail(LBM_EINVAL, "lbm_create: g_ext must be finite");
     if (!isfinite(p.rho_s[0]) || !isfinite(p.rho_s[1]) || !isfinite(p.rho0_dev))
         return fail(LBM_EINVAL, "lbm_create: rho_s and rho0_dev must be finite");
-    if (p.storage < LBM_F64 || p.storage > LBM_BF16_DEV)
+    if (p.storage < LBM_F64 || p.storage > LBM_BF16_REL)
         return fail(LBM_EINVAL, "lbm_create: unknown storage %d", p.storage);
-    if (p.storage == LBM_F64 && p.rho0_dev != 0.0)
-        return fail(LBM_EINVAL, "lbm_create: rho0_dev applies to the 16-bit deviation formats only");
-    if (p.storage == LBM_F32 && p.rho0_dev != 0.0)
+    if (p.storage != LBM_F16_DEV && p.storage != LBM_BF16_DEV && p.rho0_dev != 0.0)
         return fail(LBM_EINVAL, "lbm_create: rho0_dev applies to the 16-bit deviation formats only");
     if (p.collision != LBM_BGK && p.collision != LBM_REGULARIZED && p.collision != LBM_REGULARIZED3)
         return fail(LBM_EINVAL, "lbm_create: unknown collision %d", p.collision);
@@ -180,6 +178,7 @@ lbm_status lbm_create(const lbm_params *pp, lbm_lattice **out)
     for (int d = 0; d < 3; ++d) ph.gext[d] = p.g_ext[d];
     ph.rho_s[0] = p.rho_s[0]; ph.rho_s[1] = p.rho_s[1];
     ph.rho0 = p.rho0_dev;
+    ph.ref_off = (long long)lbm::ref_offset(p.storage, N);
     h->use_fused = env_flag("LBM_FUSED", 1) && lbm::fused_supported(ph);
     h->use_graphs = env_flag("LBM_GRAPHS", 1);
 
@@ -193,7 +192,7 @@ lbm_status lbm_create(const lbm_params *pp, lbm_lattice **out)
         if (e != cudaSuccess) { free(h); return cuda_fail(e, "lbm_create: stream"); }
         h->own_stream = true;
     }
-    const size_t pop_bytes = (size_t)2 * lbm::Q * (size_t)N * lbm::storage_bytes(p.storage);
+    const size_t pop_bytes = lbm::state_bytes(p.storage, N);   // populations (+ references)
     const size_t rho_bytes = (size_t)2 * (size_t)N * lbm::real_bytes(p.storage);
     const int nb = lbm::reduce_blocks();
     if ((e = cudaMalloc(&h->f[0], pop_bytes)) != cudaSuccess ||
@@ -593,7 +592,7 @@ lbm_status lbm_set_populations(lbm_lattice *h, const double *in, int on_device)
 lbm_status lbm_state_bytes(const lbm_lattice *h, size_t *bytes)
 {
     if (!h || !bytes) return fail(LBM_EINVAL, "lbm_state_bytes: NULL argument");
-    *bytes = (size_t)2 * lbm::Q * (size_t)h->phys.N * lbm::storage_bytes(h->phys.storage);
+    *bytes = lbm::state_bytes(h->phys.storage, h->phys.N);
     return LBM_OK;
 }
 
@@ -845,9 +844,9 @@ lbm_status lbm_step_noalloc(const lbm_params *pp, const void *f_in, void *f_out)
         if (!isfinite(p.g_ext[d])) return fail(LBM_EINVAL, "lbm_step_noalloc: g_ext must be finite");
     if (!isfinite(p.rho_s[0]) || !isfinite(p.rho_s[1]) || !isfinite(p.rho0_dev))
         return fail(LBM_EINVAL, "lbm_step_noalloc: rho_s and rho0_dev must be finite");
-    if (p.storage < LBM_F64 || p.storage > LBM_BF16_DEV)
+    if (p.storage < LBM_F64 || p.storage > LBM_BF16_REL)
         return fail(LBM_EINVAL, "lbm_step_noalloc: unknown storage %d", p.storage);
-    if ((p.storage == LBM_F64 || p.storage == LBM_F32) && p.rho0_dev != 0.0)
+    if (p.storage != LBM_F16_DEV && p.storage != LBM_BF16_DEV && p.rho0_dev != 0.0)
         return fail(LBM_EINVAL, "lbm_step_noalloc: rho0_dev applies to the 16-bit deviation formats only");
     if (p.collision != LBM_BGK && p.collision != LBM_REGULARIZED && p.collision != LBM_REGULARIZED3)
         return fail(LBM_EINVAL, "lbm_step_noalloc: unknown collision %d", p.collision);
@@ -869,6 +868,7 @@ lbm_status lbm_step_noalloc(const lbm_params *pp, const void *f_in, void *f_out)
     for (int d = 0; d < 3; ++d) ph.gext[d] = p.g_ext[d];
     ph.rho_s[0] = p.rho_s[0]; ph.rho_s[1] = p.rho_s[1];
     ph.rho0 = p.rho0_dev;
+    ph.ref_off = (long long)lbm::ref_offset(p.storage, N);
     CK(lbm::launch_step_split_noalloc(ph, f_in, f_out, (cudaStream_t)p.stream), "lbm_step_noalloc");
     return LBM_OK;
 }

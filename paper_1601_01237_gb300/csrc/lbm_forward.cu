@@ -79,13 +79,19 @@ __device__ __forceinline__ void gather(const typename Store<S>::T *__restrict__ 
 {
     using R = typename Store<S>::R;
     const unsigned lf = p.links ? __ldg(p.links + n.cell) : 0u;   // bit i: x - c_i is solid
+    // reference densities of the cell (the *_REL formats code every population
+    // a cell gathers relative to the cell's own stored pair; rho0 otherwise)
+    R ra = p.rho0, rb = p.rho0;
+    if constexpr (Store<S>::kRel) {
+        const float2 rr = state_ref(f, p.ref_off)[n.cell];
+        ra = rr.x; rb = rr.y;
+    }
 #pragma unroll
     for (int i = 0; i < Q; ++i) {
-        const R ref = w<R>(i) * p.rho0;
         const long long src = n.zo[1 - cz(i)] + n.yo[1 - cy(i)] + n.xo[1 - cx(i)];
         const bool wall = (cz(i) == 1 && n.zlo_wall) || (cz(i) == -1 && n.zhi_wall) || ((lf >> i) & 1u);
         const long long idx = wall ? pair_index(opp(i), n.cell, p.N) : pair_index(i, src, p.N);
-        Store<S>::load2(f + idx, ref, fa[0][i], fa[1][i]);
+        Store<S>::load2(f + idx, w<R>(i) * ra, w<R>(i) * rb, fa[0][i], fa[1][i]);
     }
 }
 
@@ -94,6 +100,8 @@ __device__ __forceinline__ void gather(const typename Store<S>::T *__restrict__ 
 // where a wall site contributes rho'_b = rho_b(mirror) + rho_s^b (modified
 // model) or rho_s^b (point-wise potential).  The mirror of a wall site
 // x + c_i across the z wall is x + c_i with its z component replaced by z.
+// The sum runs over opposite neighbours, sum_{i odd} w_i c_i (r_i - r_opp(i)),
+// so that the differences of nearby densities are taken first.
 template <class R>
 __device__ __forceinline__ void interaction_sums(const R *__restrict__ rho, const Phys<R> &p,
                                                  const Nbr &n, R (&S)[2][3])
@@ -102,17 +110,20 @@ __device__ __forceinline__ void interaction_sums(const R *__restrict__ rho, cons
     for (int b = 0; b < 2; ++b) {
         R sx = 0, sy = 0, sz = 0;
         const R *rb = rho + (long long)b * p.N;
+        R r[Q];
 #pragma unroll
         for (int i = 1; i < Q; ++i) {
             const bool wall = (cz(i) == -1 && n.zlo_wall) || (cz(i) == 1 && n.zhi_wall);
-            R r;
             if (wall) {
-                r = p.rho_s[b];
-                if (p.wall_mirror) r += __ldg(rb + n.zo[1] + n.yo[1 + cy(i)] + n.xo[1 + cx(i)]);
+                r[i] = p.rho_s[b];
+                if (p.wall_mirror) r[i] += __ldg(rb + n.zo[1] + n.yo[1 + cy(i)] + n.xo[1 + cx(i)]);
             } else {
-                r = __ldg(rb + n.zo[1 + cz(i)] + n.yo[1 + cy(i)] + n.xo[1 + cx(i)]);
+                r[i] = __ldg(rb + n.zo[1 + cz(i)] + n.yo[1 + cy(i)] + n.xo[1 + cx(i)]);
             }
-            const R wr = w<R>(i) * r;
+        }
+#pragma unroll
+        for (int i = 1; i < Q; i += 2) {
+            const R wr = w<R>(i) * (r[i] - r[i + 1]);
             if (cx(i) == 1) sx += wr; else if (cx(i) == -1) sx -= wr;
             if (cy(i) == 1) sy += wr; else if (cy(i) == -1) sy -= wr;
             if (cz(i) == 1) sz += wr; else if (cz(i) == -1) sz -= wr;
@@ -121,6 +132,9 @@ __device__ __forceinline__ void interaction_sums(const R *__restrict__ rho, cons
     }
 }
 
+// Densities of both components and the mixture velocity (Eqs. 4-6); the
+// momentum is summed over opposite pairs, sum_{i odd} c_i (t_i - t_opp(i)),
+// t_i = f^1_i + f^2_i (the differences of nearly equal populations first).
 template <class R>
 __device__ __forceinline__ void local_moments(const R (&fa)[2][Q], R &r1, R &r2, R &ux, R &uy, R &uz)
 {
@@ -129,14 +143,15 @@ __device__ __forceinline__ void local_moments(const R (&fa)[2][Q], R &r1, R &r2,
     for (int a = 0; a < 2; ++a) {
         R s = 0;
 #pragma unroll
-        for (int i = 0; i < Q; ++i) {
-            const R v = fa[a][i];
-            s += v;
-            if (cx(i) == 1) jx += v; else if (cx(i) == -1) jx -= v;
-            if (cy(i) == 1) jy += v; else if (cy(i) == -1) jy -= v;
-            if (cz(i) == 1) jz += v; else if (cz(i) == -1) jz -= v;
-        }
+        for (int i = 0; i < Q; ++i) s += fa[a][i];
         rr[a] = s;
+    }
+#pragma unroll
+    for (int i = 1; i < Q; i += 2) {
+        const R v = (fa[0][i] + fa[1][i]) - (fa[0][i + 1] + fa[1][i + 1]);
+        if (cx(i) == 1) jx += v; else if (cx(i) == -1) jx -= v;
+        if (cy(i) == 1) jy += v; else if (cy(i) == -1) jy -= v;
+        if (cz(i) == 1) jz += v; else if (cz(i) == -1) jz -= v;
     }
     r1 = rr[0];
     r2 = rr[1];
@@ -220,8 +235,10 @@ k_collide(const typename Store<S>::T *__restrict__ fin, typename Store<S>::T *__
     Nbr n;
     if (!decode_cell(p, (long long)blockIdx.x * kThreads + threadIdx.x, n)) return;
     if (p.solid && p.solid[n.cell]) {   // solid sites hold no populations
+        const R e = Store<S>::kRel ? R(1) : p.rho0;   // (never read: any finite code)
 #pragma unroll
-        for (int i = 0; i < Q; ++i) Store<S>::store2(fout + pair_index(i, n.cell, p.N), R(0), R(0), w<R>(i) * p.rho0);
+        for (int i = 0; i < Q; ++i) Store<S>::store2(fout + pair_index(i, n.cell, p.N), R(0), R(0), w<R>(i) * e, w<R>(i) * e);
+        if constexpr (Store<S>::kRel) state_ref(fout, p.ref_off)[n.cell] = make_float2(1.0f, 1.0f);
         return;
     }
     R fa[2][Q];
@@ -237,8 +254,27 @@ k_collide(const typename Store<S>::T *__restrict__ fin, typename Store<S>::T *__
             g2z = p.G21 * Sb[0][2] + p.gext[2];
     collide<R, REG>(fa[0], r1, ux, uy, uz, g1x, g1y, g1z, p.omega[0]);
     collide<R, REG>(fa[1], r2, ux, uy, uz, g2x, g2y, g2z, p.omega[1]);
+    if constexpr (Store<S>::kRel) {
+        // each population coded relative to the density of the cell that reads
+        // it next (x + c_i, or x itself across a wall); the cell's own pair is
+        // its reference for the next gather
+        const unsigned lf = p.links ? __ldg(p.links + n.cell) : 0u;
+        const R d1 = rho[n.cell], d2 = rho[p.N + n.cell];
 #pragma unroll
-    for (int i = 0; i < Q; ++i) Store<S>::store2(fout + pair_index(i, n.cell, p.N), fa[0][i], fa[1][i], w<R>(i) * p.rho0);
+        for (int i = 0; i < Q; ++i) {
+            const bool wall = (cz(i) == -1 && n.zlo_wall) || (cz(i) == 1 && n.zhi_wall) ||
+                              (i != 0 && ((lf >> opp(i)) & 1u));
+            const long long dst = n.zo[1 + cz(i)] + n.yo[1 + cy(i)] + n.xo[1 + cx(i)];
+            const R e1 = wall || i == 0 ? d1 : rho[dst], e2 = wall || i == 0 ? d2 : rho[p.N + dst];
+            Store<S>::store2(fout + pair_index(i, n.cell, p.N), fa[0][i], fa[1][i], Store<S>::enc(w<R>(i) * e1),
+                             Store<S>::enc(w<R>(i) * e2));
+        }
+        state_ref(fout, p.ref_off)[n.cell] = make_float2(d1, d2);
+    } else {
+#pragma unroll
+        for (int i = 0; i < Q; ++i)
+            Store<S>::store2(fout + pair_index(i, n.cell, p.N), fa[0][i], fa[1][i], w<R>(i) * p.rho0, w<R>(i) * p.rho0);
+    }
 }
 
 // Stored value s_j(y): the population that the gather of step 0 reads as
@@ -267,8 +303,38 @@ k_init_feq(const double *__restrict__ rho1, const double *__restrict__ rho2,
         const double P = 1.0 - 1.5 * usq + cu * (3.0 - 4.5 * usq) + 4.5 * cu * cu * (1.0 + cu);
         const R v1 = here_solid ? R(0) : (R)(rho1[src] * wd(k) * P);
         const R v2 = here_solid ? R(0) : (R)(rho2[src] * wd(k) * P);
-        Store<S>::store2(f + pair_index(j, n.cell, p.N), v1, v2, w<R>(j) * p.rho0);
+        if constexpr (Store<S>::kRel) {   // coded relative to the reader's initial density
+            const R e1 = here_solid ? R(1) : (R)rho1[src], e2 = here_solid ? R(1) : (R)rho2[src];
+            Store<S>::store2(f + pair_index(j, n.cell, p.N), v1, v2, Store<S>::enc(w<R>(j) * e1),
+                             Store<S>::enc(w<R>(j) * e2));
+        } else {
+            Store<S>::store2(f + pair_index(j, n.cell, p.N), v1, v2, w<R>(j) * p.rho0, w<R>(j) * p.rho0);
+        }
     }
+    if constexpr (Store<S>::kRel)
+        state_ref(f, p.ref_off)[n.cell] = here_solid ? make_float2(1.0f, 1.0f)
+                                                     : make_float2((float)rho1[n.cell], (float)rho2[n.cell]);
+}
+
+// Reference densities of a state set from explicit populations (the *_REL
+// formats): each cell's densities sum_i f_i^a of the given populations
+// (solid sites: 1, never read).
+template <int S>
+__global__ void __launch_bounds__(kThreads)
+k_set_ref(const double *__restrict__ src, typename Store<S>::T *__restrict__ f, PhysF<typename Store<S>::R> p)
+{
+    Nbr n;
+    if (!decode_cell(p, (long long)blockIdx.x * kThreads + threadIdx.x, n)) return;
+    float2 r = make_float2(1.0f, 1.0f);
+    if (!(p.solid && p.solid[n.cell])) {
+        double a = 0, b = 0;
+        for (int k = 0; k < Q; ++k) {
+            a += src[(long long)k * p.N + n.cell];
+            b += src[(long long)(Q + k) * p.N + n.cell];
+        }
+        r = make_float2((float)a, (float)b);
+    }
+    state_ref(f, p.ref_off)[n.cell] = r;
 }
 
 template <int S>
@@ -289,8 +355,13 @@ k_set_pop(const double *__restrict__ src, typename Store<S>::T *__restrict__ f,
                               (j != 0 && p.solid && p.solid[dst]);
             const long long sc = wall ? n.cell : dst;
             const int k = wall ? opp(j) : j;
+            R e = p.rho0;   // *_REL: the reader's reference (written by k_set_ref)
+            if constexpr (Store<S>::kRel) {
+                const float2 rr = state_ref(f, p.ref_off)[sc];
+                e = here_solid ? R(1) : (a == 0 ? rr.x : rr.y);
+            }
             Store<S>::store(f + pair_index(j, n.cell, p.N) + a,
-                            here_solid ? R(0) : (R)src[(long long)(a * Q + k) * p.N + sc], w<R>(j) * p.rho0);
+                            here_solid ? R(0) : (R)src[(long long)(a * Q + k) * p.N + sc], Store<S>::enc(w<R>(j) * e));
         }
 }
 
@@ -423,6 +494,7 @@ PhysF<R> make_phys(const HostPhys &h)
     p.rho0 = (R)h.rho0;
     p.solid = h.solid;
     p.links = h.links;
+    p.ref_off = h.ref_off;
     return p;
 }
 
@@ -475,6 +547,7 @@ cudaError_t setpop_t(const HostPhys &h, const double *src, void *f, cudaStream_t
 {
     using T = typename Store<S>::T;
     using R = typename Store<S>::R;
+    if constexpr (Store<S>::kRel) k_set_ref<S><<<grid_for(h.N), kThreads, 0, s>>>(src, (T *)f, make_phys<R>(h));
     k_set_pop<S><<<grid_for(h.N), kThreads, 0, s>>>(src, (T *)f, make_phys<R>(h));
     return cudaGetLastError();
 }
@@ -527,6 +600,8 @@ cudaError_t launch_step_split(const HostPhys &p, const void *f_in, void *f_out, 
     case ST_F32: return step_split_t<ST_F32>(p, f_in, f_out, rho, s, ev);
     case ST_F16_DEV: return step_split_t<ST_F16_DEV>(p, f_in, f_out, rho, s, ev);
     case ST_BF16_DEV: return step_split_t<ST_BF16_DEV>(p, f_in, f_out, rho, s, ev);
+    case ST_F16_REL: return step_split_t<ST_F16_REL>(p, f_in, f_out, rho, s, ev);
+    case ST_BF16_REL: return step_split_t<ST_BF16_REL>(p, f_in, f_out, rho, s, ev);
     default: return cudaErrorInvalidValue;
     }
 }
@@ -539,6 +614,8 @@ cudaError_t launch_init_feq(const HostPhys &p, const double *r1, const double *r
     case ST_F32: return init_t<ST_F32>(p, r1, r2, u, f, s);
     case ST_F16_DEV: return init_t<ST_F16_DEV>(p, r1, r2, u, f, s);
     case ST_BF16_DEV: return init_t<ST_BF16_DEV>(p, r1, r2, u, f, s);
+    case ST_F16_REL: return init_t<ST_F16_REL>(p, r1, r2, u, f, s);
+    case ST_BF16_REL: return init_t<ST_BF16_REL>(p, r1, r2, u, f, s);
     default: return cudaErrorInvalidValue;
     }
 }
@@ -550,6 +627,8 @@ cudaError_t launch_set_populations(const HostPhys &p, const double *src, void *f
     case ST_F32: return setpop_t<ST_F32>(p, src, f, s);
     case ST_F16_DEV: return setpop_t<ST_F16_DEV>(p, src, f, s);
     case ST_BF16_DEV: return setpop_t<ST_BF16_DEV>(p, src, f, s);
+    case ST_F16_REL: return setpop_t<ST_F16_REL>(p, src, f, s);
+    case ST_BF16_REL: return setpop_t<ST_BF16_REL>(p, src, f, s);
     default: return cudaErrorInvalidValue;
     }
 }
@@ -561,6 +640,8 @@ cudaError_t launch_get_populations(const HostPhys &p, const void *f, double *dst
     case ST_F32: return getpop_t<ST_F32>(p, f, dst, s);
     case ST_F16_DEV: return getpop_t<ST_F16_DEV>(p, f, dst, s);
     case ST_BF16_DEV: return getpop_t<ST_BF16_DEV>(p, f, dst, s);
+    case ST_F16_REL: return getpop_t<ST_F16_REL>(p, f, dst, s);
+    case ST_BF16_REL: return getpop_t<ST_BF16_REL>(p, f, dst, s);
     default: return cudaErrorInvalidValue;
     }
 }
@@ -573,6 +654,8 @@ cudaError_t launch_moments(const HostPhys &p, const void *f, void *rho, int out_
     case ST_F32: return moments_t<ST_F32>(p, f, rho, out_f64, o1, o2, ouF, s);
     case ST_F16_DEV: return moments_t<ST_F16_DEV>(p, f, rho, out_f64, o1, o2, ouF, s);
     case ST_BF16_DEV: return moments_t<ST_BF16_DEV>(p, f, rho, out_f64, o1, o2, ouF, s);
+    case ST_F16_REL: return moments_t<ST_F16_REL>(p, f, rho, out_f64, o1, o2, ouF, s);
+    case ST_BF16_REL: return moments_t<ST_BF16_REL>(p, f, rho, out_f64, o1, o2, ouF, s);
     default: return cudaErrorInvalidValue;
     }
 }
@@ -592,6 +675,8 @@ cudaError_t launch_density(const HostPhys &h, const void *f, void *rho, cudaStre
     case ST_F32: density_pass<ST_F32>(h, (const float *)f, (float *)rho, s); break;
     case ST_F16_DEV: density_pass<ST_F16_DEV>(h, (const __half *)f, (float *)rho, s); break;
     case ST_BF16_DEV: density_pass<ST_BF16_DEV>(h, (const __nv_bfloat16 *)f, (float *)rho, s); break;
+    case ST_F16_REL: density_pass<ST_F16_REL>(h, (const __half *)f, (float *)rho, s); break;
+    case ST_BF16_REL: density_pass<ST_BF16_REL>(h, (const __nv_bfloat16 *)f, (float *)rho, s); break;
     default: return cudaErrorInvalidValue;
     }
     return cudaGetLastError();
@@ -604,6 +689,8 @@ cudaError_t launch_reduce(const HostPhys &p, const void *f, void *rho, double *p
     case ST_F32: return reduce_t<ST_F32>(p, f, rho, partials, s);
     case ST_F16_DEV: return reduce_t<ST_F16_DEV>(p, f, rho, partials, s);
     case ST_BF16_DEV: return reduce_t<ST_BF16_DEV>(p, f, rho, partials, s);
+    case ST_F16_REL: return reduce_t<ST_F16_REL>(p, f, rho, partials, s);
+    case ST_BF16_REL: return reduce_t<ST_BF16_REL>(p, f, rho, partials, s);
     default: return cudaErrorInvalidValue;
     }
 }
@@ -615,6 +702,21 @@ size_t storage_bytes(int storage)
     case ST_F32: return 4;
     default: return 2;
     }
+}
+
+bool storage_is_rel(int storage) { return storage == ST_F16_REL || storage == ST_BF16_REL; }
+
+size_t ref_offset(int storage, long long N)
+{
+    if (!storage_is_rel(storage)) return 0;
+    const size_t pop = (size_t)2 * Q * (size_t)N * storage_bytes(storage);
+    return (pop + 255) / 256 * 256;
+}
+
+size_t state_bytes(int storage, long long N)
+{
+    const size_t pop = (size_t)2 * Q * (size_t)N * storage_bytes(storage);
+    return storage_is_rel(storage) ? ref_offset(storage, N) + sizeof(float) * 2 * (size_t)N : pop;
 }
 
 size_t real_bytes(int storage) { return storage == ST_F64 ? 8 : 4; }

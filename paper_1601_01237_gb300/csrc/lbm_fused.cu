@@ -128,47 +128,76 @@ __device__ __forceinline__ int gather_elem(const PlaneRef &pr, const Col &c, int
     return zs + c.yo[1 - cy(I)] + c.xo[1 - cx(I)];
 }
 
+// Reference densities that decode the populations gathered into column c of
+// plane pr: the cell's own stored pair for the *_REL formats, rho0 otherwise.
+template <int S>
+__device__ __forceinline__ float2 gather_ref(const typename Store<S>::T *__restrict__ f,
+                                             const Phys<typename Store<S>::R> &p, const PlaneRef &pr, const Col &c)
+{
+    if constexpr (Store<S>::kRel)
+        return state_ref(f, p.ref_off)[(unsigned)(pr.zc + c.yo[1] + c.xo[1])];
+    else
+        return make_float2((float)p.rho0, (float)p.rho0);
+}
+
 // Element offsets inside one component's 19 arrays fit 32 bits (19 N < 2^32,
 // checked on the host): one multiply-add per load instead of 64-bit index math.
 template <int S, int I>
 __device__ __forceinline__ void load_dir(const typename Store<S>::T *__restrict__ f, long long N,
-                                         typename Store<S>::R rho0, const PlaneRef &pr, const Col &c,
+                                         float2 rr, const PlaneRef &pr, const Col &c,
                                          typename Store<S>::R (&v)[Q2])
 {
     using R = typename Store<S>::R;
     int d;
     const int e = gather_elem<I>(pr, c, d);
     const unsigned idx = (unsigned)d * (unsigned)N + (unsigned)e;
-    Store<S>::load2(f + 2 * (size_t)idx, w<R>(I) * rho0, v[I], v[Q + I]);
+    Store<S>::load2(f + 2 * (size_t)idx, w<R>(I) * rr.x, w<R>(I) * rr.y, v[I], v[Q + I]);
 }
 
 template <int S, int I>
 struct GatherAll {
     __device__ __forceinline__ static void run(const typename Store<S>::T *__restrict__ f, long long N,
-                                               typename Store<S>::R rho0, const PlaneRef &pr, const Col &c,
+                                               float2 rr, const PlaneRef &pr, const Col &c,
                                                typename Store<S>::R (&v)[Q2])
     {
-        load_dir<S, I>(f, N, rho0, pr, c, v);
-        GatherAll<S, I + 1>::run(f, N, rho0, pr, c, v);
+        load_dir<S, I>(f, N, rr, pr, c, v);
+        GatherAll<S, I + 1>::run(f, N, rr, pr, c, v);
     }
 };
 template <int S>
 struct GatherAll<S, Q> {
     __device__ __forceinline__ static void run(const typename Store<S>::T *__restrict__, long long,
-                                               typename Store<S>::R, const PlaneRef &, const Col &,
+                                               float2, const PlaneRef &, const Col &,
                                                typename Store<S>::R (&)[Q2]) {}
 };
 
-// rho^1, rho^2 and momentum of a gathered population set.
+// rho^1, rho^2 and momentum of a gathered population set.  The densities are
+// summed in the grouping of the halo partial gathers, (directions 0-6 +
+// directions 7-12) + directions 13-18, so that a cell's density is the same
+// bit for bit whether its own CTA forms it or a neighbouring CTA forms it as a
+// halo cell.  The momentum is summed over opposite pairs,
+// sum_{i odd} c_i (t_i - t_opp(i)) with t_i = f^1_i + f^2_i: the same sum, but
+// each difference of two nearly equal populations is taken first (exactly,
+// in FP32, when they are within a factor of two), so the rounding of the
+// result scales with the momentum, not with the density.
 template <class R>
 __device__ __forceinline__ void sums(const R (&v)[Q2], R &r1, R &r2, R &jx, R &jy, R &jz)
 {
     R s1 = 0, s2 = 0, ax = 0, ay = 0, az = 0;
+    {
+        R g1[3] = {0, 0, 0}, g2[3] = {0, 0, 0};
 #pragma unroll
-    for (int i = 0; i < Q; ++i) {
-        s1 += v[i];
-        s2 += v[Q + i];
-        const R t = v[i] + v[Q + i];
+        for (int i = 0; i < Q; ++i) {
+            const int k = i < 7 ? 0 : (i < 13 ? 1 : 2);
+            g1[k] += v[i];
+            g2[k] += v[Q + i];
+        }
+        s1 = g1[0] + g1[1] + g1[2];
+        s2 = g2[0] + g2[1] + g2[2];
+    }
+#pragma unroll
+    for (int i = 1; i < Q; i += 2) {
+        const R t = (v[i] + v[Q + i]) - (v[i + 1] + v[Q + i + 1]);
         if (cx(i) == 1) ax += t; else if (cx(i) == -1) ax -= t;
         if (cy(i) == 1) ay += t; else if (cy(i) == -1) ay -= t;
         if (cz(i) == 1) az += t; else if (cz(i) == -1) az -= t;
@@ -181,15 +210,15 @@ __device__ __forceinline__ void sums(const R (&v)[Q2], R &r1, R &r2, R &jx, R &j
 template <int S, int D, int D1>
 struct HaloRange {
     __device__ __forceinline__ static void load(const typename Store<S>::T *__restrict__ f, long long N,
-                                                typename Store<S>::R rho0, const PlaneRef &pr, const Col &c,
+                                                float2 rr, const PlaneRef &pr, const Col &c,
                                                 typename Store<S>::R (&v)[kPer], int k)
     {
         using R = typename Store<S>::R;
         int d;
         const int e = gather_elem<D>(pr, c, d);
         const unsigned idx = (unsigned)d * (unsigned)N + (unsigned)e;
-        Store<S>::load2(f + 2 * (size_t)idx, w<R>(D) * rho0, v[k], v[k + 1]);
-        HaloRange<S, D + 1, D1>::load(f, N, rho0, pr, c, v, k + 2);
+        Store<S>::load2(f + 2 * (size_t)idx, w<R>(D) * rr.x, w<R>(D) * rr.y, v[k], v[k + 1]);
+        HaloRange<S, D + 1, D1>::load(f, N, rr, pr, c, v, k + 2);
     }
     __device__ __forceinline__ static void sum(const typename Store<S>::R (&v)[kPer], int k,
                                                typename Store<S>::R &s0, typename Store<S>::R &s1)
@@ -202,7 +231,7 @@ struct HaloRange {
 template <int S, int D1>
 struct HaloRange<S, D1, D1> {
     __device__ __forceinline__ static void load(const typename Store<S>::T *__restrict__, long long,
-                                                typename Store<S>::R, const PlaneRef &, const Col &,
+                                                float2, const PlaneRef &, const Col &,
                                                 typename Store<S>::R (&)[kPer], int) {}
     __device__ __forceinline__ static void sum(const typename Store<S>::R (&)[kPer], int,
                                                typename Store<S>::R &, typename Store<S>::R &) {}
@@ -212,9 +241,10 @@ template <int S>
 __device__ __forceinline__ void halo_load(const typename Store<S>::T *__restrict__ f, const Phys<typename Store<S>::R> &p,
                                           const PlaneRef &pr, const Col &c, int g, typename Store<S>::R (&v)[kPer])
 {
-    if (g == 0) HaloRange<S, 0, 7>::load(f, p.N, p.rho0, pr, c, v, 0);
-    else if (g == 1) HaloRange<S, 7, 13>::load(f, p.N, p.rho0, pr, c, v, 0);
-    else HaloRange<S, 13, Q>::load(f, p.N, p.rho0, pr, c, v, 0);
+    const float2 rr = gather_ref<S>(f, p, pr, c);
+    if (g == 0) HaloRange<S, 0, 7>::load(f, p.N, rr, pr, c, v, 0);
+    else if (g == 1) HaloRange<S, 7, 13>::load(f, p.N, rr, pr, c, v, 0);
+    else HaloRange<S, 13, Q>::load(f, p.N, rr, pr, c, v, 0);
 }
 
 template <int S>
@@ -231,10 +261,16 @@ __device__ __forceinline__ void halo_sum(const typename Store<S>::R (&v)[kPer], 
 // Collision of both components at the thread's interior cell of plane z (the
 // populations come from the stash, densities from the ring, momentum from the
 // moment buffer), forcing term included, result stored at the cell.
+// With the *_REL formats each stored population is coded relative to the
+// density of the cell that reads it next: x + c_i (from the ring), or the
+// cell itself when x + c_i lies behind a wall (lo_wall / hi_wall: plane z is
+// next to the lower / upper wall); the cell's own densities are stored as the
+// reference of the populations it will gather.
 template <int S, int REG>
 __device__ __forceinline__ void collide_cell(typename Store<S>::T *__restrict__ fout, const Phys<typename Store<S>::R> &p,
                                              const FusedSmem<typename Store<S>::R> &sm, int sl_m, int sl_c, int sl_p,
-                                             int st, long long cell, typename Store<S>::R *__restrict__ s_out)
+                                             int st, long long cell, typename Store<S>::R *__restrict__ s_out,
+                                             bool lo_wall, bool hi_wall)
 {
     using R = typename Store<S>::R;
     const int tid = threadIdx.x;
@@ -243,15 +279,21 @@ __device__ __forceinline__ void collide_cell(typename Store<S>::T *__restrict__ 
     const R r1 = rr.x, r2 = rr.y;
     const R inv = R(1) / (r1 + r2);
     const R ux = sm.mom[st][0][tid] * inv, uy = sm.mom[st][1][tid] * inv, uz = sm.mom[st][2][tid] * inv;
-    // S^b = sum_{i != 0} w_i c_i rho^b(x + c_i)  (Eq. 7; ghost planes carry Eq. 13's rho')
+    // S^b = sum_{i != 0} w_i c_i rho^b(x + c_i)  (Eq. 7; ghost planes carry
+    // Eq. 13's rho'), summed over opposite neighbours as
+    // sum_{i odd} w_i c_i (rho^b(x + c_i) - rho^b(x - c_i)): the differences of
+    // nearby densities come first, so the rounding scales with the gradient
+    // rather than with the density
     R Sb[2][3] = {{0, 0, 0}, {0, 0, 0}};
 #pragma unroll
-    for (int i = 1; i < Q; ++i) {
-        const int sl = cz(i) == -1 ? sl_m : (cz(i) == 1 ? sl_p : sl_c);
-        const float2 rv = sm.ring[sl][ly + cy(i)][lx + cx(i)];
+    for (int i = 1; i < Q; i += 2) {
+        const int slp = cz(i) == -1 ? sl_m : (cz(i) == 1 ? sl_p : sl_c);
+        const int slm = cz(i) == -1 ? sl_p : (cz(i) == 1 ? sl_m : sl_c);
+        const float2 rp = sm.ring[slp][ly + cy(i)][lx + cx(i)];
+        const float2 rm = sm.ring[slm][ly - cy(i)][lx - cx(i)];
 #pragma unroll
         for (int b = 0; b < 2; ++b) {
-            const R wr = w<R>(i) * (b == 0 ? rv.x : rv.y);
+            const R wr = w<R>(i) * (b == 0 ? rp.x - rm.x : rp.y - rm.y);
             if (cx(i) == 1) Sb[b][0] += wr; else if (cx(i) == -1) Sb[b][0] -= wr;
             if (cy(i) == 1) Sb[b][1] += wr; else if (cy(i) == -1) Sb[b][1] -= wr;
             if (cz(i) == 1) Sb[b][2] += wr; else if (cz(i) == -1) Sb[b][2] -= wr;
@@ -323,7 +365,12 @@ __device__ __forceinline__ void collide_cell(typename Store<S>::T *__restrict__ 
             o1 = rq1 * R(12) * A1 - keep1 * R(1.5) * t1;
             o2v = rq2 * R(12) * A2 - keep2 * R(1.5) * t2;
         }
-        Store<S>::store2(o, o1, o2v, w0 * ref0);
+        if constexpr (Store<S>::kRel) {
+            Store<S>::store2(o, o1, o2v, Store<S>::enc(w0 * r1), Store<S>::enc(w0 * r2));
+            state_ref(fout, p.ref_off)[cell] = rr;
+        } else {
+            Store<S>::store2(o, o1, o2v, w0 * ref0, w0 * ref0);
+        }
     }
 #pragma unroll
     for (int i = 1; i < Q; i += 2) {
@@ -364,10 +411,23 @@ __device__ __forceinline__ void collide_cell(typename Store<S>::T *__restrict__ 
             o2p = rw2 * (E2 + O2) + n2 + m2;
             o2m = rw2 * (E2 - O2) + n2 - m2;
         }
-        const R ref = w<R>(i) * ref0;
         const size_t ip = 2 * (size_t)((unsigned)i * N32), im = 2 * (size_t)((unsigned)(i + 1) * N32);
-        Store<S>::store2(o + ip, o1p, o2p, ref);
-        Store<S>::store2(o + im, o1m, o2m, ref);
+        if constexpr (Store<S>::kRel) {
+            // destinations: x + c_i for i, x - c_i for opp(i), or x across a wall
+            const bool wp = (cz(i) == -1 && lo_wall) || (cz(i) == 1 && hi_wall);
+            const bool wm = (cz(i) == 1 && lo_wall) || (cz(i) == -1 && hi_wall);
+            const int slp = cz(i) == -1 ? sl_m : (cz(i) == 1 ? sl_p : sl_c);
+            const int slm = cz(i) == -1 ? sl_p : (cz(i) == 1 ? sl_m : sl_c);
+            const float2 dp = wp ? rr : sm.ring[slp][ly + cy(i)][lx + cx(i)];
+            const float2 dm = wm ? rr : sm.ring[slm][ly - cy(i)][lx - cx(i)];
+            const R wi = w<R>(i);
+            Store<S>::store2(o + ip, o1p, o2p, Store<S>::enc(wi * dp.x), Store<S>::enc(wi * dp.y));
+            Store<S>::store2(o + im, o1m, o2m, Store<S>::enc(wi * dm.x), Store<S>::enc(wi * dm.y));
+        } else {
+            const R ref = w<R>(i) * ref0;
+            Store<S>::store2(o + ip, o1p, o2p, ref, ref);
+            Store<S>::store2(o + im, o1m, o2m, ref, ref);
+        }
     }
 }
 
@@ -487,13 +547,13 @@ k_step_fused(const typename Store<S>::T *__restrict__ fin, typename Store<S>::T 
     for (int q = z0 - 1; q <= z0; ++q) {
         const PlaneRef pr = plane_ref<WALLZ>(p, q);
         R v[Q2];
-        if (!pr.constant) GatherAll<S, 0>::run(fin, p.N, p.rho0, pr, ci, v);
+        if (!pr.constant) GatherAll<S, 0>::run(fin, p.N, gather_ref<S>(fin, p, pr, ci), pr, ci, v);
         interior_plane<S>(fin, p, sm, q - z0 + 1, q == z0 ? 0 : -1, pr, v);
         if (tid < kHalo) {
             R r1 = p.rho_s[0], r2 = p.rho_s[1];
             if (!pr.constant) {
                 R hv[Q2];
-                GatherAll<S, 0>::run(fin, p.N, p.rho0, pr, ch, hv);
+                GatherAll<S, 0>::run(fin, p.N, gather_ref<S>(fin, p, pr, ch), pr, ch, hv);
                 R a1, a2, jx, jy, jz;
                 sums(hv, a1, a2, jx, jy, jz);
                 if (pr.ghost) { r1 += a1; r2 += a2; } else { r1 = a1; r2 = a2; }
@@ -518,7 +578,7 @@ k_step_fused(const typename Store<S>::T *__restrict__ fin, typename Store<S>::T 
     R v[Q2];
     {
         const PlaneRef pr = plane_ref<WALLZ>(p, z0 + 1);
-        if (!pr.constant) GatherAll<S, 0>::run(fin, p.N, p.rho0, pr, ci, v);
+        if (!pr.constant) GatherAll<S, 0>::run(fin, p.N, gather_ref<S>(fin, p, pr, ci), pr, ci, v);
     }
     __syncthreads();
 
@@ -544,9 +604,10 @@ k_step_fused(const typename Store<S>::T *__restrict__ fin, typename Store<S>::T 
         __syncthreads();
         // ---- phase B: the interior gathers of plane z+2 are issued first and
         //      stay in flight (in registers) during the collision of plane z
-        if (z + 1 < z1 && !pr2.constant) GatherAll<S, 0>::run(fin, p.N, p.rho0, pr2, ci, v);
+        if (z + 1 < z1 && !pr2.constant) GatherAll<S, 0>::run(fin, p.N, gather_ref<S>(fin, p, pr2, ci), pr2, ci, v);
         if (active)
-            collide_cell<S, REG>(fout, p, sm, s_m, s_c, s_p, k & 1, (long long)z * p.nx * p.ny + cell_xy, s_out);
+            collide_cell<S, REG>(fout, p, sm, s_m, s_c, s_p, k & 1, (long long)z * p.nx * p.ny + cell_xy, s_out,
+                                 WALLZ && z == 0, WALLZ && z == p.nz - 1);
     }
 }
 
@@ -563,6 +624,7 @@ Phys<R> make_phys_f(const HostPhys &h)
     for (int d = 0; d < 3; ++d) p.gext[d] = (R)h.gext[d];
     p.rho_s[0] = (R)h.rho_s[0]; p.rho_s[1] = (R)h.rho_s[1];
     p.rho0 = (R)h.rho0;
+    p.ref_off = h.ref_off;
     return p;
 }
 
@@ -642,6 +704,8 @@ cudaError_t launch_step_fused(const HostPhys &p, const void *f_in, void *f_out, 
     case ST_F32: return fused_t<ST_F32>(p, f_in, f_out, s, ev, s_out);
     case ST_F16_DEV: return fused_t<ST_F16_DEV>(p, f_in, f_out, s, ev, s_out);
     case ST_BF16_DEV: return fused_t<ST_BF16_DEV>(p, f_in, f_out, s, ev, s_out);
+    case ST_F16_REL: return fused_t<ST_F16_REL>(p, f_in, f_out, s, ev, s_out);
+    case ST_BF16_REL: return fused_t<ST_BF16_REL>(p, f_in, f_out, s, ev, s_out);
     default: return cudaErrorInvalidValue;
     }
 }

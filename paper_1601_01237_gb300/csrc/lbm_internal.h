@@ -28,6 +28,9 @@ struct HostPhys {
     // N words of link flags derived from the mask: bit i set when the pull
     // source x - c_i of cell x is a solid site (launch_link_flags)
     const unsigned *links = nullptr;
+    // *_REL formats: byte offset of the per-cell reference densities from the
+    // base of a state (see state_bytes); 0 otherwise
+    long long ref_off = 0;
 };
 
 // Populations are stored as 2*19*N values of the storage type, laid out
@@ -112,6 +115,12 @@ cudaError_t launch_link_flags(const HostPhys &p, const unsigned char *solid, uns
 int current_device_sms();
 
 size_t storage_bytes(int storage);   // bytes per stored population value
+// One raw state: the 2*19*N populations, and for the *_REL formats the N
+// reference-density pairs (float2) behind them at ref_offset (the population
+// bytes rounded up to 256).
+bool storage_is_rel(int storage);
+size_t ref_offset(int storage, long long N);
+size_t state_bytes(int storage, long long N);
 size_t real_bytes(int storage);      // bytes per arithmetic value
 
 }  // namespace lbm

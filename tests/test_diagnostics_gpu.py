@@ -85,15 +85,17 @@ def test_laplace_2d_gpu_equals_oracle_fit(gpu_lib):
     assert abs(c0) < 0.1 * min(dps)
 
 
-@pytest.mark.parametrize("storage", ["f16_dev", "bf16_dev"])
+@pytest.mark.parametrize("storage", ["f16_dev", "bf16_dev", "f16_rel", "bf16_rel"])
 def test_low_precision_surface_tension_reported(gpu_lib, storage):
-    """Acceptance measurement of 16-bit deviation storage: the Laplace surface
-    tension of quasi-2D droplets against the FP64 value; a format is accepted
-    for droplet work only within 1 %.  With rho0 = 0.5 both phases of a
-    1.1 / 0.006 droplet sit far from the reference, so the deviations keep
-    few significant bits in the minority phase; the measured errors (a few
-    percent) are reported, and the test bounds them at 10 % so that a broken
-    codec still fails."""
+    """Acceptance measurement of 16-bit storage: the Laplace surface tension of
+    quasi-2D droplets against the FP64 value; a format is accepted for droplet
+    work only within 1 %.  With deviations from rho0 = 0.5 (*_DEV) both phases
+    of a 1.1 / 0.006 droplet sit far from the reference, so the deviations
+    keep few significant bits in the minority phase: their errors (a few
+    percent) are reported and bounded at 10 % so that a broken codec still
+    fails.  The relative deviations (*_REL: f / (w rho~) - 1, rho~ the reading
+    cell's previous density) keep the full 16-bit precision in both phases
+    and must meet the 1 % bar."""
     n, steps = 48, 2000
     fits = {}
     for st in ("f64", storage):
@@ -106,7 +108,7 @@ def test_low_precision_surface_tension_reported(gpu_lib, storage):
     err = abs(fits[storage] - fits["f64"]) / abs(fits["f64"])
     print("%s surface tension %.6f vs FP64 %.6f: %.3g (%s)" % (storage, fits[storage], fits["f64"], err,
                                                                "accepted" if err <= 0.01 else "not accepted"))
-    assert err <= 0.1
+    assert err <= (0.01 if storage.endswith("_rel") else 0.1)
 
 
 def test_laplace_3d_f32_within_1pct_of_f64(gpu_lib):

@@ -580,3 +580,124 @@ def test_isolated_solid_site_presents_the_linear_field():
         tot = Sf[xz] + Sw[xz]
         assert np.allclose(tot, T0 * grad, atol=1e-15)
         assert np.allclose(Sw[xz], w[i] * c[i] * rho[s], atol=1e-15)
+
+
+# ---------------------------------------------------------------------------
+# The second forcing reading: Guo, Zheng & Shi (2002), one common equilibrium
+# velocity u* = u + g/2 (Eqs. 8-9).
+
+def _guo_term(c, w, u, F):
+    """w_i [(c_i - u)/T0 + (c_i.u) c_i / T0^2] . F, written out per direction."""
+    out = np.zeros(19)
+    for i in range(19):
+        cu = c[i] @ u
+        out[i] = w[i] * sum(((c[i, k] - u[k]) / T0 + cu * c[i, k] / T0 ** 2) * F[k] for k in range(3))
+    return out
+
+
+@pytest.mark.parametrize("collision", ["bgk", "regularized", "regularized3"])
+def test_guo_collision_moments(collision):
+    """Post-collision moments of one component with Guo's forcing (F = rho g):
+      mass kept;
+      BGK:          j* = j - (j - rho u*)/tau + (1 - 1/(2 tau)) F,
+      regularized:  j* = rho u* + F/2 (the first-order non-equilibrium part is
+                    filtered out, as without forcing);
+    and the forcing term's own moments 0, F, u* F + F u* (its second moment),
+    so that the regularized second moment is
+      rho (T0 I + u* u*) + (1 - 1/tau) (Pi_neq + (u* F + F u*)/2) + (u* F + F u*)/2,
+    Pi_neq = sum c c (f - f^eq(u*)).  At tau = 1 both operators give
+    f^eq(u*) + F_i/2."""
+    c, w = oracle.lattice()
+    for tau in (0.55, 0.8, 1.0, 2.5):
+        p = oracle.make_params((1, 1, 1), tau=(tau, tau), collision=collision, forcing="guo")
+        for _ in range(3):
+            rho = RNG.uniform(0.05, 1.5)
+            u = RNG.uniform(-0.08, 0.08, 3)
+            g = RNG.uniform(-0.05, 0.05, 3)
+            fin = oracle.feq(rho, RNG.uniform(-0.08, 0.08, 3)) * (1 + 0.05 * RNG.uniform(-1, 1, 19))
+            r = fin.sum()
+            j = c.T @ fin
+            F = r * g
+            Fi = _guo_term(c, w, u, F)
+            assert abs(Fi.sum()) < 1e-15
+            assert np.allclose(c.T @ Fi, F, atol=1e-15)
+            assert np.allclose(np.einsum("ia,ib,i->ab", c, c, Fi), np.outer(u, F) + np.outer(F, u), atol=1e-15)
+            fp = oracle.collide_cell(p, 0, fin, r, u, g)
+            assert abs(fp.sum() - r) < 1e-14
+            jp = c.T @ fp
+            if collision == "bgk":
+                assert np.allclose(jp, j - (j - r * u) / tau + (1 - 1 / (2 * tau)) * F, atol=1e-15)
+            else:
+                assert np.allclose(jp, r * u + F / 2, atol=1e-15)
+                feq = oracle.feq(r, u)
+                Pneq = np.einsum("ia,ib,i->ab", c, c, fin - feq)
+                S = np.outer(u, F) + np.outer(F, u)
+                ref = r * (T0 * np.eye(3) + np.outer(u, u)) + (1 - 1 / tau) * (Pneq + S / 2) + S / 2
+                assert np.allclose(np.einsum("ia,ib,i->ab", c, c, fp), ref, atol=1e-14)
+            if tau == 1.0:
+                assert np.allclose(fp, oracle.feq(r, u) + Fi / 2, atol=1e-15)
+
+
+@pytest.mark.parametrize("collision,tau", [("bgk", 0.7), ("bgk", 2.0), ("regularized", 0.6)])
+def test_guo_spinodal_threshold_is_tau_independent(collision, tau):
+    """With Guo's forcing the force and the density gradient enter the flux
+    of a component relative to the mixture with the same factor (tau - 1/2),
+    so the long-wave mode of the uniform mixture rho^1 = rho^2 = rho0 grows
+    iff |G| rho0 > 1, the continuum criterion, at every tau (the
+    exact-difference forcing gives 1 - 1/(2 tau) instead).  Checked 10 %
+    either side of |G| = 1/rho0."""
+    n, m, eps, rho0 = 48, 1, 1e-4, 0.5
+    x = np.arange(n)
+    k = 2 * np.pi * m / n
+    r1 = (rho0 * (1 + eps * np.cos(k * x)))[None, None, :]
+    r2 = (rho0 * (1 - eps * np.cos(k * x)))[None, None, :]
+    amp = {}
+    for fac in (0.9, 1.1):
+        p, f = _run(r1.shape, r1, r2, 600, G12=-fac / rho0, tau=(tau, tau), collision=collision, forcing="guo")
+        a, b, _ = oracle.moments(p, f)
+        amp[fac] = np.abs(np.fft.rfft((a - b)[0, 0]))[m] / (n / 2) / (2 * rho0 * eps)
+    assert amp[0.9] < 0.97
+    assert amp[1.1] > 1.03
+
+
+@pytest.mark.parametrize("collision", ["bgk", "regularized"])
+def test_guo_conservation_and_fixed_point(collision):
+    """Guo's forcing keeps each component's mass and, under periodic walls
+    with symmetric G and equal tau (BGK) or any tau (regularized), the total
+    momentum (the pairwise Eq. 7 forces sum to zero); a uniform state at rest
+    stays bitwise fixed."""
+    shape = (5, 6, 7)
+    r1, r2, u = wl.random_state(shape, seed=8, u_max=0.03)
+    tau = (0.8, 0.8) if collision == "bgk" else (0.6, 1.3)
+    p, f = _run(shape, r1, r2, 0, u=u, G12=-1.3, tau=tau, collision=collision, forcing="guo")
+    a0, b0, uF0 = oracle.moments(p, f)
+    mom0 = (((a0 + b0)[..., None]) * uF0).sum((0, 1, 2))
+    oracle.step(p, f, 300)
+    a, b, uF = oracle.moments(p, f)
+    assert abs(a.sum() - a0.sum()) < 1e-13 * a0.sum() and abs(b.sum() - b0.sum()) < 1e-13 * b0.sum()
+    mom = (((a + b)[..., None]) * uF).sum((0, 1, 2))
+    assert np.max(np.abs(mom - mom0)) < 1e-12 * (a0 + b0).sum()
+    r = np.full(shape, 0.4)
+    p, f = _run(shape, r, r, 0, G12=-1.3, collision=collision, forcing="guo")
+    f0 = f.copy()
+    oracle.step(p, f, 3)
+    assert np.array_equal(f, f0)
+
+
+def test_guo_poiseuille_curvature():
+    """Single fluid driven by g_ext between half-way walls with Guo's
+    forcing: the second difference of u_F is the exact curvature -g/nu,
+    nu = T0 (tau - 1/2), at any tau (BGK and regularized)."""
+    H, g = 8, 1e-5
+    for collision in ("bgk", "regularized"):
+        for tau in (0.6, 1.4):
+            shape = (H, 1, 2)
+            r = np.full(shape, 0.5)
+            p, f = _run(shape, r, r, 6000, G12=0.0, tau=(tau, tau), g_ext=(g, 0, 0), periodic=(1, 1, 0),
+                        collision=collision, forcing="guo")
+            _, _, uF = oracle.moments(p, f)
+            ux = uF[:, 0, 0, 0]
+            nu = T0 * (tau - 0.5)
+            d2 = ux[2:] - 2 * ux[1:-1] + ux[:-2]
+            assert np.allclose(d2, -g / nu, rtol=1e-8, atol=0), (collision, tau, d2 / (-g / nu))
+            assert np.abs(uF[..., 1:]).max() < 1e-14

@@ -92,16 +92,20 @@ def test_droplet_c0_f64(gpu_lib):
     assert abs(red["max_uF"] - np.sqrt((uF ** 2).sum(-1)).max()) < 1e-10
 
 
-def _interface_split(gpu, ref, centre, periodic, W=2.0, hemisphere=False, thr=None):
-    """Per-cell relative error |gpu - ref| / ref split by the distance from
-    the interface of a (hemi)spherical droplet in the reference field: the
-    interface is the sphere of the reference's equivalent radius (cells above
-    the mid density); cells farther than 3 W from it are "far".  Also the
-    near-interface error expressed as an interface displacement,
-    max |gpu - ref| / |grad ref| over the near cells (in cells)."""
+def _interface_split(gpu, ref, centre, periodic, W=2.0, hemisphere=False):
+    """Per-cell relative error |gpu - ref| / ref of one density field, split
+    by the distance from the interface of a (hemi)spherical droplet in the
+    reference field (the sphere of the reference's equivalent radius; cells
+    farther than 3 W from it are "far"), and the error of the interface cells
+    read as a radial displacement of the profile: over the cells where
+    |d ref / dr| is at least a tenth of its maximum, the least-squares
+    delta_R of gpu - ref = -delta_R d ref / dr, and the fraction of the error
+    that this rigid shift leaves unexplained.
+    Returns (far max, far cells, near max, delta_R, unexplained fraction, R_eq)."""
     nz, ny, nx = ref.shape
-    mid = 0.5 * (ref.max() + ref.min()) if thr is None else thr
-    vol = float((ref > mid).sum()) if ref[tuple(int(round(c)) for c in centre)] > mid else float((ref < mid).sum())
+    mid = 0.5 * (ref.max() + ref.min())
+    inside_high = ref[tuple(int(round(max(c, 0))) for c in centre)] > mid
+    vol = float((ref > mid).sum() if inside_high else (ref < mid).sum())
     Req = (3.0 * vol / (2.0 if hemisphere else 4.0) / np.pi) ** (1.0 / 3.0)
     z, y, x = np.meshgrid(np.arange(nz), np.arange(ny), np.arange(nx), indexing="ij")
     d = []
@@ -113,22 +117,25 @@ def _interface_split(gpu, ref, centre, periodic, W=2.0, hemisphere=False, thr=No
     r = np.sqrt(d[0] ** 2 + d[1] ** 2 + d[2] ** 2)
     far = np.abs(r - Req) > 3.0 * W
     err = np.abs(gpu - ref) / ref
-    grad = np.sqrt(sum(g ** 2 for g in np.gradient(ref)))
-    near = ~far
-    disp = float(np.max(np.abs(gpu - ref)[near] / np.maximum(grad[near], 1e-12)))
-    return float(err[far].max()), int(far.sum()), float(err[near].max()), disp, Req
+    gz, gy, gx = np.gradient(ref)
+    dr = (gz * d[0] + gy * d[1] + gx * d[2]) / np.maximum(r, 1e-12)
+    band = np.abs(dr) >= 0.1 * np.abs(dr).max()
+    diff = (gpu - ref)[band]
+    shift = -float((diff * dr[band]).sum() / (dr[band] ** 2).sum())
+    unexplained = float(np.linalg.norm(diff + shift * dr[band]) / max(np.linalg.norm(diff), 1e-300))
+    return float(err[far].max()), int(far.sum()), float(err[~far].max()), shift, unexplained, Req
 
 
 def test_f32_droplet_1000_steps(gpu_lib):
     """FP32 storage and arithmetic, 3D droplet on 24^3 (tau = 1, relaxing to
     coexisting densities about 1.06 / 0.005), 1000 steps, against the FP64
-    oracle.  The stated FP32 bar, max |d rho| / rho <= 1e-5 per cell, holds for
-    every cell farther than 3 W from the interface (both phases, both
-    components).  Next to the interface FP32 rounding shifts the interface by
-    a tiny displacement delta; there |d rho| = delta |grad rho|, which relative
-    to the minority density of a cell in the interface's tail is far larger
-    than delta.  Near the interface the test bounds the displacement
-    (|d rho| / |grad rho| <= 1e-4 cells) and the per-cell error (2e-4)."""
+    oracle: the stated FP32 bar max |d rho| / rho <= 1e-5 in every cell, both
+    components.  The error is reported separately for the cells within 3 W of
+    the interface, where the minority-side tail is most sensitive (measured
+    4.0e-6 there, 2.6e-6 elsewhere), with the part of it that a rigid radial
+    shift of the profile explains.  (Before the interaction and momentum sums
+    took opposite directions in pairs, the cancellation of O(1) terms in
+    those FP32 sums put 1.6e-5 into the interface's minority tail.)"""
     import oracle
     shape = (24, 24, 24)
     r1, r2 = wl.droplet(shape, 7)
@@ -139,16 +146,37 @@ def test_f32_droplet_1000_steps(gpu_lib):
     lat.close()
     c = (11.5, 11.5, 11.5)
     res = [_interface_split(g, o, c, (1, 1, 1)) for g, o in ((ga, a), (gb, b))]
-    for k, (far, nfar, near, disp, Req) in enumerate(res):
+    for k, (far, nfar, near, shift, unexp, Req) in enumerate(res):
         print("FP32 droplet 1000 steps, component %d: R_eq %.2f; far from the interface (%d cells) "
-              "max|drho|/rho = %.3g; near it %.3g, displacement %.3g cells" % (k + 1, Req, nfar, far, near, disp))
-    g1 = np.max(np.abs(ga - a)) / a.max()
-    g2 = np.max(np.abs(gb - b)) / b.max()
-    assert g1 <= 1e-5 and g2 <= 1e-5
-    for far, nfar, near, disp, _ in res:
+              "max|drho|/rho = %.3g; near it %.3g; radial shift %.3g cells, unexplained %.2f"
+              % (k + 1, Req, nfar, far, near, shift, unexp))
+    for far, nfar, near, shift, unexp, _ in res:
         assert nfar > 1000
-        assert far <= 1e-5
-        assert near <= 2e-4 and disp <= 1e-4
+        assert far <= 1e-5 and near <= 1e-5
+
+
+def test_f32_regularized_wall(gpu_lib):
+    """FP32, regularized collision, mirror wetting walls, tilted gravity: 300
+    steps: max |d rho| / rho <= 1e-5 in every cell (measured 2e-6 next to the
+    interface, 5e-7 away from it)."""
+    import oracle
+    shape = (12, 16, 16)
+    r1, r2 = wl.hemisphere(shape, 6)
+    kw = dict(tau=(0.7, 0.7), G12=-1.2, collision="regularized", periodic=(1, 1, 0),
+              g_ext=wl.tilted_gravity(1e-5, 30.0))
+    p, f_or = oracle_run(shape, r1, r2, None, 300, **kw)
+    a, b, uF = oracle.moments(p, f_or)
+    lat = gpu_run(shape, r1, r2, None, 300, storage="f32", **kw)
+    ga, gb, guF = lat.moments()
+    lat.close()
+    c = (-0.5, 7.5, 7.5)
+    res = [_interface_split(gg, o, c, (1, 1, 0), hemisphere=True) for gg, o in ((ga, a), (gb, b))]
+    for k, (far, nfar, near, shift, unexp, Req) in enumerate(res):
+        print("FP32 regularized wall 300 steps, component %d: R_eq %.2f; far (%d cells) %.3g; near %.3g; "
+              "radial shift %.3g cells, unexplained %.2f" % (k + 1, Req, nfar, far, near, shift, unexp))
+    e = max(np.max(np.abs(ga - a) / a), np.max(np.abs(gb - b) / b))
+    assert e <= 1e-5
+    assert np.max(np.abs(guF - uF)) < 2e-7
 
 
 def test_f32_mixture_1000_steps_per_cell(gpu_lib):
@@ -167,34 +195,6 @@ def test_f32_mixture_1000_steps_per_cell(gpu_lib):
     e = max(np.max(np.abs(ga - a) / a), np.max(np.abs(gb - b) / b))
     print("FP32 mixture 1000 steps: max|drho|/rho = %.3g" % e)
     assert e <= 1e-5
-
-
-def test_f32_regularized_wall(gpu_lib):
-    """FP32, regularized collision, mirror wetting walls, tilted gravity: 300
-    steps.  As for the droplet: 1e-5 per cell farther than 3 W from the
-    interface, the displacement bound near it."""
-    import oracle
-    shape = (12, 16, 16)
-    r1, r2 = wl.hemisphere(shape, 6)
-    kw = dict(tau=(0.7, 0.7), G12=-1.2, collision="regularized", periodic=(1, 1, 0),
-              g_ext=wl.tilted_gravity(1e-5, 30.0))
-    p, f_or = oracle_run(shape, r1, r2, None, 300, **kw)
-    a, b, uF = oracle.moments(p, f_or)
-    lat = gpu_run(shape, r1, r2, None, 300, storage="f32", **kw)
-    ga, gb, guF = lat.moments()
-    lat.close()
-    g = max(np.max(np.abs(ga - a)) / a.max(), np.max(np.abs(gb - b)) / b.max())
-    c = (-0.5, 7.5, 7.5)
-    res = [_interface_split(gg, o, c, (1, 1, 0), hemisphere=True) for gg, o in ((ga, a), (gb, b))]
-    for k, (far, nfar, near, disp, Req) in enumerate(res):
-        print("FP32 regularized wall 300 steps, component %d: R_eq %.2f; far (%d cells) %.3g; near %.3g, "
-              "displacement %.3g cells" % (k + 1, Req, nfar, far, near, disp))
-    assert g < 1e-5
-    for far, nfar, near, disp, _ in res:
-        assert nfar > 300
-        assert far <= 1e-5
-        assert near <= 1e-4 and disp <= 1e-4
-    assert np.max(np.abs(guF - uF)) < 2e-7
 
 
 @pytest.mark.parametrize("storage", ["f16_dev", "bf16_dev"])
@@ -333,7 +333,7 @@ FUSED_CASES = [
 ]
 
 
-@pytest.mark.parametrize("storage", ["f32", "bf16_dev"])
+@pytest.mark.parametrize("storage", ["f32", "bf16_dev", "f16_rel", "bf16_rel"])
 @pytest.mark.parametrize("name,shape,kw", FUSED_CASES, ids=[c[0] for c in FUSED_CASES])
 def test_fused_matches_split(gpu_lib, monkeypatch, name, shape, kw, storage):
     """The fused single-pass kernel performs the same arithmetic in the same
@@ -351,6 +351,10 @@ def test_fused_matches_split(gpu_lib, monkeypatch, name, shape, kw, storage):
         lat.close()
     if storage == "f32":
         assert rel_err(out["1"], out["0"]) < 1e-6
+    elif storage.endswith("_rel"):
+        # a flipped rounding of the relative deviation s changes a population
+        # by one 16-bit ulp of s times w rho~ (a fraction of the population)
+        assert np.max(np.abs(out["1"] - out["0"])) <= 2.0 ** -5 * np.abs(out["0"]).max()
     else:
         # a one-ulp FP32 difference can flip a BF16 rounding, and flips compound
         # over the steps: bound by a few BF16 ulps of the largest deviation
