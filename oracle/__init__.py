@@ -28,6 +28,7 @@ class OracleParams(ctypes.Structure):
         ("collision", ctypes.c_int),
         ("wall_model", ctypes.c_int),
         ("solid", ctypes.c_void_p),
+        ("forcing", ctypes.c_int),
     ]
 
 
@@ -66,9 +67,12 @@ def _dp(a):
 
 
 def make_params(shape, tau=(1.0, 1.0), G12=0.0, G21=None, g_ext=(0.0, 0.0, 0.0),
-                periodic=(1, 1, 1), rho_s=(0.0, 0.0), collision="bgk", wall_model="mirror", solid=None):
+                periodic=(1, 1, 1), rho_s=(0.0, 0.0), collision="bgk", wall_model="mirror", solid=None,
+                forcing="edm"):
     """shape = (nz, ny, nx).  G12/G21 are the signed G^{12}, G^{21} of Eq. 7.
-    solid: optional (nz, ny, nx) array, non-zero at solid sites."""
+    solid: optional (nz, ny, nx) array, non-zero at solid sites.  forcing:
+    "edm" (exact difference of equilibria) or "guo" (Guo, Zheng & Shi 2002
+    with the common equilibrium velocity u + g/2)."""
     nz, ny, nx = shape
     p = OracleParams()
     p.nx, p.ny, p.nz = nx, ny, nz
@@ -83,6 +87,7 @@ def make_params(shape, tau=(1.0, 1.0), G12=0.0, G21=None, g_ext=(0.0, 0.0, 0.0),
     p.rho_s[0], p.rho_s[1] = float(rho_s[0]), float(rho_s[1])
     p.collision = {"bgk": 0, "regularized": 1, "regularized3": 2}[collision]
     p.wall_model = {"potential": 0, "mirror": 1}[wall_model]
+    p.forcing = {"edm": 0, "guo": 1}[forcing]
     if solid is not None:
         m = np.ascontiguousarray(np.asarray(solid).reshape(shape) != 0, dtype=np.uint8)
         p._solid = m            # keeps the flags alive as long as the params

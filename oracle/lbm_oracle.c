@@ -26,7 +26,14 @@
  *  - The forcing term cites a reference that is not available (Sec. 2): the
  *    exact-difference form F_i = f^eq_i(rho^a, u + g^a) - f^eq_i(rho^a, u),
  *    which makes the velocity averaged over pre- and post-collision equal to
- *    u + g/2 as Eq. 8 states.
+ *    u + g/2 as Eq. 8 states (forcing = 0).  The second reading (forcing = 1)
+ *    is the scheme of Guo, Zheng & Shi, Phys. Rev. E 65, 046308 (2002),
+ *    applied per component with one common equilibrium velocity
+ *    u* = u + g/2 (Eqs. 8-9): f^eq(rho^a, u*), forcing term
+ *    (1 - 1/(2 tau)) w_i [(c_i - u*)/T0 + (c_i.u*) c_i / T0^2] . rho^a g^a for
+ *    BGK; for the regularized filter the same scheme written as
+ *    f* = f^eq + (1 - 1/tau) P[f - f^eq + F/2] + F/2, P the Hermite
+ *    projection of Eq. 11 (so Pi^neq gains (u* F + F u*) / 2).
  *  - The regularized non-equilibrium part (Eq. 11) is the second-order Hermite
  *    projection w_i/(2 T0^2) Q_i : Pi^neq, Q_i = c_i c_i - T0 I, with Pi^neq
  *    from the pre-collision populations and f^eq(rho^a, u).  Sec. 2 also
@@ -71,7 +78,13 @@ typedef struct {
     int wall_model;    /* 0 = point-wise wall potential, 1 = mirrored rho' + rho_s */
     const unsigned char *solid;  /* N flags, 1 = solid site inside the lattice
                                     (staircase walls of any shape); NULL = none */
+    int forcing;       /* 0 = exact difference of equilibria, 1 = Guo, Zheng &
+                          Shi (2002) with the half-force velocity shift */
 } oracle_params;
+
+/* Lattices below this many cells run every pass on one thread (a parallel
+ * region costs more than their work). */
+#define OMP_BIG(p) ((long)(p)->nx * (p)->ny * (p)->nz > 32768L)
 
 static int C[Q][3];
 static double W[Q];
@@ -183,7 +196,7 @@ void oracle_moments_raw(const oracle_params *p, const double *f,
 {
     build_lattice();
     long N = (long)p->nx * p->ny * p->nz;
-#pragma omp parallel for schedule(static)
+#pragma omp parallel for schedule(static) if (OMP_BIG(p))
     for (long s = 0; s < N; ++s) {
         if (p->solid && p->solid[s]) {   /* no fluid at a solid site */
             rho1[s] = rho2[s] = 0.0;
@@ -253,7 +266,7 @@ void oracle_interaction_sums(const oracle_params *p, const double *rho_b, double
                              double *S_fluid, double *S_wall)
 {
     build_lattice();
-#pragma omp parallel for schedule(static)
+#pragma omp parallel for schedule(static) if (OMP_BIG(p))
     for (int z = 0; z < p->nz; ++z)
         for (int y = 0; y < p->ny; ++y)
             for (int x = 0; x < p->nx; ++x) {
@@ -292,7 +305,7 @@ void oracle_accelerations(const oracle_params *p, const double *rho1, const doub
         Sw[b] = (double *)malloc(sizeof(double) * 3 * N);
         oracle_interaction_sums(p, rho[b], p->rho_s[b], Sf[b], Sw[b]);
     }
-#pragma omp parallel for schedule(static)
+#pragma omp parallel for schedule(static) if (OMP_BIG(p))
     for (long s = 0; s < N; ++s)
         for (int a = 0; a < 2; ++a)
             for (int d = 0; d < 3; ++d) {
@@ -309,17 +322,66 @@ void oracle_accelerations(const oracle_params *p, const double *rho1, const doub
 }
 
 /* Collision of one component at one cell, producing the post-collision
- * populations fpost (the right-hand side of Eq. 1 or of Eq. 10). */
+ * populations fpost (the right-hand side of Eq. 1 or of Eq. 10).  u is the
+ * velocity of the equilibrium: the mixture velocity of Eq. 6 for the
+ * exact-difference forcing, the common u* = u + g/2 for Guo's forcing. */
 static void collide_cell(const oracle_params *p, int a, const double fin[Q], double rho_a,
                          const double u[3], const double g_a[3], double fpost[Q])
 {
-    double feq[Q], feq_shift[Q], Fi[Q];
-    double ug[3] = {u[0] + g_a[0], u[1] + g_a[1], u[2] + g_a[2]};
-    oracle_feq(rho_a, u, feq);
-    oracle_feq(rho_a, ug, feq_shift);
-    /* forcing term: exact difference of equilibria (reading of Sec. 2) */
-    for (int i = 0; i < Q; ++i) Fi[i] = feq_shift[i] - feq[i];
+    double feq[Q], Fi[Q];
     double tau = p->tau[a];
+    oracle_feq(rho_a, u, feq);
+    if (p->forcing == 1) {
+        /* Guo, Zheng & Shi (2002): F_i = w_i [(c_i - u)/T0 + (c_i.u) c_i / T0^2] . F
+         * with the component's force F = rho^a g^a */
+        double F[3] = {rho_a * g_a[0], rho_a * g_a[1], rho_a * g_a[2]};
+        for (int i = 0; i < Q; ++i) {
+            double cu = C[i][0] * u[0] + C[i][1] * u[1] + C[i][2] * u[2];
+            double s = 0.0;
+            for (int k = 0; k < 3; ++k) s += ((C[i][k] - u[k]) / T0 + cu * C[i][k] / (T0 * T0)) * F[k];
+            Fi[i] = W[i] * s;
+        }
+        if (p->collision == 0) {
+            /* Eq. 1 with the BGK operator of Eq. 2 and Guo's forcing */
+            for (int i = 0; i < Q; ++i)
+                fpost[i] = fin[i] - (fin[i] - feq[i]) / tau + (1.0 - 1.0 / (2.0 * tau)) * Fi[i];
+            return;
+        }
+        /* Eqs. 10-11 with Guo's forcing: the non-equilibrium part filtered is
+         * f - f^eq + F/2, and F/2 is added after the collision */
+        double d[Q];
+        for (int i = 0; i < Q; ++i) d[i] = fin[i] - feq[i] + 0.5 * Fi[i];
+        double Pi[3][3] = {{0}};
+        for (int i = 0; i < Q; ++i)
+            for (int r = 0; r < 3; ++r)
+                for (int c = 0; c < 3; ++c)
+                    Pi[r][c] += C[i][r] * C[i][c] * d[i];
+        for (int i = 0; i < Q; ++i) {
+            double contr = 0.0;
+            for (int r = 0; r < 3; ++r)
+                for (int c = 0; c < 3; ++c) {
+                    double Qrc = C[i][r] * C[i][c] - (r == c ? T0 : 0.0);
+                    contr += Qrc * Pi[r][c];
+                }
+            double fneq = W[i] / (2.0 * T0 * T0) * contr;
+            fpost[i] = feq[i] + (1.0 - 1.0 / tau) * fneq + 0.5 * Fi[i];
+        }
+        if (p->collision == 2) {
+            for (int k = 0; k < N3; ++k) {
+                double coef = 0.0;
+                for (int i = 0; i < Q; ++i) coef += E3[k][i] * d[i];
+                for (int i = 0; i < Q; ++i) fpost[i] += (1.0 - 1.0 / tau) * W[i] * E3[k][i] * coef;
+            }
+        }
+        return;
+    }
+    {
+        double ug[3] = {u[0] + g_a[0], u[1] + g_a[1], u[2] + g_a[2]};
+        double feq_shift[Q];
+        oracle_feq(rho_a, ug, feq_shift);
+        /* forcing term: exact difference of equilibria (reading of Sec. 2) */
+        for (int i = 0; i < Q; ++i) Fi[i] = feq_shift[i] - feq[i];
+    }
     if (p->collision == 0) {
         /* Eq. 1 with the BGK operator of Eq. 2 */
         for (int i = 0; i < Q; ++i)
@@ -360,7 +422,7 @@ static void stream(const oracle_params *p, const double *fpost, double *fnew)
     long N = (long)p->nx * p->ny * p->nz;
     for (int a = 0; a < 2; ++a)
         for (int i = 0; i < Q; ++i)
-#pragma omp parallel for schedule(static)
+#pragma omp parallel for schedule(static) if (OMP_BIG(p))
             for (int z = 0; z < p->nz; ++z)
                 for (int y = 0; y < p->ny; ++y)
                     for (int x = 0; x < p->nx; ++x) {
@@ -390,7 +452,7 @@ void oracle_step(const oracle_params *p, double *f, double *work, long nsteps)
     for (long t = 0; t < nsteps; ++t) {
         oracle_moments_raw(p, f, rho1, rho2, u);
         oracle_accelerations(p, rho1, rho2, g1, g2);
-#pragma omp parallel for schedule(static)
+#pragma omp parallel for schedule(static) if (OMP_BIG(p))
         for (long s = 0; s < N; ++s)
             for (int a = 0; a < 2; ++a) {
                 double fin[Q], fpost[Q];
@@ -399,7 +461,11 @@ void oracle_step(const oracle_params *p, double *f, double *work, long nsteps)
                     continue;
                 }
                 for (int i = 0; i < Q; ++i) fin[i] = f[((long)a * Q + i) * N + s];
-                collide_cell(p, a, fin, a == 0 ? rho1[s] : rho2[s], &u[3 * s],
+                double ueq[3] = {u[3 * s], u[3 * s + 1], u[3 * s + 2]};
+                if (p->forcing == 1)   /* common equilibrium velocity u + g/2 (Eqs. 8-9) */
+                    for (int d = 0; d < 3; ++d)
+                        ueq[d] += (rho1[s] * g1[3 * s + d] + rho2[s] * g2[3 * s + d]) / (2.0 * (rho1[s] + rho2[s]));
+                collide_cell(p, a, fin, a == 0 ? rho1[s] : rho2[s], ueq,
                              a == 0 ? &g1[3 * s] : &g2[3 * s], fpost);
                 for (int i = 0; i < Q; ++i) work[((long)a * Q + i) * N + s] = fpost[i];
             }
@@ -414,7 +480,7 @@ void oracle_init(const oracle_params *p, const double *rho1, const double *rho2,
 {
     build_lattice();
     long N = (long)p->nx * p->ny * p->nz;
-#pragma omp parallel for schedule(static)
+#pragma omp parallel for schedule(static) if (OMP_BIG(p))
     for (long s = 0; s < N; ++s) {
         double uz[3] = {0, 0, 0};
         const double *us = u ? &u[3 * s] : uz;
@@ -437,7 +503,7 @@ void oracle_moments(const oracle_params *p, const double *f,
     double *g2 = (double *)malloc(sizeof(double) * 3 * N);
     oracle_moments_raw(p, f, rho1, rho2, u);
     oracle_accelerations(p, rho1, rho2, g1, g2);
-#pragma omp parallel for schedule(static)
+#pragma omp parallel for schedule(static) if (OMP_BIG(p))
     for (long s = 0; s < N; ++s) {
         double rho = rho1[s] + rho2[s];
         if (p->solid && p->solid[s]) { uF[3 * s] = uF[3 * s + 1] = uF[3 * s + 2] = 0.0; continue; }
@@ -450,7 +516,8 @@ void oracle_moments(const oracle_params *p, const double *f,
 }
 
 /* Post-collision populations of one cell and component, exposed so that
- * tests can check the collision alone (closed forms, invariants). */
+ * tests can check the collision alone (closed forms, invariants).  u is the
+ * equilibrium velocity (with Guo's forcing the caller passes u + g/2). */
 void oracle_collide_cell(const oracle_params *p, int a, const double fin[Q], double rho_a,
                          const double u[3], const double g_a[3], double fpost[Q])
 {
