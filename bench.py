@@ -158,7 +158,7 @@ def measured_hbm_peak():
 
 # source files that define each timed kernel (a change to any of them voids
 # the committed DRAM-traffic figure of that kernel)
-KERNEL_SOURCES = {"k_step_fused": ("d3q19.cuh", "lbm_fused.cu"),
+KERNEL_SOURCES = {"k_step_fused": ("d3q19.cuh", "lbm_fused_impl.cuh"),
                   "k_density": ("d3q19.cuh", "lbm_forward.cu"),
                   "k_collide": ("d3q19.cuh", "lbm_forward.cu")}
 

@@ -77,6 +77,19 @@ typedef enum {
                              carries (6 + 6 of them) */
 } lbm_collision;
 
+/* The forcing term of Eq. 1 (Sec. 2 cites the scheme without printing it). */
+typedef enum {
+    LBM_FORCING_EDM = 0,  /* exact difference of equilibria:
+                             F_i = f^eq_i(rho^a, u + g^a) - f^eq_i(rho^a, u), f^eq at
+                             the mixture velocity u of Eq. 6 */
+    LBM_FORCING_GUO = 1   /* Guo, Zheng & Shi (2002) per component with the common
+                             equilibrium velocity u* = u + g/2 of Eqs. 8-9:
+                             F_i = (1 - 1/(2 tau)) w_i [(c_i - u*)/T0 + (c_i.u*) c_i / T0^2]
+                             . rho^a g^a for BGK; the regularized filter keeps
+                             f^eq(u*) + (1 - 1/tau) P[f - f^eq(u*) + F/2] + F/2 with
+                             F the bracket without the tau factor */
+} lbm_forcing;
+
 /* Density a solid site presents to the interaction sum of Eq. 13. */
 typedef enum {
     LBM_WALL_POTENTIAL = 0, /* rho'_b = rho_s^b (point-wise wall potential, Sec. 4) */
@@ -100,6 +113,7 @@ typedef struct {
     int collision;         /* lbm_collision */
     int wall_model;        /* lbm_wall_model (used only when periodic[2] == 0) */
     void *stream;          /* cudaStream_t to issue work on; NULL = library-owned stream */
+    int forcing;           /* lbm_forcing */
 } lbm_params;
 
 typedef struct lbm_lattice lbm_lattice;   /* opaque handle */
@@ -228,7 +242,8 @@ lbm_status lbm_sync(lbm_lattice *h);
  * segment of states and of their densities); both are held until the next
  * lbm_record or lbm_destroy, so that lbm_adjoint allocates nothing.
  * Synchronizes.  Errors: LBM_EINVAL, LBM_ENOMEM, LBM_ECUDA, LBM_ENOTSUP
- * (a lattice with a solid mask, which has no reverse pass). */
+ * (a lattice with a solid mask or with Guo forcing, which have no reverse
+ * pass). */
 lbm_status lbm_record(lbm_lattice *h, long n_steps, int ckpt_every);
 
 /* Reverse pass over the last lbm_record.  Inputs dL_drho1, dL_drho2: N values
@@ -244,7 +259,7 @@ lbm_status lbm_record(lbm_lattice *h, long n_steps, int ckpt_every);
  * lattice state at the end of the recorded run.
  * Synchronizes.  Errors: LBM_EINVAL (no recording), LBM_ENOTSUP
  * (initial-density gradient requested for a recording that did not start at
- * rest from lbm_init_fields, or a lattice of more than 2^32 cells),
+ * rest from lbm_init_fields, or a lattice with 19 N >= 2^32 cells),
  * LBM_ENOMEM, LBM_ECUDA. */
 lbm_status lbm_adjoint(lbm_lattice *h, const double *dL_drho1, const double *dL_drho2, int on_device,
                        double *dL_drho1_0, double *dL_drho2_0, double dL_dparams[4]);
@@ -260,8 +275,9 @@ lbm_status lbm_adjoint(lbm_lattice *h, const double *dL_drho1, const double *dL_
  *
  * It advances the state in f_in by one step into f_out with the two-kernel
  * step (density pass, then force + collision + streaming).  f_in and f_out are
- * distinct caller-owned device buffers in the raw state format (the layout
- * lbm_get_state writes; lbm_state_bytes of a lattice with the same params).
+ * caller-owned device buffers in the raw state format (the layout
+ * lbm_get_state writes; lbm_state_bytes of a lattice with the same params)
+ * that must not overlap (LBM_EINVAL otherwise).
  * *params is validated as by lbm_create, except that params->stream = NULL
  * means the default stream.  No handle is created and nothing is allocated:
  * the density scratch is a static device array of 32 MiB built into the
@@ -272,9 +288,12 @@ lbm_status lbm_adjoint(lbm_lattice *h, const double *dL_drho1, const double *dL_
  * the collision reads it, so nothing needs clearing between calls, but every
  * call shares it: calls whose work overlaps on the GPU (other streams, other
  * host threads) race and must be serialised by the caller.  The first call on
- * a device looks up the scratch's device address (set-up); make that first
- * call before any stream capture.  Asynchronous on the stream; errors:
- * LBM_EINVAL, LBM_ENOTSUP, LBM_ECUDA. */
+ * a device looks up the scratch's device address (set-up); with lazy module
+ * loading that lookup also loads the library's device code and makes the
+ * 32 MiB array resident on the device, which is an allocation by the CUDA
+ * runtime.  A caller whose policy forbids any allocation while stepping, or
+ * that captures streams, makes that first call during set-up.  Asynchronous
+ * on the stream; errors: LBM_EINVAL, LBM_ENOTSUP, LBM_ECUDA. */
 lbm_status lbm_step_noalloc(const lbm_params *params, const void *f_in, void *f_out);
 
 /* Release every resource of the handle.  NULL-safe. */

@@ -19,6 +19,7 @@ STATUS_NAMES = {0: "LBM_OK", 1: "LBM_EINVAL", 2: "LBM_ENOMEM", 3: "LBM_ECUDA",
 STORAGE = {"f64": 0, "f32": 1, "f16_dev": 2, "bf16_dev": 3, "f16_rel": 4, "bf16_rel": 5}
 COLLISION = {"bgk": 0, "regularized": 1, "regularized3": 2}
 WALL_MODEL = {"potential": 0, "mirror": 1}
+FORCING = {"edm": 0, "guo": 1}
 
 
 class lbm_params(ctypes.Structure):
@@ -34,6 +35,7 @@ class lbm_params(ctypes.Structure):
         ("collision", ctypes.c_int),
         ("wall_model", ctypes.c_int),
         ("stream", ctypes.c_void_p),
+        ("forcing", ctypes.c_int),
     ]
 
 

@@ -332,18 +332,101 @@ __device__ __forceinline__ R cdot(int i, R ux, R uy, R uz)
     return r;
 }
 
+// Forcing schemes of the Sec. 2 forcing term (the paper cites the scheme
+// without printing it; two readings are built):
+//   FORCE_EDM: exact difference of equilibria, F_i = f^eq_i(rho, u + g) - f^eq_i(rho, u),
+//              f^eq at the mixture velocity u of Eq. 6;
+//   FORCE_GUO: Guo, Zheng & Shi (2002), per component with the common
+//              equilibrium velocity u* = u + g/2 of Eqs. 8-9 and
+//              F_i = w_i [(c_i - u*)/T0 + (c_i.u*) c_i / T0^2] . rho g.
+enum ForcingKind { FORCE_EDM = 0, FORCE_GUO = 1 };
+
 // Collision of one component in place: f[] holds the pre-collision f_i^a and
-// receives the post-collision f*_i^a (Eq. 1 with Eq. 2, or Eq. 10), including
-// the forcing term F_i = f^eq_i(rho, u + g) - f^eq_i(rho, u).
+// receives the post-collision f*_i^a (Eq. 1 with Eq. 2, or Eq. 10).
+// Exact-difference forcing (FORCE = FORCE_EDM; u = mixture velocity, g = g^a):
 //   BGK (REG = 0):         f* = f^eq(u + g) + (1 - 1/tau) (f - f^eq(u))
 //   regularized (REG = 1): f* = f^eq(u + g) + (1 - 1/tau) w_i/(2 T0^2) Q_i : Pi^neq,
 //                 Pi^neq = sum_i c_i c_i f_i - rho (T0 I + u u);
 //                 w_i/(2 T0^2) = k_i / 8 and Q_i : Pi = c_i c_i : Pi - tr(Pi)/3.
 //   REG = 2: the regularized f^neq plus its third-order part (struct Third).
-template <class R, int REG>
+// Guo forcing (FORCE = FORCE_GUO; u = u* = u + g/2 of the mixture, g = g^a):
+//   BGK:         f* = f^eq(u*) + (1 - 1/tau) (f - f^eq(u*)) + (1 - 1/(2 tau)) F
+//   regularized: f* = f^eq(u*) + (1 - 1/tau) P[f - f^eq(u*) + F/2] + F/2, P the
+//                projection above (Pi^neq gains (u* F + F u*)/2, the second
+//                moment of F/2; F has no third-order part).
+template <class R, int REG, int FORCE = FORCE_EDM>
 __device__ __forceinline__ void collide(R (&f)[Q], R rho, R ux, R uy, R uz,
                                         R gx, R gy, R gz, R omega)
 {
+    if (FORCE == FORCE_GUO) {
+        const R usq = ux * ux + uy * uy + uz * uz;
+        const R keep = R(1) - omega;
+        const R rq = rho / R(36);
+        const R Fx = rho * gx, Fy = rho * gy, Fz = rho * gz;
+        const R uF = ux * Fx + uy * Fy + uz * Fz;
+        const R cf = REG ? R(0.5) : R(1) - R(0.5) * omega;   // weight of the forcing term
+        // F_i = (k_i / 36) (even_i +- odd_i): even = 9 (c.u)(c.F) - 3 u.F, odd = 3 c.F
+        R pxx = 0, pyy = 0, pzz = 0, pxy = 0, pxz = 0, pyz = 0, t = 0;
+        Third<R> th;
+        if (REG) {
+#pragma unroll
+            for (int i = 1; i < Q; ++i) {
+                const R v = f[i];
+                if (cx(i)) pxx += v;
+                if (cy(i)) pyy += v;
+                if (cz(i)) pzz += v;
+                if (cx(i) && cy(i)) { if (cx(i) == cy(i)) pxy += v; else pxy -= v; }
+                if (cx(i) && cz(i)) { if (cx(i) == cz(i)) pxz += v; else pxz -= v; }
+                if (cy(i) && cz(i)) { if (cy(i) == cz(i)) pyz += v; else pyz -= v; }
+            }
+            const R T0 = R(1) / R(3);
+            // Pi of f - f^eq(u*) + F/2
+            pxx += -rho * (T0 + ux * ux) + ux * Fx;
+            pyy += -rho * (T0 + uy * uy) + uy * Fy;
+            pzz += -rho * (T0 + uz * uz) + uz * Fz;
+            pxy += -rho * ux * uy + R(0.5) * (ux * Fy + uy * Fx);
+            pxz += -rho * ux * uz + R(0.5) * (ux * Fz + uz * Fx);
+            pyz += -rho * uy * uz + R(0.5) * (uy * Fz + uz * Fy);
+            t = (pxx + pyy + pzz) / R(3);
+            if (REG == 2) {
+                th.zero();
+#pragma unroll
+                for (int i = 1; i < Q; ++i) th.add(i, f[i]);
+                th.finish(rho, ux, uy, uz);
+            }
+        }
+        {
+            const R e0 = rq * R(12) * (R(1) - R(1.5) * usq);
+            const R F0 = R(12) / R(36) * (R(-3) * uF);
+            f[0] = REG ? e0 + keep * (R(-1.5) * t) + cf * F0 : e0 + keep * (f[0] - e0) + cf * F0;
+        }
+#pragma unroll
+        for (int i = 1; i < Q; i += 2) {
+            const R cu = cdot<R>(i, ux, uy, uz);
+            const R cF = cdot<R>(i, Fx, Fy, Fz);
+            R ep, em;
+            feq_pair<R>(rq * R(k36(i)), cu, usq, ep, em);
+            const R kq = R(k36(i)) / R(36);
+            const R Fe = kq * (R(9) * cu * cF - R(3) * uF), Fo = kq * (R(3) * cF);
+            if (!REG) {
+                f[i] = ep + keep * (f[i] - ep) + cf * (Fe + Fo);
+                f[i + 1] = em + keep * (f[i + 1] - em) + cf * (Fe - Fo);
+            } else {
+                R cc = R(0);
+                if (cx(i)) cc += pxx;
+                if (cy(i)) cc += pyy;
+                if (cz(i)) cc += pzz;
+                if (cx(i) && cy(i)) cc += (cx(i) == cy(i) ? R(2) : R(-2)) * pxy;
+                if (cx(i) && cz(i)) cc += (cx(i) == cz(i) ? R(2) : R(-2)) * pxz;
+                if (cy(i) && cz(i)) cc += (cy(i) == cz(i) ? R(2) : R(-2)) * pyz;
+                const R fneq = R(k36(i)) * R(0.125) * (cc - t);
+                const R f3 = REG == 2 ? th.odd(i) : R(0);
+                f[i] = ep + keep * (fneq + f3) + cf * (Fe + Fo);
+                f[i + 1] = em + keep * (fneq - f3) + cf * (Fe - Fo);
+            }
+        }
+        return;
+    }
     const R usq = ux * ux + uy * uy + uz * uz;
     const R vx = ux + gx, vy = uy + gy, vz = uz + gz;
     const R vsq = vx * vx + vy * vy + vz * vz;

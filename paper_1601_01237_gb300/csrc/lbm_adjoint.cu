@@ -86,10 +86,13 @@ __device__ __forceinline__ void adj_half(const typename Store<S>::T *__restrict_
                                          const typename Store<S>::R *__restrict__ Dn,
                                          typename Store<S>::R *__restrict__ lam_loc, typename Store<S>::R *__restrict__ aout,
                                          const Phys<typename Store<S>::R> &p, const Nb &n, int a, bool store,
-                                         double &par_g, double &par_t)
+                                         typename Store<S>::R &par_g, typename Store<S>::R &par_t)
 {
     using R = typename Store<S>::R;
     const long long N = p.N;
+    // element offsets inside one component's 19 arrays fit 32 bits (19 N < 2^32,
+    // checked on the host): one 32-bit multiply-add per access
+    const unsigned N32 = (unsigned)N;
     const unsigned full = 0xffffffffu;
     // ---- forward recomputation ------------------------------------------
     R fa[Q];
@@ -101,16 +104,18 @@ __device__ __forceinline__ void adj_half(const typename Store<S>::T *__restrict_
 #pragma unroll
     for (int i = 0; i < Q; ++i) {
         const bool wall = (cz(i) == 1 && n.zlo) || (cz(i) == -1 && n.zhi);
-        const long long idx = (wall ? pair_index(opp(i), n.cell, N) : pair_index(i, at(n, -cx(i), -cy(i), -cz(i)), N)) + a;
-        fa[i] = Store<S>::load(f + idx, w<R>(i) * rref);
+        const unsigned e = wall ? (unsigned)opp(i) * N32 + n.cell : (unsigned)i * N32 + at(n, -cx(i), -cy(i), -cz(i));
+        fa[i] = Store<S>::load(f + a + 2 * (size_t)e, w<R>(i) * rref);
     }
     R ra = 0, jx = 0, jy = 0, jz = 0;
 #pragma unroll
-    for (int i = 0; i < Q; ++i) {
-        ra += fa[i];
-        if (cx(i) == 1) jx += fa[i]; else if (cx(i) == -1) jx -= fa[i];
-        if (cy(i) == 1) jy += fa[i]; else if (cy(i) == -1) jy -= fa[i];
-        if (cz(i) == 1) jz += fa[i]; else if (cz(i) == -1) jz -= fa[i];
+    for (int i = 0; i < Q; ++i) ra += fa[i];
+#pragma unroll
+    for (int i = 1; i < Q; i += 2) {   // opposite pairs: f_i - f_opp(i) first
+        const R d = fa[i] - fa[i + 1];
+        if (cx(i) == 1) jx += d; else if (cx(i) == -1) jx -= d;
+        if (cy(i) == 1) jy += d; else if (cy(i) == -1) jy -= d;
+        if (cz(i) == 1) jz += d; else if (cz(i) == -1) jz -= d;
     }
     // mixture density and momentum: both lanes of the pair form the same sums
     const R rt = ra + __shfl_xor_sync(full, ra, 16);
@@ -182,12 +187,16 @@ __device__ __forceinline__ void adj_half(const typename Store<S>::T *__restrict_
     }
     // ---- incoming sensitivities ---------------------------------------------
     R mu[Q];
+    {
+        const R *lam_a = lam_next + (size_t)a * Q * (size_t)N;
+        const R *D_a = Dn + (size_t)a * (size_t)N;
 #pragma unroll
-    for (int i = 0; i < Q; ++i) {
-        const bool wall = (cz(i) == -1 && n.zlo) || (cz(i) == 1 && n.zhi);
-        const unsigned cell = wall ? n.cell : at(n, cx(i), cy(i), cz(i));
-        const int d = wall ? opp(i) : i;
-        mu[i] = lam_next[(long long)(a * Q + d) * N + cell] + Dn[(long long)a * N + cell];
+        for (int i = 0; i < Q; ++i) {
+            const bool wall = (cz(i) == -1 && n.zlo) || (cz(i) == 1 && n.zhi);
+            const unsigned cell = wall ? n.cell : at(n, cx(i), cy(i), cz(i));
+            const unsigned d = wall ? (unsigned)opp(i) : (unsigned)i;
+            mu[i] = lam_a[d * N32 + cell] + D_a[cell];
+        }
     }
     // ---- reverse pass -------------------------------------------------------
     // BGK:         f* = E(rho, v) + keep (f - E(rho, u))
@@ -308,7 +317,7 @@ __device__ __forceinline__ void adj_half(const typename Store<S>::T *__restrict_
     const R jb0 = U0 / rt, jb1 = U1 / rt, jb2 = U2 / rt;
     const R base = rbar - (U0 * u0 + U1 * u1 + U2 * u2) / rt;
     if (store) {
-        R *lo = lam_loc + (long long)a * Q * N + n.cell;
+        R *lo = lam_loc + (size_t)a * Q * (size_t)N + n.cell;
 #pragma unroll
         for (int i = 0; i < Q; ++i) {
             R l = base + cdot<R>(i, jb0, jb1, jb2);
@@ -326,15 +335,15 @@ __device__ __forceinline__ void adj_half(const typename Store<S>::T *__restrict_
                     }
                 }
             }
-            lo[(long long)i * N] = l;
+            lo[(unsigned)i * N32] = l;
         }
         // g^a = G^{ab} S^b + g_ext:  dL/dS^b = G^{ab} vbar,  dL/dG^{ab} = vbar . S^b
         aout[((long long)b * 3 + 0) * N + n.cell] = Ga * vbar0;
         aout[((long long)b * 3 + 1) * N + n.cell] = Ga * vbar1;
         aout[((long long)b * 3 + 2) * N + n.cell] = Ga * vbar2;
-        par_g += (double)(vbar0 * Sb0 + vbar1 * Sb1 + vbar2 * Sb2);
+        par_g += vbar0 * Sb0 + vbar1 * Sb1 + vbar2 * Sb2;
         // keep = 1 - 1/tau: dkeep/dtau = 1/tau^2
-        par_t += (double)(Kbar * omega * omega);
+        par_t += Kbar * omega * omega;
     }
 }
 
@@ -352,7 +361,10 @@ k_adj_local(const typename Store<S>::T *__restrict__ f, const typename Store<S>:
     const int a = lane >> 4;
     const long long warps = (long long)gridDim.x * (kThreadsA / 32);
     const long long groups = (p.N + 15) / 16;
-    double pg = 0, pt = 0;
+    // per-thread partials in the arithmetic type over the thread's cells (a few
+    // tens per step), summed in FP64 across the block: the FP64 pipe is a
+    // small fraction of the FP32 one on this GPU
+    typename Store<S>::R pg = 0, pt = 0;
     for (long long wg = (long long)blockIdx.x * (kThreadsA / 32) + (threadIdx.x >> 5); wg < groups; wg += warps) {
         const long long c = wg * 16 + (lane & 15);
         const bool valid = c < p.N;

@@ -158,6 +158,8 @@ lbm_status lbm_create(const lbm_params *pp, lbm_lattice **out)
         return fail(LBM_EINVAL, "lbm_create: unknown collision %d", p.collision);
     if (p.wall_model != LBM_WALL_POTENTIAL && p.wall_model != LBM_WALL_MIRROR)
         return fail(LBM_EINVAL, "lbm_create: unknown wall model %d", p.wall_model);
+    if (p.forcing != LBM_FORCING_EDM && p.forcing != LBM_FORCING_GUO)
+        return fail(LBM_EINVAL, "lbm_create: unknown forcing %d", p.forcing);
     for (int d = 0; d < 3; ++d)
         if (p.periodic[d] != 0 && p.periodic[d] != 1)
             return fail(LBM_EINVAL, "lbm_create: periodic[%d] must be 0 or 1", d);
@@ -173,6 +175,7 @@ lbm_status lbm_create(const lbm_params *pp, lbm_lattice **out)
     ph.wall_mirror = p.wall_model == LBM_WALL_MIRROR;
     ph.storage = p.storage;
     ph.collision = p.collision;
+    ph.forcing = p.forcing;
     ph.tau[0] = p.tau[0]; ph.tau[1] = p.tau[1];
     ph.G12 = p.G[0][1]; ph.G21 = p.G[1][0];
     for (int d = 0; d < 3; ++d) ph.gext[d] = p.g_ext[d];
@@ -642,6 +645,8 @@ lbm_status lbm_record(lbm_lattice *h, long n_steps, int ckpt_every)
     if (n_steps < 1 || ckpt_every < 1)
         return fail(LBM_EINVAL, "lbm_record: n_steps = %ld and ckpt_every = %d must be >= 1", n_steps, ckpt_every);
     if (h->solid) return fail(LBM_ENOTSUP, "lbm_record: lattices with a solid mask have no reverse pass");
+    if (h->phys.forcing != LBM_FORCING_EDM)
+        return fail(LBM_ENOTSUP, "lbm_record: the reverse pass differentiates the exact-difference forcing only");
     DeviceGuard g(h->device);
     size_t sb = 0;
     lbm_state_bytes(h, &sb);
@@ -690,7 +695,8 @@ lbm_status lbm_adjoint(lbm_lattice *h, const double *dL_drho1, const double *dL_
     if ((dL_drho1_0 || dL_drho2_0) && !h->rec_at_rest)
         return fail(LBM_ENOTSUP, "lbm_adjoint: initial-density gradients need a recording that starts at rest "
                                  "right after lbm_init_fields(u = NULL)");
-    if (h->phys.N > 0xffffffffLL) return fail(LBM_ENOTSUP, "lbm_adjoint: more than 2^32 cells");
+    if ((long long)lbm::Q * h->phys.N > 0xffffffffLL)
+        return fail(LBM_ENOTSUP, "lbm_adjoint: 19 N must stay below 2^32 (N <= 226,050,910 cells)");
     DeviceGuard g(h->device);
     const size_t N = (size_t)h->phys.N;
     const size_t rb = lbm::real_bytes(h->phys.storage);
@@ -852,6 +858,15 @@ lbm_status lbm_step_noalloc(const lbm_params *pp, const void *f_in, void *f_out)
         return fail(LBM_EINVAL, "lbm_step_noalloc: unknown collision %d", p.collision);
     if (p.wall_model != LBM_WALL_POTENTIAL && p.wall_model != LBM_WALL_MIRROR)
         return fail(LBM_EINVAL, "lbm_step_noalloc: unknown wall model %d", p.wall_model);
+    if (p.forcing != LBM_FORCING_EDM && p.forcing != LBM_FORCING_GUO)
+        return fail(LBM_EINVAL, "lbm_step_noalloc: unknown forcing %d", p.forcing);
+    {
+        // the step reads all of f_in while it writes f_out: the two states must not overlap
+        const size_t sb = lbm::state_bytes(p.storage, N);
+        const char *a0 = (const char *)f_in, *b0 = (const char *)f_out;
+        if (a0 < b0 + sb && b0 < a0 + sb)
+            return fail(LBM_EINVAL, "lbm_step_noalloc: f_in and f_out overlap (each state is %zu bytes)", sb);
+    }
     for (int d = 0; d < 3; ++d)
         if (p.periodic[d] != 0 && p.periodic[d] != 1)
             return fail(LBM_EINVAL, "lbm_step_noalloc: periodic[%d] must be 0 or 1", d);
@@ -863,6 +878,7 @@ lbm_status lbm_step_noalloc(const lbm_params *pp, const void *f_in, void *f_out)
     ph.wall_mirror = p.wall_model == LBM_WALL_MIRROR;
     ph.storage = p.storage;
     ph.collision = p.collision;
+    ph.forcing = p.forcing;
     ph.tau[0] = p.tau[0]; ph.tau[1] = p.tau[1];
     ph.G12 = p.G[0][1]; ph.G21 = p.G[1][0];
     for (int d = 0; d < 3; ++d) ph.gext[d] = p.g_ext[d];

@@ -226,7 +226,7 @@ k_link_flags(const unsigned char *__restrict__ solid, unsigned *__restrict__ lin
     links[n.cell] = f;
 }
 
-template <int S, int REG>
+template <int S, int REG, int FORCE>
 __global__ void __launch_bounds__(kThreads)
 k_collide(const typename Store<S>::T *__restrict__ fin, typename Store<S>::T *__restrict__ fout,
           const typename Store<S>::R *__restrict__ rho, PhysF<typename Store<S>::R> p)
@@ -252,8 +252,14 @@ k_collide(const typename Store<S>::T *__restrict__ fin, typename Store<S>::T *__
             g1z = p.G12 * Sb[1][2] + p.gext[2];
     const R g2x = p.G21 * Sb[0][0] + p.gext[0], g2y = p.G21 * Sb[0][1] + p.gext[1],
             g2z = p.G21 * Sb[0][2] + p.gext[2];
-    collide<R, REG>(fa[0], r1, ux, uy, uz, g1x, g1y, g1z, p.omega[0]);
-    collide<R, REG>(fa[1], r2, ux, uy, uz, g2x, g2y, g2z, p.omega[1]);
+    if (FORCE == FORCE_GUO) {   // common equilibrium velocity u* = u + g/2 (Eqs. 8-9)
+        const R hi = R(0.5) / (r1 + r2);
+        ux += (r1 * g1x + r2 * g2x) * hi;
+        uy += (r1 * g1y + r2 * g2y) * hi;
+        uz += (r1 * g1z + r2 * g2z) * hi;
+    }
+    collide<R, REG, FORCE>(fa[0], r1, ux, uy, uz, g1x, g1y, g1z, p.omega[0]);
+    collide<R, REG, FORCE>(fa[1], r2, ux, uy, uz, g2x, g2y, g2z, p.omega[1]);
     if constexpr (Store<S>::kRel) {
         // each population coded relative to the density of the cell that reads
         // it next (x + c_i, or x itself across a wall); the cell's own pair is
@@ -522,12 +528,14 @@ cudaError_t step_split_t(const HostPhys &h, const void *fin, void *fout, void *r
     if (ev) cudaEventRecord(ev[0], s);
     density_pass<S>(h, (const T *)fin, (R *)rho, s);
     if (ev) cudaEventRecord(ev[1], s);
-    if (h.collision == LBM_REGULARIZED)
-        k_collide<S, 1><<<g, kThreads, 0, s>>>((const T *)fin, (T *)fout, (const R *)rho, p);
-    else if (h.collision == LBM_REGULARIZED3)
-        k_collide<S, 2><<<g, kThreads, 0, s>>>((const T *)fin, (T *)fout, (const R *)rho, p);
-    else
-        k_collide<S, 0><<<g, kThreads, 0, s>>>((const T *)fin, (T *)fout, (const R *)rho, p);
+#define LBM_COLLIDE(REG_, F_) k_collide<S, REG_, F_><<<g, kThreads, 0, s>>>((const T *)fin, (T *)fout, (const R *)rho, p)
+    const int reg = h.collision == LBM_REGULARIZED ? 1 : (h.collision == LBM_REGULARIZED3 ? 2 : 0);
+    if (h.forcing == FORCE_GUO) {
+        if (reg == 1) LBM_COLLIDE(1, FORCE_GUO); else if (reg == 2) LBM_COLLIDE(2, FORCE_GUO); else LBM_COLLIDE(0, FORCE_GUO);
+    } else {
+        if (reg == 1) LBM_COLLIDE(1, FORCE_EDM); else if (reg == 2) LBM_COLLIDE(2, FORCE_EDM); else LBM_COLLIDE(0, FORCE_EDM);
+    }
+#undef LBM_COLLIDE
     if (ev) cudaEventRecord(ev[2], s);
     return cudaGetLastError();
 }

@@ -16,6 +16,7 @@ struct HostPhys {
     int wall_mirror;
     int storage;
     int collision;
+    int forcing = 0;   // lbm_forcing (0 exact difference, 1 Guo)
     double tau[2];
     double G12, G21;
     double gext[3];

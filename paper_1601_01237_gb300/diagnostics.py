@@ -193,3 +193,25 @@ def spinodal_stats(rho1, rho2):
     return {"mass1": float(a.sum()), "mass2": float(b.sum()), "mean_abs_phi": float(np.abs(phi).mean()),
             "k_star": float((k * S).sum() / S.sum()), "k_peak": int(k[int(np.argmax(S))]),
             "interface_area": area}
+
+
+def mass_radius(rho, center, r_in, r_out, dims=2):
+    """Radius of a droplet of the component with density field rho from its
+    excess mass, a continuous measure (the count of cells above a threshold
+    jumps by whole rings of cells): with rho_in, rho_out the mean densities
+    over r < r_in and r > r_out around center = (x, y, z) (minimum image),
+    the droplet holds (sum rho - rho_out N) / (rho_in - rho_out) cells of
+    interior density, a disc (dims = 2, nz = 1) or sphere of that area or
+    volume.  Returns (R, rho_in, rho_out)."""
+    a = np.asarray(rho, dtype=float)
+    nz, ny, nx = a.shape
+    z, y, x = np.meshgrid(np.arange(nz), np.arange(ny), np.arange(nx), indexing="ij")
+
+    def mi(d, n):
+        return (d + n / 2.0) % n - n / 2.0
+    dz = mi(z - center[2], nz) if dims == 3 else 0.0
+    r = np.sqrt(mi(x - center[0], nx) ** 2 + mi(y - center[1], ny) ** 2 + dz ** 2)
+    rin, rout = float(a[r < r_in].mean()), float(a[r > r_out].mean())
+    vol = (a.sum() - rout * a.size) / (rin - rout)
+    R = math.sqrt(vol / math.pi) if dims == 2 else (3.0 * vol / (4.0 * math.pi)) ** (1.0 / 3.0)
+    return R, rin, rout

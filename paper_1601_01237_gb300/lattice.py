@@ -189,9 +189,10 @@ def lbm_destroy(h):
 
 def make_params(shape, tau=(1.0, 1.0), G12=0.0, G21=None, g_ext=(0.0, 0.0, 0.0), periodic=(1, 1, 1),
                 rho_s=(0.0, 0.0), rho0_dev=0.0, storage="f32", collision="bgk", wall_model="mirror",
-                stream=None):
+                stream=None, forcing="edm"):
     """lbm_params for a lattice of shape (nz, ny, nx).  G12, G21 are the signed
-    G^{12}, G^{21} of Eq. 7 (G21 defaults to G12)."""
+    G^{12}, G^{21} of Eq. 7 (G21 defaults to G12).  forcing: "edm" (exact
+    difference of equilibria) or "guo" (Guo, Zheng & Shi 2002)."""
     nz, ny, nx = shape
     p = nat.lbm_params()
     p.nx, p.ny, p.nz = int(nx), int(ny), int(nz)
@@ -208,6 +209,7 @@ def make_params(shape, tau=(1.0, 1.0), G12=0.0, G21=None, g_ext=(0.0, 0.0, 0.0),
     p.storage = nat.STORAGE[storage]
     p.collision = nat.COLLISION[collision]
     p.wall_model = nat.WALL_MODEL[wall_model]
+    p.forcing = nat.FORCING[forcing]
     # A handle of 0 is the legacy default stream (torch's default stream);
     # the C ABI reserves NULL for "library-owned stream", so pass the
     # runtime's explicit legacy-stream handle instead.

@@ -75,21 +75,24 @@ def run_c0(steps=None):
             "MLUPS": np.prod(shape) * steps / dt / 1e6}
 
 
-def run_c1(steps=None, radii=None, taus=None, shape=None, storage=None):
+def run_c1(steps=None, radii=None, taus=None, shape=None, storage=None, forcing="edm"):
     c = wl.CONFIGS["c1_droplet3d_f32"]
     steps = steps or c["steps"]
     shape = tuple(shape or c["shape"])
     storage = storage or c["storage"]
     radii = radii or c["radii"]
     taus = taus or c["taus"]
-    G = c["G"]
-    out = {"case": "c1", "steps": steps, "shape": shape, "storage": storage, "G_eq7": G, "fits": {}}
+    G = wl.g_droplet(forcing)
+    out = {"case": "c1", "steps": steps, "shape": shape, "storage": storage, "G_eq7": G, "forcing": forcing,
+           "fits": {}}
     ctr = ((shape[2] - 1) / 2.0, (shape[1] - 1) / 2.0, (shape[0] - 1) / 2.0)
     for tau in taus:
-        col = c["collision_for_tau"].get(tau, "regularized")
-        Rs, dps, spur, diverged = [], [], [], []
+        # Guo forcing: the regularized operator at every tau (at tau = 1 it
+        # equals BGK); exact difference: BGK at tau = 1, regularized below
+        col = "regularized" if forcing == "guo" else c["collision_for_tau"].get(tau, "regularized")
+        Rs, dps, spur, diverged, Rm = [], [], [], [], []
         for R0 in radii:
-            lat = Lattice(shape, storage=storage, tau=(tau, tau), G12=G, collision=col)
+            lat = Lattice(shape, storage=storage, tau=(tau, tau), G12=G, collision=col, forcing=forcing)
             r1, r2 = wl.droplet(shape, R0)
             lat.init_fields(r1, r2)
             lat.step(steps)
@@ -101,14 +104,18 @@ def run_c1(steps=None, radii=None, taus=None, shape=None, storage=None):
                 continue
             _, _, dp = lat.pressure_jump(ctr, R0 / 2.0, R0 + 8.0)
             st = lat.droplet_stats(0.5 * (1.0 + 0.03), origin=ctr)
+            a, _, _ = lat.moments(out_f64=False)
             spur.append(red["max_uF"])
             lat.close()
             Rs.append(dg.equivalent_radius(st["volume"], False))
+            Rm.append(dg.mass_radius(a, ctr, R0 / 2.0, R0 + 8.0, dims=3)[0])
             dps.append(dp)
-        fit = {"collision": col, "R": Rs, "delta_p": dps, "spurious_max_uF": spur, "diverged_R0": diverged}
+        fit = {"collision": col, "R": Rs, "R_mass": Rm, "delta_p": dps, "spurious_max_uF": spur,
+               "diverged_R0": diverged}
         if len(Rs) >= 2:
             sigma, icpt, res = dg.laplace_fit(Rs, dps, dims=3)
-            fit.update(sigma=sigma, intercept=icpt, max_residual=res)
+            fit.update(sigma=sigma, intercept=icpt, max_residual=res,
+                       sigma_mass_radius=dg.laplace_fit(Rm, dps, dims=3)[0])
         out["fits"][str(tau)] = fit
     return out
 
@@ -162,18 +169,23 @@ def run_c3(steps=None):
             "adjoint_forward_ratio": t_a / t_f}
 
 
-def run_c4(steps=None, shape=None, gravity=False, wall_model="mirror"):
+def run_c4(steps=None, shape=None, gravity=False, wall_model="mirror", forcing="edm"):
     """Wall-attached droplet.  No body force by default (the paper's inclined-
     wall test has none); gravity=True adds g_mag_tilted rotated by tilt_deg,
     which in a channel periodic along x drives a bulk Poiseuille flow that
-    carries the droplet."""
-    c = wl.CONFIGS["c4_wall512"]
+    carries the droplet.  With the exact-difference forcing no droplet holds
+    at tau = 0.55 at the droplet G, so the case runs at G = -1.2 from that G's
+    coexistence densities; with Guo's forcing it runs as configured, a
+    1.0 / 0.03 hemisphere at G = -3.6 (coexistence 1.047 / 0.019)."""
+    c = dict(wl.CONFIGS["c4_wall512"])
+    if forcing == "guo":
+        c.update(G=wl.G_DROPLET_GUO, rho_in=1.0, rho_out=0.03)
     steps = steps or c["steps"]
     shape = tuple(shape or c["shape"])
     g = wl.tilted_gravity(c["g_mag_tilted"] if gravity else c["g_mag"], c["tilt_deg"])
     R = c["R"] * shape[2] / c["shape"][2]
     lat = Lattice(shape, storage=c["storage"], tau=c["tau"], G12=c["G"], collision=c["collision"],
-                  periodic=c["periodic"], g_ext=g, wall_model=wall_model)
+                  periodic=c["periodic"], g_ext=g, wall_model=wall_model, forcing=forcing)
     r1, r2 = wl.hemisphere(shape, R, rho_in=c["rho_in"], rho_out=c["rho_out"])
     lat.init_fields(r1, r2)
     nz, ny, nx = shape
@@ -191,6 +203,7 @@ def run_c4(steps=None, shape=None, gravity=False, wall_model="mirror"):
     lat.close()
     v = dg.drift_velocity(s_a["com"], s_b["com"], steps - t_a)
     return {"case": "c4", "steps": steps, "shape": shape, "R": R, "g_ext": g, "wall_model": wall_model,
+            "forcing": forcing, "G_eq7": c["G"],
             "MLUPS": np.prod(shape) * steps / dt / 1e6,
             "HBM_GBs_algorithmic": np.prod(shape) * steps * 304 / dt / 1e9,
             "drift_velocity": v.tolist(), "film_rho1": s_b["film_rho"], "bulk_minority_rho1": c["rho_out"],
@@ -199,21 +212,24 @@ def run_c4(steps=None, shape=None, gravity=False, wall_model="mirror"):
 
 
 def run_s1(steps=None, radii=(8, 12, 16, 24), taus=(0.7, 0.8, 1.0, 1.5, 2.0, 3.0),
-           collisions=("bgk", "regularized"), storage="f32"):
+           collisions=("bgk", "regularized"), storage="f32", forcing="edm"):
     """The paper's static-droplet study (Sec. 3): quasi-2D droplets on square
     periodic domains of side 5 R, the surface tension from Delta p = sigma / R
     (Eq. 12) per tau, for BGK and the regularized operator, and the largest
-    spurious velocity.  G = -1.8, 1.0 / 0.03 start (coexistence)."""
+    spurious velocity.  G = -1.8 (exact-difference forcing) or -3.6 (Guo's
+    forcing), 1.0 / 0.03 start (near coexistence).  sigma is fitted with the
+    equivalent radius of the cells above the mid density and with the
+    continuous excess-mass radius."""
     steps = steps or 20000
-    G = wl.G_DROPLET
-    out = {"case": "s1", "steps": steps, "G_eq7": G, "storage": storage, "runs": {}}
+    G = wl.g_droplet(forcing)
+    out = {"case": "s1", "steps": steps, "G_eq7": G, "storage": storage, "forcing": forcing, "runs": {}}
     for col in collisions:
         for tau in taus:
-            Rs, dps, spur, diverged, dissolved = [], [], [], [], []
+            Rs, dps, spur, diverged, dissolved, Rm = [], [], [], [], [], []
             for R0 in radii:
                 n = 5 * R0
                 shape = (1, n, n)
-                lat = Lattice(shape, storage=storage, tau=(tau, tau), G12=G, collision=col)
+                lat = Lattice(shape, storage=storage, tau=(tau, tau), G12=G, collision=col, forcing=forcing)
                 r1, r2 = wl.droplet(shape, R0)
                 lat.init_fields(r1, r2)
                 lat.step(steps)
@@ -230,15 +246,18 @@ def run_s1(steps=None, radii=(8, 12, 16, 24), taus=(0.7, 0.8, 1.0, 1.5, 2.0, 3.0
                     lat.close()
                     continue
                 _, _, dp = lat.pressure_jump(ctr, R0 / 2.0, R0 + 0.5 * R0)
+                a, _, _ = lat.moments(out_f64=False)
                 lat.close()
                 Rs.append(dg.equivalent_radius(st["volume"], True))
+                Rm.append(dg.mass_radius(a, ctr, R0 / 2.0, R0 + 0.5 * R0)[0])
                 dps.append(dp)
                 spur.append(red["max_uF"])
-            run = {"R": Rs, "delta_p": dps, "sigma_per_R": [d * r for d, r in zip(dps, Rs)],
+            run = {"R": Rs, "R_mass": Rm, "delta_p": dps, "sigma_per_R": [d * r for d, r in zip(dps, Rs)],
                    "spurious_max_uF": spur, "diverged_R0": diverged, "dissolved_R0": dissolved}
             if len(Rs) >= 2 and all(np.isfinite(dps)):
                 sigma, icpt, res = dg.laplace_fit(Rs, dps, dims=2)
-                run.update(sigma=sigma, intercept=icpt, max_residual=res)
+                run.update(sigma=sigma, intercept=icpt, max_residual=res,
+                           sigma_mass_radius=dg.laplace_fit(Rm, dps, dims=2)[0])
             out["runs"]["%s/%g" % (col, tau)] = run
     return out
 
@@ -326,7 +345,8 @@ def run_s3(steps=None, shape=(32, 1, 192), width=96, rho_s2=(0.0, 0.088, 0.4),
 
 
 def run_s4(steps=None, angles=(10, 30, 50, 70), taus=((0.55, 1.5), (1.0, 1.0), (1.5, 0.55)),
-           models=("mirror", "potential"), rho_s2=0.4, R=8.0, collision="regularized", window=5000):
+           models=("mirror", "potential"), rho_s2=0.4, R=8.0, collision="regularized", window=5000,
+           forcing="edm"):
     """The inclined-wall case of Sec. 4.2: a quasi-2D droplet of component 2
     on the lower wall of a channel of height 16 inclined by 10-70 degrees
     (staircase solid sites, periodic along the channel), no driving force,
@@ -334,12 +354,13 @@ def run_s4(steps=None, angles=(10, 30, 50, 70), taus=((0.55, 1.5), (1.0, 1.0), (
     the droplet's velocity along the channel from its centre of mass over the
     last `window` steps, and the droplet volume (rho^2 above 0.18 / 0.22 of
     the liquid density) over the fluid volume, for the modified (mirror) and
-    the original (point-wise potential) wall model."""
+    the original (point-wise potential) wall model.  forcing: the reading of
+    the forcing term (G = -1.8 exact difference, -3.6 Guo)."""
     steps = steps or 85000
-    G = wl.G_DROPLET
+    G = wl.g_droplet(forcing)
     thr = 0.18 / 0.22
     out = {"case": "s4", "steps": steps, "window": window, "G_eq7": G, "rho_s2": rho_s2, "R": R,
-           "collision": collision, "runs": {}}
+           "collision": collision, "forcing": forcing, "runs": {}}
     for ang in angles:
         shape, solid, info = wl.inclined_channel(ang)
         r1, r2 = wl.channel_droplet(shape, info, R)
@@ -347,7 +368,7 @@ def run_s4(steps=None, angles=(10, 30, 50, 70), taus=((0.55, 1.5), (1.0, 1.0), (
             for model in models:
                 key = "%s/%g-%g/%g" % (model, tau[0], tau[1], ang)
                 lat = Lattice(shape, storage="f32", tau=tau, G12=G, rho_s=(0.0, rho_s2), wall_model=model,
-                              collision=collision)
+                              collision=collision, forcing=forcing)
                 lat.set_solid(solid)
                 lat.init_fields(r1, r2)
                 vol0, _, nfl = dg.channel_droplet_stats(r2, solid, info, thr)
@@ -428,14 +449,18 @@ def main():
     ap.add_argument("--taus", type=float, nargs="+", default=None, help="c1, s1")
     ap.add_argument("--collisions", nargs="+", default=None, choices=["bgk", "regularized", "regularized3"],
                     help="s1")
+    ap.add_argument("--forcing", default="edm", choices=["edm", "guo"],
+                    help="forcing reading: exact difference (edm) or Guo's scheme (c1, c4, s1, s4)")
     args = ap.parse_args()
     if args.case == "c4":
-        r = run_c4(args.steps, args.shape, args.gravity, args.wall_model)
+        r = run_c4(args.steps, args.shape, args.gravity, args.wall_model, forcing=args.forcing)
     elif args.case == "s1":
         kw = {k: v for k, v in (("taus", args.taus), ("collisions", args.collisions)) if v}
-        r = run_s1(args.steps, **kw)
+        r = run_s1(args.steps, forcing=args.forcing, **kw)
+    elif args.case == "s4":
+        r = run_s4(args.steps, forcing=args.forcing)
     elif args.case == "c1":
-        r = run_c1(args.steps, radii=args.radii, taus=args.taus, shape=args.shape)
+        r = run_c1(args.steps, radii=args.radii, taus=args.taus, shape=args.shape, forcing=args.forcing)
     else:
         r = {"c0": run_c0, "c2": run_c2, "c3": run_c3, "s1": run_s1, "s2": run_s2,
              "s3": run_s3, "s4": run_s4, "s5": run_s5}[args.case](args.steps)

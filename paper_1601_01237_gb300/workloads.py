@@ -201,6 +201,19 @@ def random_state(shape, seed, rho_lo=0.2, rho_hi=1.0, u_max=0.05):
 # operator at any tau (BGK at tau < 1 separates further and diverges).
 G_DROPLET = -1.8
 G_MIXTURE = -1.2
+# With Guo's forcing (the second reading of the forcing term) the force and
+# the density gradient enter a component's flux with the same factor, so the
+# coexistence of the regularized operator is that of the continuum criterion
+# at G itself, where the exact-difference forcing acts like 2 G: the Guo
+# values below give the same coexisting densities (1.047 / 0.019 and
+# 0.918 / 0.141 on flat interfaces of the oracle) at every tau from 0.525 to 3.
+G_DROPLET_GUO = -3.6
+G_MIXTURE_GUO = -2.4
+
+
+def g_droplet(forcing="edm"):
+    """Signed Eq. 7 G of the droplet cases for a forcing reading."""
+    return G_DROPLET_GUO if forcing == "guo" else G_DROPLET
 
 CONFIGS = {
     "c0_droplet2d_f64": dict(shape=(1, 64, 64), storage="f64", tau=(1.0, 1.0), G=G_DROPLET,

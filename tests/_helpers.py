@@ -24,9 +24,9 @@ def direction_map():
 
 def oracle_run(shape, rho1, rho2, u, nsteps, tau=(1.0, 1.0), G12=0.0, G21=None, g_ext=(0, 0, 0),
                periodic=(1, 1, 1), rho_s=(0.0, 0.0), collision="bgk", wall_model="mirror", rho0_dev=None,
-               solid=None):
+               solid=None, forcing="edm"):
     p = oracle.make_params(shape, tau=tau, G12=G12, G21=G21, g_ext=g_ext, periodic=periodic, rho_s=rho_s,
-                           collision=collision, wall_model=wall_model, solid=solid)
+                           collision=collision, wall_model=wall_model, solid=solid, forcing=forcing)
     f = oracle.init(p, rho1, rho2, u)
     if nsteps:
         oracle.step(p, f, nsteps)

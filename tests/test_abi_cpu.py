@@ -60,6 +60,8 @@ def _status(L, **kw):
     (dict(shape=(4, 4, 4), G12=float("inf")), 1),
     (dict(shape=(4, 4, 4), periodic=(0, 1, 1)), 4),
     (dict(shape=(4, 4, 4), periodic=(1, 0, 1)), 4),
+    (dict(shape=(4, 4, 4), storage="f16_rel", rho0_dev=0.5), 1),
+    (dict(shape=(4, 4, 4), forcing="guo", storage="f32", rho0_dev=0.1), 1),
 ])
 def test_validation_codes(L, kw, code):
     st, msg = _status(L, **kw)
@@ -98,3 +100,26 @@ def test_product_never_touches_the_oracle():
                 src = open(os.path.join(dirpath, f)).read()
                 assert not re.search(r"^\s*(import|from)\s+oracle", src, flags=re.M), f
                 assert "lbm_oracle" not in src, f
+
+
+def test_unknown_forcing_and_storage_rejected(L):
+    from paper_1601_01237_gb300 import make_params
+    for field, val in (("forcing", 2), ("storage", 6)):
+        p = make_params((4, 4, 4))
+        setattr(p, field, val)
+        h = ctypes.c_void_p()
+        assert L.lbm_create(ctypes.byref(p), ctypes.byref(h)) == 1
+        assert field in L.lbm_last_error(None).decode()
+
+
+def test_noalloc_rejects_overlapping_states(L):
+    """The allocation-free step refuses f_out overlapping f_in (any part of
+    the state, not only the same address) before it touches either buffer:
+    the pointers here are never dereferenced."""
+    from paper_1601_01237_gb300 import make_params
+    for storage, shift in (("f32", 8), ("f32", 16 * 16 * 16 * 152 - 4), ("bf16_rel", 16 * 16 * 16 * 84 - 8)):
+        p = make_params((16, 16, 16), storage=storage)
+        base = 1 << 40
+        st = L.lbm_step_noalloc(ctypes.byref(p), ctypes.c_void_p(base), ctypes.c_void_p(base + shift))
+        assert st == 1
+        assert "overlap" in L.lbm_last_error(None).decode()

@@ -8,6 +8,7 @@ import numpy as np
 import pytest
 
 from paper_1601_01237_gb300 import diagnostics as dg
+from paper_1601_01237_gb300 import workloads as wl
 
 W = 2.0
 HI, LO = 1.0, 0.03
@@ -193,3 +194,28 @@ def test_spinodal_stats_closed_forms():
     phi = 0.2 * np.cos(2 * np.pi * (2 * xx + 2 * y + z + 0.1) / L)
     st = dg.spinodal_stats(0.5 + 0.5 * phi, 0.5 - 0.5 * phi)
     assert abs(st["k_star"] - 3) < 1e-9
+
+
+def test_mass_radius_of_exact_discs_and_spheres():
+    """The excess-mass radius equals the radius of a hard-edged disc or
+    sphere of known area or volume (the count of its cells), and for a tanh
+    profile of width W it moves continuously with R (no jumps of whole
+    rings)."""
+    n = 48
+    z, y, x = np.meshgrid(np.arange(1), np.arange(n), np.arange(n), indexing="ij")
+    c = ((n - 1) / 2.0, (n - 1) / 2.0, 0.0)
+    r = np.sqrt((x - c[0]) ** 2 + (y - c[1]) ** 2)
+    for R0 in (6.0, 9.3, 12.0):
+        disc = np.where(r < R0, 1.1, 0.02)
+        R, rin, rout = dg.mass_radius(disc, c, R0 / 2, R0 + 4)
+        assert abs(R - np.sqrt((r < R0).sum() / np.pi)) < 1e-12
+        assert abs(rin - 1.1) < 1e-14 and abs(rout - 0.02) < 1e-14
+    m = 32
+    z, y, x = np.meshgrid(np.arange(m), np.arange(m), np.arange(m), indexing="ij")
+    c3 = ((m - 1) / 2.0,) * 3
+    r3 = np.sqrt((x - c3[0]) ** 2 + (y - c3[1]) ** 2 + (z - c3[2]) ** 2)
+    ball = np.where(r3 < 7.5, 1.0, 0.1)
+    R, _, _ = dg.mass_radius(ball, c3, 3.0, 11.0, dims=3)
+    assert abs(R - (3 * (r3 < 7.5).sum() / (4 * np.pi)) ** (1 / 3)) < 1e-12
+    Rs = [dg.mass_radius(wl.droplet((1, n, n), R0)[0], c, R0 / 2, R0 + 8)[0] for R0 in np.linspace(8, 9, 11)]
+    assert np.all(np.diff(Rs) > 0) and np.max(np.diff(Rs)) < 0.2
