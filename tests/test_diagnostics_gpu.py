@@ -48,7 +48,8 @@ def test_pressure_jump_and_droplet_stats_match_oracle(gpu_lib):
     assert abs(st["com"][0]) < 1e-9 and abs(st["com"][1]) < 1e-9
 
 
-def _droplet_dp(storage, shape, R0, steps, Gv=G, tau=(1.0, 1.0), collision="bgk", mass_radius=False, **kw):
+def _droplet_dp(storage, shape, R0, steps, Gv=G, tau=(1.0, 1.0), collision="bgk", mass_radius=False,
+                thr=0.5 * (1.1 + 0.006), **kw):
     """Pressure jump and radius of a relaxed droplet: the equivalent radius
     of the cells above the mid density, or (mass_radius) the continuous
     excess-mass radius of diagnostics.mass_radius."""
@@ -65,7 +66,7 @@ def _droplet_dp(storage, shape, R0, steps, Gv=G, tau=(1.0, 1.0), collision="bgk"
         a, _, _ = lat.moments()
         R = dg.mass_radius(a, c, R0 / 2.0, R0 + 8.0, dims=2 if quasi else 3)[0]
     else:
-        R = dg.equivalent_radius(lat.droplet_stats(0.5 * (1.1 + 0.006), origin=c)["volume"], quasi)
+        R = dg.equivalent_radius(lat.droplet_stats(thr, origin=c)["volume"], quasi)
     lat.close()
     return dp, R
 
@@ -158,3 +159,30 @@ def test_neutral_wetting_keeps_90_degrees(gpu_lib):
     print("neutral wetting: theta %.2f deg (h %.2f, b %.2f), film %.4f" % (theta, h, b, st["film_rho"]))
     assert abs(theta - 90.0) <= 2.0
     assert st["film_rho"] < 0.06
+
+
+def test_c1_sigma_against_oracle_fit(gpu_lib):
+    """The c1 measurement against the oracle's own fit: 3D droplets of the c1
+    recipe (1.0 / 0.03, G = -1.8, BGK, tau = 1) on 64^3 with R0 = 10-16 after
+    3000 steps, FP32 on the GPU; the fit dp = 2 sigma / R + c (pressure jump
+    of Eq. 12, equivalent radius of the cells with rho^1 > 0.515) within 1 %
+    of the FP64 oracle's (tests/golden/c1_laplace64_oracle.json, written by
+    make_oracle_golden.py from the oracle only)."""
+    import json
+    import os
+    with open(os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden", "c1_laplace64_oracle.json")) as fh:
+        gold = json.load(fh)
+    par = gold["params"]
+    shape = (par["n"],) * 3
+    Rs, dps = [], []
+    for R0 in par["radii"]:
+        dp, R = _droplet_dp("f32", shape, R0, par["steps"], Gv=par["G"], tau=tuple(par["tau"]),
+                            collision=par["collision"], thr=par["thr"])
+        Rs.append(R)
+        dps.append(dp)
+    sigma = dg.laplace_fit(Rs, dps, dims=3)[0]
+    err = abs(sigma - gold["sigma"]) / abs(gold["sigma"])
+    print("c1 sigma GPU FP32 %.7f oracle FP64 %.7f (%.2g)" % (sigma, gold["sigma"], err))
+    for (R, dp), row in zip(zip(Rs, dps), gold["droplets"]):
+        print("   R0 %d: R %.4f vs %.4f, dp %.6e vs %.6e" % (row["R0"], R, row["R_eq"], dp, row["dp"]))
+    assert err <= 0.01
