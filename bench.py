@@ -57,6 +57,10 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-adjoint", action="store_true")
+    ap.add_argument("--adjoint-steps", type=int, default=None,
+                    help="steps of the differentiation case (default: its configured 500; shorter for captures)")
+    ap.add_argument("--mask", choices=["none", "inclined"], default="none",
+                    help="inclined: staircase slab of solid sites (30 degrees, 8 cells thick) on the workload")
     ap.add_argument("--shape", type=int, nargs=3, default=None, metavar=("NZ", "NY", "NX"),
                     help="run the workload's parameters on another lattice (small profiling captures)")
     return ap.parse_args()
@@ -313,7 +317,7 @@ def cpu_baseline(args, cfg):
                       "(single_core_value: one process alone)" % n}
 
 
-def adjoint_ratio(stream):
+def adjoint_ratio(stream, steps=None):
     """Adjoint/forward time ratio on the differentiation case: 96^3 droplet
     (R = 20), FP32, 500 steps, checkpoints every 25.  Forward = lbm_step(500)
     after a warm-up lbm_step(100); reverse = lbm_adjoint over an lbm_record of
@@ -323,7 +327,7 @@ def adjoint_ratio(stream):
     import torch
     from paper_1601_01237_gb300 import Lattice
     c = wl.CONFIGS["c3_adjoint96"]
-    shape, n, every = c["shape"], c["steps"], c["ckpt_every"]
+    shape, n, every = c["shape"], steps or c["steps"], c["ckpt_every"]
     r1, r2 = wl.droplet(shape, c["R"])
     tgt, _ = wl.ellipsoid(shape, c["target_axes"])
     lat = Lattice(shape, storage=c["storage"], tau=c["tau"], G12=c["G"], stream=stream.cuda_stream)
@@ -373,6 +377,13 @@ def run_ours(args, rank, world, local_rank):
     r1, r2 = wl.fields_for(args.workload, shape=shape)
     stream = torch.cuda.current_stream()
     lat = Lattice(shape, stream=stream.cuda_stream, **kw)
+    mask_desc = None
+    if args.mask == "inclined":
+        solid = wl.inclined_slab(shape)
+        lat.set_solid(solid)
+        mask_desc = "staircase slab inclined 30 deg, 8 cells thick: %.1f %% solid sites (wall model %s)" % (
+            100.0 * solid.mean(), kw.get("wall_model", "mirror"))
+        del solid
     d1 = torch.from_numpy(r1).cuda()
     d2 = torch.from_numpy(r2).cuda()
     lat.init_fields(d1, d2)
@@ -447,15 +458,17 @@ def run_ours(args, rank, world, local_rank):
         "config": dict(workload_desc(args.workload, cfg, storage),
                        l2="inputs larger than L2: %.1f GB of populations per copy" % (
                            state_bytes_per_cell(storage) * cells / 1e9),
-                       parallelism="replicas" if world > 1 else "single GPU"),
+                       parallelism="replicas" if world > 1 else "single GPU",
+                       **({"mask": mask_desc} if mask_desc else {})),
         "roofline": roofline,
-        "gpu_launches": sum(v[1] for v in kern.values()),
+        # (a mask adds the two wall-density kernels of the mirror model per step)
+        "gpu_launches": sum(v[1] for v in kern.values()) * (3 if mask_desc and "k_step_fused" in kern else 1),
         "clocks": clocks,
         "e2e": e2e,
         "mass": [red["mass1"], red["mass2"]],
     }
     if not args.no_adjoint:
-        line["adjoint"] = adjoint_ratio(torch.cuda.current_stream())
+        line["adjoint"] = adjoint_ratio(torch.cuda.current_stream(), args.adjoint_steps)
     if world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(args, cfg)
     return line

@@ -192,15 +192,22 @@ lbm_status lbm_droplet_stats(lbm_lattice *h, double threshold, const double orig
  * and velocities read as 0); in Eq. 13 a solid site presents the w-weighted
  * mean of rho^b over its fluid neighbours plus rho_s^b (LBM_WALL_MIRROR) or
  * rho_s^b alone (LBM_WALL_POTENTIAL).  NULL removes the mask.  A lattice
- * with a mask steps with the two-kernel step; lbm_record returns
- * LBM_ENOTSUP for it; lbm_pressure_jump and lbm_droplet_stats leave solid
- * sites out, and the thin-film layer of lbm_droplet_stats is then the fluid
- * cells next to a solid site.  Set
- * the mask before lbm_init_fields (a state set earlier keeps the populations
- * of the new solid sites, which are never read).  The library keeps the
- * mask and one 32-bit word of link flags per cell on the device (5 bytes per
- * cell) until the mask is removed or the lattice destroyed.  Drops the
- * lattice's recording.  Synchronizes.  Errors: LBM_EINVAL (NULL handle),
+ * with a mask steps with the fused step (the FP32 and 16-bit formats) or
+ * the two-kernel step (LBM_F64); under the mirror model the fused step first
+ * refreshes the wall densities of the solid sites next to fluid with two
+ * small kernels over those sites and their fluid neighbours.  lbm_record and
+ * lbm_adjoint take the mask (bounce-back links and, for the mirror model,
+ * the dependence of the wall densities on the fluid densities).
+ * lbm_pressure_jump and lbm_droplet_stats leave solid sites out, and the
+ * thin-film layer of lbm_droplet_stats is then the fluid cells next to a
+ * solid site.  Set the mask before lbm_init_fields (a state set earlier
+ * keeps the populations of the new solid sites, which are never read).  The
+ * library keeps on the device, until the mask is removed or the lattice
+ * destroyed: the mask, one 32-bit word of link flags per cell (bit i: the
+ * site x - c_i is solid, bit 0: x itself), a pair of FP32 wall densities per
+ * cell, and the lists of the solid sites next to fluid and of the fluid
+ * cells next to a solid site (13 bytes per cell and 4 per listed cell).
+ * Drops the lattice's recording.  Synchronizes.  Errors: LBM_EINVAL (NULL handle),
  * LBM_ENOTSUP (lattice with walls along z), LBM_ENOMEM, LBM_ECUDA. */
 lbm_status lbm_set_solid(lbm_lattice *h, const unsigned char *solid, int on_device);
 
@@ -242,8 +249,7 @@ lbm_status lbm_sync(lbm_lattice *h);
  * segment of states and of their densities); both are held until the next
  * lbm_record or lbm_destroy, so that lbm_adjoint allocates nothing.
  * Synchronizes.  Errors: LBM_EINVAL, LBM_ENOMEM, LBM_ECUDA, LBM_ENOTSUP
- * (a lattice with a solid mask or with Guo forcing, which have no reverse
- * pass). */
+ * (a lattice with Guo forcing, which has no reverse pass). */
 lbm_status lbm_record(lbm_lattice *h, long n_steps, int ckpt_every);
 
 /* Reverse pass over the last lbm_record.  Inputs dL_drho1, dL_drho2: N values

@@ -23,6 +23,8 @@
 // f^eq(rho_0, u = 0)).
 #include <cuda_runtime.h>
 
+#include <atomic>
+
 #include "d3q19.cuh"
 #include "lbm_internal.h"
 
@@ -79,14 +81,14 @@ __device__ __forceinline__ unsigned at(const Nb &n, int dx, int dy, int dz)
 //   mu_i(y) = lambda^{n+1}_i(y + c_i) = lambda_loc^{n+1}_i(y + c_i) + D^{n+1}_a(y + c_i)
 // (or lambda^{n+1}_opp(i)(y) at a wall), and writes lambda_loc^n_i(y) of its
 // component and a^n_b(y) of the other component b = 1 - a.
-template <int S, int REG, bool SIN>
+template <int S, int REG, bool SIN, bool MASK>
 __device__ __forceinline__ void adj_half(const typename Store<S>::T *__restrict__ f,
                                          const typename Store<S>::R *__restrict__ rho,
                                          const typename Store<S>::R *__restrict__ lam_next,
                                          const typename Store<S>::R *__restrict__ Dn,
                                          typename Store<S>::R *__restrict__ lam_loc, typename Store<S>::R *__restrict__ aout,
                                          const Phys<typename Store<S>::R> &p, const Nb &n, int a, bool store,
-                                         typename Store<S>::R &par_g, typename Store<S>::R &par_t)
+                                         typename Store<S>::R &par_g, typename Store<S>::R &par_t, unsigned lw)
 {
     using R = typename Store<S>::R;
     const long long N = p.N;
@@ -103,9 +105,25 @@ __device__ __forceinline__ void adj_half(const typename Store<S>::T *__restrict_
     }
 #pragma unroll
     for (int i = 0; i < Q; ++i) {
-        const bool wall = (cz(i) == 1 && n.zlo) || (cz(i) == -1 && n.zhi);
+        // x - c_i behind a z wall or a solid site of a mask: the link bounces back
+        const bool wall = (cz(i) == 1 && n.zlo) || (cz(i) == -1 && n.zhi) || (MASK && i != 0 && ((lw >> i) & 1u));
         const unsigned e = wall ? (unsigned)opp(i) * N32 + n.cell : (unsigned)i * N32 + at(n, -cx(i), -cy(i), -cz(i));
         fa[i] = Store<S>::load(f + a + 2 * (size_t)e, w<R>(i) * rref);
+    }
+    // ---- incoming sensitivities (issued with the population loads, so that
+    //      both sets of gathers are in flight together) ----------------------
+    R mu[Q];
+    {
+        const R *lam_a = lam_next + (size_t)a * Q * (size_t)N;
+        const R *D_a = Dn + (size_t)a * (size_t)N;
+#pragma unroll
+        for (int i = 0; i < Q; ++i) {
+            const bool wall = (cz(i) == -1 && n.zlo) || (cz(i) == 1 && n.zhi) ||
+                              (MASK && i != 0 && ((lw >> opp(i)) & 1u));   // y + c_i solid
+            const unsigned cell = wall ? n.cell : at(n, cx(i), cy(i), cz(i));
+            const unsigned d = wall ? (unsigned)opp(i) : (unsigned)i;
+            mu[i] = lam_a[d * N32 + cell] + D_a[cell];
+        }
     }
     R ra = 0, jx = 0, jy = 0, jz = 0;
 #pragma unroll
@@ -184,19 +202,6 @@ __device__ __forceinline__ void adj_half(const typename Store<S>::T *__restrict_
 #pragma unroll
         for (int i = 1; i < Q; ++i) th.add(i, fa[i]);
         th.finish(ra, u0, u1, u2);
-    }
-    // ---- incoming sensitivities ---------------------------------------------
-    R mu[Q];
-    {
-        const R *lam_a = lam_next + (size_t)a * Q * (size_t)N;
-        const R *D_a = Dn + (size_t)a * (size_t)N;
-#pragma unroll
-        for (int i = 0; i < Q; ++i) {
-            const bool wall = (cz(i) == -1 && n.zlo) || (cz(i) == 1 && n.zhi);
-            const unsigned cell = wall ? n.cell : at(n, cx(i), cy(i), cz(i));
-            const unsigned d = wall ? (unsigned)opp(i) : (unsigned)i;
-            mu[i] = lam_a[d * N32 + cell] + D_a[cell];
-        }
     }
     // ---- reverse pass -------------------------------------------------------
     // BGK:         f* = E(rho, v) + keep (f - E(rho, u))
@@ -316,7 +321,14 @@ __device__ __forceinline__ void adj_half(const typename Store<S>::T *__restrict_
     const R U2 = ub2 + __shfl_xor_sync(full, ub2, 16);
     const R jb0 = U0 / rt, jb1 = U1 / rt, jb2 = U2 / rt;
     const R base = rbar - (U0 * u0 + U1 * u1 + U2 * u2) / rt;
-    if (store) {
+    if (store && MASK && (lw & 1u)) {
+        // solid site: no populations, no sensitivities (a = 0 keeps it out of D)
+        R *lo = lam_loc + (size_t)a * Q * (size_t)N + n.cell;
+#pragma unroll
+        for (int i = 0; i < Q; ++i) lo[(unsigned)i * N32] = R(0);
+#pragma unroll
+        for (int d = 0; d < 3; ++d) aout[((long long)b * 3 + d) * N + n.cell] = R(0);
+    } else if (store) {
         R *lo = lam_loc + (size_t)a * Q * (size_t)N + n.cell;
 #pragma unroll
         for (int i = 0; i < Q; ++i) {
@@ -350,12 +362,16 @@ __device__ __forceinline__ void adj_half(const typename Store<S>::T *__restrict_
 // Grid-stride over groups of 16 cells per warp; lanes 0-15 take component 0
 // and lanes 16-31 component 1 of the same 16 cells.  Per-block FP64 partials
 // of dL/dG^{12}, dL/dG^{21}, dL/dtau_1, dL/dtau_2 accumulate over the steps.
-template <int S, int REG, bool SIN>
+// MASK: links holds the mask's link words (bit 0: solid site; bit i: x - c_i
+// solid).  The lanes of a solid site still run the arithmetic (on meaningless
+// values), so that both lanes of every pair take part in the shuffles, and
+// store zeros.
+template <int S, int REG, bool SIN, bool MASK>
 __global__ void __launch_bounds__(kThreadsA, 2)
 k_adj_local(const typename Store<S>::T *__restrict__ f, const typename Store<S>::R *__restrict__ rho,
             const typename Store<S>::R *__restrict__ lam_next, const typename Store<S>::R *__restrict__ Dn,
             typename Store<S>::R *__restrict__ lam_loc, typename Store<S>::R *__restrict__ aout,
-            double *__restrict__ partials, Phys<typename Store<S>::R> p)
+            double *__restrict__ partials, Phys<typename Store<S>::R> p, const unsigned *__restrict__ links)
 {
     const int lane = threadIdx.x & 31;
     const int a = lane >> 4;
@@ -370,7 +386,8 @@ k_adj_local(const typename Store<S>::T *__restrict__ f, const typename Store<S>:
         const bool valid = c < p.N;
         Nb n;
         nb_of(p, (unsigned)(valid ? c : p.N - 1), n);
-        adj_half<S, REG, SIN>(f, rho, lam_next, Dn, lam_loc, aout, p, n, a, valid, pg, pt);
+        const unsigned lw = MASK ? __ldg(links + n.cell) : 0u;
+        adj_half<S, REG, SIN, MASK>(f, rho, lam_next, Dn, lam_loc, aout, p, n, a, valid, pg, pt, lw);
     }
     // lanes of component a hold parts of par[a] and par[2 + a]
     __shared__ double sh[4][kThreadsA];
@@ -387,45 +404,151 @@ k_adj_local(const typename Store<S>::T *__restrict__ f, const typename Store<S>:
     if (t < 4) partials[(long long)blockIdx.x * 4 + t] += sh[t][0];
 }
 
-// c_k . a(src), loading only the components along which c_k is non-zero.
-template <class R>
-__device__ __forceinline__ R cdot_a(int k, const R *__restrict__ ab, long long N, unsigned src)
-{
-    R s = 0;
-    if (cx(k)) s += R(cx(k)) * ab[src];
-    if (cy(k)) s += R(cy(k)) * ab[N + src];
-    if (cz(k)) s += R(cz(k)) * ab[2 * N + src];
-    return s;
-}
-
 // D_b(x) = dL/drho^b(x) = sum_k w_k c_k . a_b(x - c_k), plus the mirror-wall
 // terms: a wall site y + c_k seen from y presents the density of its mirror
 // cell y + (c_kx, c_ky, 0).
+//
+// Output tiles of 32 x 8 x DZ cells: the six fields a_b,d over the tile and a
+// one-cell margin (periodic images in x and y; in z periodic images, or zeros
+// for wall sites, whose terms the sum leaves out) are staged in shared memory
+// with coalesced loads, then each thread sums its z column of DZ cells from
+// shared memory, in the order of the per-link formula above.
+constexpr int kDX = 32, kDY = 8;
+template <class R>
+struct DTile {
+    static constexpr int DZ = sizeof(R) == 8 ? 4 : 8;   // 98 KB (FP64) / 82 KB (FP32) of staging
+    static constexpr int BX = kDX + 2, BY = kDY + 2, BZ = DZ + 2;
+    static constexpr int BOX = BX * BY * BZ;
+    static constexpr size_t kSmem = sizeof(R) * 6 * (size_t)BOX;
+};
+
+template <class R>
+__global__ void __launch_bounds__(kThreadsA, 2)
+k_adj_D(const R *__restrict__ a, R *__restrict__ D, Phys<R> p, int ntx)
+{
+    using T = DTile<R>;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    R *box = reinterpret_cast<R *>(smem_raw);   // [6][BZ][BY][BX]
+    // wrapped offsets of the box's rows (hz, hy) and columns hx, formed once per
+    // CTA (a row behind a z wall is marked -1 and staged as zeros)
+    __shared__ int row_off[T::BZ * T::BY];
+    __shared__ int col_off[T::BX];
+    const int t = threadIdx.x;
+    const int x0 = (blockIdx.x % ntx) * kDX, y0 = (blockIdx.x / ntx) * kDY, z0 = blockIdx.y * T::DZ;
+    const int nx = p.nx, ny = p.ny, nz = p.nz;
+    const unsigned N32 = (unsigned)p.N;   // 6 N < 2^32 (19 N is, on the host)
+    if (t < T::BZ * T::BY) {
+        const int hy = t % T::BY, hz = t / T::BY;
+        int gy = (y0 - 1 + hy) % ny;
+        if (gy < 0) gy += ny;
+        int gz = z0 - 1 + hz;
+        bool inside = true;
+        if (p.wall_z) {
+            inside = gz >= 0 && gz < nz;
+        } else {
+            gz %= nz;
+            if (gz < 0) gz += nz;
+        }
+        row_off[t] = inside ? (gz * ny + gy) * nx : -1;
+    } else if (t - T::BZ * T::BY < T::BX) {
+        const int hx = t - T::BZ * T::BY;
+        int gx = (x0 - 1 + hx) % nx;
+        if (gx < 0) gx += nx;
+        col_off[hx] = gx;
+    }
+    static_assert(T::BZ * T::BY + T::BX <= kThreadsA, "one offset per thread");
+    __syncthreads();
+    // all of the thread's loads are issued before the first shared-memory
+    // store, so that they are in flight together
+    constexpr int kIt = (T::BOX + kThreadsA - 1) / kThreadsA;
+    R val[kIt][6];
+#pragma unroll
+    for (int it = 0; it < kIt; ++it) {
+        const int h = it * kThreadsA + t;
+        const int ro = h < T::BOX ? row_off[h / T::BX] : -1;
+        const unsigned c = ro >= 0 ? (unsigned)(ro + col_off[h % T::BX]) : 0u;
+#pragma unroll
+        for (int q = 0; q < 6; ++q) val[it][q] = ro >= 0 ? __ldg(a + (unsigned)q * N32 + c) : R(0);
+    }
+#pragma unroll
+    for (int it = 0; it < kIt; ++it) {
+        const int h = it * kThreadsA + t;
+        if (h < T::BOX) {
+#pragma unroll
+            for (int q = 0; q < 6; ++q) box[q * T::BOX + h] = val[it][q];
+        }
+    }
+    __syncthreads();
+    const int lx = t % kDX, ly = t / kDX;
+    const int x = x0 + lx, y = y0 + ly;
+    if (x >= nx || y >= ny) return;
+    for (int k = 0; k < T::DZ; ++k) {
+        const int z = z0 + k;
+        if (z >= nz) break;
+        const bool zlo = p.wall_z && z == 0, zhi = p.wall_z && z == nz - 1;
+        const unsigned cell = ((unsigned)z * (unsigned)ny + (unsigned)y) * (unsigned)nx + (unsigned)x;
+#pragma unroll
+        for (int b = 0; b < 2; ++b) {
+            const R *bb = box + 3 * b * T::BOX;
+            // box value of field d at offset (dx, dy, dz) from this cell
+            auto at3 = [&](int d, int dx, int dy, int dz) {
+                return bb[d * T::BOX + ((k + 1 + dz) * T::BY + (ly + 1 + dy)) * T::BX + (lx + 1 + dx)];
+            };
+            R s = 0;
+#pragma unroll
+            for (int q = 1; q < Q; ++q) {
+                // wall sources hold zeros in the box, so their terms vanish
+                R c = 0;
+                if (cx(q)) c += R(cx(q)) * at3(0, -cx(q), -cy(q), -cz(q));
+                if (cy(q)) c += R(cy(q)) * at3(1, -cx(q), -cy(q), -cz(q));
+                if (cz(q)) c += R(cz(q)) * at3(2, -cx(q), -cy(q), -cz(q));
+                s += w<R>(q) * c;
+                if (p.wall_mirror && ((cz(q) == -1 && zlo) || (cz(q) == 1 && zhi))) {
+                    R m = 0;
+                    if (cx(q)) m += R(cx(q)) * at3(0, -cx(q), -cy(q), 0);
+                    if (cy(q)) m += R(cy(q)) * at3(1, -cx(q), -cy(q), 0);
+                    m += R(cz(q)) * at3(2, -cx(q), -cy(q), 0);
+                    s += w<R>(q) * m;
+                }
+            }
+            D[(unsigned)b * N32 + cell] = s;
+        }
+    }
+}
+
+// Mirror wall model under a mask: a solid site s presents
+// rho_w(s) = sum_j k_j rho(s + c_j) / sum_j k_j + rho_s over its fluid
+// neighbours s + c_j (Eq. 13, modified model), so each fluid cell x next to s
+// gains dL/drho_w(s) k_j / sum_j k_j.  dL/drho_w(s) is the regular D sum at s
+// (k_adj_D, with a = 0 at solid sites), which this pass reads and leaves as
+// it is; it runs over the fluid cells with a solid neighbour.
 template <class R>
 __global__ void __launch_bounds__(kThreadsA)
-k_adj_D(const R *__restrict__ a, R *__restrict__ D, Phys<R> p)
+k_adj_D_wall(R *__restrict__ D, const unsigned char *__restrict__ solid, Phys<R> p,
+             const unsigned *__restrict__ cells, long long n)
 {
-    const long long c = (long long)blockIdx.x * kThreadsA + threadIdx.x;
-    if (c >= p.N) return;
-    Nb n;
-    nb_of(p, (unsigned)c, n);
-    const long long N = p.N;
+    const long long t = (long long)blockIdx.x * kThreadsA + threadIdx.x;
+    if (t >= n) return;
+    Nb nx_;
+    nb_of(p, cells[t], nx_);
+    const unsigned N32 = (unsigned)p.N;
+    R add0 = 0, add1 = 0;
 #pragma unroll
-    for (int b = 0; b < 2; ++b) {
-        R s = 0;
-        const R *ab = a + (long long)b * 3 * N;
+    for (int i = 1; i < Q; ++i) {
+        const unsigned sc = at(nx_, cx(i), cy(i), cz(i));
+        if (!__ldg(solid + sc)) continue;
+        Nb ns;
+        nb_of(p, sc, ns);
+        int den36 = 0;
 #pragma unroll
-        for (int k = 1; k < Q; ++k) {
-            // regular term: x - c_k is a fluid cell whose neighbour x is this cell
-            const bool src_wall = (cz(k) == 1 && n.zlo) || (cz(k) == -1 && n.zhi);
-            if (!src_wall) s += w<R>(k) * cdot_a(k, ab, N, at(n, -cx(k), -cy(k), -cz(k)));
-            if (p.wall_mirror) {
-                const bool mirror = (cz(k) == -1 && n.zlo) || (cz(k) == 1 && n.zhi);
-                if (mirror) s += w<R>(k) * cdot_a(k, ab, N, at(n, -cx(k), -cy(k), 0));
-            }
-        }
-        D[(long long)b * N + c] = s;
+        for (int j = 1; j < Q; ++j)
+            if (!__ldg(solid + at(ns, cx(j), cy(j), cz(j)))) den36 += k36(j);
+        const R wgt = R(k36(i)) / R(den36);
+        add0 += wgt * D[sc];
+        add1 += wgt * D[N32 + sc];
     }
+    D[nx_.cell] += add0;
+    D[N32 + nx_.cell] += add1;
 }
 
 template <class R, class G>
@@ -447,10 +570,15 @@ k_adj_seed(const G *__restrict__ g1, const G *__restrict__ g2, R *__restrict__ l
 template <class R>
 __global__ void __launch_bounds__(kThreadsA)
 k_adj_rho0(const R *__restrict__ lam, const R *__restrict__ D, double *__restrict__ g1, double *__restrict__ g2,
-           long long N)
+           long long N, const unsigned char *__restrict__ solid)
 {
     const long long c = (long long)blockIdx.x * kThreadsA + threadIdx.x;
     if (c >= N) return;
+    if (solid && solid[c]) {   // a solid site holds no fluid: its initial density does not enter
+        if (g1) g1[c] = 0.0;
+        if (g2) g2[c] = 0.0;
+        return;
+    }
     double s1 = 0, s2 = 0;
 #pragma unroll
     for (int i = 0; i < Q; ++i) {
@@ -480,6 +608,31 @@ Phys<R> make_phys_a(const HostPhys &h)
 
 inline unsigned gridA(long long N) { return (unsigned)((N + kThreadsA - 1) / kThreadsA); }
 
+constexpr int kMaxAttrDevices = 64;
+
+// Launch of the tiled D pass; its dynamic shared-memory attribute belongs to
+// the device context and is set once per device.
+template <class R>
+cudaError_t launch_adj_D(const HostPhys &h, const R *a, R *D, const Phys<R> &p, cudaStream_t s)
+{
+    using T = DTile<R>;
+    const int ntx = (h.nx + kDX - 1) / kDX, nty = (h.ny + kDY - 1) / kDY;
+    const long long zb = (h.nz + T::DZ - 1) / T::DZ;
+    if ((long long)ntx * nty >= (1LL << 31) || zb > 65535) return cudaErrorInvalidConfiguration;
+    static std::atomic<int> attr_set[kMaxAttrDevices];
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    const bool cached = dev >= 0 && dev < kMaxAttrDevices;
+    if (!cached || !attr_set[dev].load(std::memory_order_acquire)) {
+        e = cudaFuncSetAttribute((const void *)k_adj_D<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)T::kSmem);
+        if (e != cudaSuccess) return e;
+        if (cached) attr_set[dev].store(1, std::memory_order_release);
+    }
+    k_adj_D<R><<<dim3((unsigned)(ntx * nty), (unsigned)zb), kThreadsA, T::kSmem, s>>>(a, D, p, ntx);
+    return cudaGetLastError();
+}
+
 template <int S>
 cudaError_t adj_step_t(const HostPhys &h, const void *f, const void *rho, int rho_is_sums, const void *lam_next,
                        const void *Dn, void *lam_loc, void *a, void *Dout, double *partials, cudaStream_t s)
@@ -487,16 +640,32 @@ cudaError_t adj_step_t(const HostPhys &h, const void *f, const void *rho, int rh
     using T = typename Store<S>::T;
     using R = typename Store<S>::R;
     const Phys<R> p = make_phys_a<R>(h);
-#define LBM_ADJ(REG_, SIN_)                                                                                  \
-    k_adj_local<S, REG_, SIN_><<<adjoint_blocks(), kThreadsA, 0, s>>>((const T *)f, (const R *)rho,         \
-                                                                      (const R *)lam_next, (const R *)Dn,  \
-                                                                      (R *)lam_loc, (R *)a, partials, p)
+#define LBM_ADJ(REG_, SIN_, MASK_)                                                                              \
+    k_adj_local<S, REG_, SIN_, MASK_><<<adjoint_blocks(), kThreadsA, 0, s>>>(                                  \
+        (const T *)f, (const R *)rho, (const R *)lam_next, (const R *)Dn, (R *)lam_loc, (R *)a, partials, p,  \
+        h.links)
+#define LBM_ADJ_REG(SIN_, MASK_)                  \
+    do {                                          \
+        if (reg == 1) LBM_ADJ(1, SIN_, MASK_);    \
+        else if (reg == 2) LBM_ADJ(2, SIN_, MASK_); \
+        else LBM_ADJ(0, SIN_, MASK_);             \
+    } while (0)
     const int reg = h.collision == LBM_REGULARIZED ? 1 : (h.collision == LBM_REGULARIZED3 ? 2 : 0);
-    if (rho_is_sums) { if (reg == 1) LBM_ADJ(1, true); else if (reg == 2) LBM_ADJ(2, true); else LBM_ADJ(0, true); }
-    else { if (reg == 1) LBM_ADJ(1, false); else if (reg == 2) LBM_ADJ(2, false); else LBM_ADJ(0, false); }
+    if (h.links) {
+        if (rho_is_sums) LBM_ADJ_REG(true, true);
+        else LBM_ADJ_REG(false, true);
+    } else {
+        if (rho_is_sums) LBM_ADJ_REG(true, false);
+        else LBM_ADJ_REG(false, false);
+    }
+#undef LBM_ADJ_REG
 #undef LBM_ADJ
-    k_adj_D<R><<<gridA(h.N), kThreadsA, 0, s>>>((const R *)a, (R *)Dout, p);
-    return cudaGetLastError();
+    cudaError_t e = launch_adj_D<R>(h, (const R *)a, (R *)Dout, p, s);
+    if (e == cudaSuccess && h.links && h.wall_mirror && h.n_bfluid > 0) {
+        k_adj_D_wall<R><<<gridA(h.n_bfluid), kThreadsA, 0, s>>>((R *)Dout, h.solid, p, h.bfluid, h.n_bfluid);
+        e = cudaGetLastError();
+    }
+    return e;
 }
 
 }  // namespace
@@ -536,9 +705,11 @@ cudaError_t launch_adjoint_rho0(const HostPhys &p, const void *lam, const void *
                                 cudaStream_t s)
 {
     if (p.storage == ST_F64)
-        k_adj_rho0<double><<<gridA(p.N), kThreadsA, 0, s>>>((const double *)lam, (const double *)D, g1, g2, p.N);
+        k_adj_rho0<double><<<gridA(p.N), kThreadsA, 0, s>>>((const double *)lam, (const double *)D, g1, g2, p.N,
+                                                            p.solid);
     else
-        k_adj_rho0<float><<<gridA(p.N), kThreadsA, 0, s>>>((const float *)lam, (const float *)D, g1, g2, p.N);
+        k_adj_rho0<float><<<gridA(p.N), kThreadsA, 0, s>>>((const float *)lam, (const float *)D, g1, g2, p.N,
+                                                           p.solid);
     return cudaGetLastError();
 }
 

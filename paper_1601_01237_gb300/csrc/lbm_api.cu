@@ -9,6 +9,7 @@
 
 #include <string>
 #include <utility>
+#include <algorithm>
 #include <vector>
 
 #include "../../include/lbm.h"
@@ -50,6 +51,10 @@ struct lbm_lattice {
     int use_graphs;
     unsigned char *solid;   // device mask of solid sites (N bytes) or nullptr
     unsigned *links;        // its link flags (N words) or nullptr
+    // fused step under the mask: wall densities (N pairs) and the boundary
+    // cells of the mirror model (see HostPhys)
+    float *wall_rho;
+    unsigned *bfluid, *bsolid;
 };
 
 namespace {
@@ -239,6 +244,26 @@ void free_workspace(lbm_lattice *h)
 
 }  // namespace
 
+namespace {
+
+// Releases a lattice's mask and everything derived from it.
+void free_mask(lbm_lattice *h)
+{
+    void *bufs[5] = {h->solid, h->links, h->wall_rho, h->bfluid, h->bsolid};
+    for (void *b : bufs) cudaFree(b);
+    h->solid = nullptr;
+    h->links = nullptr;
+    h->wall_rho = nullptr;
+    h->bfluid = h->bsolid = nullptr;
+    h->phys.solid = nullptr;
+    h->phys.links = nullptr;
+    h->phys.wall_rho = nullptr;
+    h->phys.bfluid = h->phys.bsolid = nullptr;
+    h->phys.n_bfluid = h->phys.n_bsolid = 0;
+}
+
+}  // namespace
+
 void lbm_destroy(lbm_lattice *h)
 {
     if (!h) return;
@@ -249,8 +274,7 @@ void lbm_destroy(lbm_lattice *h)
     cudaFree(h->rho);
     cudaFree(h->ckpt);
     free_workspace(h);
-    cudaFree(h->solid);
-    cudaFree(h->links);
+    free_mask(h);
     cudaFree(h->partials);
     if (h->graph) cudaGraphExecDestroy(h->graph);
     if (h->partials_h) cudaFreeHost(h->partials_h);
@@ -529,26 +553,64 @@ lbm_status lbm_set_solid(lbm_lattice *h, const unsigned char *solid, int on_devi
     h->ckpt = nullptr;
     h->rec_steps = 0;
     free_workspace(h);
+    free_mask(h);
     if (!solid) {
-        cudaFree(h->solid);
-        cudaFree(h->links);
-        h->solid = nullptr;
-        h->links = nullptr;
-        h->phys.solid = nullptr;
-        h->phys.links = nullptr;
         h->use_fused = env_flag("LBM_FUSED", 1) && lbm::fused_supported(h->phys);
         return LBM_OK;
     }
     const size_t N = (size_t)h->phys.N;
-    if (!h->solid) CK(cudaMalloc((void **)&h->solid, N), "lbm_set_solid: mask");
-    if (!h->links) CK(cudaMalloc((void **)&h->links, N * sizeof(unsigned)), "lbm_set_solid: link flags");
+    CK(cudaMalloc((void **)&h->solid, N), "lbm_set_solid: mask");
+    CK(cudaMalloc((void **)&h->links, N * sizeof(unsigned)), "lbm_set_solid: link flags");
     CK(cudaMemcpyAsync(h->solid, solid, N, on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice,
                        h->stream), "lbm_set_solid: copy");
     CK(lbm::launch_link_flags(h->phys, h->solid, h->links, h->stream), "lbm_set_solid: link flags");
-    CK(cudaStreamSynchronize(h->stream), "lbm_set_solid: sync");
     h->phys.solid = h->solid;
     h->phys.links = h->links;
-    h->use_fused = 0;   // the fused kernel takes no mask
+    h->use_fused = env_flag("LBM_FUSED", 1) && lbm::fused_supported(h->phys);
+    {
+        // wall densities (fused step) and the boundary lists of the mirror
+        // model (fused step and reverse pass): count, then list
+        unsigned long long *cnt = nullptr, cnt_h[2] = {0, 0};
+        CK(cudaMalloc((void **)&h->wall_rho, 2 * N * sizeof(float)), "lbm_set_solid: wall densities");
+        CK(cudaMemsetAsync(h->wall_rho, 0, 2 * N * sizeof(float), h->stream), "lbm_set_solid: wall densities");
+        CK(cudaMalloc((void **)&cnt, 2 * sizeof(unsigned long long)), "lbm_set_solid: counters");
+        cudaError_t e = cudaMemsetAsync(cnt, 0, 2 * sizeof(unsigned long long), h->stream);
+        if (e == cudaSuccess)
+            e = lbm::launch_mask_setup(h->phys, h->solid, h->wall_rho, nullptr, nullptr, cnt, h->stream);
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(cnt_h, cnt, sizeof cnt_h, cudaMemcpyDeviceToHost, h->stream);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+        if (e == cudaSuccess) e = cudaMalloc((void **)&h->bfluid, sizeof(unsigned) * (cnt_h[0] ? cnt_h[0] : 1));
+        if (e == cudaSuccess) e = cudaMalloc((void **)&h->bsolid, sizeof(unsigned) * (cnt_h[1] ? cnt_h[1] : 1));
+        if (e == cudaSuccess) e = cudaMemsetAsync(cnt, 0, 2 * sizeof(unsigned long long), h->stream);
+        if (e == cudaSuccess)
+            e = lbm::launch_mask_setup(h->phys, h->solid, h->wall_rho, h->bfluid, h->bsolid, cnt, h->stream);
+        // the lists come out in the order of the counters' atomics: sorted by
+        // cell, the wall-density kernels gather along rows
+        for (int q = 0; q < 2 && e == cudaSuccess; ++q) {
+            unsigned *lst = q == 0 ? h->bfluid : h->bsolid;
+            std::vector<unsigned> v((size_t)cnt_h[q]);
+            if (v.empty()) continue;
+            e = cudaMemcpyAsync(v.data(), lst, v.size() * sizeof(unsigned), cudaMemcpyDeviceToHost, h->stream);
+            if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+            if (e != cudaSuccess) break;
+            std::sort(v.begin(), v.end());
+            e = cudaMemcpyAsync(lst, v.data(), v.size() * sizeof(unsigned), cudaMemcpyHostToDevice, h->stream);
+            if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+        }
+        if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+        cudaFree(cnt);
+        if (e != cudaSuccess) {
+            free_mask(h);
+            return cuda_fail(e, "lbm_set_solid: boundary lists");
+        }
+        h->phys.wall_rho = h->wall_rho;
+        h->phys.bfluid = h->bfluid;
+        h->phys.bsolid = h->bsolid;
+        h->phys.n_bfluid = (long long)cnt_h[0];
+        h->phys.n_bsolid = (long long)cnt_h[1];
+    }
+    CK(cudaStreamSynchronize(h->stream), "lbm_set_solid: sync");
     return LBM_OK;
 }
 
@@ -644,7 +706,6 @@ lbm_status lbm_record(lbm_lattice *h, long n_steps, int ckpt_every)
     if (!h) return fail(LBM_EINVAL, "lbm_record: NULL handle");
     if (n_steps < 1 || ckpt_every < 1)
         return fail(LBM_EINVAL, "lbm_record: n_steps = %ld and ckpt_every = %d must be >= 1", n_steps, ckpt_every);
-    if (h->solid) return fail(LBM_ENOTSUP, "lbm_record: lattices with a solid mask have no reverse pass");
     if (h->phys.forcing != LBM_FORCING_EDM)
         return fail(LBM_ENOTSUP, "lbm_record: the reverse pass differentiates the exact-difference forcing only");
     DeviceGuard g(h->device);

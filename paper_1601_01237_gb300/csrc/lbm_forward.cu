@@ -212,8 +212,9 @@ k_wall_rho(R *__restrict__ rho, PhysF<R> p)
     rho[p.N + n.cell] = (den36 ? num2 / R(den36) : R(0)) + p.rho_s[1];
 }
 
-// Link flags of a mask: bit i of cell x set when x - c_i is a solid site, so
-// that the gather tests one word per cell instead of one byte per link.
+// Link flags of a mask: bit i of cell x set when x - c_i is a solid site (so
+// bit 0, x - c_0 = x, marks a solid site itself), so that the gather tests
+// one word per cell instead of one byte per link.
 __global__ void __launch_bounds__(kThreads)
 k_link_flags(const unsigned char *__restrict__ solid, unsigned *__restrict__ links, PhysF<float> p)
 {
@@ -221,9 +222,39 @@ k_link_flags(const unsigned char *__restrict__ solid, unsigned *__restrict__ lin
     if (!decode_cell(p, (long long)blockIdx.x * kThreads + threadIdx.x, n)) return;
     unsigned f = 0;
 #pragma unroll
-    for (int i = 1; i < Q; ++i)
+    for (int i = 0; i < Q; ++i)
         if (solid[n.zo[1 - cz(i)] + n.yo[1 - cy(i)] + n.xo[1 - cx(i)]]) f |= 1u << i;
     links[n.cell] = f;
+}
+
+// Mask set-up of the fused step: wall_rho = rho_s at solid sites, and the
+// boundary cells of the mirror model counted (lists == nullptr) or listed
+// (positions from the counters; the order of a list does not matter, every
+// entry is processed on its own).
+__global__ void __launch_bounds__(kThreads)
+k_mask_setup(const unsigned char *__restrict__ solid, const unsigned *__restrict__ links, PhysF<float> p,
+             float2 *__restrict__ wall_rho, unsigned *__restrict__ bfluid, unsigned *__restrict__ bsolid,
+             unsigned long long *__restrict__ counts)
+{
+    Nbr n;
+    if (!decode_cell(p, (long long)blockIdx.x * kThreads + threadIdx.x, n)) return;
+    const unsigned lf = links[n.cell];
+    if (!(lf & 1u)) {
+        if (lf) {   // a fluid cell with a solid neighbour
+            const unsigned long long k = atomicAdd(counts, 1ull);
+            if (bfluid) bfluid[k] = (unsigned)n.cell;
+        }
+        return;
+    }
+    wall_rho[n.cell] = make_float2(p.rho_s[0], p.rho_s[1]);
+    bool fluid_nb = false;
+#pragma unroll
+    for (int i = 1; i < Q; ++i)
+        if (!solid[n.zo[1 + cz(i)] + n.yo[1 + cy(i)] + n.xo[1 + cx(i)]]) fluid_nb = true;
+    if (fluid_nb) {
+        const unsigned long long k = atomicAdd(counts + 1, 1ull);
+        if (bsolid) bsolid[k] = (unsigned)n.cell;
+    }
 }
 
 template <int S, int REG, int FORCE>
@@ -669,6 +700,14 @@ cudaError_t launch_moments(const HostPhys &p, const void *f, void *rho, int out_
 }
 
 int reduce_blocks() { return kReduceBlocks; }
+
+cudaError_t launch_mask_setup(const HostPhys &h, const unsigned char *solid, float *wall_rho, unsigned *bfluid,
+                              unsigned *bsolid, unsigned long long *counts, cudaStream_t s)
+{
+    k_mask_setup<<<grid_for(h.N), kThreads, 0, s>>>(solid, h.links, make_phys<float>(h), (float2 *)wall_rho, bfluid,
+                                                     bsolid, counts);
+    return cudaGetLastError();
+}
 
 cudaError_t launch_link_flags(const HostPhys &h, const unsigned char *solid, unsigned *links, cudaStream_t s)
 {

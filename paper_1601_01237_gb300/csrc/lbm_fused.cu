@@ -22,6 +22,33 @@ bool fused_supported(const HostPhys &p)
            (p.nz + 7) / 8 < 65536;
 }
 
+int fused_planes(long long cols, int nz, int sms)
+{
+    // A CTA that marches over lz planes reads lz + 2 planes of populations
+    // (the planes below and above its chunk feed its first and last
+    // collisions), and the CTAs of one launch run in waves of two per SM.
+    // Among equal-length chunkings with lz in [8, 64] (fewer when nz < 8),
+    // take the one with the fewest waves x (lz + 2); lz = 64 stays unless
+    // another length is at least 5 % cheaper (large lattices, where the last
+    // wave is a small part of the launch).
+    const long long slots = 2LL * (sms > 0 ? sms : 1);
+    auto cost = [&](int lz) {
+        const long long ctas = cols * ((nz + lz - 1) / lz);
+        return ((ctas + slots - 1) / slots) * (long long)(lz + 2);
+    };
+    int best = nz < kPlanesMax ? nz : kPlanesMax;
+    const long long c64 = cost(best);
+    if (c64 > 16LL * (best + 2)) return best;   // more than 16 waves: the last one costs < 6 %
+    long long cbest = c64;
+    for (int nch = (nz + kPlanesMax - 1) / kPlanesMax; nch <= nz; ++nch) {
+        const int lz = (nz + nch - 1) / nch;
+        if (lz < kPlanesMin && nch > 1) break;
+        const long long c = cost(lz);
+        if (c < cbest) { cbest = c; best = lz; }
+    }
+    return cbest * 20 <= c64 * 19 ? best : (nz < kPlanesMax ? nz : kPlanesMax);
+}
+
 cudaError_t launch_step_fused(const HostPhys &p, const void *f_in, void *f_out, cudaStream_t s, cudaEvent_t *ev,
                               void *s_out)
 {

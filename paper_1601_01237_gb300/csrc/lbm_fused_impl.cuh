@@ -5,7 +5,8 @@
 // streaming in one kernel, with no global scratch.
 //
 // Each CTA owns a 32 x 8 column tile of the xy plane and marches along z over
-// a chunk of planes (64, or 8 for small lattices), one thread per column.
+// a chunk of 8 to 64 planes (fused_planes balances the CTA waves), one
+// thread per column.
 // The force at plane z needs rho^b at planes z-1, z, z+1 over the tile plus a
 // one-cell halo; those densities live in a ring of four shared-memory planes.
 // Iteration z:
@@ -51,8 +52,6 @@ constexpr int kThreadsF = kTX * kTY;
 constexpr int kHalo = 2 * (kTX + 2) + 2 * kTY;   // perimeter cells of the (TX+2) x (TY+2) box
 constexpr int kGroups = 3;                        // halo directions split 7 + 6 + 6 (both components each)
 constexpr int kPer = 14;
-constexpr int kLZmax = 64;                        // planes per CTA (large lattices)
-constexpr int kLZsmall = 8;                       // planes per CTA (small lattices)
 constexpr int Q2 = 2 * Q;
 static_assert(kGroups * kHalo <= kThreadsF, "one halo group per thread");
 
@@ -138,11 +137,13 @@ __device__ __forceinline__ PlaneRef plane_ref(const Phys<R> &p, int zp)
 }
 
 // Element index (within its population array) and array number of the
-// pull-gathered population i of component a at column c of plane pr.
+// pull-gathered population i of component a at column c of plane pr.  lw is
+// the cell's link word under a solid mask (bit i: x - c_i is a solid site,
+// whose link bounces back), 0 without one.
 template <int I>
-__device__ __forceinline__ int gather_elem(const PlaneRef &pr, const Col &c, int &arr_dir)
+__device__ __forceinline__ int gather_elem(const PlaneRef &pr, const Col &c, unsigned lw, int &arr_dir)
 {
-    const bool wall = (cz(I) == 1 && pr.lo_wall) || (cz(I) == -1 && pr.hi_wall);
+    const bool wall = (cz(I) == 1 && pr.lo_wall) || (cz(I) == -1 && pr.hi_wall) || (I != 0 && ((lw >> I) & 1u));
     if (wall) {
         arr_dir = opp(I);
         return pr.zc + c.yo[1] + c.xo[1];
@@ -168,12 +169,12 @@ __device__ __forceinline__ float2 gather_ref(const typename Store<S>::T *__restr
 // checked on the host): one multiply-add per load instead of 64-bit index math.
 template <int S, int I>
 __device__ __forceinline__ void load_dir(const typename Store<S>::T *__restrict__ f, long long N,
-                                         float2 rr, const PlaneRef &pr, const Col &c,
+                                         float2 rr, const PlaneRef &pr, const Col &c, unsigned lw,
                                          typename Store<S>::R (&v)[Q2])
 {
     using R = typename Store<S>::R;
     int d;
-    const int e = gather_elem<I>(pr, c, d);
+    const int e = gather_elem<I>(pr, c, lw, d);
     const unsigned idx = (unsigned)d * (unsigned)N + (unsigned)e;
     Store<S>::load2(f + 2 * (size_t)idx, w<R>(I) * rr.x, w<R>(I) * rr.y, v[I], v[Q + I]);
 }
@@ -181,17 +182,17 @@ __device__ __forceinline__ void load_dir(const typename Store<S>::T *__restrict_
 template <int S, int I>
 struct GatherAll {
     __device__ __forceinline__ static void run(const typename Store<S>::T *__restrict__ f, long long N,
-                                               float2 rr, const PlaneRef &pr, const Col &c,
+                                               float2 rr, const PlaneRef &pr, const Col &c, unsigned lw,
                                                typename Store<S>::R (&v)[Q2])
     {
-        load_dir<S, I>(f, N, rr, pr, c, v);
-        GatherAll<S, I + 1>::run(f, N, rr, pr, c, v);
+        load_dir<S, I>(f, N, rr, pr, c, lw, v);
+        GatherAll<S, I + 1>::run(f, N, rr, pr, c, lw, v);
     }
 };
 template <int S>
 struct GatherAll<S, Q> {
     __device__ __forceinline__ static void run(const typename Store<S>::T *__restrict__, long long,
-                                               float2, const PlaneRef &, const Col &,
+                                               float2, const PlaneRef &, const Col &, unsigned,
                                                typename Store<S>::R (&)[Q2]) {}
 };
 
@@ -234,15 +235,15 @@ __device__ __forceinline__ void sums(const R (&v)[Q2], R &r1, R &r2, R &jx, R &j
 template <int S, int D, int D1>
 struct HaloRange {
     __device__ __forceinline__ static void load(const typename Store<S>::T *__restrict__ f, long long N,
-                                                float2 rr, const PlaneRef &pr, const Col &c,
+                                                float2 rr, const PlaneRef &pr, const Col &c, unsigned lw,
                                                 typename Store<S>::R (&v)[kPer], int k)
     {
         using R = typename Store<S>::R;
         int d;
-        const int e = gather_elem<D>(pr, c, d);
+        const int e = gather_elem<D>(pr, c, lw, d);
         const unsigned idx = (unsigned)d * (unsigned)N + (unsigned)e;
         Store<S>::load2(f + 2 * (size_t)idx, w<R>(D) * rr.x, w<R>(D) * rr.y, v[k], v[k + 1]);
-        HaloRange<S, D + 1, D1>::load(f, N, rr, pr, c, v, k + 2);
+        HaloRange<S, D + 1, D1>::load(f, N, rr, pr, c, lw, v, k + 2);
     }
     __device__ __forceinline__ static void sum(const typename Store<S>::R (&v)[kPer], int k,
                                                typename Store<S>::R &s0, typename Store<S>::R &s1)
@@ -255,7 +256,7 @@ struct HaloRange {
 template <int S, int D1>
 struct HaloRange<S, D1, D1> {
     __device__ __forceinline__ static void load(const typename Store<S>::T *__restrict__, long long,
-                                                float2, const PlaneRef &, const Col &,
+                                                float2, const PlaneRef &, const Col &, unsigned,
                                                 typename Store<S>::R (&)[kPer], int) {}
     __device__ __forceinline__ static void sum(const typename Store<S>::R (&)[kPer], int,
                                                typename Store<S>::R &, typename Store<S>::R &) {}
@@ -263,12 +264,13 @@ struct HaloRange<S, D1, D1> {
 
 template <int S>
 __device__ __forceinline__ void halo_load(const typename Store<S>::T *__restrict__ f, const Phys<typename Store<S>::R> &p,
-                                          const PlaneRef &pr, const Col &c, int g, typename Store<S>::R (&v)[kPer])
+                                          const PlaneRef &pr, const Col &c, unsigned lw, int g,
+                                          typename Store<S>::R (&v)[kPer])
 {
     const float2 rr = gather_ref<S>(f, p, pr, c);
-    if (g == 0) HaloRange<S, 0, 7>::load(f, p.N, rr, pr, c, v, 0);
-    else if (g == 1) HaloRange<S, 7, 13>::load(f, p.N, rr, pr, c, v, 0);
-    else HaloRange<S, 13, Q>::load(f, p.N, rr, pr, c, v, 0);
+    if (g == 0) HaloRange<S, 0, 7>::load(f, p.N, rr, pr, c, lw, v, 0);
+    else if (g == 1) HaloRange<S, 7, 13>::load(f, p.N, rr, pr, c, lw, v, 0);
+    else HaloRange<S, 13, Q>::load(f, p.N, rr, pr, c, lw, v, 0);
 }
 
 template <int S>
@@ -290,15 +292,36 @@ __device__ __forceinline__ void halo_sum(const typename Store<S>::R (&v)[kPer], 
 // cell itself when x + c_i lies behind a wall (lo_wall / hi_wall: plane z is
 // next to the lower / upper wall); the cell's own densities are stored as the
 // reference of the populations it will gather.
+// Under a solid mask, lw is the cell's link word: a solid site (bit 0) stores
+// zero populations (reference densities 1 for the *_REL formats) and zero
+// interaction sums, and a population whose destination x + c_i is solid
+// (bit opp(i)) returns to the cell itself.
 template <int S, int REG, int FORCE>
 __device__ __forceinline__ void collide_cell(typename Store<S>::T *__restrict__ fout, const Phys<typename Store<S>::R> &p,
                                              const FusedSmem<typename Store<S>::R> &sm, const InvRing *rinv,
                                              int sl_m, int sl_c, int sl_p,
                                              int st, long long cell, typename Store<S>::R *__restrict__ s_out,
-                                             bool lo_wall, bool hi_wall)
+                                             bool lo_wall, bool hi_wall, unsigned lw = 0u)
 {
     using R = typename Store<S>::R;
     const int tid = threadIdx.x;
+    if (lw & 1u) {   // solid site
+        typename Store<S>::T *os = fout + 2 * cell;
+        const unsigned n32 = (unsigned)p.N;
+#pragma unroll
+        for (int i = 0; i < Q; ++i) {
+            // zero in every format: the deviation formats code it against w_i rho0,
+            // the relative ones code 0 as 0 whatever their parameter
+            const R ref = Store<S>::kRel ? R(1) : w<R>(i) * R(p.rho0);
+            Store<S>::store2(os + 2 * (size_t)((unsigned)i * n32), R(0), R(0), ref, ref);
+        }
+        if constexpr (Store<S>::kRel) state_ref(fout, p.ref_off)[cell] = make_float2(1.0f, 1.0f);
+        if (s_out) {
+#pragma unroll
+            for (int k = 0; k < 6; ++k) s_out[(long long)k * p.N + cell] = R(0);
+        }
+        return;
+    }
     const int lx = tid % kTX + 1, ly = tid / kTX + 1;
     const float2 rr = sm.ring[sl_c][ly][lx];
     const R r1 = rr.x, r2 = rr.y;
@@ -477,8 +500,8 @@ __device__ __forceinline__ void collide_cell(typename Store<S>::T *__restrict__ 
         const size_t ip = 2 * (size_t)((unsigned)i * N32), im = 2 * (size_t)((unsigned)(i + 1) * N32);
         if constexpr (Store<S>::kRel) {
             // destinations: x + c_i for i, x - c_i for opp(i), or x across a wall
-            const bool wp = (cz(i) == -1 && lo_wall) || (cz(i) == 1 && hi_wall);
-            const bool wm = (cz(i) == 1 && lo_wall) || (cz(i) == -1 && hi_wall);
+            const bool wp = (cz(i) == -1 && lo_wall) || (cz(i) == 1 && hi_wall) || ((lw >> (i + 1)) & 1u);
+            const bool wm = (cz(i) == 1 && lo_wall) || (cz(i) == -1 && hi_wall) || ((lw >> i) & 1u);
             const int slp = cz(i) == -1 ? sl_m : (cz(i) == 1 ? sl_p : sl_c);
             const int slm = cz(i) == -1 ? sl_p : (cz(i) == 1 ? sl_m : sl_c);
             const float2 dp = wp ? rinv[sl_c][ly][lx] : rinv[slp][ly + cy(i)][lx + cx(i)];
@@ -496,17 +519,22 @@ __device__ __forceinline__ void collide_cell(typename Store<S>::T *__restrict__ 
 
 // Interior part of plane zp for this thread's column: rho^1, rho^2 into ring
 // slot `slot`; when st >= 0 the populations and momentum into stash slot st.
+// A solid site of a mask (solid) presents its wall density wd instead.
 template <int S>
 __device__ __forceinline__ void interior_plane(const typename Store<S>::T *__restrict__ f,
                                                const Phys<typename Store<S>::R> &p, FusedSmem<typename Store<S>::R> &sm,
                                                InvRing *inv,
-                                               int slot, int st, const PlaneRef &pr, const typename Store<S>::R (&v)[Q2])
+                                               int slot, int st, const PlaneRef &pr, const typename Store<S>::R (&v)[Q2],
+                                               bool solid = false, float2 wd = make_float2(0.f, 0.f))
 {
     using R = typename Store<S>::R;
     const int tid = threadIdx.x;
     const int lx = tid % kTX + 1, ly = tid / kTX + 1;
     R r1 = p.rho_s[0], r2 = p.rho_s[1];
-    if (!pr.constant) {
+    if (solid) {
+        r1 = wd.x;
+        r2 = wd.y;
+    } else if (!pr.constant) {
         R a1, a2, jx, jy, jz;
         sums(v, a1, a2, jx, jy, jz);
         if (pr.ghost) {
@@ -541,14 +569,22 @@ __device__ __forceinline__ void halo_combine(const Phys<R> &p, FusedSmem<R> &sm,
     put_ring<S>(sm, inv, slot, hy, hx, r1, r2);
 }
 
-template <int S, int REG, bool WALLZ, int LZ, int FORCE>
+// MASK: staircase walls given as a mask of solid sites (the lattice is then
+// periodic along z).  links holds every cell's link word (bit 0: the cell is
+// solid; bit i: x - c_i is solid, so that link bounces back) and wrho the
+// densities (rho^1, rho^2) that each solid site presents to Eq. 13.  The link
+// words of the planes a thread gathers are loaded one plane ahead; a solid
+// site puts its wall density into the ring (a solid halo cell through its
+// first partial, the others zero) and stores zero populations.
+template <int S, int REG, bool WALLZ, bool MASK, int FORCE>
 __global__ void __launch_bounds__(kThreadsF, 2)
 k_step_fused(const typename Store<S>::T *__restrict__ fin, typename Store<S>::T *__restrict__ fout,
-             Phys<typename Store<S>::R> p, int ntx, typename Store<S>::R *__restrict__ s_out)
+             Phys<typename Store<S>::R> p, int ntx, int lz, typename Store<S>::R *__restrict__ s_out,
+             const unsigned *__restrict__ links, const float2 *__restrict__ wrho)
 {
-    constexpr int lz = LZ;
     using R = typename Store<S>::R;
     static_assert(sizeof(R) == sizeof(float), "the fused step runs FP32 arithmetic");
+    static_assert(!(MASK && WALLZ), "a solid mask needs a lattice periodic along z");
     extern __shared__ __align__(16) unsigned char smem_raw[];
     FusedSmem<R> &sm = *reinterpret_cast<FusedSmem<R> *>(smem_raw);
     InvRing *inv = reinterpret_cast<InvRing *>(smem_raw + sizeof(FusedSmem<R>));   // *_REL formats only
@@ -609,16 +645,36 @@ k_step_fused(const typename Store<S>::T *__restrict__ fin, typename Store<S>::T 
     // ring slot of plane q: (q - z0 + 1) & 3; stash, moment and halo-partial
     // slot of plane q: (q - z0) & 1.
     // prologue: planes z0-1 and z0 in full, halo partials of z0+1
+    // link word of column c at plane pr (0 without a mask)
+    auto link_of = [&](const PlaneRef &pr, const Col &c) -> unsigned {
+        return MASK ? __ldg(links + (unsigned)(pr.zc + c.yo[1] + c.xo[1])) : 0u;
+    };
+    // wall density of a solid site: rho_s (point-wise potential), or the
+    // refreshed mean of the mirror model
+    auto wall_rho = [&](const PlaneRef &pr, const Col &c) -> float2 {
+        if (!p.wall_mirror) return make_float2((float)p.rho_s[0], (float)p.rho_s[1]);
+        return __ldg(wrho + (unsigned)(pr.zc + c.yo[1] + c.xo[1]));
+    };
+    unsigned lwA = 0;   // link word of the thread's column at plane z (its collision)
     for (int q = z0 - 1; q <= z0; ++q) {
         const PlaneRef pr = plane_ref<WALLZ>(p, q);
+        const unsigned lw = link_of(pr, ci);
+        if (q == z0) lwA = lw;
         R v[Q2];
-        if (!pr.constant) GatherAll<S, 0>::run(fin, p.N, gather_ref<S>(fin, p, pr, ci), pr, ci, v);
-        interior_plane<S>(fin, p, sm, inv, q - z0 + 1, q == z0 ? 0 : -1, pr, v);
+        if (!pr.constant) GatherAll<S, 0>::run(fin, p.N, gather_ref<S>(fin, p, pr, ci), pr, ci, lw, v);
+        const bool sol = MASK && (lw & 1u);
+        interior_plane<S>(fin, p, sm, inv, q - z0 + 1, q == z0 ? 0 : -1, pr, v, sol,
+                          sol ? wall_rho(pr, ci) : make_float2(0.f, 0.f));
         if (tid < kHalo) {
             R r1 = p.rho_s[0], r2 = p.rho_s[1];
-            if (!pr.constant) {
+            const unsigned hl = link_of(pr, ch);
+            if (MASK && (hl & 1u)) {
+                const float2 wd = wall_rho(pr, ch);
+                r1 = wd.x;
+                r2 = wd.y;
+            } else if (!pr.constant) {
                 R hv[Q2];
-                GatherAll<S, 0>::run(fin, p.N, gather_ref<S>(fin, p, pr, ch), pr, ch, hv);
+                GatherAll<S, 0>::run(fin, p.N, gather_ref<S>(fin, p, pr, ch), pr, ch, hl, hv);
                 R a1, a2, jx, jy, jz;
                 sums(hv, a1, a2, jx, jy, jz);
                 if (pr.ghost) { r1 += a1; r2 += a2; } else { r1 = a1; r2 = a2; }
@@ -626,24 +682,42 @@ k_step_fused(const typename Store<S>::T *__restrict__ fin, typename Store<S>::T 
             put_ring<S>(sm, inv, q - z0 + 1, hy, hx, r1, r2);
         }
     }
-    {
-        const PlaneRef pr = plane_ref<WALLZ>(p, z0 + 1);
-        if (has_halo) {
-            R hv[kPer];
-            R s1 = 0, s2 = 0;
-            if (!pr.constant) {
-                halo_load<S>(fin, p, pr, cht, g, hv);
-                halo_sum<S>(hv, g, s1, s2);
+    // halo partials of plane z0+1; a solid halo cell gives its wall density
+    // as the first group's partial and zeros as the others
+    auto halo_task = [&](const PlaneRef &pr, unsigned hl, int slot) {
+        R hv[kPer];
+        R s1 = 0, s2 = 0;
+        if (MASK && (hl & 1u)) {
+            if (g == 0) {
+                const float2 wd = wall_rho(pr, cht);
+                s1 = wd.x;
+                s2 = wd.y;
             }
-            sm.hpart[1][g][0][ht] = s1;
-            sm.hpart[1][g][1][ht] = s2;
+        } else if (!pr.constant) {
+            halo_load<S>(fin, p, pr, cht, hl, g, hv);
+            halo_sum<S>(hv, g, s1, s2);
         }
+        sm.hpart[slot][g][0][ht] = s1;
+        sm.hpart[slot][g][1][ht] = s2;
+    };
+    if (has_halo) {
+        const PlaneRef pr = plane_ref<WALLZ>(p, z0 + 1);
+        halo_task(pr, link_of(pr, cht), 1);
     }
     // interior populations of plane z0+1, in registers until the first iteration
     R v[Q2];
+    unsigned lwB, lwC = 0, hlw = 0;   // link words: column at z+1, z+2; halo task cell at z+2
+    float2 wdB = make_float2(0.f, 0.f);   // wall density of the column at z+1 (a solid site)
     {
         const PlaneRef pr = plane_ref<WALLZ>(p, z0 + 1);
-        if (!pr.constant) GatherAll<S, 0>::run(fin, p.N, gather_ref<S>(fin, p, pr, ci), pr, ci, v);
+        lwB = link_of(pr, ci);
+        if (!pr.constant) GatherAll<S, 0>::run(fin, p.N, gather_ref<S>(fin, p, pr, ci), pr, ci, lwB, v);
+        if (MASK) {
+            if (lwB & 1u) wdB = wall_rho(pr, ci);
+            const PlaneRef pr2 = plane_ref<WALLZ>(p, z0 + 2);
+            lwC = link_of(pr2, ci);
+            if (has_halo) hlw = link_of(pr2, cht);
+        }
     }
     __syncthreads();
 
@@ -657,22 +731,45 @@ k_step_fused(const typename Store<S>::T *__restrict__ fin, typename Store<S>::T 
         const bool need2 = z + 2 <= z1;           // rho(z+2) feeds the collision of z+1
         const PlaneRef pr2 = plane_ref<WALLZ>(p, z + 2);
         R hv[kPer];
-        if (need2 && has_halo && !pr2.constant) halo_load<S>(fin, p, pr2, cht, g, hv);
+        const bool hsol = MASK && (hlw & 1u);   // the halo task's cell is a solid site
+        float2 hwd = make_float2(0.f, 0.f);
+        if (hsol && g == 0 && need2 && has_halo) hwd = wall_rho(pr2, cht);   // in flight with the gathers
+        if (need2 && has_halo && !hsol && !pr2.constant) halo_load<S>(fin, p, pr2, cht, hlw, g, hv);
         if (tid < kHalo) halo_combine<S>(p, sm, inv, s_p, (k + 1) & 1, pr1, h, hx, hy);
-        interior_plane<S>(fin, p, sm, inv, s_p, z + 1 < z1 ? ((k + 1) & 1) : -1, pr1, v);
+        const bool sol = MASK && (lwB & 1u);
+        interior_plane<S>(fin, p, sm, inv, s_p, z + 1 < z1 ? ((k + 1) & 1) : -1, pr1, v, sol, wdB);
         if (need2 && has_halo) {
             R s1 = 0, s2 = 0;
-            if (!pr2.constant) halo_sum<S>(hv, g, s1, s2);
+            if (hsol) {
+                if (g == 0) {
+                    s1 = hwd.x;
+                    s2 = hwd.y;
+                }
+            } else if (!pr2.constant) {
+                halo_sum<S>(hv, g, s1, s2);
+            }
             sm.hpart[k & 1][g][0][ht] = s1;
             sm.hpart[k & 1][g][1][ht] = s2;
         }
         __syncthreads();
         // ---- phase B: the interior gathers of plane z+2 are issued first and
         //      stay in flight (in registers) during the collision of plane z
-        if (z + 1 < z1 && !pr2.constant) GatherAll<S, 0>::run(fin, p.N, gather_ref<S>(fin, p, pr2, ci), pr2, ci, v);
+        if (z + 1 < z1 && !pr2.constant) GatherAll<S, 0>::run(fin, p.N, gather_ref<S>(fin, p, pr2, ci), pr2, ci, lwC, v);
+        unsigned lwD = 0;
+        float2 wdC = make_float2(0.f, 0.f);
+        if (MASK) {   // link words of plane z+3 (periodic z: always a lattice plane)
+            const PlaneRef pr3 = plane_ref<WALLZ>(p, z + 3);
+            lwD = link_of(pr3, ci);
+            if (has_halo) hlw = link_of(pr3, cht);
+            if (lwC & 1u) wdC = wall_rho(pr2, ci);   // the column at z+2 is a solid site
+        }
         if (active)
             collide_cell<S, REG, FORCE>(fout, p, sm, inv, s_m, s_c, s_p, k & 1, (long long)z * p.nx * p.ny + cell_xy, s_out,
-                                 WALLZ && z == 0, WALLZ && z == p.nz - 1);
+                                 WALLZ && z == 0, WALLZ && z == p.nz - 1, lwA);
+        lwA = lwB;
+        lwB = lwC;
+        lwC = lwD;
+        wdB = wdC;
     }
 }
 
@@ -698,9 +795,10 @@ constexpr int kMaxAttrDevices = 64;
 // Launch of one kernel instance.  The dynamic shared-memory size attribute
 // belongs to the device context: each instance sets it once per device
 // (several host threads may race to set the same value, which is harmless).
-template <int S, int REG, bool WALLZ, int LZ, int FORCE>
+template <int S, int REG, bool WALLZ, bool MASK, int FORCE>
 cudaError_t launch_inst(dim3 grid, cudaStream_t s, const typename Store<S>::T *fi, typename Store<S>::T *fo,
-                        const Phys<typename Store<S>::R> &p, int ntx, typename Store<S>::R *s_out)
+                        const Phys<typename Store<S>::R> &p, int ntx, int lz, typename Store<S>::R *s_out,
+                        const unsigned *links, const float2 *wrho)
 {
     static std::atomic<int> attr_set[kMaxAttrDevices];
     int dev = 0;
@@ -708,37 +806,92 @@ cudaError_t launch_inst(dim3 grid, cudaStream_t s, const typename Store<S>::T *f
     if (e != cudaSuccess) return e;
     const bool cached = dev >= 0 && dev < kMaxAttrDevices;
     if (!cached || !attr_set[dev].load(std::memory_order_acquire)) {
-        e = cudaFuncSetAttribute((const void *)k_step_fused<S, REG, WALLZ, LZ, FORCE>,
+        e = cudaFuncSetAttribute((const void *)k_step_fused<S, REG, WALLZ, MASK, FORCE>,
                                  cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_bytes<S>());
         if (e != cudaSuccess) return e;
         if (cached) attr_set[dev].store(1, std::memory_order_release);
     }
-    k_step_fused<S, REG, WALLZ, LZ, FORCE><<<grid, kThreadsF, smem_bytes<S>(), s>>>(fi, fo, p, ntx, s_out);
+    k_step_fused<S, REG, WALLZ, MASK, FORCE><<<grid, kThreadsF, smem_bytes<S>(), s>>>(fi, fo, p, ntx, lz, s_out, links, wrho);
     return cudaSuccess;
 }
 
 template <int S, int REG, int FORCE>
-cudaError_t launch_geom(const HostPhys &h, bool small, dim3 grid, cudaStream_t s, const typename Store<S>::T *fi,
+cudaError_t launch_geom(const HostPhys &h, int lz, dim3 grid, cudaStream_t s, const typename Store<S>::T *fi,
                         typename Store<S>::T *fo, const Phys<typename Store<S>::R> &p, int ntx,
                         typename Store<S>::R *s_out)
 {
-    if (h.wall_z)
-        return small ? launch_inst<S, REG, true, kLZsmall, FORCE>(grid, s, fi, fo, p, ntx, s_out)
-                     : launch_inst<S, REG, true, kLZmax, FORCE>(grid, s, fi, fo, p, ntx, s_out);
-    return small ? launch_inst<S, REG, false, kLZsmall, FORCE>(grid, s, fi, fo, p, ntx, s_out)
-                 : launch_inst<S, REG, false, kLZmax, FORCE>(grid, s, fi, fo, p, ntx, s_out);
+    if (h.wall_z) return launch_inst<S, REG, true, false, FORCE>(grid, s, fi, fo, p, ntx, lz, s_out, nullptr, nullptr);
+    if (h.links)
+        return launch_inst<S, REG, false, true, FORCE>(grid, s, fi, fo, p, ntx, lz, s_out, h.links,
+                                                       (const float2 *)h.wall_rho);
+    return launch_inst<S, REG, false, false, FORCE>(grid, s, fi, fo, p, ntx, lz, s_out, nullptr, nullptr);
 }
 
 template <int S, int FORCE>
-cudaError_t launch_coll(const HostPhys &h, bool small, dim3 grid, cudaStream_t s, const typename Store<S>::T *fi,
+cudaError_t launch_coll(const HostPhys &h, int lz, dim3 grid, cudaStream_t s, const typename Store<S>::T *fi,
                         typename Store<S>::T *fo, const Phys<typename Store<S>::R> &p, int ntx,
                         typename Store<S>::R *s_out)
 {
     switch (h.collision) {
-    case LBM_REGULARIZED: return launch_geom<S, 1, FORCE>(h, small, grid, s, fi, fo, p, ntx, s_out);
-    case LBM_REGULARIZED3: return launch_geom<S, 2, FORCE>(h, small, grid, s, fi, fo, p, ntx, s_out);
-    default: return launch_geom<S, 0, FORCE>(h, small, grid, s, fi, fo, p, ntx, s_out);
+    case LBM_REGULARIZED: return launch_geom<S, 1, FORCE>(h, lz, grid, s, fi, fo, p, ntx, s_out);
+    case LBM_REGULARIZED3: return launch_geom<S, 2, FORCE>(h, lz, grid, s, fi, fo, p, ntx, s_out);
+    default: return launch_geom<S, 0, FORCE>(h, lz, grid, s, fi, fo, p, ntx, s_out);
     }
+}
+
+// Wall densities of the mirror model under a mask (Eq. 13, modified model),
+// refreshed before each fused step: first the densities of the fluid cells
+// that have a solid neighbour, summed like the fused kernel sums its ring
+// (same gathers, same grouping), into their own entries of wall_rho; then each
+// solid site with a fluid neighbour takes the w_i-weighted mean of its fluid
+// neighbours' densities plus rho_s.
+template <int S>
+__global__ void __launch_bounds__(256)
+k_wall_fluid_rho(const typename Store<S>::T *__restrict__ f, Phys<typename Store<S>::R> p,
+                 const unsigned *__restrict__ links, const unsigned *__restrict__ cells, long long n,
+                 float2 *__restrict__ wr)
+{
+    using R = typename Store<S>::R;
+    const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= n) return;
+    const unsigned c = cells[t];
+    const unsigned plane = (unsigned)p.nx * (unsigned)p.ny;
+    const int z = (int)(c / plane);
+    const unsigned rem = c - (unsigned)z * plane;
+    const int y = (int)(rem / (unsigned)p.nx), x = (int)(rem - (unsigned)y * (unsigned)p.nx);
+    const Col col = make_col(x, y, p.nx, p.ny);
+    const PlaneRef pr = plane_ref<false>(p, z);
+    R v[Q2];
+    GatherAll<S, 0>::run(f, p.N, gather_ref<S>(f, p, pr, col), pr, col, __ldg(links + c), v);
+    R r1, r2, jx, jy, jz;
+    sums(v, r1, r2, jx, jy, jz);
+    wr[c] = make_float2(r1, r2);
+}
+
+template <int S>   // (instantiated per storage format's translation unit)
+__global__ void __launch_bounds__(256)
+k_wall_solid_rho(const unsigned char *__restrict__ solid, Phys<float> p, const unsigned *__restrict__ cells,
+                 long long n, float2 *__restrict__ wr)
+{
+    const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= n) return;
+    const unsigned c = cells[t];
+    const unsigned nx = (unsigned)p.nx, ny = (unsigned)p.ny, nz = (unsigned)p.nz, plane = nx * ny;
+    const unsigned z = c / plane, rem = c - z * plane, y = rem / nx, x = rem - y * nx;
+    float num1 = 0, num2 = 0;
+    int den36 = 0;
+#pragma unroll
+    for (int i = 1; i < Q; ++i) {
+        const unsigned xn = (x + nx + cx(i)) % nx, yn = (y + ny + cy(i)) % ny, zn = (z + nz + cz(i)) % nz;
+        const unsigned nb = (zn * ny + yn) * nx + xn;
+        if (__ldg(solid + nb)) continue;
+        const float k = (float)k36(i);
+        const float2 r = wr[nb];
+        num1 += k * r.x;
+        num2 += k * r.y;
+        den36 += k36(i);
+    }
+    wr[c] = make_float2((den36 ? num1 / (float)den36 : 0.f) + p.rho_s[0], (den36 ? num2 / (float)den36 : 0.f) + p.rho_s[1]);
 }
 
 template <int S>
@@ -749,18 +902,22 @@ cudaError_t fused_t(const HostPhys &h, const void *fin, void *fout, cudaStream_t
     const Phys<R> p = make_phys_f<R>(h);
     const int ntx = (h.nx + kTX - 1) / kTX;
     const int nty = (h.ny + kTY - 1) / kTY;
-    // planes per CTA: 64, or 8 when 64 would leave fewer than two CTAs per SM
-    // (small lattices get shorter chunks and more CTAs)
-    const int sms = current_device_sms();
-    const bool small = (long long)ntx * nty * ((h.nz + kLZmax - 1) / kLZmax) < 2LL * sms;
-    const int lz = small ? kLZsmall : kLZmax;
+    const int lz = fused_planes((long long)ntx * nty, h.nz, current_device_sms());
     const dim3 grid((unsigned)(ntx * nty), (unsigned)((h.nz + lz - 1) / lz));
     if (ev) cudaEventRecord(ev[0], s);
     const T *fi = (const T *)fin;
     T *fo = (T *)fout;
+    if (h.links && h.wall_mirror && h.n_bsolid > 0) {
+        float2 *wr = (float2 *)h.wall_rho;
+        if (h.n_bfluid > 0)
+            k_wall_fluid_rho<S><<<(unsigned)((h.n_bfluid + 255) / 256), 256, 0, s>>>(fi, p, h.links, h.bfluid,
+                                                                                   h.n_bfluid, wr);
+        k_wall_solid_rho<S><<<(unsigned)((h.n_bsolid + 255) / 256), 256, 0, s>>>(h.solid, make_phys_f<float>(h), h.bsolid,
+                                                                             h.n_bsolid, wr);
+    }
     const cudaError_t e = h.forcing == FORCE_GUO
-                              ? launch_coll<S, FORCE_GUO>(h, small, grid, s, fi, fo, p, ntx, (R *)s_out)
-                              : launch_coll<S, FORCE_EDM>(h, small, grid, s, fi, fo, p, ntx, (R *)s_out);
+                              ? launch_coll<S, FORCE_GUO>(h, lz, grid, s, fi, fo, p, ntx, (R *)s_out)
+                              : launch_coll<S, FORCE_EDM>(h, lz, grid, s, fi, fo, p, ntx, (R *)s_out);
     if (e != cudaSuccess) return e;
     if (ev) cudaEventRecord(ev[1], s);
     return cudaGetLastError();

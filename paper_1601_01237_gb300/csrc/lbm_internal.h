@@ -27,11 +27,20 @@ struct HostPhys {
     // take a mask.
     const unsigned char *solid = nullptr;
     // N words of link flags derived from the mask: bit i set when the pull
-    // source x - c_i of cell x is a solid site (launch_link_flags)
+    // source x - c_i of cell x is a solid site (bit 0: x itself is solid;
+    // launch_link_flags)
     const unsigned *links = nullptr;
     // *_REL formats: byte offset of the per-cell reference densities from the
     // base of a state (see state_bytes); 0 otherwise
     long long ref_off = 0;
+    // Fused step under a mask: N pairs (rho^1, rho^2) holding, at each solid
+    // site, the density it presents to Eq. 13 (rho_s; for the mirror model
+    // the sites listed in bsolid are refreshed before every fused step, through
+    // the entries of the fluid cells listed in bfluid).  nullptr = no mask.
+    const float *wall_rho = nullptr;
+    const unsigned *bfluid = nullptr;   // fluid cells with a solid neighbour
+    const unsigned *bsolid = nullptr;   // solid sites with a fluid neighbour
+    long long n_bfluid = 0, n_bsolid = 0;
 };
 
 // Populations are stored as 2*19*N values of the storage type, laid out
@@ -54,6 +63,17 @@ cudaError_t launch_step_split(const HostPhys &p, const void *f_in, void *f_out, 
 cudaError_t launch_step_fused(const HostPhys &p, const void *f_in, void *f_out, cudaStream_t s,
                               cudaEvent_t *ev = nullptr, void *s_out = nullptr);
 bool fused_supported(const HostPhys &p);
+// Planes per CTA of the fused step for a lattice of cols = ceil(nx/32) *
+// ceil(ny/8) tile columns and nz planes on a device with sms SMs.
+constexpr int kPlanesMax = 64, kPlanesMin = 8;
+int fused_planes(long long cols, int nz, int sms);
+
+// Mask set-up for the fused step: wall_rho = rho_s at every solid site, and
+// the counts (lists == nullptr) or the lists themselves of the boundary cells
+// of the mirror model (fluid cells with a solid neighbour, solid sites with a
+// fluid one); counts[0..1] must be zero on entry.
+cudaError_t launch_mask_setup(const HostPhys &h, const unsigned char *solid, float *wall_rho, unsigned *bfluid,
+                              unsigned *bsolid, unsigned long long *counts, cudaStream_t s);
 
 // State set-up: populations from (rho1, rho2, u) via f^eq (u may be NULL),
 // or from explicit populations f[a][i][cell] in library order (doubles).

@@ -146,6 +146,18 @@ def inclined_channel(theta_deg, H=16, min_len=96, min_gap=4, max_side=400):
     return (nz, 1, nx), solid, info
 
 
+def inclined_slab(shape, theta_deg=30.0, thickness=8):
+    """Staircase wall for a 3D lattice periodic in every direction: the solid
+    sites are the cells with (z - x tan(theta)) mod nz < thickness, a slab
+    inclined by theta to the x axis along x and uniform along y (the inclined
+    walls of Sec. 4.2 extruded across the lattice).  Returns the (nz, ny, nx)
+    uint8 mask."""
+    nz, ny, nx = shape
+    z, x = np.meshgrid(np.arange(nz), np.arange(nx), indexing="ij")
+    h = np.mod(z - np.floor(x * math.tan(math.radians(theta_deg))), nz)
+    return np.repeat((h < thickness).astype(np.uint8)[:, None, :], ny, axis=1)
+
+
 def channel_droplet(shape, info, R, s0=0.0, rho_in=1.0, rho_out=0.03, width=2.0):
     """Droplet of component 2 in an inclined_channel: a disc of radius R
     centred on the lower wall, s0 along the centre line from the lattice

@@ -38,16 +38,16 @@ def oracle_loss(r1, r2, tgt, G, tau1, tau2, steps, **kw):
     return float(((a - tgt) ** 2).sum())
 
 
-def fd_grads(r1, r2, tgt, G, tau1, tau2, steps, cells=None, **kw):
+def fd_grads(r1, r2, tgt, G, tau1, tau2, steps, cells=None, h=H, **kw):
     L = lambda **o: oracle_loss(o.get("r1", r1), r2, tgt, o.get("G", G), o.get("tau1", tau1), tau2, steps, **kw)
-    gG = (L(G=G + H) - L(G=G - H)) / (2 * H)
-    gT = (L(tau1=tau1 + H) - L(tau1=tau1 - H)) / (2 * H)
+    gG = (L(G=G + h) - L(G=G - h)) / (2 * h)
+    gT = (L(tau1=tau1 + h) - L(tau1=tau1 - h)) / (2 * h)
     gr = np.zeros(r1.shape)
     idx = list(np.ndindex(r1.shape)) if cells is None else cells
     for c in idx:
-        rp = r1.copy(); rp[c] += H
-        rm = r1.copy(); rm[c] -= H
-        gr[c] = (L(r1=rp) - L(r1=rm)) / (2 * H)
+        rp = r1.copy(); rp[c] += h
+        rm = r1.copy(); rm[c] -= h
+        gr[c] = (L(r1=rp) - L(r1=rm)) / (2 * h)
     return gG, gT, gr
 
 
@@ -114,6 +114,62 @@ def test_adjoint_walls_and_forcing(gpu_lib, collision, storage):
     scale = np.abs([fr[q] for q in cells]).max()
     for c in cells:
         assert abs(d1[c] - fr[c]) <= tol * scale, (c, d1[c], fr[c])
+
+
+def _staircase(shape, seed):
+    """A staircase along the bottom, a pillar and a few scattered solid
+    sites on a periodic lattice."""
+    nz, ny, nx = shape
+    m = np.zeros(shape, np.uint8)
+    for x in range(nx):
+        m[: 1 + (2 * x) // nx, :, x] = 1
+    m[nz // 2:, : ny // 2, nx // 2] = 1
+    rng = np.random.default_rng(seed)
+    for _ in range(3):
+        m[rng.integers(0, nz), rng.integers(0, ny), rng.integers(0, nx)] = 1
+    return m
+
+
+@pytest.mark.parametrize("storage", ["f64", "f32"])
+@pytest.mark.parametrize("wall_model,collision", [("mirror", "bgk"), ("mirror", "regularized"),
+                                                  ("potential", "bgk")])
+def test_adjoint_solid_mask(gpu_lib, wall_model, collision, storage):
+    """Reverse pass through a mask of solid sites (Sec. 4.2 staircase walls):
+    bounce-back links and, for the mirror model, the wall densities' dependence
+    on the fluid densities (Eq. 13), on sampled fluid cells, many of them next
+    to a solid site, against the oracle's central differences (FP64 1e-5,
+    FP32 1e-4); solid sites get a zero initial-density gradient.  The step is
+    h = 1e-4: this case's dL/dG is small (-0.0192), and at h = 1e-3 the
+    central difference is 2.3e-5 away from its limit (the oracle's
+    differences at h = 1e-2 .. 1e-4 converge to -0.01920134)."""
+    shape = (7, 5, 6)
+    solid = _staircase(shape, seed=2)
+    r1, r2, _ = wl.random_state(shape, seed=21, u_max=0.0)
+    tgt = np.roll(r1, 1, axis=2)
+    kw = dict(g_ext=(2e-4, -1e-4, 3e-4), collision=collision, rho_s=(0.03, 0.1), wall_model=wall_model)
+    G, t1, t2, steps = -1.3, 0.8, 1.2, 6
+    fluid = [tuple(int(v) for v in c) for c in np.argwhere(solid == 0)]
+    rng = np.random.default_rng(5)
+    cells = [fluid[k] for k in rng.choice(len(fluid), 14, replace=False)]
+    fG, fT, fr = fd_grads(r1, r2, tgt, G, t1, t2, steps, cells=cells, h=1e-4, solid=solid, **kw)
+    from paper_1601_01237_gb300 import Lattice
+    lat = Lattice(shape, storage=storage, tau=(t1, t2), G12=G, G21=G, **kw)
+    lat.set_solid(solid)
+    lat.init_fields(r1, r2)
+    lat.record(steps, 4)
+    a, _, _ = lat.moments()
+    d1 = np.empty(shape)
+    par = lat.adjoint(2 * (a - tgt), None, d1, None)
+    lat.close()
+    tol = 1e-5 if storage == "f64" else 1e-4
+    print("%s %s %s mask: dG %.6g vs %.6g, dtau1 %.6g vs %.6g" % (storage, wall_model, collision,
+                                                                   par[0] + par[1], fG, par[2], fT))
+    assert abs(par[0] + par[1] - fG) <= tol * abs(fG)
+    assert abs(par[2] - fT) <= tol * abs(fT)
+    scale = np.abs([fr[q] for q in cells]).max()
+    for c in cells:
+        assert abs(d1[c] - fr[c]) <= tol * scale, (c, d1[c], fr[c])
+    assert np.all(d1[solid == 1] == 0)
 
 
 def test_autograd_rollout_matches_adjoint(gpu_lib):
