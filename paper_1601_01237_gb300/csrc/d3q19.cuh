@@ -204,6 +204,10 @@ template <> struct Store<ST_F32> {
         a = v.x; b = v.y;
     }
     __device__ static __forceinline__ void store2(T *p, R a, R b, R, R) { *reinterpret_cast<float2 *>(p) = make_float2(a, b); }
+    // a loaded pair as it is stored (Raw), decoded later (decode2): load2 in two halves
+    using Raw = float2;
+    __device__ static __forceinline__ Raw load_raw(const T *p) { return ld_pair_f32(p); }
+    __device__ static __forceinline__ void decode2(Raw r, R, R, R &a, R &b) { a = r.x; b = r.y; }
 };
 
 // 16-bit conversions of the two formats.
@@ -251,6 +255,13 @@ template <class C> struct StoreDev {
     {
         *reinterpret_cast<typename C::T2 *>(p) = C::pack(a - ea, b - eb);
     }
+    using Raw = unsigned;
+    __device__ static __forceinline__ Raw load_raw(const T *p) { return ld_pair_b16(p); }
+    __device__ static __forceinline__ void decode2(Raw r, R da, R db, R &a, R &b)
+    {
+        C::unpack(r, a, b);
+        a += da; b += db;
+    }
 };
 // Relative deviation s = f / (w rho~) - 1 (load parameter d = w rho~, store
 // parameter e = 1 / (w rho~)).
@@ -270,6 +281,14 @@ template <class C> struct StoreRel {
     __device__ static __forceinline__ void store2(T *p, R a, R b, R ea, R eb)
     {
         *reinterpret_cast<typename C::T2 *>(p) = C::pack(fmaf(a, ea, -1.0f), fmaf(b, eb, -1.0f));
+    }
+    using Raw = unsigned;
+    __device__ static __forceinline__ Raw load_raw(const T *p) { return ld_pair_b16(p); }
+    __device__ static __forceinline__ void decode2(Raw r, R da, R db, R &a, R &b)
+    {
+        float sa, sb;
+        C::unpack(r, sa, sb);
+        a = fmaf(da, sa, da); b = fmaf(db, sb, db);
     }
 };
 template <> struct Store<ST_F16_DEV> : StoreDev<H16> {};

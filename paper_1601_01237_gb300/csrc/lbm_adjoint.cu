@@ -1,674 +1,29 @@
-// Reverse-mode (adjoint) step of the two-component D3Q19 Shan-Chen update.
-// The paper has no adjoint; this differentiates the forward step of
-// Sec. 2 (Eqs. 1-7, 10-11, 13 with the exact-difference forcing) by hand.
-//
-// Notation: f^n = pre-collision populations at step n (the gathered values),
-// lambda^n = dL/df^n.  One forward step is
-//   f*(y) = C(f^n(y), S(y)),  S^b(y) = sum_k w_k c_k rho^b(y + c_k),
-//   f^{n+1}_i(y + c_i) = f*_i(y)      (or f^{n+1}_opp(i)(y) at a wall),
-// so one reverse step is
-//   lambda^n_i(x) = lambda_loc^n_i(x) + D^n_b(x)    (b = component of i),
-//   lambda_loc^n  = (dC/df)^T mu,   a^n_b(y) = (dC/dS^b)^T mu,
-//   D^n_b(x)      = dL/drho^b(x) = sum_k w_k c_k . a^n_b(x - c_k)
-//                   (+ mirror-wall terms),
-//   mu_i(y)       = lambda^{n+1}_i(y + c_i)  (or lambda^{n+1}_opp(i)(y) at a wall).
-// lambda itself is never stored: the reverse step gathers
-// mu_i(y) = lambda_loc^{n+1}_i(y + c_i) + D^{n+1}_b(y + c_i) from the previous
-// step's lambda_loc and the small field D^{n+1}.  Parameter sensitivities
-// dL/dG^{ab} and dL/dtau_a are accumulated per block in FP64.
-//
-// Kernels: k_adj_seed (lambda_loc^N = dL/drho at the last step, D^N = 0),
-// k_adj_D (D from a), k_adj_local (mu gather + local reverse pass),
-// k_adj_rho0 (dL/drho_0 = sum_i w_i lambda^0_i for an initial state
-// f^eq(rho_0, u = 0)).
-#include <cuda_runtime.h>
-
-#include <atomic>
-
-#include "d3q19.cuh"
-#include "lbm_internal.h"
+// Reverse-mode step of the two-component D3Q19 Shan-Chen update: dispatch
+// over the storage formats (the per-format instances of the reverse step live
+// in lbm_adjoint_<format>.cu), the seed of the adjoint fields and the
+// initial-density gradient.  Kernels and notation: lbm_adjoint_impl.cuh.
+#include "lbm_adjoint_impl.cuh"
 
 namespace lbm {
 
-namespace {
-
-constexpr int kThreadsA = 256;
-constexpr int kAdjBlocksPerSM = 2;   // k_adj_local: 128 registers x 256 threads
-
-// A cell and its wrapped neighbour offsets.  Cell indices fit 32 bits (a
-// lattice of 2^32 cells would need 650 GB of populations); element offsets
-// into the 2 x 19 arrays are formed in 64 bits.
-struct Nb {
-    unsigned cell;
-    unsigned xo[3], yo[3], zo[3];
-    bool zlo, zhi;   // z - 1 (resp. z + 1) is a wall site
-};
-
-template <class R>
-__device__ __forceinline__ void nb_of(const Phys<R> &p, unsigned cell, Nb &n)
-{
-    const unsigned nx = (unsigned)p.nx, ny = (unsigned)p.ny, nz = (unsigned)p.nz;
-    const unsigned plane = nx * ny;
-    const unsigned z = cell / plane;
-    const unsigned rem = cell - z * plane;
-    const unsigned y = rem / nx;
-    const unsigned x = rem - y * nx;
-    n.cell = cell;
-    n.xo[0] = x == 0 ? nx - 1 : x - 1;
-    n.xo[1] = x;
-    n.xo[2] = x == nx - 1 ? 0 : x + 1;
-    n.yo[0] = (y == 0 ? ny - 1 : y - 1) * nx;
-    n.yo[1] = y * nx;
-    n.yo[2] = (y == ny - 1 ? 0 : y + 1) * nx;
-    n.zo[0] = (z == 0 ? nz - 1 : z - 1) * plane;
-    n.zo[1] = z * plane;
-    n.zo[2] = (z == nz - 1 ? 0 : z + 1) * plane;
-    n.zlo = p.wall_z && z == 0;
-    n.zhi = p.wall_z && z == nz - 1;
-}
-
-__device__ __forceinline__ unsigned at(const Nb &n, int dx, int dy, int dz)
-{
-    return n.zo[1 + dz] + n.yo[1 + dy] + n.xo[1 + dx];
-}
-
-
-// Local reverse pass of one component a at one cell, run by a pair of lanes
-// (lane l: component 0, lane l ^ 16: component 1, same cell).  The two
-// components are coupled only through the mixture momentum and density, whose
-// sums and sensitivities the pair exchanges by shuffles; each lane holds its
-// component's 19 populations and 19 incoming sensitivities
-//   mu_i(y) = lambda^{n+1}_i(y + c_i) = lambda_loc^{n+1}_i(y + c_i) + D^{n+1}_a(y + c_i)
-// (or lambda^{n+1}_opp(i)(y) at a wall), and writes lambda_loc^n_i(y) of its
-// component and a^n_b(y) of the other component b = 1 - a.
-template <int S, int REG, bool SIN, bool MASK>
-__device__ __forceinline__ void adj_half(const typename Store<S>::T *__restrict__ f,
-                                         const typename Store<S>::R *__restrict__ rho,
-                                         const typename Store<S>::R *__restrict__ lam_next,
-                                         const typename Store<S>::R *__restrict__ Dn,
-                                         typename Store<S>::R *__restrict__ lam_loc, typename Store<S>::R *__restrict__ aout,
-                                         const Phys<typename Store<S>::R> &p, const Nb &n, int a, bool store,
-                                         typename Store<S>::R &par_g, typename Store<S>::R &par_t, unsigned lw)
-{
-    using R = typename Store<S>::R;
-    const long long N = p.N;
-    // element offsets inside one component's 19 arrays fit 32 bits (19 N < 2^32,
-    // checked on the host): one 32-bit multiply-add per access
-    const unsigned N32 = (unsigned)N;
-    const unsigned full = 0xffffffffu;
-    // ---- forward recomputation ------------------------------------------
-    R fa[Q];
-    R rref = p.rho0;   // *_REL formats: the cell's own reference density of component a
-    if constexpr (Store<S>::kRel) {
-        const float2 rr = state_ref(f, p.ref_off)[n.cell];
-        rref = a == 0 ? rr.x : rr.y;
-    }
-#pragma unroll
-    for (int i = 0; i < Q; ++i) {
-        // x - c_i behind a z wall or a solid site of a mask: the link bounces back
-        const bool wall = (cz(i) == 1 && n.zlo) || (cz(i) == -1 && n.zhi) || (MASK && i != 0 && ((lw >> i) & 1u));
-        const unsigned e = wall ? (unsigned)opp(i) * N32 + n.cell : (unsigned)i * N32 + at(n, -cx(i), -cy(i), -cz(i));
-        fa[i] = Store<S>::load(f + a + 2 * (size_t)e, w<R>(i) * rref);
-    }
-    // ---- incoming sensitivities (issued with the population loads, so that
-    //      both sets of gathers are in flight together) ----------------------
-    R mu[Q];
-    {
-        const R *lam_a = lam_next + (size_t)a * Q * (size_t)N;
-        const R *D_a = Dn + (size_t)a * (size_t)N;
-#pragma unroll
-        for (int i = 0; i < Q; ++i) {
-            const bool wall = (cz(i) == -1 && n.zlo) || (cz(i) == 1 && n.zhi) ||
-                              (MASK && i != 0 && ((lw >> opp(i)) & 1u));   // y + c_i solid
-            const unsigned cell = wall ? n.cell : at(n, cx(i), cy(i), cz(i));
-            const unsigned d = wall ? (unsigned)opp(i) : (unsigned)i;
-            mu[i] = lam_a[d * N32 + cell] + D_a[cell];
-        }
-    }
-    R ra = 0, jx = 0, jy = 0, jz = 0;
-#pragma unroll
-    for (int i = 0; i < Q; ++i) ra += fa[i];
-#pragma unroll
-    for (int i = 1; i < Q; i += 2) {   // opposite pairs: f_i - f_opp(i) first
-        const R d = fa[i] - fa[i + 1];
-        if (cx(i) == 1) jx += d; else if (cx(i) == -1) jx -= d;
-        if (cy(i) == 1) jy += d; else if (cy(i) == -1) jy -= d;
-        if (cz(i) == 1) jz += d; else if (cz(i) == -1) jz -= d;
-    }
-    // mixture density and momentum: both lanes of the pair form the same sums
-    const R rt = ra + __shfl_xor_sync(full, ra, 16);
-    const R u0 = (jx + __shfl_xor_sync(full, jx, 16)) / rt;
-    const R u1 = (jy + __shfl_xor_sync(full, jy, 16)) / rt;
-    const R u2 = (jz + __shfl_xor_sync(full, jz, 16)) / rt;
-    const R usq = u0 * u0 + u1 * u1 + u2 * u2;
-    // S^b of the other component b (Eq. 7; wall sites carry Eq. 13's rho'):
-    // stored by the replayed forward step (SIN, rho = the sums [3 b + d][cell])
-    // or formed from the densities
-    const int b = 1 - a;
-    R Sb0 = 0, Sb1 = 0, Sb2 = 0;
-    if (SIN) {
-        Sb0 = rho[(long long)(3 * b + 0) * N + n.cell];
-        Sb1 = rho[(long long)(3 * b + 1) * N + n.cell];
-        Sb2 = rho[(long long)(3 * b + 2) * N + n.cell];
-    } else {
-        const R *rbp = rho + (long long)b * N;
-#pragma unroll
-        for (int i = 1; i < Q; ++i) {
-            const bool wall = (cz(i) == -1 && n.zlo) || (cz(i) == 1 && n.zhi);
-            R rv;
-            if (wall) {
-                rv = p.rho_s[b];
-                if (p.wall_mirror) rv += rbp[at(n, cx(i), cy(i), 0)];
-            } else {
-                rv = rbp[at(n, cx(i), cy(i), cz(i))];
-            }
-            const R wr = w<R>(i) * rv;
-            if (cx(i) == 1) Sb0 += wr; else if (cx(i) == -1) Sb0 -= wr;
-            if (cy(i) == 1) Sb1 += wr; else if (cy(i) == -1) Sb1 -= wr;
-            if (cz(i) == 1) Sb2 += wr; else if (cz(i) == -1) Sb2 -= wr;
-        }
-    }
-    const R Ga = a == 0 ? p.G12 : p.G21;
-    const R v0 = u0 + Ga * Sb0 + p.gext[0], v1 = u1 + Ga * Sb1 + p.gext[1], v2 = u2 + Ga * Sb2 + p.gext[2];
-    const R vsq = v0 * v0 + v1 * v1 + v2 * v2;
-    const R omega = a == 0 ? p.omega[0] : p.omega[1];
-    const R keep = R(1) - omega;
-    const R rq = ra / R(36);
-    // regularized: Pi = sum c c f - rho (T0 I + u u), as xx, yy, zz, xy, xz, yz
-    R Pi[6] = {0, 0, 0, 0, 0, 0}, tr = 0;
-    if (REG) {
-        const R T0 = R(1) / R(3);
-#pragma unroll
-        for (int i = 1; i < Q; ++i) {
-            if (cx(i)) Pi[0] += fa[i];
-            if (cy(i)) Pi[1] += fa[i];
-            if (cz(i)) Pi[2] += fa[i];
-            if (cx(i) && cy(i)) Pi[3] += R(cx(i) * cy(i)) * fa[i];
-            if (cx(i) && cz(i)) Pi[4] += R(cx(i) * cz(i)) * fa[i];
-            if (cy(i) && cz(i)) Pi[5] += R(cy(i) * cz(i)) * fa[i];
-        }
-        Pi[0] -= ra * (T0 + u0 * u0);
-        Pi[1] -= ra * (T0 + u1 * u1);
-        Pi[2] -= ra * (T0 + u2 * u2);
-        Pi[3] -= ra * u0 * u1;
-        Pi[4] -= ra * u0 * u2;
-        Pi[5] -= ra * u1 * u2;
-        tr = Pi[0] + Pi[1] + Pi[2];
-    }
-    // third-order part (REG = 2): S_a, D_a of struct Third for this component
-    Third<R> th;
-    if (REG == 2) {
-        th.zero();
-#pragma unroll
-        for (int i = 1; i < Q; ++i) th.add(i, fa[i]);
-        th.finish(ra, u0, u1, u2);
-    }
-    // ---- reverse pass -------------------------------------------------------
-    // BGK:         f* = E(rho, v) + keep (f - E(rho, u))
-    // regularized: f* = E(rho, v) + keep (k_i / 8) (c c : Pi - tr(Pi) / 3)
-    // with E_i(rho, x) = (rho / 36) k_i P(c_i . x, x . x)
-    // Opposite directions (i, i + 1) share k_i and |c_i . x|: with s = k (mu_i +
-    // mu_opp), d = k (mu_i - mu_opp) and P(+-c) = E +- O, grad P(+-c) = A +- B,
-    // the pair contributes E s + O d to the density sensitivity and (A d + B s)
-    // c_i to the velocity one.
-    R Kbar = 0, rbar = 0;
-    R vbx = 0, vby = 0, vbz = 0, vbv = 0, ubx = 0, uby = 0, ubz = 0, ubv = 0;
-    R pb[6] = {0, 0, 0, 0, 0, 0};
-    R sb[3] = {0, 0, 0}, db[3] = {0, 0, 0};   // dL/dS_a, dL/dD_a (REG = 2)
-    {
-        // rest population: c = 0, k = 12
-        const R m = mu[0], mk = m * R(12);
-        rbar += mk * (R(1) - R(1.5) * vsq);
-        vbv += R(3) * mk;
-        if (!REG) {
-            const R Pu = R(1) - R(1.5) * usq;
-            Kbar += m * (fa[0] - rq * R(12) * Pu);
-            rbar -= keep * mk * Pu;
-            ubv += R(3) * mk;
-        } else {
-            Kbar += mk * R(0.125) * (-tr / R(3));
-            const R nb = keep * mk * R(0.125);
-            pb[0] -= nb / R(3);
-            pb[1] -= nb / R(3);
-            pb[2] -= nb / R(3);
-        }
-    }
-#pragma unroll
-    for (int i = 1; i < Q; i += 2) {
-        const R ki = R(k36(i));
-        const R sg = (mu[i] + mu[i + 1]) * ki, df = (mu[i] - mu[i + 1]) * ki;
-        const R cv = cdot<R>(i, v0, v1, v2), cv2 = cv * cv;
-        const R E = R(1) + R(4.5) * cv2 - R(1.5) * vsq, O = cv * (R(3) + R(4.5) * cv2 - R(4.5) * vsq);
-        rbar += E * sg + O * df;
-        const R t = (R(3) + R(13.5) * cv2 - R(4.5) * vsq) * df + R(9) * cv * sg;
-        if (cx(i)) vbx += R(cx(i)) * t;
-        if (cy(i)) vby += R(cy(i)) * t;
-        if (cz(i)) vbz += R(cz(i)) * t;
-        vbv += R(3) * sg + R(9) * cv * df;
-        if (!REG) {
-            const R cu = cdot<R>(i, u0, u1, u2), cu2 = cu * cu;
-            const R Eu = R(1) + R(4.5) * cu2 - R(1.5) * usq, Ou = cu * (R(3) + R(4.5) * cu2 - R(4.5) * usq);
-            const R Pm = Eu * sg + Ou * df;
-            Kbar += mu[i] * fa[i] + mu[i + 1] * fa[i + 1] - rq * Pm;
-            rbar -= keep * Pm;
-            const R tu = (R(3) + R(13.5) * cu2 - R(4.5) * usq) * df + R(9) * cu * sg;
-            if (cx(i)) ubx += R(cx(i)) * tu;
-            if (cy(i)) uby += R(cy(i)) * tu;
-            if (cz(i)) ubz += R(cz(i)) * tu;
-            ubv += R(3) * sg + R(9) * cu * df;
-        } else {
-            const int c0 = cx(i), c1 = cy(i), c2 = cz(i);
-            const R ccP = R(c0 * c0) * Pi[0] + R(c1 * c1) * Pi[1] + R(c2 * c2) * Pi[2] + R(2 * c0 * c1) * Pi[3] +
-                          R(2 * c0 * c2) * Pi[4] + R(2 * c1 * c2) * Pi[5];
-            Kbar += sg * R(0.125) * (ccP - tr / R(3));
-            const R nb = keep * sg * R(0.125);
-            pb[0] += nb * (R(c0 * c0) - R(1) / R(3));
-            pb[1] += nb * (R(c1 * c1) - R(1) / R(3));
-            pb[2] += nb * (R(c2 * c2) - R(1) / R(3));
-            if (c0 && c1) pb[3] += nb * R(c0 * c1);
-            if (c0 && c2) pb[4] += nb * R(c0 * c2);
-            if (c1 && c2) pb[5] += nb * R(c1 * c2);
-            if (REG == 2) {
-                // f*_i +- keep (k_i / 8) sum_a (S_a h3s3(i, a) + D_a h3d(i, a)) for i, opp(i)
-                Kbar += df * R(0.125) * (th.odd(i) / (R(k36(i)) * R(0.125)));
-                const R nd = keep * df * R(0.125);
-#pragma unroll
-                for (int q = 0; q < 3; ++q) {
-                    if (h3s3(i, q)) sb[q] += nd * R(h3s3(i, q));
-                    if (h3d(i, q)) db[q] += nd * R(h3d(i, q));
-                }
-            }
-        }
-    }
-    rbar /= R(36);
-    // dL/dv^a
-    const R vbar0 = rq * (vbx - v0 * vbv), vbar1 = rq * (vby - v1 * vbv), vbar2 = rq * (vbz - v2 * vbv);
-    R ub0 = vbar0, ub1 = vbar1, ub2 = vbar2;
-    if (!REG) {
-        ub0 -= keep * rq * (ubx - u0 * ubv);
-        ub1 -= keep * rq * (uby - u1 * ubv);
-        ub2 -= keep * rq * (ubz - u2 * ubv);
-    } else {
-        // pb holds dL/dPi for xx, yy, zz and one of each symmetric off-diagonal pair
-        const R T0 = R(1) / R(3);
-        rbar -= pb[0] * (T0 + u0 * u0) + pb[1] * (T0 + u1 * u1) + pb[2] * (T0 + u2 * u2) +
-                R(2) * (pb[3] * u0 * u1 + pb[4] * u0 * u2 + pb[5] * u1 * u2);
-        ub0 -= R(2) * ra * (pb[0] * u0 + pb[3] * u1 + pb[4] * u2);
-        ub1 -= R(2) * ra * (pb[3] * u0 + pb[1] * u1 + pb[5] * u2);
-        ub2 -= R(2) * ra * (pb[4] * u0 + pb[5] * u1 + pb[2] * u2);
-        if (REG == 2) {
-            // S_a = (1/3) sum h3s3 f - rho u_a (u_b^2 + u_c^2) / 2,
-            // D_a = sum h3d f - 3/2 rho u_a (u_b^2 - u_c^2)   (b < c the other axes)
-            const R u[3] = {u0, u1, u2};
-            R ubq[3] = {0, 0, 0};
-#pragma unroll
-            for (int q = 0; q < 3; ++q) {
-                const int qb = q == 0 ? 1 : 0, qc = q == 2 ? 1 : 2;
-                const R ua = u[q], ubb = u[qb], ucc = u[qc];
-                rbar -= sb[q] * R(0.5) * ua * (ubb * ubb + ucc * ucc) + db[q] * R(1.5) * ua * (ubb * ubb - ucc * ucc);
-                ubq[q] -= ra * (sb[q] * R(0.5) * (ubb * ubb + ucc * ucc) + db[q] * R(1.5) * (ubb * ubb - ucc * ucc));
-                ubq[qb] -= ra * ua * ubb * (sb[q] + R(3) * db[q]);
-                ubq[qc] -= ra * ua * ucc * (sb[q] - R(3) * db[q]);
-            }
-            ub0 += ubq[0];
-            ub1 += ubq[1];
-            ub2 += ubq[2];
-        }
-    }
-    // u = j / rho over both components: dL/dj = ubar / rho, dL/drho += -(ubar . u) / rho
-    const R U0 = ub0 + __shfl_xor_sync(full, ub0, 16);
-    const R U1 = ub1 + __shfl_xor_sync(full, ub1, 16);
-    const R U2 = ub2 + __shfl_xor_sync(full, ub2, 16);
-    const R jb0 = U0 / rt, jb1 = U1 / rt, jb2 = U2 / rt;
-    const R base = rbar - (U0 * u0 + U1 * u1 + U2 * u2) / rt;
-    if (store && MASK && (lw & 1u)) {
-        // solid site: no populations, no sensitivities (a = 0 keeps it out of D)
-        R *lo = lam_loc + (size_t)a * Q * (size_t)N + n.cell;
-#pragma unroll
-        for (int i = 0; i < Q; ++i) lo[(unsigned)i * N32] = R(0);
-#pragma unroll
-        for (int d = 0; d < 3; ++d) aout[((long long)b * 3 + d) * N + n.cell] = R(0);
-    } else if (store) {
-        R *lo = lam_loc + (size_t)a * Q * (size_t)N + n.cell;
-#pragma unroll
-        for (int i = 0; i < Q; ++i) {
-            R l = base + cdot<R>(i, jb0, jb1, jb2);
-            if (!REG) {
-                l += keep * mu[i];
-            } else {
-                const int c0 = cx(i), c1 = cy(i), c2 = cz(i);
-                l += R(c0 * c0) * pb[0] + R(c1 * c1) * pb[1] + R(c2 * c2) * pb[2] + R(2 * c0 * c1) * pb[3] +
-                     R(2 * c0 * c2) * pb[4] + R(2 * c1 * c2) * pb[5];
-                if (REG == 2) {
-#pragma unroll
-                    for (int q = 0; q < 3; ++q) {
-                        if (h3s3(i, q)) l += sb[q] * (R(h3s3(i, q)) / R(3));
-                        if (h3d(i, q)) l += db[q] * R(h3d(i, q));
-                    }
-                }
-            }
-            lo[(unsigned)i * N32] = l;
-        }
-        // g^a = G^{ab} S^b + g_ext:  dL/dS^b = G^{ab} vbar,  dL/dG^{ab} = vbar . S^b
-        aout[((long long)b * 3 + 0) * N + n.cell] = Ga * vbar0;
-        aout[((long long)b * 3 + 1) * N + n.cell] = Ga * vbar1;
-        aout[((long long)b * 3 + 2) * N + n.cell] = Ga * vbar2;
-        par_g += vbar0 * Sb0 + vbar1 * Sb1 + vbar2 * Sb2;
-        // keep = 1 - 1/tau: dkeep/dtau = 1/tau^2
-        par_t += Kbar * omega * omega;
-    }
-}
-
-// Grid-stride over groups of 16 cells per warp; lanes 0-15 take component 0
-// and lanes 16-31 component 1 of the same 16 cells.  Per-block FP64 partials
-// of dL/dG^{12}, dL/dG^{21}, dL/dtau_1, dL/dtau_2 accumulate over the steps.
-// MASK: links holds the mask's link words (bit 0: solid site; bit i: x - c_i
-// solid).  The lanes of a solid site still run the arithmetic (on meaningless
-// values), so that both lanes of every pair take part in the shuffles, and
-// store zeros.
-template <int S, int REG, bool SIN, bool MASK>
-__global__ void __launch_bounds__(kThreadsA, 2)
-k_adj_local(const typename Store<S>::T *__restrict__ f, const typename Store<S>::R *__restrict__ rho,
-            const typename Store<S>::R *__restrict__ lam_next, const typename Store<S>::R *__restrict__ Dn,
-            typename Store<S>::R *__restrict__ lam_loc, typename Store<S>::R *__restrict__ aout,
-            double *__restrict__ partials, Phys<typename Store<S>::R> p, const unsigned *__restrict__ links)
-{
-    const int lane = threadIdx.x & 31;
-    const int a = lane >> 4;
-    const long long warps = (long long)gridDim.x * (kThreadsA / 32);
-    const long long groups = (p.N + 15) / 16;
-    // per-thread partials in the arithmetic type over the thread's cells (a few
-    // tens per step), summed in FP64 across the block: the FP64 pipe is a
-    // small fraction of the FP32 one on this GPU
-    typename Store<S>::R pg = 0, pt = 0;
-    for (long long wg = (long long)blockIdx.x * (kThreadsA / 32) + (threadIdx.x >> 5); wg < groups; wg += warps) {
-        const long long c = wg * 16 + (lane & 15);
-        const bool valid = c < p.N;
-        Nb n;
-        nb_of(p, (unsigned)(valid ? c : p.N - 1), n);
-        const unsigned lw = MASK ? __ldg(links + n.cell) : 0u;
-        adj_half<S, REG, SIN, MASK>(f, rho, lam_next, Dn, lam_loc, aout, p, n, a, valid, pg, pt, lw);
-    }
-    // lanes of component a hold parts of par[a] and par[2 + a]
-    __shared__ double sh[4][kThreadsA];
-    const int t = threadIdx.x;
-    for (int k = 0; k < 4; ++k) sh[k][t] = 0;
-    sh[a][t] = pg;
-    sh[2 + a][t] = pt;
-    __syncthreads();
-    for (int s = kThreadsA / 2; s > 0; s >>= 1) {
-        if (t < s)
-            for (int k = 0; k < 4; ++k) sh[k][t] += sh[k][t + s];
-        __syncthreads();
-    }
-    if (t < 4) partials[(long long)blockIdx.x * 4 + t] += sh[t][0];
-}
-
-// D_b(x) = dL/drho^b(x) = sum_k w_k c_k . a_b(x - c_k), plus the mirror-wall
-// terms: a wall site y + c_k seen from y presents the density of its mirror
-// cell y + (c_kx, c_ky, 0).
-//
-// Output tiles of 32 x 8 x DZ cells: the six fields a_b,d over the tile and a
-// one-cell margin (periodic images in x and y; in z periodic images, or zeros
-// for wall sites, whose terms the sum leaves out) are staged in shared memory
-// with coalesced loads, then each thread sums its z column of DZ cells from
-// shared memory, in the order of the per-link formula above.
-constexpr int kDX = 32, kDY = 8;
-template <class R>
-struct DTile {
-    static constexpr int DZ = sizeof(R) == 8 ? 4 : 8;   // 98 KB (FP64) / 82 KB (FP32) of staging
-    static constexpr int BX = kDX + 2, BY = kDY + 2, BZ = DZ + 2;
-    static constexpr int BOX = BX * BY * BZ;
-    static constexpr size_t kSmem = sizeof(R) * 6 * (size_t)BOX;
-};
-
-template <class R>
-__global__ void __launch_bounds__(kThreadsA, 2)
-k_adj_D(const R *__restrict__ a, R *__restrict__ D, Phys<R> p, int ntx)
-{
-    using T = DTile<R>;
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    R *box = reinterpret_cast<R *>(smem_raw);   // [6][BZ][BY][BX]
-    // wrapped offsets of the box's rows (hz, hy) and columns hx, formed once per
-    // CTA (a row behind a z wall is marked -1 and staged as zeros)
-    __shared__ int row_off[T::BZ * T::BY];
-    __shared__ int col_off[T::BX];
-    const int t = threadIdx.x;
-    const int x0 = (blockIdx.x % ntx) * kDX, y0 = (blockIdx.x / ntx) * kDY, z0 = blockIdx.y * T::DZ;
-    const int nx = p.nx, ny = p.ny, nz = p.nz;
-    const unsigned N32 = (unsigned)p.N;   // 6 N < 2^32 (19 N is, on the host)
-    if (t < T::BZ * T::BY) {
-        const int hy = t % T::BY, hz = t / T::BY;
-        int gy = (y0 - 1 + hy) % ny;
-        if (gy < 0) gy += ny;
-        int gz = z0 - 1 + hz;
-        bool inside = true;
-        if (p.wall_z) {
-            inside = gz >= 0 && gz < nz;
-        } else {
-            gz %= nz;
-            if (gz < 0) gz += nz;
-        }
-        row_off[t] = inside ? (gz * ny + gy) * nx : -1;
-    } else if (t - T::BZ * T::BY < T::BX) {
-        const int hx = t - T::BZ * T::BY;
-        int gx = (x0 - 1 + hx) % nx;
-        if (gx < 0) gx += nx;
-        col_off[hx] = gx;
-    }
-    static_assert(T::BZ * T::BY + T::BX <= kThreadsA, "one offset per thread");
-    __syncthreads();
-    // all of the thread's loads are issued before the first shared-memory
-    // store, so that they are in flight together
-    constexpr int kIt = (T::BOX + kThreadsA - 1) / kThreadsA;
-    R val[kIt][6];
-#pragma unroll
-    for (int it = 0; it < kIt; ++it) {
-        const int h = it * kThreadsA + t;
-        const int ro = h < T::BOX ? row_off[h / T::BX] : -1;
-        const unsigned c = ro >= 0 ? (unsigned)(ro + col_off[h % T::BX]) : 0u;
-#pragma unroll
-        for (int q = 0; q < 6; ++q) val[it][q] = ro >= 0 ? __ldg(a + (unsigned)q * N32 + c) : R(0);
-    }
-#pragma unroll
-    for (int it = 0; it < kIt; ++it) {
-        const int h = it * kThreadsA + t;
-        if (h < T::BOX) {
-#pragma unroll
-            for (int q = 0; q < 6; ++q) box[q * T::BOX + h] = val[it][q];
-        }
-    }
-    __syncthreads();
-    const int lx = t % kDX, ly = t / kDX;
-    const int x = x0 + lx, y = y0 + ly;
-    if (x >= nx || y >= ny) return;
-    for (int k = 0; k < T::DZ; ++k) {
-        const int z = z0 + k;
-        if (z >= nz) break;
-        const bool zlo = p.wall_z && z == 0, zhi = p.wall_z && z == nz - 1;
-        const unsigned cell = ((unsigned)z * (unsigned)ny + (unsigned)y) * (unsigned)nx + (unsigned)x;
-#pragma unroll
-        for (int b = 0; b < 2; ++b) {
-            const R *bb = box + 3 * b * T::BOX;
-            // box value of field d at offset (dx, dy, dz) from this cell
-            auto at3 = [&](int d, int dx, int dy, int dz) {
-                return bb[d * T::BOX + ((k + 1 + dz) * T::BY + (ly + 1 + dy)) * T::BX + (lx + 1 + dx)];
-            };
-            R s = 0;
-#pragma unroll
-            for (int q = 1; q < Q; ++q) {
-                // wall sources hold zeros in the box, so their terms vanish
-                R c = 0;
-                if (cx(q)) c += R(cx(q)) * at3(0, -cx(q), -cy(q), -cz(q));
-                if (cy(q)) c += R(cy(q)) * at3(1, -cx(q), -cy(q), -cz(q));
-                if (cz(q)) c += R(cz(q)) * at3(2, -cx(q), -cy(q), -cz(q));
-                s += w<R>(q) * c;
-                if (p.wall_mirror && ((cz(q) == -1 && zlo) || (cz(q) == 1 && zhi))) {
-                    R m = 0;
-                    if (cx(q)) m += R(cx(q)) * at3(0, -cx(q), -cy(q), 0);
-                    if (cy(q)) m += R(cy(q)) * at3(1, -cx(q), -cy(q), 0);
-                    m += R(cz(q)) * at3(2, -cx(q), -cy(q), 0);
-                    s += w<R>(q) * m;
-                }
-            }
-            D[(unsigned)b * N32 + cell] = s;
-        }
-    }
-}
-
-// Mirror wall model under a mask: a solid site s presents
-// rho_w(s) = sum_j k_j rho(s + c_j) / sum_j k_j + rho_s over its fluid
-// neighbours s + c_j (Eq. 13, modified model), so each fluid cell x next to s
-// gains dL/drho_w(s) k_j / sum_j k_j.  dL/drho_w(s) is the regular D sum at s
-// (k_adj_D, with a = 0 at solid sites), which this pass reads and leaves as
-// it is; it runs over the fluid cells with a solid neighbour.
-template <class R>
-__global__ void __launch_bounds__(kThreadsA)
-k_adj_D_wall(R *__restrict__ D, const unsigned char *__restrict__ solid, Phys<R> p,
-             const unsigned *__restrict__ cells, long long n)
-{
-    const long long t = (long long)blockIdx.x * kThreadsA + threadIdx.x;
-    if (t >= n) return;
-    Nb nx_;
-    nb_of(p, cells[t], nx_);
-    const unsigned N32 = (unsigned)p.N;
-    R add0 = 0, add1 = 0;
-#pragma unroll
-    for (int i = 1; i < Q; ++i) {
-        const unsigned sc = at(nx_, cx(i), cy(i), cz(i));
-        if (!__ldg(solid + sc)) continue;
-        Nb ns;
-        nb_of(p, sc, ns);
-        int den36 = 0;
-#pragma unroll
-        for (int j = 1; j < Q; ++j)
-            if (!__ldg(solid + at(ns, cx(j), cy(j), cz(j)))) den36 += k36(j);
-        const R wgt = R(k36(i)) / R(den36);
-        add0 += wgt * D[sc];
-        add1 += wgt * D[N32 + sc];
-    }
-    D[nx_.cell] += add0;
-    D[N32 + nx_.cell] += add1;
-}
-
-template <class R, class G>
-__global__ void __launch_bounds__(kThreadsA)
-k_adj_seed(const G *__restrict__ g1, const G *__restrict__ g2, R *__restrict__ lam, long long N)
-{
-    const long long c = (long long)blockIdx.x * kThreadsA + threadIdx.x;
-    if (c >= N) return;
-    const R v1 = g1 ? (R)g1[c] : R(0);
-    const R v2 = g2 ? (R)g2[c] : R(0);
-#pragma unroll
-    for (int i = 0; i < Q; ++i) {
-        lam[(long long)i * N + c] = v1;
-        lam[(long long)(Q + i) * N + c] = v2;
-    }
-}
-
-// dL/drho^a_0 = sum_i w_i lambda^0_i = sum_i w_i lambda_loc^0_i + D^0_a (sum_i w_i = 1).
-template <class R>
-__global__ void __launch_bounds__(kThreadsA)
-k_adj_rho0(const R *__restrict__ lam, const R *__restrict__ D, double *__restrict__ g1, double *__restrict__ g2,
-           long long N, const unsigned char *__restrict__ solid)
-{
-    const long long c = (long long)blockIdx.x * kThreadsA + threadIdx.x;
-    if (c >= N) return;
-    if (solid && solid[c]) {   // a solid site holds no fluid: its initial density does not enter
-        if (g1) g1[c] = 0.0;
-        if (g2) g2[c] = 0.0;
-        return;
-    }
-    double s1 = 0, s2 = 0;
-#pragma unroll
-    for (int i = 0; i < Q; ++i) {
-        s1 += wd(i) * (double)lam[(long long)i * N + c];
-        s2 += wd(i) * (double)lam[(long long)(Q + i) * N + c];
-    }
-    if (g1) g1[c] = s1 + (double)D[c];
-    if (g2) g2[c] = s2 + (double)D[N + c];
-}
-
-template <class R>
-Phys<R> make_phys_a(const HostPhys &h)
-{
-    Phys<R> p;
-    p.nx = h.nx; p.ny = h.ny; p.nz = h.nz; p.N = h.N;
-    p.wall_z = h.wall_z;
-    p.wall_mirror = h.wall_mirror;
-    p.omega[0] = (R)(1.0 / h.tau[0]);
-    p.omega[1] = (R)(1.0 / h.tau[1]);
-    p.G12 = (R)h.G12; p.G21 = (R)h.G21;
-    for (int d = 0; d < 3; ++d) p.gext[d] = (R)h.gext[d];
-    p.rho_s[0] = (R)h.rho_s[0]; p.rho_s[1] = (R)h.rho_s[1];
-    p.rho0 = (R)h.rho0;
-    p.ref_off = h.ref_off;
-    return p;
-}
-
-inline unsigned gridA(long long N) { return (unsigned)((N + kThreadsA - 1) / kThreadsA); }
-
-constexpr int kMaxAttrDevices = 64;
-
-// Launch of the tiled D pass; its dynamic shared-memory attribute belongs to
-// the device context and is set once per device.
-template <class R>
-cudaError_t launch_adj_D(const HostPhys &h, const R *a, R *D, const Phys<R> &p, cudaStream_t s)
-{
-    using T = DTile<R>;
-    const int ntx = (h.nx + kDX - 1) / kDX, nty = (h.ny + kDY - 1) / kDY;
-    const long long zb = (h.nz + T::DZ - 1) / T::DZ;
-    if ((long long)ntx * nty >= (1LL << 31) || zb > 65535) return cudaErrorInvalidConfiguration;
-    static std::atomic<int> attr_set[kMaxAttrDevices];
-    int dev = 0;
-    cudaError_t e = cudaGetDevice(&dev);
-    if (e != cudaSuccess) return e;
-    const bool cached = dev >= 0 && dev < kMaxAttrDevices;
-    if (!cached || !attr_set[dev].load(std::memory_order_acquire)) {
-        e = cudaFuncSetAttribute((const void *)k_adj_D<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)T::kSmem);
-        if (e != cudaSuccess) return e;
-        if (cached) attr_set[dev].store(1, std::memory_order_release);
-    }
-    k_adj_D<R><<<dim3((unsigned)(ntx * nty), (unsigned)zb), kThreadsA, T::kSmem, s>>>(a, D, p, ntx);
-    return cudaGetLastError();
-}
-
-template <int S>
-cudaError_t adj_step_t(const HostPhys &h, const void *f, const void *rho, int rho_is_sums, const void *lam_next,
-                       const void *Dn, void *lam_loc, void *a, void *Dout, double *partials, cudaStream_t s)
-{
-    using T = typename Store<S>::T;
-    using R = typename Store<S>::R;
-    const Phys<R> p = make_phys_a<R>(h);
-#define LBM_ADJ(REG_, SIN_, MASK_)                                                                              \
-    k_adj_local<S, REG_, SIN_, MASK_><<<adjoint_blocks(), kThreadsA, 0, s>>>(                                  \
-        (const T *)f, (const R *)rho, (const R *)lam_next, (const R *)Dn, (R *)lam_loc, (R *)a, partials, p,  \
-        h.links)
-#define LBM_ADJ_REG(SIN_, MASK_)                  \
-    do {                                          \
-        if (reg == 1) LBM_ADJ(1, SIN_, MASK_);    \
-        else if (reg == 2) LBM_ADJ(2, SIN_, MASK_); \
-        else LBM_ADJ(0, SIN_, MASK_);             \
-    } while (0)
-    const int reg = h.collision == LBM_REGULARIZED ? 1 : (h.collision == LBM_REGULARIZED3 ? 2 : 0);
-    if (h.links) {
-        if (rho_is_sums) LBM_ADJ_REG(true, true);
-        else LBM_ADJ_REG(false, true);
-    } else {
-        if (rho_is_sums) LBM_ADJ_REG(true, false);
-        else LBM_ADJ_REG(false, false);
-    }
-#undef LBM_ADJ_REG
-#undef LBM_ADJ
-    cudaError_t e = launch_adj_D<R>(h, (const R *)a, (R *)Dout, p, s);
-    if (e == cudaSuccess && h.links && h.wall_mirror && h.n_bfluid > 0) {
-        k_adj_D_wall<R><<<gridA(h.n_bfluid), kThreadsA, 0, s>>>((R *)Dout, h.solid, p, h.bfluid, h.n_bfluid);
-        e = cudaGetLastError();
-    }
-    return e;
-}
-
-}  // namespace
+extern template cudaError_t adj::adj_step_t<ST_F64>(const HostPhys &, const void *, const void *, int,
+                                       const void *, const void *, void *, void *, void *, double *,
+                                       cudaStream_t);
+extern template cudaError_t adj::adj_step_t<ST_F32>(const HostPhys &, const void *, const void *, int,
+                                       const void *, const void *, void *, void *, void *, double *,
+                                       cudaStream_t);
+extern template cudaError_t adj::adj_step_t<ST_F16_DEV>(const HostPhys &, const void *, const void *, int,
+                                       const void *, const void *, void *, void *, void *, double *,
+                                       cudaStream_t);
+extern template cudaError_t adj::adj_step_t<ST_BF16_DEV>(const HostPhys &, const void *, const void *, int,
+                                       const void *, const void *, void *, void *, void *, double *,
+                                       cudaStream_t);
+extern template cudaError_t adj::adj_step_t<ST_F16_REL>(const HostPhys &, const void *, const void *, int,
+                                       const void *, const void *, void *, void *, void *, double *,
+                                       cudaStream_t);
+extern template cudaError_t adj::adj_step_t<ST_BF16_REL>(const HostPhys &, const void *, const void *, int,
+                                       const void *, const void *, void *, void *, void *, double *,
+                                       cudaStream_t);
 
 // One resident wave of k_adj_local on the current device: kAdjBlocksPerSM
 // CTAs on every SM.
@@ -678,12 +33,12 @@ cudaError_t launch_adjoint_step(const HostPhys &p, const void *f, const void *rh
                                 const void *Dn, void *lam_loc, void *a, void *Dout, double *partials, cudaStream_t s)
 {
     switch (p.storage) {
-    case ST_F64: return adj_step_t<ST_F64>(p, f, rho, rho_is_sums, lam_next, Dn, lam_loc, a, Dout, partials, s);
-    case ST_F32: return adj_step_t<ST_F32>(p, f, rho, rho_is_sums, lam_next, Dn, lam_loc, a, Dout, partials, s);
-    case ST_F16_DEV: return adj_step_t<ST_F16_DEV>(p, f, rho, rho_is_sums, lam_next, Dn, lam_loc, a, Dout, partials, s);
-    case ST_BF16_DEV: return adj_step_t<ST_BF16_DEV>(p, f, rho, rho_is_sums, lam_next, Dn, lam_loc, a, Dout, partials, s);
-    case ST_F16_REL: return adj_step_t<ST_F16_REL>(p, f, rho, rho_is_sums, lam_next, Dn, lam_loc, a, Dout, partials, s);
-    case ST_BF16_REL: return adj_step_t<ST_BF16_REL>(p, f, rho, rho_is_sums, lam_next, Dn, lam_loc, a, Dout, partials, s);
+    case ST_F64: return adj::adj_step_t<ST_F64>(p, f, rho, rho_is_sums, lam_next, Dn, lam_loc, a, Dout, partials, s);
+    case ST_F32: return adj::adj_step_t<ST_F32>(p, f, rho, rho_is_sums, lam_next, Dn, lam_loc, a, Dout, partials, s);
+    case ST_F16_DEV: return adj::adj_step_t<ST_F16_DEV>(p, f, rho, rho_is_sums, lam_next, Dn, lam_loc, a, Dout, partials, s);
+    case ST_BF16_DEV: return adj::adj_step_t<ST_BF16_DEV>(p, f, rho, rho_is_sums, lam_next, Dn, lam_loc, a, Dout, partials, s);
+    case ST_F16_REL: return adj::adj_step_t<ST_F16_REL>(p, f, rho, rho_is_sums, lam_next, Dn, lam_loc, a, Dout, partials, s);
+    case ST_BF16_REL: return adj::adj_step_t<ST_BF16_REL>(p, f, rho, rho_is_sums, lam_next, Dn, lam_loc, a, Dout, partials, s);
     default: return cudaErrorInvalidValue;
     }
 }

@@ -1,0 +1,10 @@
+// Instances of the reverse step for the bf16rel storage format.
+#include "lbm_adjoint_impl.cuh"
+
+namespace lbm {
+namespace adj {
+template cudaError_t adj_step_t<ST_BF16_REL>(const HostPhys &, const void *, const void *, int,
+                                       const void *, const void *, void *, void *, void *, double *,
+                                       cudaStream_t);
+}  // namespace adj
+}  // namespace lbm

@@ -725,7 +725,7 @@ lbm_status lbm_record(lbm_lattice *h, long n_steps, int ckpt_every)
         CK(cudaMalloc(&h->ws_lam_loc, rb * 2 * lbm::Q * N), "lbm_record: reverse-pass lambda_loc");
         CK(cudaMalloc(&h->ws_a, rb * 6 * N), "lbm_record: reverse-pass a");
         CK(cudaMalloc(&h->ws_d, rb * 4 * N), "lbm_record: reverse-pass D");
-        CK(cudaMalloc(&h->ws_seg, sb * (E + 1)), "lbm_record: reverse-pass segment states");
+        CK(cudaMalloc(&h->ws_seg, sb * E), "lbm_record: reverse-pass segment states");
         // per replayed step: the interaction sums (fused step, 6 N) or the
         // densities (two-kernel step, 2 N)
         CK(cudaMalloc(&h->ws_rseg, rb * (h->use_fused ? 6 : 2) * N * E), "lbm_record: reverse-pass segment sums");
@@ -796,10 +796,9 @@ lbm_status lbm_adjoint(lbm_lattice *h, const double *dL_drho1, const double *dL_
     // One checkpoint segment of len steps on stream st: recompute its forward
     // states and their densities, then len reverse steps with the adjoint
     // fields ping-ponging from (la, da).
-    // The fused replay keeps each step's interaction sums (6 N reals; the
-    // last state of a segment is stepped once more into the spare state slot
-    // for them); the two-kernel replay keeps each step's densities (2 N reals;
-    // the last state's from a density pass).
+    // The fused replay keeps each step's interaction sums (6 N reals; for the
+    // last state of a segment a sums-only launch); the two-kernel replay keeps
+    // each step's densities (2 N reals; the last state's from a density pass).
     const size_t rstride = rb * (use_fused ? 6 : 2) * N;
     // One checkpoint segment of len steps on stream st: recompute its forward
     // states, then len reverse steps with the adjoint fields ping-ponging from
@@ -809,7 +808,8 @@ lbm_status lbm_adjoint(lbm_lattice *h, const double *dL_drho1, const double *dL_
         const long nrec = use_fused ? len : len - 1;
         for (long t = 0; t < nrec && er == cudaSuccess; ++t) {
             const void *fi = (char *)seg + sb * (size_t)t;
-            void *fo = (char *)seg + sb * (size_t)(t + 1);
+            // the fused replay's last step only supplies the interaction sums
+            void *fo = (use_fused && t == nrec - 1) ? nullptr : (char *)seg + sb * (size_t)(t + 1);
             void *rt = (char *)rseg + rstride * (size_t)t;
             er = use_fused ? lbm::launch_step_fused(h->phys, fi, fo, st, nullptr, rt)
                            : lbm::launch_step_split(h->phys, fi, fo, rt, st);

@@ -196,6 +196,36 @@ struct GatherAll<S, Q> {
                                                typename Store<S>::R (&)[Q2]) {}
 };
 
+// The same gather with the pairs kept as stored (one 32-bit word per pair in
+// the 16-bit formats), decoded where they are used (decode_all): a plane in
+// flight across the collision then holds 19 registers instead of 38.
+template <int S, int I>
+struct GatherRaw {
+    __device__ __forceinline__ static void run(const typename Store<S>::T *__restrict__ f, long long N,
+                                               const PlaneRef &pr, const Col &c, unsigned lw,
+                                               typename Store<S>::Raw (&r)[Q])
+    {
+        int d;
+        const int e = gather_elem<I>(pr, c, lw, d);
+        r[I] = Store<S>::load_raw(f + 2 * (size_t)((unsigned)d * (unsigned)N + (unsigned)e));
+        GatherRaw<S, I + 1>::run(f, N, pr, c, lw, r);
+    }
+};
+template <int S>
+struct GatherRaw<S, Q> {
+    __device__ __forceinline__ static void run(const typename Store<S>::T *__restrict__, long long, const PlaneRef &,
+                                               const Col &, unsigned, typename Store<S>::Raw (&)[Q]) {}
+};
+
+template <int S>
+__device__ __forceinline__ void decode_all(const typename Store<S>::Raw (&r)[Q], float2 rr,
+                                           typename Store<S>::R (&v)[Q2])
+{
+    using R = typename Store<S>::R;
+#pragma unroll
+    for (int i = 0; i < Q; ++i) Store<S>::decode2(r[i], w<R>(i) * rr.x, w<R>(i) * rr.y, v[i], v[Q + i]);
+}
+
 // rho^1, rho^2 and momentum of a gathered population set.  The densities are
 // summed in the grouping of the halo partial gathers, (directions 0-6 +
 // directions 7-12) + directions 13-18, so that a cell's density is the same
@@ -309,13 +339,15 @@ __device__ __forceinline__ void collide_cell(typename Store<S>::T *__restrict__ 
         typename Store<S>::T *os = fout + 2 * cell;
         const unsigned n32 = (unsigned)p.N;
 #pragma unroll
-        for (int i = 0; i < Q; ++i) {
+        for (int i = 0; i < Q && fout; ++i) {
             // zero in every format: the deviation formats code it against w_i rho0,
             // the relative ones code 0 as 0 whatever their parameter
             const R ref = Store<S>::kRel ? R(1) : w<R>(i) * R(p.rho0);
             Store<S>::store2(os + 2 * (size_t)((unsigned)i * n32), R(0), R(0), ref, ref);
         }
-        if constexpr (Store<S>::kRel) state_ref(fout, p.ref_off)[cell] = make_float2(1.0f, 1.0f);
+        if constexpr (Store<S>::kRel) {
+            if (fout) state_ref(fout, p.ref_off)[cell] = make_float2(1.0f, 1.0f);
+        }
         if (s_out) {
 #pragma unroll
             for (int k = 0; k < 6; ++k) s_out[(long long)k * p.N + cell] = R(0);
@@ -353,6 +385,7 @@ __device__ __forceinline__ void collide_cell(typename Store<S>::T *__restrict__ 
 #pragma unroll
             for (int d = 0; d < 3; ++d) s_out[(long long)(3 * b + d) * p.N + cell] = Sb[b][d];
     }
+    if (!fout) return;   // the interaction sums alone (the last step of a replayed segment)
     // g^a = sum_b F^{ab} / rho^a + g_ext = G^{ab} S^b + g_ext
     R v1x = ux + p.G12 * Sb[1][0] + p.gext[0], v1y = uy + p.G12 * Sb[1][1] + p.gext[1],
       v1z = uz + p.G12 * Sb[1][2] + p.gext[2];
@@ -705,13 +738,29 @@ k_step_fused(const typename Store<S>::T *__restrict__ fin, typename Store<S>::T 
         halo_task(pr, link_of(pr, cht), 1);
     }
     // interior populations of plane z0+1, in registers until the first iteration
+    // Interior populations of plane z+1, in registers from the gathers issued
+    // before the previous collision until phase A: decoded (v), or, in the
+    // 16-bit instances that run periodic lattices without a mask (the ones
+    // measured to gain from it), as stored (rv, with the reference densities
+    // rrv), which keeps 19 registers instead of 38 live across the collision.
+    constexpr bool kRaw = sizeof(typename Store<S>::Raw) < sizeof(float2) && !WALLZ && !MASK;
     R v[Q2];
+    typename Store<S>::Raw rv[Q];
+    float2 rrv = make_float2(0.f, 0.f);
     unsigned lwB, lwC = 0, hlw = 0;   // link words: column at z+1, z+2; halo task cell at z+2
     float2 wdB = make_float2(0.f, 0.f);   // wall density of the column at z+1 (a solid site)
+    auto gather_interior = [&](const PlaneRef &pr, unsigned lw) {
+        if constexpr (kRaw) {
+            rrv = gather_ref<S>(fin, p, pr, ci);
+            GatherRaw<S, 0>::run(fin, p.N, pr, ci, lw, rv);
+        } else {
+            GatherAll<S, 0>::run(fin, p.N, gather_ref<S>(fin, p, pr, ci), pr, ci, lw, v);
+        }
+    };
     {
         const PlaneRef pr = plane_ref<WALLZ>(p, z0 + 1);
         lwB = link_of(pr, ci);
-        if (!pr.constant) GatherAll<S, 0>::run(fin, p.N, gather_ref<S>(fin, p, pr, ci), pr, ci, lwB, v);
+        if (!pr.constant) gather_interior(pr, lwB);
         if (MASK) {
             if (lwB & 1u) wdB = wall_rho(pr, ci);
             const PlaneRef pr2 = plane_ref<WALLZ>(p, z0 + 2);
@@ -737,6 +786,9 @@ k_step_fused(const typename Store<S>::T *__restrict__ fin, typename Store<S>::T 
         if (need2 && has_halo && !hsol && !pr2.constant) halo_load<S>(fin, p, pr2, cht, hlw, g, hv);
         if (tid < kHalo) halo_combine<S>(p, sm, inv, s_p, (k + 1) & 1, pr1, h, hx, hy);
         const bool sol = MASK && (lwB & 1u);
+        if constexpr (kRaw) {
+            if (!pr1.constant) decode_all<S>(rv, rrv, v);
+        }
         interior_plane<S>(fin, p, sm, inv, s_p, z + 1 < z1 ? ((k + 1) & 1) : -1, pr1, v, sol, wdB);
         if (need2 && has_halo) {
             R s1 = 0, s2 = 0;
@@ -754,7 +806,7 @@ k_step_fused(const typename Store<S>::T *__restrict__ fin, typename Store<S>::T 
         __syncthreads();
         // ---- phase B: the interior gathers of plane z+2 are issued first and
         //      stay in flight (in registers) during the collision of plane z
-        if (z + 1 < z1 && !pr2.constant) GatherAll<S, 0>::run(fin, p.N, gather_ref<S>(fin, p, pr2, ci), pr2, ci, lwC, v);
+        if (z + 1 < z1 && !pr2.constant) gather_interior(pr2, lwC);
         unsigned lwD = 0;
         float2 wdC = make_float2(0.f, 0.f);
         if (MASK) {   // link words of plane z+3 (periodic z: always a lattice plane)
@@ -845,6 +897,9 @@ cudaError_t launch_coll(const HostPhys &h, int lz, dim3 grid, cudaStream_t s, co
 // (same gathers, same grouping), into their own entries of wall_rho; then each
 // solid site with a fluid neighbour takes the w_i-weighted mean of its fluid
 // neighbours' densities plus rho_s.
+// Three lanes per fluid cell (ten cells per warp), one population group each
+// as in the halo partial gathers, so that the groups' loads are in flight
+// together; the first lane combines the three partials in the halo order.
 template <int S>
 __global__ void __launch_bounds__(256)
 k_wall_fluid_rho(const typename Store<S>::T *__restrict__ f, Phys<typename Store<S>::R> p,
@@ -852,20 +907,29 @@ k_wall_fluid_rho(const typename Store<S>::T *__restrict__ f, Phys<typename Store
                  float2 *__restrict__ wr)
 {
     using R = typename Store<S>::R;
-    const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (t >= n) return;
-    const unsigned c = cells[t];
-    const unsigned plane = (unsigned)p.nx * (unsigned)p.ny;
-    const int z = (int)(c / plane);
-    const unsigned rem = c - (unsigned)z * plane;
-    const int y = (int)(rem / (unsigned)p.nx), x = (int)(rem - (unsigned)y * (unsigned)p.nx);
-    const Col col = make_col(x, y, p.nx, p.ny);
-    const PlaneRef pr = plane_ref<false>(p, z);
-    R v[Q2];
-    GatherAll<S, 0>::run(f, p.N, gather_ref<S>(f, p, pr, col), pr, col, __ldg(links + c), v);
-    R r1, r2, jx, jy, jz;
-    sums(v, r1, r2, jx, jy, jz);
-    wr[c] = make_float2(r1, r2);
+    const int lane = threadIdx.x & 31;
+    const long long warp = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int g = lane % 3;
+    const long long t = warp * 10 + lane / 3;
+    const bool ok = lane < 30 && t < n;
+    R s1 = 0, s2 = 0;
+    unsigned c = 0;
+    if (ok) {
+        c = cells[t];
+        const unsigned plane = (unsigned)p.nx * (unsigned)p.ny;
+        const int z = (int)(c / plane);
+        const unsigned rem = c - (unsigned)z * plane;
+        const int y = (int)(rem / (unsigned)p.nx), x = (int)(rem - (unsigned)y * (unsigned)p.nx);
+        const Col col = make_col(x, y, p.nx, p.ny);
+        const PlaneRef pr = plane_ref<false>(p, z);
+        R v[kPer];
+        halo_load<S>(f, p, pr, col, __ldg(links + c), g, v);
+        halo_sum<S>(v, g, s1, s2);
+    }
+    const unsigned full = 0xffffffffu;
+    const R a1 = __shfl_down_sync(full, s1, 1), a2 = __shfl_down_sync(full, s2, 1);
+    const R b1 = __shfl_down_sync(full, s1, 2), b2 = __shfl_down_sync(full, s2, 2);
+    if (ok && g == 0) wr[c] = make_float2(s1 + a1 + b1, s2 + a2 + b2);
 }
 
 template <int S>   // (instantiated per storage format's translation unit)
@@ -910,8 +974,8 @@ cudaError_t fused_t(const HostPhys &h, const void *fin, void *fout, cudaStream_t
     if (h.links && h.wall_mirror && h.n_bsolid > 0) {
         float2 *wr = (float2 *)h.wall_rho;
         if (h.n_bfluid > 0)
-            k_wall_fluid_rho<S><<<(unsigned)((h.n_bfluid + 255) / 256), 256, 0, s>>>(fi, p, h.links, h.bfluid,
-                                                                                   h.n_bfluid, wr);
+            k_wall_fluid_rho<S><<<(unsigned)((h.n_bfluid + 79) / 80), 256, 0, s>>>(fi, p, h.links, h.bfluid,
+                                                                                 h.n_bfluid, wr);
         k_wall_solid_rho<S><<<(unsigned)((h.n_bsolid + 255) / 256), 256, 0, s>>>(h.solid, make_phys_f<float>(h), h.bsolid,
                                                                              h.n_bsolid, wr);
     }

@@ -59,7 +59,8 @@ cudaError_t launch_step_split(const HostPhys &p, const void *f_in, void *f_out, 
 // One full time step with the fused single-pass kernel (no scratch).
 // ev (optional, 2 events): recorded before and after the launch.
 // s_out (optional, 6*N FP32 values, [3 b + d][cell]): receives the step's
-// interaction sums S^b_d of Eq. 7 (the replay of the reverse pass uses them).
+// interaction sums S^b_d of Eq. 7 (the replay of the reverse pass uses them);
+// with f_out == nullptr the launch computes and stores the sums alone.
 cudaError_t launch_step_fused(const HostPhys &p, const void *f_in, void *f_out, cudaStream_t s,
                               cudaEvent_t *ev = nullptr, void *s_out = nullptr);
 bool fused_supported(const HostPhys &p);
