@@ -240,7 +240,9 @@ lbm_status lbm_sync(lbm_lattice *h);
 /* Differentiation (reverse mode).  The paper has no adjoint; these calls give
  * gradients of a loss L(rho^1_N, rho^2_N) of the final densities with respect
  * to the initial densities, G^{12}, G^{21}, tau_1 and tau_2, by a hand-written
- * reverse pass through the update of Sec. 2 (Eqs. 1-7, 10-11, 13).
+ * reverse pass through the update of Sec. 2 (Eqs. 1-7, 10-11, 13), for either
+ * forcing reading, every collision operator, periodic lattices, z walls and
+ * solid masks.
  *
  * lbm_record runs n_steps >= 1 forward exactly as lbm_step does and keeps the
  * raw state every ckpt_every >= 1 steps (a library-owned checkpoint store of
@@ -248,8 +250,7 @@ lbm_status lbm_sync(lbm_lattice *h);
  * reverse pass (adjoint fields of 2 x 19 values per cell, one checkpoint
  * segment of states and of their densities); both are held until the next
  * lbm_record or lbm_destroy, so that lbm_adjoint allocates nothing.
- * Synchronizes.  Errors: LBM_EINVAL, LBM_ENOMEM, LBM_ECUDA, LBM_ENOTSUP
- * (a lattice with Guo forcing, which has no reverse pass). */
+ * Synchronizes.  Errors: LBM_EINVAL, LBM_ENOMEM, LBM_ECUDA. */
 lbm_status lbm_record(lbm_lattice *h, long n_steps, int ckpt_every);
 
 /* Reverse pass over the last lbm_record.  Inputs dL_drho1, dL_drho2: N values

@@ -87,7 +87,7 @@ __device__ __forceinline__ unsigned at(const Nb &n, int dx, int dy, int dz)
 //   mu_i(y) = lambda^{n+1}_i(y + c_i) = lambda_loc^{n+1}_i(y + c_i) + D^{n+1}_a(y + c_i)
 // (or lambda^{n+1}_opp(i)(y) at a wall), and writes lambda_loc^n_i(y) of its
 // component and a^n_b(y) of the other component b = 1 - a.
-template <int S, int REG, bool SIN, bool MASK, bool WZ>
+template <int S, int REG, bool SIN, bool MASK, bool WZ, int FORCE>
 __device__ __forceinline__ void adj_half(const typename Store<S>::T *__restrict__ f,
                                          const typename Store<S>::R *__restrict__ rho,
                                          const typename Store<S>::R *__restrict__ lam_next,
@@ -145,10 +145,9 @@ __device__ __forceinline__ void adj_half(const typename Store<S>::T *__restrict_
     }
     // mixture density and momentum: both lanes of the pair form the same sums
     const R rt = ra + __shfl_xor_sync(full, ra, 16);
-    const R u0 = (jx + __shfl_xor_sync(full, jx, 16)) / rt;
-    const R u1 = (jy + __shfl_xor_sync(full, jy, 16)) / rt;
-    const R u2 = (jz + __shfl_xor_sync(full, jz, 16)) / rt;
-    const R usq = u0 * u0 + u1 * u1 + u2 * u2;
+    R u0 = (jx + __shfl_xor_sync(full, jx, 16)) / rt;
+    R u1 = (jy + __shfl_xor_sync(full, jy, 16)) / rt;
+    R u2 = (jz + __shfl_xor_sync(full, jz, 16)) / rt;
     // S^b of the other component b (Eq. 7; wall sites carry Eq. 13's rho'):
     // stored by the replayed forward step (SIN, rho = the sums [3 b + d][cell])
     // or formed from the densities
@@ -177,7 +176,22 @@ __device__ __forceinline__ void adj_half(const typename Store<S>::T *__restrict_
         }
     }
     const R Ga = a == 0 ? p.G12 : p.G21;
-    const R v0 = u0 + Ga * Sb0 + p.gext[0], v1 = u1 + Ga * Sb1 + p.gext[1], v2 = u2 + Ga * Sb2 + p.gext[2];
+    const R ga0 = Ga * Sb0 + p.gext[0], ga1 = Ga * Sb1 + p.gext[1], ga2 = Ga * Sb2 + p.gext[2];   // g^a
+    // Guo's forcing (R2b): both components relax toward f^eq at the common
+    // u* = u + (F^1 + F^2) / (2 rho), F^a = rho^a g^a; from here on u stands
+    // for u* and v = u* (the exact-difference formulas below then hold with
+    // v = u, and the forcing term's derivatives are added)
+    R F0 = 0, F1 = 0, F2 = 0;
+    if constexpr (FORCE == FORCE_GUO) {
+        F0 = ra * ga0; F1 = ra * ga1; F2 = ra * ga2;
+        const R h = R(0.5) / rt;
+        u0 += (F0 + __shfl_xor_sync(full, F0, 16)) * h;
+        u1 += (F1 + __shfl_xor_sync(full, F1, 16)) * h;
+        u2 += (F2 + __shfl_xor_sync(full, F2, 16)) * h;
+    }
+    const R usq = u0 * u0 + u1 * u1 + u2 * u2;
+    const bool guo = FORCE == FORCE_GUO;
+    const R v0 = guo ? u0 : u0 + ga0, v1 = guo ? u1 : u1 + ga1, v2 = guo ? u2 : u2 + ga2;
     const R vsq = v0 * v0 + v1 * v1 + v2 * v2;
     const R omega = a == 0 ? p.omega[0] : p.omega[1];
     const R keep = R(1) - omega;
@@ -201,6 +215,12 @@ __device__ __forceinline__ void adj_half(const typename Store<S>::T *__restrict_
         Pi[3] -= ra * u0 * u1;
         Pi[4] -= ra * u0 * u2;
         Pi[5] -= ra * u1 * u2;
+        if constexpr (FORCE == FORCE_GUO) {   // Pi of f - f^eq(u*) + F/2: + (u* F + F u*) / 2
+            Pi[0] += u0 * F0; Pi[1] += u1 * F1; Pi[2] += u2 * F2;
+            Pi[3] += R(0.5) * (u0 * F1 + u1 * F0);
+            Pi[4] += R(0.5) * (u0 * F2 + u2 * F0);
+            Pi[5] += R(0.5) * (u1 * F2 + u2 * F1);
+        }
         tr = Pi[0] + Pi[1] + Pi[2];
     }
     // third-order part (REG = 2): S_a, D_a of struct Third for this component
@@ -223,9 +243,17 @@ __device__ __forceinline__ void adj_half(const typename Store<S>::T *__restrict_
     R vbx = 0, vby = 0, vbz = 0, vbv = 0, ubx = 0, uby = 0, ubz = 0, ubv = 0;
     R pb[6] = {0, 0, 0, 0, 0, 0};
     R sb[3] = {0, 0, 0}, db[3] = {0, 0, 0};   // dL/dS_a, dL/dD_a (REG = 2)
+    // Guo forcing term T_i = (k_i / 36) (9 (c.u*) (c.F) - 3 u*.F + 3 c.F), times cf:
+    // 36 sum mu T, and 36 x its gradients in u* (Tu - 3 F sgs) and F (TF - 3 u* sgs)
+    const R uF = u0 * F0 + u1 * F1 + u2 * F2;
+    R Tsum = 0, sgs = 0, Tux = 0, Tuy = 0, Tuz = 0, TFx = 0, TFy = 0, TFz = 0;
     {
         // rest population: c = 0, k = 12
         const R m = mu[0], mk = m * R(12);
+        if constexpr (FORCE == FORCE_GUO) {
+            Tsum += mk * (R(-3) * uF);
+            sgs += mk;
+        }
         rbar += mk * (R(1) - R(1.5) * vsq);
         vbv += R(3) * mk;
         if (!REG) {
@@ -248,6 +276,15 @@ __device__ __forceinline__ void adj_half(const typename Store<S>::T *__restrict_
         const R cv = cdot<R>(i, v0, v1, v2), cv2 = cv * cv;
         const R E = R(1) + R(4.5) * cv2 - R(1.5) * vsq, O = cv * (R(3) + R(4.5) * cv2 - R(4.5) * vsq);
         rbar += E * sg + O * df;
+        if constexpr (FORCE == FORCE_GUO) {
+            const R cu = cdot<R>(i, u0, u1, u2), cF = cdot<R>(i, F0, F1, F2);
+            Tsum += sg * (R(9) * cu * cF - R(3) * uF) + R(3) * df * cF;
+            sgs += sg;
+            const R tu = R(9) * sg * cF, tF = R(9) * sg * cu + R(3) * df;
+            if (cx(i)) { Tux += R(cx(i)) * tu; TFx += R(cx(i)) * tF; }
+            if (cy(i)) { Tuy += R(cy(i)) * tu; TFy += R(cy(i)) * tF; }
+            if (cz(i)) { Tuz += R(cz(i)) * tu; TFz += R(cz(i)) * tF; }
+        }
         const R t = (R(3) + R(13.5) * cv2 - R(4.5) * vsq) * df + R(9) * cv * sg;
         if (cx(i)) vbx += R(cx(i)) * t;
         if (cy(i)) vby += R(cy(i)) * t;
@@ -323,12 +360,43 @@ __device__ __forceinline__ void adj_half(const typename Store<S>::T *__restrict_
             ub2 += ubq[2];
         }
     }
+    // Guo: the forcing term's u* and F^a derivatives (and, regularized, those of
+    // the (u* F + F u*) / 2 part of Pi); dL/dF^a collects them
+    R Fb0 = 0, Fb1 = 0, Fb2 = 0;
+    if constexpr (FORCE == FORCE_GUO) {
+        const R cf = (REG ? R(0.5) : R(1) - R(0.5) * omega) / R(36);
+        ub0 += cf * (Tux - R(3) * F0 * sgs);
+        ub1 += cf * (Tuy - R(3) * F1 * sgs);
+        ub2 += cf * (Tuz - R(3) * F2 * sgs);
+        Fb0 = cf * (TFx - R(3) * u0 * sgs);
+        Fb1 = cf * (TFy - R(3) * u1 * sgs);
+        Fb2 = cf * (TFz - R(3) * u2 * sgs);
+        if (REG) {
+            ub0 += pb[0] * F0 + pb[3] * F1 + pb[4] * F2;
+            ub1 += pb[3] * F0 + pb[1] * F1 + pb[5] * F2;
+            ub2 += pb[4] * F0 + pb[5] * F1 + pb[2] * F2;
+            Fb0 += pb[0] * u0 + pb[3] * u1 + pb[4] * u2;
+            Fb1 += pb[3] * u0 + pb[1] * u1 + pb[5] * u2;
+            Fb2 += pb[4] * u0 + pb[5] * u1 + pb[2] * u2;
+        } else {
+            Kbar += Tsum / R(72);   // cf = 1 - omega / 2 = (1 + keep) / 2
+        }
+    }
     // u = j / rho over both components: dL/dj = ubar / rho, dL/drho += -(ubar . u) / rho
+    // (Guo: u* = j / rho + (F^1 + F^2) / (2 rho) gives the same with u*, and
+    // dL/dF^a += ubar / (2 rho))
     const R U0 = ub0 + __shfl_xor_sync(full, ub0, 16);
     const R U1 = ub1 + __shfl_xor_sync(full, ub1, 16);
     const R U2 = ub2 + __shfl_xor_sync(full, ub2, 16);
     const R jb0 = U0 / rt, jb1 = U1 / rt, jb2 = U2 / rt;
+    if constexpr (FORCE == FORCE_GUO) {
+        const R h = R(0.5) / rt;
+        Fb0 += U0 * h; Fb1 += U1 * h; Fb2 += U2 * h;
+        rbar += Fb0 * ga0 + Fb1 * ga1 + Fb2 * ga2;   // F^a = rho^a g^a
+    }
     const R base = rbar - (U0 * u0 + U1 * u1 + U2 * u2) / rt;
+    // dL/dg^a: the velocity shift v = u + g^a (exact difference), or rho^a dL/dF^a (Guo)
+    const R gb0 = guo ? ra * Fb0 : vbar0, gb1 = guo ? ra * Fb1 : vbar1, gb2 = guo ? ra * Fb2 : vbar2;
     if (store && MASK && (lw & 1u)) {
         // solid site: no populations, no sensitivities (a = 0 keeps it out of D)
         R *lo = lam_loc + (size_t)a * Q * (size_t)N + n.cell;
@@ -357,11 +425,11 @@ __device__ __forceinline__ void adj_half(const typename Store<S>::T *__restrict_
             }
             lo[(unsigned)i * N32] = l;
         }
-        // g^a = G^{ab} S^b + g_ext:  dL/dS^b = G^{ab} vbar,  dL/dG^{ab} = vbar . S^b
-        aout[((long long)b * 3 + 0) * N + n.cell] = Ga * vbar0;
-        aout[((long long)b * 3 + 1) * N + n.cell] = Ga * vbar1;
-        aout[((long long)b * 3 + 2) * N + n.cell] = Ga * vbar2;
-        par_g += vbar0 * Sb0 + vbar1 * Sb1 + vbar2 * Sb2;
+        // g^a = G^{ab} S^b + g_ext:  dL/dS^b = G^{ab} dL/dg^a,  dL/dG^{ab} = dL/dg^a . S^b
+        aout[((long long)b * 3 + 0) * N + n.cell] = Ga * gb0;
+        aout[((long long)b * 3 + 1) * N + n.cell] = Ga * gb1;
+        aout[((long long)b * 3 + 2) * N + n.cell] = Ga * gb2;
+        par_g += gb0 * Sb0 + gb1 * Sb1 + gb2 * Sb2;
         // keep = 1 - 1/tau: dkeep/dtau = 1/tau^2
         par_t += Kbar * omega * omega;
     }
@@ -374,7 +442,7 @@ __device__ __forceinline__ void adj_half(const typename Store<S>::T *__restrict_
 // solid).  The lanes of a solid site still run the arithmetic (on meaningless
 // values), so that both lanes of every pair take part in the shuffles, and
 // store zeros.
-template <int S, int REG, bool SIN, bool MASK, bool WZ>
+template <int S, int REG, bool SIN, bool MASK, bool WZ, int FORCE>
 __global__ void __launch_bounds__(kThreadsA, 2)
 k_adj_local(const typename Store<S>::T *__restrict__ f, const typename Store<S>::R *__restrict__ rho,
             const typename Store<S>::R *__restrict__ lam_next, const typename Store<S>::R *__restrict__ Dn,
@@ -395,7 +463,7 @@ k_adj_local(const typename Store<S>::T *__restrict__ f, const typename Store<S>:
         Nb n;
         nb_of(p, (unsigned)(valid ? c : p.N - 1), n);
         const unsigned lw = MASK ? __ldg(links + n.cell) : 0u;
-        adj_half<S, REG, SIN, MASK, WZ>(f, rho, lam_next, Dn, lam_loc, aout, p, n, a, valid, pg, pt, lw);
+        adj_half<S, REG, SIN, MASK, WZ, FORCE>(f, rho, lam_next, Dn, lam_loc, aout, p, n, a, valid, pg, pt, lw);
     }
     // lanes of component a hold parts of par[a] and par[2 + a]
     __shared__ double sh[4][kThreadsA];
@@ -652,10 +720,17 @@ cudaError_t adj_step_t(const HostPhys &h, const void *f, const void *rho, int rh
     using T = typename Store<S>::T;
     using R = typename Store<S>::R;
     const Phys<R> p = make_phys_a<R>(h);
-#define LBM_ADJ(REG_, SIN_, MASK_, WZ_)                                                                         \
-    k_adj_local<S, REG_, SIN_, MASK_, WZ_><<<adjoint_blocks(), kThreadsA, 0, s>>>(                             \
-        (const T *)f, (const R *)rho, (const R *)lam_next, (const R *)Dn, (R *)lam_loc, (R *)a, partials, p,  \
-        h.links)
+#define LBM_ADJ(REG_, SIN_, MASK_, WZ_)                                                                           \
+    do {                                                                                                          \
+        if (h.forcing == FORCE_GUO)                                                                               \
+            k_adj_local<S, REG_, SIN_, MASK_, WZ_, FORCE_GUO><<<adjoint_blocks(), kThreadsA, 0, s>>>(             \
+                (const T *)f, (const R *)rho, (const R *)lam_next, (const R *)Dn, (R *)lam_loc, (R *)a, partials, \
+                p, h.links);                                                                                      \
+        else                                                                                                      \
+            k_adj_local<S, REG_, SIN_, MASK_, WZ_, FORCE_EDM><<<adjoint_blocks(), kThreadsA, 0, s>>>(             \
+                (const T *)f, (const R *)rho, (const R *)lam_next, (const R *)Dn, (R *)lam_loc, (R *)a, partials, \
+                p, h.links);                                                                                      \
+    } while (0)
 #define LBM_ADJ_REG(SIN_, MASK_, WZ_)                  \
     do {                                               \
         if (reg == 1) LBM_ADJ(1, SIN_, MASK_, WZ_);    \

@@ -706,8 +706,6 @@ lbm_status lbm_record(lbm_lattice *h, long n_steps, int ckpt_every)
     if (!h) return fail(LBM_EINVAL, "lbm_record: NULL handle");
     if (n_steps < 1 || ckpt_every < 1)
         return fail(LBM_EINVAL, "lbm_record: n_steps = %ld and ckpt_every = %d must be >= 1", n_steps, ckpt_every);
-    if (h->phys.forcing != LBM_FORCING_EDM)
-        return fail(LBM_ENOTSUP, "lbm_record: the reverse pass differentiates the exact-difference forcing only");
     DeviceGuard g(h->device);
     size_t sb = 0;
     lbm_state_bytes(h, &sb);

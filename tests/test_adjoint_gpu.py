@@ -172,6 +172,54 @@ def test_adjoint_solid_mask(gpu_lib, wall_model, collision, storage):
     assert np.all(d1[solid == 1] == 0)
 
 
+GUO_CASES = [
+    ("bgk_walls", dict(periodic=(1, 1, 0), collision="bgk", rho_s=(0.03, 0.0)), None),
+    ("reg_walls", dict(periodic=(1, 1, 0), collision="regularized", rho_s=(0.03, 0.0)), None),
+    ("reg3_walls", dict(periodic=(1, 1, 0), collision="regularized3", rho_s=(0.03, 0.0)), None),
+    ("reg_mask_mirror", dict(collision="regularized", rho_s=(0.03, 0.1)), "mask"),
+]
+
+
+@pytest.mark.parametrize("storage", ["f64", "f32"])
+@pytest.mark.parametrize("name,kw,geom", GUO_CASES, ids=[c[0] for c in GUO_CASES])
+def test_adjoint_guo_forcing(gpu_lib, name, kw, geom, storage):
+    """Reverse pass under Guo's forcing (the second reading of the Sec. 2
+    forcing term: f^eq at the common u* = u + (F^1 + F^2)/(2 rho), forcing
+    term with F^a = rho^a g^a) through z walls or a mask, g_ext and unequal
+    tau, against the oracle's central differences (FP64 1e-5, FP32 1e-4).
+    The step is h = 1e-4: at h = 1e-3 the oracle's difference in tau_1 is
+    1.1e-4 (relative) from its limit in the BGK case."""
+    shape = (6, 5, 7)
+    r1, r2, _ = wl.random_state(shape, seed=17, u_max=0.0)
+    tgt = np.roll(r1, 2, axis=2)
+    kw = dict(kw, g_ext=(2e-4, -1e-4, 3e-4), forcing="guo")
+    solid = _staircase(shape, seed=4) if geom == "mask" else None
+    G, t1, t2, steps = -1.3, 0.8, 1.2, 6
+    rng = np.random.default_rng(3)
+    pool = [tuple(int(v) for v in c) for c in np.argwhere(solid == 0)] if solid is not None else \
+        [tuple(int(v) for v in c) for c in np.ndindex(shape)]
+    cells = [pool[k] for k in rng.choice(len(pool), 12, replace=False)]
+    extra = {"solid": solid} if solid is not None else {}
+    fG, fT, fr = fd_grads(r1, r2, tgt, G, t1, t2, steps, cells=cells, h=1e-4, **kw, **extra)
+    from paper_1601_01237_gb300 import Lattice
+    lat = Lattice(shape, storage=storage, tau=(t1, t2), G12=G, G21=G, **kw)
+    if solid is not None:
+        lat.set_solid(solid)
+    lat.init_fields(r1, r2)
+    lat.record(steps, 4)
+    a, _, _ = lat.moments()
+    d1 = np.empty(shape)
+    par = lat.adjoint(2 * (a - tgt), None, d1, None)
+    lat.close()
+    tol = 1e-5 if storage == "f64" else 1e-4
+    print("%s %s Guo: dG %.8g vs %.8g, dtau1 %.8g vs %.8g" % (storage, name, par[0] + par[1], fG, par[2], fT))
+    assert abs(par[0] + par[1] - fG) <= tol * abs(fG)
+    assert abs(par[2] - fT) <= tol * abs(fT)
+    scale = np.abs([fr[q] for q in cells]).max()
+    for c in cells:
+        assert abs(d1[c] - fr[c]) <= tol * scale, (c, d1[c], fr[c])
+
+
 def test_autograd_rollout_matches_adjoint(gpu_lib):
     """torch.autograd through LBMRollout equals the direct lbm_adjoint call."""
     import torch
