@@ -25,9 +25,13 @@ extern template cudaError_t adj::adj_step_t<ST_BF16_REL>(const HostPhys &, const
                                        const void *, const void *, void *, void *, void *, double *,
                                        cudaStream_t);
 
-// One resident wave of k_adj_local on the current device: kAdjBlocksPerSM
-// CTAs on every SM.
-int adjoint_blocks() { return kAdjBlocksPerSM * current_device_sms(); }
+// One resident wave of k_adj_local on the current device for a storage
+// format: AdjLaunch::blocks CTAs on every SM.
+int adjoint_blocks(int storage)
+{
+    const int per_sm = storage == ST_F64 ? AdjLaunch<double>::blocks : AdjLaunch<float>::blocks;
+    return per_sm * current_device_sms();
+}
 
 cudaError_t launch_adjoint_step(const HostPhys &p, const void *f, const void *rho, int rho_is_sums, const void *lam_next,
                                 const void *Dn, void *lam_loc, void *a, void *Dout, double *partials, cudaStream_t s)

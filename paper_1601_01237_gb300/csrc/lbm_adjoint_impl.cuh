@@ -1,6 +1,6 @@
 // Reverse-mode (adjoint) step of the two-component D3Q19 Shan-Chen update.
 // The paper has no adjoint; this differentiates the forward step of
-// Sec. 2 (Eqs. 1-7, 10-11, 13 with the exact-difference forcing) by hand.
+// Sec. 2 (Eqs. 1-7, 10-11, 13, with either reading of the forcing term) by hand.
 //
 // Notation: f^n = pre-collision populations at step n (the gathered values),
 // lambda^n = dL/df^n.  One forward step is
@@ -39,7 +39,15 @@ namespace lbm {
 namespace {
 
 constexpr int kThreadsA = 256;
-constexpr int kAdjBlocksPerSM = 2;   // k_adj_local: 128 registers x 256 threads
+// Launch shape of k_adj_local per arithmetic type: CTAs of `threads` (a
+// power of two), `blocks` of them resident per SM.  FP32: 128 x 5 (20 warps
+// per SM at 96 registers, a few spilled, measured faster than 16 warps at 128
+// registers without spills: the kernel waits on loads); FP64: 256 x 2.
+template <class R>
+struct AdjLaunch {
+    static constexpr int threads = sizeof(R) == 8 ? 256 : 128;
+    static constexpr int blocks = sizeof(R) == 8 ? 2 : 5;
+};
 
 // A cell and its wrapped neighbour offsets.  Cell indices fit 32 bits (a
 // lattice of 2^32 cells would need 650 GB of populations); element offsets
@@ -443,21 +451,22 @@ __device__ __forceinline__ void adj_half(const typename Store<S>::T *__restrict_
 // values), so that both lanes of every pair take part in the shuffles, and
 // store zeros.
 template <int S, int REG, bool SIN, bool MASK, bool WZ, int FORCE>
-__global__ void __launch_bounds__(kThreadsA, 2)
+__global__ void __launch_bounds__(AdjLaunch<typename Store<S>::R>::threads, AdjLaunch<typename Store<S>::R>::blocks)
 k_adj_local(const typename Store<S>::T *__restrict__ f, const typename Store<S>::R *__restrict__ rho,
             const typename Store<S>::R *__restrict__ lam_next, const typename Store<S>::R *__restrict__ Dn,
             typename Store<S>::R *__restrict__ lam_loc, typename Store<S>::R *__restrict__ aout,
             double *__restrict__ partials, Phys<typename Store<S>::R> p, const unsigned *__restrict__ links)
 {
+    constexpr int kThreadsL = AdjLaunch<typename Store<S>::R>::threads;
     const int lane = threadIdx.x & 31;
     const int a = lane >> 4;
-    const long long warps = (long long)gridDim.x * (kThreadsA / 32);
+    const long long warps = (long long)gridDim.x * (kThreadsL / 32);
     const long long groups = (p.N + 15) / 16;
     // per-thread partials in the arithmetic type over the thread's cells (a few
     // tens per step), summed in FP64 across the block: the FP64 pipe is a
     // small fraction of the FP32 one on this GPU
     typename Store<S>::R pg = 0, pt = 0;
-    for (long long wg = (long long)blockIdx.x * (kThreadsA / 32) + (threadIdx.x >> 5); wg < groups; wg += warps) {
+    for (long long wg = (long long)blockIdx.x * (kThreadsL / 32) + (threadIdx.x >> 5); wg < groups; wg += warps) {
         const long long c = wg * 16 + (lane & 15);
         const bool valid = c < p.N;
         Nb n;
@@ -466,13 +475,13 @@ k_adj_local(const typename Store<S>::T *__restrict__ f, const typename Store<S>:
         adj_half<S, REG, SIN, MASK, WZ, FORCE>(f, rho, lam_next, Dn, lam_loc, aout, p, n, a, valid, pg, pt, lw);
     }
     // lanes of component a hold parts of par[a] and par[2 + a]
-    __shared__ double sh[4][kThreadsA];
+    __shared__ double sh[4][kThreadsL];
     const int t = threadIdx.x;
     for (int k = 0; k < 4; ++k) sh[k][t] = 0;
     sh[a][t] = pg;
     sh[2 + a][t] = pt;
     __syncthreads();
-    for (int s = kThreadsA / 2; s > 0; s >>= 1) {
+    for (int s = kThreadsL / 2; s > 0; s >>= 1) {
         if (t < s)
             for (int k = 0; k < 4; ++k) sh[k][t] += sh[k][t + s];
         __syncthreads();
@@ -488,7 +497,7 @@ k_adj_local(const typename Store<S>::T *__restrict__ f, const typename Store<S>:
 // one-cell margin (periodic images in x and y; in z periodic images, or zeros
 // for wall sites, whose terms the sum leaves out) are staged in shared memory
 // with coalesced loads, then each thread sums its z column of DZ cells from
-// shared memory, in the order of the per-link formula above.
+// shared memory, plane by plane (below).
 constexpr int kDX = 32, kDY = 8;
 template <class R>
 struct DTile {
@@ -558,36 +567,60 @@ k_adj_D(const R *__restrict__ a, R *__restrict__ D, Phys<R> p, int ntx)
     const int lx = t % kDX, ly = t / kDX;
     const int x = x0 + lx, y = y0 + ly;
     if (x >= nx || y >= ny) return;
-    for (int k = 0; k < T::DZ; ++k) {
-        const int z = z0 + k;
-        if (z >= nz) break;
-        const bool zlo = p.wall_z && z == 0, zhi = p.wall_z && z == nz - 1;
-        const unsigned cell = ((unsigned)z * (unsigned)ny + (unsigned)y) * (unsigned)nx + (unsigned)x;
+    // Sweep over the box planes P = 0 .. DZ + 1.  Grouped by source plane, the
+    // 18 links of D at a cell split into the 8 links within its plane (in),
+    // the 5 from the plane below (lo: c_z = +1) and the 5 from the plane above
+    // (hi: c_z = -1); each needs only these 17 values of a source plane
+    // (offsets (dx, dy) from the cell's column):
+    //   a_x at (-+1, 0), (-+1, -+1);  a_y at (0, -+1), (-+1, -+1);
+    //   a_z at (0, 0), (-+1, 0), (0, -+1),
+    // with  A = a_x(-1,0) - a_x(1,0) + a_y(0,-1) - a_y(0,1),
+    //       Zs = a_z(-1,0) + a_z(1,0) + a_z(0,-1) + a_z(0,1):
+    //   in = A / 18 + [a_x(-1,-1) + a_y(-1,-1) - a_x(1,1) - a_y(1,1)
+    //                  + a_x(-1,1) - a_y(-1,1) - a_x(1,-1) + a_y(1,-1)] / 36,
+    //   lo =  a_z(0,0) / 18 + (A + Zs) / 36,   hi = -a_z(0,0) / 18 + (A - Zs) / 36.
+    // Plane P is the lower plane of cell P, the own plane of cell P - 1 and
+    // the upper plane of cell P - 2, so each plane's values are read once.
+    // The mirror terms of a cell next to a z wall are the links that would
+    // come through the wall, evaluated in its own plane: hi at z = 0, lo at
+    // z = nz - 1.
+    const R r18 = R(1) / R(18), r36 = R(1) / R(36);
+    R acc[T::DZ][2];
+#pragma unroll
+    for (int k = 0; k < T::DZ; ++k) acc[k][0] = acc[k][1] = R(0);
+#pragma unroll
+    for (int P = 0; P < T::DZ + 2; ++P) {
 #pragma unroll
         for (int b = 0; b < 2; ++b) {
-            const R *bb = box + 3 * b * T::BOX;
-            // box value of field d at offset (dx, dy, dz) from this cell
-            auto at3 = [&](int d, int dx, int dy, int dz) {
-                return bb[d * T::BOX + ((k + 1 + dz) * T::BY + (ly + 1 + dy)) * T::BX + (lx + 1 + dx)];
-            };
-            R s = 0;
-#pragma unroll
-            for (int q = 1; q < Q; ++q) {
-                // wall sources hold zeros in the box, so their terms vanish
-                R c = 0;
-                if (cx(q)) c += R(cx(q)) * at3(0, -cx(q), -cy(q), -cz(q));
-                if (cy(q)) c += R(cy(q)) * at3(1, -cx(q), -cy(q), -cz(q));
-                if (cz(q)) c += R(cz(q)) * at3(2, -cx(q), -cy(q), -cz(q));
-                s += w<R>(q) * c;
-                if (p.wall_mirror && ((cz(q) == -1 && zlo) || (cz(q) == 1 && zhi))) {
-                    R m = 0;
-                    if (cx(q)) m += R(cx(q)) * at3(0, -cx(q), -cy(q), 0);
-                    if (cy(q)) m += R(cy(q)) * at3(1, -cx(q), -cy(q), 0);
-                    m += R(cz(q)) * at3(2, -cx(q), -cy(q), 0);
-                    s += w<R>(q) * m;
+            const R *bx = box + (3 * b + 0) * T::BOX + (P * T::BY + ly + 1) * T::BX + lx + 1;
+            const R *by = bx + T::BOX, *bz = bx + 2 * T::BOX;
+            auto o = [](int dx, int dy) { return dy * T::BX + dx; };
+            const R A = bx[o(-1, 0)] - bx[o(1, 0)] + by[o(0, -1)] - by[o(0, 1)];
+            const R Zc = bz[o(0, 0)];
+            const R Zs = bz[o(-1, 0)] + bz[o(1, 0)] + bz[o(0, -1)] + bz[o(0, 1)];
+            const R lo = Zc * r18 + (A + Zs) * r36;
+            const R hi = (A - Zs) * r36 - Zc * r18;
+            if (P < T::DZ) acc[P][b] += lo;
+            if (P >= 1 && P - 1 < T::DZ) {
+                const R E = bx[o(-1, -1)] + by[o(-1, -1)] - bx[o(1, 1)] - by[o(1, 1)] + bx[o(-1, 1)] -
+                            by[o(-1, 1)] - bx[o(1, -1)] + by[o(1, -1)];
+                acc[P - 1][b] += A * r18 + E * r36;
+                if (p.wall_z && p.wall_mirror) {
+                    const int z = z0 + P - 1;
+                    if (z == 0) acc[P - 1][b] += hi;
+                    if (z == nz - 1) acc[P - 1][b] += lo;
                 }
             }
-            D[(unsigned)b * N32 + cell] = s;
+            if (P >= 2) acc[P - 2][b] += hi;
+        }
+    }
+#pragma unroll
+    for (int k = 0; k < T::DZ; ++k) {
+        const int z = z0 + k;
+        if (z < nz) {
+            const unsigned cell = ((unsigned)z * (unsigned)ny + (unsigned)y) * (unsigned)nx + (unsigned)x;
+            D[cell] = acc[k][0];
+            D[N32 + cell] = acc[k][1];
         }
     }
 }
@@ -723,11 +756,11 @@ cudaError_t adj_step_t(const HostPhys &h, const void *f, const void *rho, int rh
 #define LBM_ADJ(REG_, SIN_, MASK_, WZ_)                                                                           \
     do {                                                                                                          \
         if (h.forcing == FORCE_GUO)                                                                               \
-            k_adj_local<S, REG_, SIN_, MASK_, WZ_, FORCE_GUO><<<adjoint_blocks(), kThreadsA, 0, s>>>(             \
+            k_adj_local<S, REG_, SIN_, MASK_, WZ_, FORCE_GUO><<<nblk, AdjLaunch<R>::threads, 0, s>>>(             \
                 (const T *)f, (const R *)rho, (const R *)lam_next, (const R *)Dn, (R *)lam_loc, (R *)a, partials, \
                 p, h.links);                                                                                      \
         else                                                                                                      \
-            k_adj_local<S, REG_, SIN_, MASK_, WZ_, FORCE_EDM><<<adjoint_blocks(), kThreadsA, 0, s>>>(             \
+            k_adj_local<S, REG_, SIN_, MASK_, WZ_, FORCE_EDM><<<nblk, AdjLaunch<R>::threads, 0, s>>>(             \
                 (const T *)f, (const R *)rho, (const R *)lam_next, (const R *)Dn, (R *)lam_loc, (R *)a, partials, \
                 p, h.links);                                                                                      \
     } while (0)
@@ -738,6 +771,7 @@ cudaError_t adj_step_t(const HostPhys &h, const void *f, const void *rho, int rh
         else LBM_ADJ(0, SIN_, MASK_, WZ_);             \
     } while (0)
     const int reg = h.collision == LBM_REGULARIZED ? 1 : (h.collision == LBM_REGULARIZED3 ? 2 : 0);
+    const int nblk = adjoint_blocks(h.storage);
     // geometry instances: a mask (periodic z), z walls, or periodic
     if (h.links) {
         if (rho_is_sums) LBM_ADJ_REG(true, true, false);

@@ -723,12 +723,13 @@ lbm_status lbm_record(lbm_lattice *h, long n_steps, int ckpt_every)
         CK(cudaMalloc(&h->ws_lam_loc, rb * 2 * lbm::Q * N), "lbm_record: reverse-pass lambda_loc");
         CK(cudaMalloc(&h->ws_a, rb * 6 * N), "lbm_record: reverse-pass a");
         CK(cudaMalloc(&h->ws_d, rb * 4 * N), "lbm_record: reverse-pass D");
-        CK(cudaMalloc(&h->ws_seg, sb * E), "lbm_record: reverse-pass segment states");
+        // states 1 .. E-1 of a segment (state 0 is read from its checkpoint)
+        CK(cudaMalloc(&h->ws_seg, sb * (size_t)(E > 1 ? E - 1 : 1)), "lbm_record: reverse-pass segment states");
         // per replayed step: the interaction sums (fused step, 6 N) or the
         // densities (two-kernel step, 2 N)
         CK(cudaMalloc(&h->ws_rseg, rb * (h->use_fused ? 6 : 2) * N * E), "lbm_record: reverse-pass segment sums");
         CK(cudaMalloc(&h->ws_io, sizeof(double) * 2 * N), "lbm_record: reverse-pass staging");
-        CK(cudaMalloc((void **)&h->ws_part, sizeof(double) * 4 * lbm::adjoint_blocks()), "lbm_record: partials");
+        CK(cudaMalloc((void **)&h->ws_part, sizeof(double) * 4 * lbm::adjoint_blocks(h->phys.storage)), "lbm_record: partials");
     }
     h->rec_at_rest = h->init_at_rest && h->steps == 0;
     for (long t = 0; t < n_steps; ++t) {
@@ -762,7 +763,7 @@ lbm_status lbm_adjoint(lbm_lattice *h, const double *dL_drho1, const double *dL_
     size_t sb = 0;
     lbm_state_bytes(h, &sb);
     const long E = h->rec_every;
-    const int nb = lbm::adjoint_blocks();
+    const int nb = lbm::adjoint_blocks(h->phys.storage);
     // working memory reserved by lbm_record
     void *lam = h->ws_lam, *lam_loc = h->ws_lam_loc, *abuf = h->ws_a, *seg = h->ws_seg, *io = h->ws_io;
     void *dbuf = h->ws_d, *rseg = h->ws_rseg;
@@ -772,7 +773,11 @@ lbm_status lbm_adjoint(lbm_lattice *h, const double *dL_drho1, const double *dL_
     std::vector<double> parth((size_t)nb * 4);
     cudaError_t e;
     lbm_status st = LBM_OK;
-    auto cleanup = [&]() {};
+    cudaStream_t cs = nullptr;   // capture stream of the segment graphs
+    auto cleanup = [&]() {
+        if (cs) cudaStreamDestroy(cs);
+        cs = nullptr;
+    };
 #define CKA(expr, where)                                  \
     do {                                                  \
         e = (expr);                                       \
@@ -801,22 +806,27 @@ lbm_status lbm_adjoint(lbm_lattice *h, const double *dL_drho1, const double *dL_
     // One checkpoint segment of len steps on stream st: recompute its forward
     // states, then len reverse steps with the adjoint fields ping-ponging from
     // (la, da).
-    auto enqueue_segment = [&](cudaStream_t st, long len, void *la, void *lb, void *da, void *db) -> cudaError_t {
+    // The segment's first state is read in place from the checkpoint store
+    // (first); its later states go to the segment buffer (state t at slot t - 1).
+    auto enqueue_segment = [&](cudaStream_t st, long len, const void *first, void *la, void *lb, void *da,
+                               void *db) -> cudaError_t {
+        auto state = [&](long t) -> void * {
+            return t == 0 ? const_cast<void *>(first) : (void *)((char *)seg + sb * (size_t)(t - 1));
+        };
         cudaError_t er = cudaSuccess;
         const long nrec = use_fused ? len : len - 1;
         for (long t = 0; t < nrec && er == cudaSuccess; ++t) {
-            const void *fi = (char *)seg + sb * (size_t)t;
+            const void *fi = state(t);
             // the fused replay's last step only supplies the interaction sums
-            void *fo = (use_fused && t == nrec - 1) ? nullptr : (char *)seg + sb * (size_t)(t + 1);
+            void *fo = (use_fused && t == nrec - 1) ? nullptr : state(t + 1);
             void *rt = (char *)rseg + rstride * (size_t)t;
             er = use_fused ? lbm::launch_step_fused(h->phys, fi, fo, st, nullptr, rt)
                            : lbm::launch_step_split(h->phys, fi, fo, rt, st);
         }
         if (er == cudaSuccess && !use_fused)
-            er = lbm::launch_density(h->phys, (char *)seg + sb * (size_t)(len - 1),
-                                     (char *)rseg + rstride * (size_t)(len - 1), st);
+            er = lbm::launch_density(h->phys, state(len - 1), (char *)rseg + rstride * (size_t)(len - 1), st);
         for (long t = len - 1; t >= 0 && er == cudaSuccess; --t) {
-            const void *fn = (char *)seg + sb * (size_t)t;
+            const void *fn = state(t);
             const void *rn = (char *)rseg + rstride * (size_t)t;
             // step t reads (la, da) and writes (lb, db)
             er = lbm::launch_adjoint_step(h->phys, fn, rn, use_fused ? 1 : 0, la, da, lb, abuf, db, part, st);
@@ -825,39 +835,49 @@ lbm_status lbm_adjoint(lbm_lattice *h, const double *dL_drho1, const double *dL_
         }
         return er;
     };
-    // A full segment replays a captured graph (one per ping-pong parity): the
-    // same launches with one launch instead of about 3E.
-    auto segment_graph = [&](int par) -> cudaGraphExec_t {
-        if (h->seg_graph_state[par] == 0) {
-            h->seg_graph_state[par] = -1;
-            cudaStream_t cs = nullptr;
-            if (cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking) == cudaSuccess) {
-                cudaGraph_t gr = nullptr;
-                if (cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal) == cudaSuccess) {
-                    const cudaError_t er = enqueue_segment(cs, E, lam, lam_loc, d_cur, d_nxt);
-                    const cudaError_t ee = cudaStreamEndCapture(cs, &gr);
-                    if (er == cudaSuccess && ee == cudaSuccess && gr &&
-                        cudaGraphInstantiate(&h->seg_graph[par], gr, 0) == cudaSuccess)
-                        h->seg_graph_state[par] = 1;
-                    else
-                        h->seg_graph[par] = nullptr;
-                }
-                if (gr) cudaGraphDestroy(gr);
-                cudaStreamDestroy(cs);
-            }
-            cudaGetLastError();
+    // A full segment replays a captured graph (one executable graph per
+    // ping-pong parity of the adjoint fields): the same launches with one
+    // launch instead of about 3E.  Each segment starts from its own
+    // checkpoint, so its launches are captured afresh and applied to the
+    // parity's executable graph (cudaGraphExecUpdate changes only later
+    // launches; the host captures the next segment while the device runs the
+    // current one).
+    if (h->use_graphs && cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking) != cudaSuccess) {
+        cs = nullptr;
+        cudaGetLastError();
+    }
+    auto segment_graph = [&](int par, const void *first) -> cudaGraphExec_t {
+        if (!cs || h->seg_graph_state[par] == -1) return nullptr;
+        cudaGraph_t gr = nullptr;
+        bool ok = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal) == cudaSuccess;
+        if (ok) {
+            const cudaError_t er = enqueue_segment(cs, E, first, lam, lam_loc, d_cur, d_nxt);
+            const cudaError_t ee = cudaStreamEndCapture(cs, &gr);
+            ok = er == cudaSuccess && ee == cudaSuccess && gr;
         }
-        return h->seg_graph_state[par] == 1 ? h->seg_graph[par] : nullptr;
+        if (ok && h->seg_graph_state[par] == 1) {
+            cudaGraphExecUpdateResultInfo info;
+            if (cudaGraphExecUpdate(h->seg_graph[par], gr, &info) != cudaSuccess) {
+                cudaGraphExecDestroy(h->seg_graph[par]);
+                h->seg_graph[par] = nullptr;
+                h->seg_graph_state[par] = 0;
+            }
+        }
+        if (ok && h->seg_graph_state[par] == 0)
+            h->seg_graph_state[par] = cudaGraphInstantiate(&h->seg_graph[par], gr, 0) == cudaSuccess ? 1 : -1;
+        if (!ok && h->seg_graph_state[par] == 0) h->seg_graph_state[par] = -1;
+        if (gr) cudaGraphDestroy(gr);
+        cudaGetLastError();
+        return ok && h->seg_graph_state[par] == 1 ? h->seg_graph[par] : nullptr;
     };
     for (long k = h->rec_nck - 1; k >= 0; --k) {
         const long t0 = k * E;
         const long t1 = (t0 + E < h->rec_steps) ? t0 + E : h->rec_steps;
         const long len = t1 - t0;
-        CKA(cudaMemcpyAsync(seg, (char *)h->ckpt + sb * (size_t)k, sb, cudaMemcpyDeviceToDevice, h->stream),
-            "lbm_adjoint: restore");
-        cudaGraphExec_t gx = (len == E && h->use_graphs) ? segment_graph(lam == h->ws_lam ? 0 : 1) : nullptr;
+        const void *first = (char *)h->ckpt + sb * (size_t)k;
+        cudaGraphExec_t gx = len == E ? segment_graph(lam == h->ws_lam ? 0 : 1, first) : nullptr;
         if (gx) CKA(cudaGraphLaunch(gx, h->stream), "lbm_adjoint: segment graph");
-        else CKA(enqueue_segment(h->stream, len, lam, lam_loc, d_cur, d_nxt), "lbm_adjoint: segment");
+        else CKA(enqueue_segment(h->stream, len, first, lam, lam_loc, d_cur, d_nxt), "lbm_adjoint: segment");
         if (len & 1) {
             std::swap(lam, lam_loc);
             std::swap(d_cur, d_nxt);

@@ -104,9 +104,9 @@ cudaError_t launch_step_split_noalloc(const HostPhys &p, const void *f_in, void 
 // (rho, 2*N reals) or, when rho_is_sums, its interaction sums (rho, 6*N reals
 // [3 b + d][cell], as written by launch_step_fused's s_out), writes
 // lambda_loc^n, a^n (6*N reals, scratch) and D^n; partials
-// (adjoint_blocks() x 4 doubles: dG12, dG21, dtau1, dtau2) accumulate.
+// (adjoint_blocks(storage) x 4 doubles: dG12, dG21, dtau1, dtau2) accumulate.
 // lambda^n = lambda_loc^n + D^n of the population's component.
-int adjoint_blocks();
+int adjoint_blocks(int storage);
 cudaError_t launch_adjoint_step(const HostPhys &p, const void *f, const void *rho, int rho_is_sums,
                                 const void *lam_next, const void *Dn, void *lam_loc, void *a, void *Dout,
                                 double *partials, cudaStream_t s);
