@@ -309,7 +309,7 @@ struct Phys {
     R gext[3];
     R rho_s[2];
     R rho0;                 // reference density of deviation storage (0 otherwise)
-    const unsigned char *solid = nullptr;   // N flags, 1 = solid site (two-kernel step only)
+    const unsigned char *solid = nullptr;   // N flags, 1 = solid site (nullptr without a mask)
     long long ref_off = 0;  // *_REL formats: byte offset of the per-cell reference
                             // densities (float2 per cell) from the state's base
 };
