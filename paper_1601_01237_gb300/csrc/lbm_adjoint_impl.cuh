@@ -59,15 +59,11 @@ struct Nb {
 };
 
 template <class R>
-__device__ __forceinline__ void nb_of(const Phys<R> &p, unsigned cell, Nb &n)
+__device__ __forceinline__ void nb_at(const Phys<R> &p, unsigned x, unsigned y, unsigned z, Nb &n)
 {
     const unsigned nx = (unsigned)p.nx, ny = (unsigned)p.ny, nz = (unsigned)p.nz;
     const unsigned plane = nx * ny;
-    const unsigned z = cell / plane;
-    const unsigned rem = cell - z * plane;
-    const unsigned y = rem / nx;
-    const unsigned x = rem - y * nx;
-    n.cell = cell;
+    n.cell = z * plane + y * nx + x;
     n.xo[0] = x == 0 ? nx - 1 : x - 1;
     n.xo[1] = x;
     n.xo[2] = x == nx - 1 ? 0 : x + 1;
@@ -79,6 +75,16 @@ __device__ __forceinline__ void nb_of(const Phys<R> &p, unsigned cell, Nb &n)
     n.zo[2] = (z == nz - 1 ? 0 : z + 1) * plane;
     n.zlo = p.wall_z && z == 0;
     n.zhi = p.wall_z && z == nz - 1;
+}
+
+template <class R>
+__device__ __forceinline__ void nb_of(const Phys<R> &p, unsigned cell, Nb &n)
+{
+    const unsigned nx = (unsigned)p.nx, plane = nx * (unsigned)p.ny;
+    const unsigned z = cell / plane;
+    const unsigned rem = cell - z * plane;
+    const unsigned y = rem / nx;
+    nb_at(p, rem - y * nx, y, z, n);
 }
 
 __device__ __forceinline__ unsigned at(const Nb &n, int dx, int dy, int dz)
@@ -466,11 +472,29 @@ k_adj_local(const typename Store<S>::T *__restrict__ f, const typename Store<S>:
     // tens per step), summed in FP64 across the block: the FP64 pipe is a
     // small fraction of the FP32 one on this GPU
     typename Store<S>::R pg = 0, pt = 0;
-    for (long long wg = (long long)blockIdx.x * (kThreadsL / 32) + (threadIdx.x >> 5); wg < groups; wg += warps) {
+    // the lane's cell advances by the fixed stride 16 warps per iteration: its
+    // coordinates advance by the stride's (sx, sy, sz) with carries, so the
+    // loop divides by the lattice sizes only once
+    // (19 N < 2^32, checked on the host, so cells, strides and z fit 32 bits)
+    const unsigned nx = (unsigned)p.nx, ny = (unsigned)p.ny, plane = nx * ny;
+    const unsigned stride = (unsigned)warps * 16u;
+    const unsigned sx = stride % nx, sy = (stride / nx) % ny, sz = stride / plane;
+    const long long wg0 = (long long)blockIdx.x * (kThreadsL / 32) + (threadIdx.x >> 5);
+    const unsigned c0 = (unsigned)wg0 * 16u + (unsigned)(lane & 15);
+    unsigned px = c0 % nx, py = (c0 / nx) % ny, pz = c0 / plane;
+    for (long long wg = wg0; wg < groups; wg += warps) {
         const long long c = wg * 16 + (lane & 15);
         const bool valid = c < p.N;
         Nb n;
-        nb_of(p, (unsigned)(valid ? c : p.N - 1), n);
+        if (valid) nb_at(p, px, py, pz, n);
+        else nb_at(p, nx - 1, ny - 1, (unsigned)(p.nz - 1), n);
+        px += sx;
+        const unsigned cxr = px >= nx ? 1u : 0u;
+        px -= cxr * nx;
+        py += sy + cxr;
+        const unsigned cyr = py >= ny ? 1u : 0u;
+        py -= cyr * ny;
+        pz += sz + cyr;
         const unsigned lw = MASK ? __ldg(links + n.cell) : 0u;
         adj_half<S, REG, SIN, MASK, WZ, FORCE>(f, rho, lam_next, Dn, lam_loc, aout, p, n, a, valid, pg, pt, lw);
     }
