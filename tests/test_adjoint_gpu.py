@@ -83,6 +83,27 @@ def test_adjoint_matches_finite_differences(gpu_lib, fd_reference, storage):
     assert np.max(np.abs(gr - fr)[big] / np.abs(fr)[big]) <= 1e-3
 
 
+@pytest.mark.parametrize("storage", ["f16_dev", "bf16_dev", "f16_rel", "bf16_rel"])
+def test_adjoint_16bit_storage_tracks_fp32(gpu_lib, storage):
+    """The reverse pass on 16-bit storage (states decoded to FP32, the
+    rounding of the stored values taken as identity) against the FP32 reverse
+    pass on the differentiation crop: the gradients differ by the 16-bit
+    trajectory's own deviation from the FP32 one."""
+    r1, r2, tgt = crop_case()
+    G = G_STRONG
+    ref = gpu_grads(r1, r2, tgt, G, 1.0, 1.0, STEPS, "f32")
+    extra = {"rho0_dev": 0.5} if storage.endswith("_dev") else {}
+    got = gpu_grads(r1, r2, tgt, G, 1.0, 1.0, STEPS, storage, **extra)
+    eG = abs(got[0] - ref[0]) / abs(ref[0])
+    eT = abs(got[1] - ref[1]) / abs(ref[1])
+    er = np.linalg.norm(got[2] - ref[2]) / np.linalg.norm(ref[2])
+    print("%s vs FP32 adjoint: dG %.3g, dtau1 %.3g, drho1_0 %.3g" % (storage, eG, eT, er))
+    # measured: FP16-dev <= 5.5e-4, FP16-rel <= 4.3e-4, BF16-rel <= 1.9e-3,
+    # BF16-dev <= 5.1e-3 (the tau_1 derivative is the most sensitive)
+    bound = 2e-3 if storage.startswith("f16") else 2e-2
+    assert eG <= bound and eT <= bound and er <= bound
+
+
 @pytest.mark.parametrize("storage", ["f64", "f32"])
 @pytest.mark.parametrize("collision", ["bgk", "regularized", "regularized3"])
 def test_adjoint_walls_and_forcing(gpu_lib, collision, storage):
