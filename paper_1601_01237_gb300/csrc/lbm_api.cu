@@ -512,7 +512,7 @@ lbm_status lbm_pressure_jump(lbm_lattice *h, const double center[3], double r_in
     if (!h || !center || !out) return fail(LBM_EINVAL, "lbm_pressure_jump: NULL argument");
     if (!(r_in > 0) || !(r_out >= r_in)) return fail(LBM_EINVAL, "lbm_pressure_jump: need 0 < r_in <= r_out");
     DeviceGuard g(h->device);
-    double s[4];
+    double s[4] = {0, 0, 0, 0};
     lbm_status st = diag_run(h, 0, center, r_in, r_out, s, 4);
     if (st != LBM_OK) return st;
     if (s[1] < 1 || s[3] < 1) return fail(LBM_EINVAL, "lbm_pressure_jump: empty inner or outer region");
@@ -526,7 +526,7 @@ lbm_status lbm_droplet_stats(lbm_lattice *h, double threshold, const double orig
 {
     if (!h || !origin || !out) return fail(LBM_EINVAL, "lbm_droplet_stats: NULL argument");
     DeviceGuard g(h->device);
-    double s[7];
+    double s[7] = {0, 0, 0, 0, 0, 0, 0};
     lbm_status st = diag_run(h, 1, origin, threshold, 0.0, s, 7);
     if (st != LBM_OK) return st;
     out[0] = s[0];
