@@ -181,6 +181,7 @@ template <> struct Store<ST_F64> {
     using T = double;
     using R = double;
     static constexpr bool kRel = false;
+    static constexpr bool kDev = false;
     __device__ static __forceinline__ R enc(R wr) { return wr; }
     __device__ static __forceinline__ R load(const T *p, R) { return __ldg(p); }
     __device__ static __forceinline__ void store(T *p, R v, R) { *p = v; }
@@ -195,6 +196,7 @@ template <> struct Store<ST_F32> {
     using T = float;
     using R = float;
     static constexpr bool kRel = false;
+    static constexpr bool kDev = false;
     __device__ static __forceinline__ R enc(R wr) { return wr; }
     __device__ static __forceinline__ R load(const T *p, R) { return __ldg(p); }
     __device__ static __forceinline__ void store(T *p, R v, R) { *p = v; }
@@ -243,6 +245,7 @@ template <class C> struct StoreDev {
     using T = typename C::T;
     using R = float;
     static constexpr bool kRel = false;
+    static constexpr bool kDev = true;
     __device__ static __forceinline__ R enc(R wr) { return wr; }
     __device__ static __forceinline__ R load(const T *p, R d) { return C::to_f(__ldg(p)) + d; }
     __device__ static __forceinline__ void store(T *p, R v, R e) { *p = C::from_f(v - e); }
@@ -262,6 +265,13 @@ template <class C> struct StoreDev {
         C::unpack(r, a, b);
         a += da; b += db;
     }
+    // the deviations d themselves (the fused step computes in d = f - w rho0)
+    __device__ static __forceinline__ void load2_d(const T *p, R &a, R &b) { C::unpack(ld_pair_b16(p), a, b); }
+    __device__ static __forceinline__ void decode2_d(Raw r, R &a, R &b) { C::unpack(r, a, b); }
+    __device__ static __forceinline__ void store2_d(T *p, R a, R b)
+    {
+        *reinterpret_cast<typename C::T2 *>(p) = C::pack(a, b);
+    }
 };
 // Relative deviation s = f / (w rho~) - 1 (load parameter d = w rho~, store
 // parameter e = 1 / (w rho~)).
@@ -269,6 +279,7 @@ template <class C> struct StoreRel {
     using T = typename C::T;
     using R = float;
     static constexpr bool kRel = true;
+    static constexpr bool kDev = false;
     __device__ static __forceinline__ R enc(R wr) { return __frcp_rn(wr); }
     __device__ static __forceinline__ R load(const T *p, R d) { return fmaf(d, C::to_f(__ldg(p)), d); }
     __device__ static __forceinline__ void store(T *p, R v, R e) { *p = C::from_f(fmaf(v, e, -1.0f)); }

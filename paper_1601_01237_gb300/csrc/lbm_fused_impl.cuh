@@ -61,6 +61,7 @@ struct FusedSmem {
     R hpart[2][kGroups][2][kHalo];         // halo partial densities of the next two planes
     R mom[2][3][kThreadsF];                // sum_a sum_i c_i f_i of the stashed planes
     float2 stash[2][Q][kThreadsF];         // pre-collision (f^1_i, f^2_i) of planes z, z+1
+    unsigned char hsolid[2][kHalo];        // under a mask: the halo cell is a solid site
 };
 
 // *_REL formats: the reciprocals (1/rho^1, 1/rho^2) of the ring densities, in
@@ -176,7 +177,10 @@ __device__ __forceinline__ void load_dir(const typename Store<S>::T *__restrict_
     int d;
     const int e = gather_elem<I>(pr, c, lw, d);
     const unsigned idx = (unsigned)d * (unsigned)N + (unsigned)e;
-    Store<S>::load2(f + 2 * (size_t)idx, w<R>(I) * rr.x, w<R>(I) * rr.y, v[I], v[Q + I]);
+    if constexpr (Store<S>::kDev)   // the deviation formats compute in d = f - w rho0
+        Store<S>::load2_d(f + 2 * (size_t)idx, v[I], v[Q + I]);
+    else
+        Store<S>::load2(f + 2 * (size_t)idx, w<R>(I) * rr.x, w<R>(I) * rr.y, v[I], v[Q + I]);
 }
 
 template <int S, int I>
@@ -223,7 +227,12 @@ __device__ __forceinline__ void decode_all(const typename Store<S>::Raw (&r)[Q],
 {
     using R = typename Store<S>::R;
 #pragma unroll
-    for (int i = 0; i < Q; ++i) Store<S>::decode2(r[i], w<R>(i) * rr.x, w<R>(i) * rr.y, v[i], v[Q + i]);
+    for (int i = 0; i < Q; ++i) {
+        if constexpr (Store<S>::kDev)
+            Store<S>::decode2_d(r[i], v[i], v[Q + i]);
+        else
+            Store<S>::decode2(r[i], w<R>(i) * rr.x, w<R>(i) * rr.y, v[i], v[Q + i]);
+    }
 }
 
 // rho^1, rho^2 and momentum of a gathered population set.  The densities are
@@ -272,7 +281,10 @@ struct HaloRange {
         int d;
         const int e = gather_elem<D>(pr, c, lw, d);
         const unsigned idx = (unsigned)d * (unsigned)N + (unsigned)e;
-        Store<S>::load2(f + 2 * (size_t)idx, w<R>(D) * rr.x, w<R>(D) * rr.y, v[k], v[k + 1]);
+        if constexpr (Store<S>::kDev)
+            Store<S>::load2_d(f + 2 * (size_t)idx, v[k], v[k + 1]);
+        else
+            Store<S>::load2(f + 2 * (size_t)idx, w<R>(D) * rr.x, w<R>(D) * rr.y, v[k], v[k + 1]);
         HaloRange<S, D + 1, D1>::load(f, N, rr, pr, c, lw, v, k + 2);
     }
     __device__ __forceinline__ static void sum(const typename Store<S>::R (&v)[kPer], int k,
@@ -421,6 +433,12 @@ __device__ __forceinline__ void collide_cell(typename Store<S>::T *__restrict__ 
     typename Store<S>::T *o = fout + 2 * cell;   // (component 1, component 2) of direction 0
     const unsigned N32 = (unsigned)p.N;
     const R ref0 = p.rho0;
+    // Deviation formats: the stash holds d = f - w rho0 and the outputs are
+    // stored as f* - w rho0; that adds to each output a constant per unit
+    // weight: -omega rho0 under BGK (keep f = keep d + keep w rho0), -rho0
+    // under the regularized filter (which keeps no f of its own)
+    const R dc1 = Store<S>::kDev ? (REG ? ref0 : p.omega[0] * ref0) : R(0);
+    const R dc2 = Store<S>::kDev ? (REG ? ref0 : p.omega[1] * ref0) : R(0);
 
     // Regularized: second moments of f - f^eq(u): Pi = sum c c f - rho (T0 I + u u)
     R P1[6], P2[6], t1 = 0, t2 = 0;
@@ -442,6 +460,11 @@ __device__ __forceinline__ void collide_cell(typename Store<S>::T *__restrict__ 
             if (cy(i) && cz(i)) { if (cy(i) == cz(i)) { P1[5] += fa; P2[5] += fb; } else { P1[5] -= fa; P2[5] -= fb; } }
         }
         const R T0 = R(1) / R(3);
+        if constexpr (Store<S>::kDev) {   // sum_i c_i c_i w_i rho0 = rho0 T0 I
+            const R d = ref0 * T0;
+            P1[0] += d; P1[1] += d; P1[2] += d;
+            P2[0] += d; P2[1] += d; P2[2] += d;
+        }
         P1[0] -= r1 * (T0 + ux * ux); P2[0] -= r2 * (T0 + ux * ux);
         P1[1] -= r1 * (T0 + uy * uy); P2[1] -= r2 * (T0 + uy * uy);
         P1[2] -= r1 * (T0 + uz * uz); P2[2] -= r2 * (T0 + uz * uz);
@@ -479,6 +502,8 @@ __device__ __forceinline__ void collide_cell(typename Store<S>::T *__restrict__ 
             const float2 iv = rinv[sl_c][ly][lx];   // 1/rho of the cell itself; 1/w_0 = 3
             Store<S>::store2(o, o1, o2v, R(3) * iv.x, R(3) * iv.y);
             state_ref(fout, p.ref_off)[cell] = rr;
+        } else if constexpr (Store<S>::kDev) {
+            Store<S>::store2_d(o, o1 - w0 * dc1, o2v - w0 * dc2);
         } else {
             Store<S>::store2(o, o1, o2v, w0 * ref0, w0 * ref0);
         }
@@ -496,8 +521,9 @@ __device__ __forceinline__ void collide_cell(typename Store<S>::T *__restrict__ 
         if (!REG) {
             // f* = f^eq(v) + keep (f - f^eq(u)); f^eq(u) shares its polynomial between components
             const R Eu = Au + R(4.5) * cu * cu, Ou = cu * (Bu + R(4.5) * cu * cu);
-            const R P1e = rw1 * (E1 - keep1 * Eu), M1 = rw1 * (O1 - keep1 * Ou);
-            const R P2e = rw2 * (E2 - keep2 * Eu), M2 = rw2 * (O2 - keep2 * Ou);
+            R P1e = rw1 * (E1 - keep1 * Eu), M1 = rw1 * (O1 - keep1 * Ou);
+            R P2e = rw2 * (E2 - keep2 * Eu), M2 = rw2 * (O2 - keep2 * Ou);
+            if constexpr (Store<S>::kDev) { P1e -= w<R>(i) * dc1; P2e -= w<R>(i) * dc2; }
             const float2 fp = s0[i * kThreadsF], fm = s0[(i + 1) * kThreadsF];
             o1p = P1e + M1 + keep1 * fp.x;
             o1m = P1e - M1 + keep1 * fm.x;
@@ -512,8 +538,9 @@ __device__ __forceinline__ void collide_cell(typename Store<S>::T *__restrict__ 
             if (cx(i) && cy(i)) { const R sg = cx(i) == cy(i) ? R(2) : R(-2); cc1 += sg * P1[3]; cc2 += sg * P2[3]; }
             if (cx(i) && cz(i)) { const R sg = cx(i) == cz(i) ? R(2) : R(-2); cc1 += sg * P1[4]; cc2 += sg * P2[4]; }
             if (cy(i) && cz(i)) { const R sg = cy(i) == cz(i) ? R(2) : R(-2); cc1 += sg * P1[5]; cc2 += sg * P2[5]; }
-            const R n1 = keep1 * (R(k36(i)) * R(0.125)) * (cc1 - t1);
-            const R n2 = keep2 * (R(k36(i)) * R(0.125)) * (cc2 - t2);
+            R n1 = keep1 * (R(k36(i)) * R(0.125)) * (cc1 - t1);
+            R n2 = keep2 * (R(k36(i)) * R(0.125)) * (cc2 - t2);
+            if constexpr (Store<S>::kDev) { n1 -= w<R>(i) * dc1; n2 -= w<R>(i) * dc2; }
             // third-order part, odd in c_i: + for i, - for opp(i)
             const R m1 = REG == 2 ? keep1 * th1.odd(i) : R(0);
             const R m2 = REG == 2 ? keep2 * th2.odd(i) : R(0);
@@ -542,6 +569,9 @@ __device__ __forceinline__ void collide_cell(typename Store<S>::T *__restrict__ 
             const R sk = R(36 / k36(i));   // 1 / w_i: the code parameter is 1 / (w_i rho~)
             Store<S>::store2(o + ip, o1p, o2p, sk * dp.x, sk * dp.y);
             Store<S>::store2(o + im, o1m, o2m, sk * dm.x, sk * dm.y);
+        } else if constexpr (Store<S>::kDev) {
+            Store<S>::store2_d(o + ip, o1p, o2p);
+            Store<S>::store2_d(o + im, o1m, o2m);
         } else {
             const R ref = w<R>(i) * ref0;
             Store<S>::store2(o + ip, o1p, o2p, ref, ref);
@@ -570,6 +600,7 @@ __device__ __forceinline__ void interior_plane(const typename Store<S>::T *__res
     } else if (!pr.constant) {
         R a1, a2, jx, jy, jz;
         sums(v, a1, a2, jx, jy, jz);
+        if constexpr (Store<S>::kDev) { a1 += p.rho0; a2 += p.rho0; }   // sum_i w_i rho0 = rho0
         if (pr.ghost) {
             r1 += a1; r2 += a2;
         } else {
@@ -585,10 +616,11 @@ __device__ __forceinline__ void interior_plane(const typename Store<S>::T *__res
 }
 
 // Halo densities of a plane in ring slot `slot` from the partials of the
-// population groups.
+// population groups (mask: the kernel runs a solid mask, whose solid halo
+// cells are marked in hsolid).
 template <int S, class R>
 __device__ __forceinline__ void halo_combine(const Phys<R> &p, FusedSmem<R> &sm, InvRing *inv, int slot, int hs,
-                                             const PlaneRef &pr, int h, int hx, int hy)
+                                             const PlaneRef &pr, int h, int hx, int hy, bool mask = false)
 {
     R r1, r2;
     if (pr.constant) {
@@ -597,6 +629,10 @@ __device__ __forceinline__ void halo_combine(const Phys<R> &p, FusedSmem<R> &sm,
     } else {
         r1 = sm.hpart[hs][0][0][h] + sm.hpart[hs][1][0][h] + sm.hpart[hs][2][0][h];
         r2 = sm.hpart[hs][0][1][h] + sm.hpart[hs][1][1][h] + sm.hpart[hs][2][1][h];
+        // partials of deviations (a solid halo cell's first partial is its wall density)
+        if constexpr (Store<S>::kDev) {
+            if (!(mask && sm.hsolid[hs][h])) { r1 += p.rho0; r2 += p.rho0; }
+        }
         if (pr.ghost) { r1 += p.rho_s[0]; r2 += p.rho_s[1]; }
     }
     put_ring<S>(sm, inv, slot, hy, hx, r1, r2);
@@ -710,6 +746,7 @@ k_step_fused(const typename Store<S>::T *__restrict__ fin, typename Store<S>::T 
                 GatherAll<S, 0>::run(fin, p.N, gather_ref<S>(fin, p, pr, ch), pr, ch, hl, hv);
                 R a1, a2, jx, jy, jz;
                 sums(hv, a1, a2, jx, jy, jz);
+                if constexpr (Store<S>::kDev) { a1 += p.rho0; a2 += p.rho0; }
                 if (pr.ghost) { r1 += a1; r2 += a2; } else { r1 = a1; r2 = a2; }
             }
             put_ring<S>(sm, inv, q - z0 + 1, hy, hx, r1, r2);
@@ -730,6 +767,7 @@ k_step_fused(const typename Store<S>::T *__restrict__ fin, typename Store<S>::T 
             halo_load<S>(fin, p, pr, cht, hl, g, hv);
             halo_sum<S>(hv, g, s1, s2);
         }
+        if (MASK && g == 0) sm.hsolid[slot][ht] = (hl & 1u) ? 1 : 0;
         sm.hpart[slot][g][0][ht] = s1;
         sm.hpart[slot][g][1][ht] = s2;
     };
@@ -784,7 +822,7 @@ k_step_fused(const typename Store<S>::T *__restrict__ fin, typename Store<S>::T 
         float2 hwd = make_float2(0.f, 0.f);
         if (hsol && g == 0 && need2 && has_halo) hwd = wall_rho(pr2, cht);   // in flight with the gathers
         if (need2 && has_halo && !hsol && !pr2.constant) halo_load<S>(fin, p, pr2, cht, hlw, g, hv);
-        if (tid < kHalo) halo_combine<S>(p, sm, inv, s_p, (k + 1) & 1, pr1, h, hx, hy);
+        if (tid < kHalo) halo_combine<S>(p, sm, inv, s_p, (k + 1) & 1, pr1, h, hx, hy, MASK);
         const bool sol = MASK && (lwB & 1u);
         if constexpr (kRaw) {
             if (!pr1.constant) decode_all<S>(rv, rrv, v);
@@ -800,6 +838,7 @@ k_step_fused(const typename Store<S>::T *__restrict__ fin, typename Store<S>::T 
             } else if (!pr2.constant) {
                 halo_sum<S>(hv, g, s1, s2);
             }
+            if (MASK && g == 0) sm.hsolid[k & 1][ht] = hsol ? 1 : 0;
             sm.hpart[k & 1][g][0][ht] = s1;
             sm.hpart[k & 1][g][1][ht] = s2;
         }
@@ -929,7 +968,9 @@ k_wall_fluid_rho(const typename Store<S>::T *__restrict__ f, Phys<typename Store
     const unsigned full = 0xffffffffu;
     const R a1 = __shfl_down_sync(full, s1, 1), a2 = __shfl_down_sync(full, s2, 1);
     const R b1 = __shfl_down_sync(full, s1, 2), b2 = __shfl_down_sync(full, s2, 2);
-    if (ok && g == 0) wr[c] = make_float2(s1 + a1 + b1, s2 + a2 + b2);
+    R d1 = s1 + a1 + b1, d2 = s2 + a2 + b2;
+    if constexpr (Store<S>::kDev) { d1 += p.rho0; d2 += p.rho0; }   // the partials sum deviations
+    if (ok && g == 0) wr[c] = make_float2(d1, d2);
 }
 
 template <int S>   // (instantiated per storage format's translation unit)
