@@ -132,8 +132,11 @@ lbm_status lbm_create(const lbm_params *params, lbm_lattice **out);
 
 /* Initial state f_i^a(x, 0) = f^eq_i(rho^a_0(x), u_0(x)) (Eq. 3).  rho1, rho2:
  * N = nx*ny*nz doubles each; u: 3N doubles [cell][3] or NULL for u = 0.
- * Host or device pointers (on_device); contents are copied.  Resets the step
- * counter to 0.  Errors: LBM_EINVAL, LBM_ECUDA. */
+ * Host or device pointers (on_device); contents are copied, host fields
+ * through the lattice's second population copy (no allocation), and the call
+ * synchronizes before it returns when they are host pointers, so the caller
+ * may reuse them.  Resets the step counter to 0.  Errors: LBM_EINVAL,
+ * LBM_ECUDA. */
 lbm_status lbm_init_fields(lbm_lattice *h, const double *rho1, const double *rho2,
                            const double *u, int on_device);
 

@@ -289,11 +289,19 @@ lbm_status lbm_init_fields(lbm_lattice *h, const double *rho1, const double *rho
     DeviceGuard g(h->device);
     const size_t N = (size_t)h->phys.N;
     const double *d1 = rho1, *d2 = rho2, *du = u;
+    // The other state copy is free until the first step: it stages host fields
+    // (no allocation) and then holds the rest values of a state at rest.
+    char *spare = (char *)h->f[1];
+    const size_t cap = lbm::state_bytes(h->phys.storage, N);
+    const size_t stage = on_device ? 0 : sizeof(double) * N * (u ? 5 : 2);
+    const size_t rest = 8 * N * lbm::real_bytes(h->phys.storage);
     void *tmp = nullptr;
     if (!on_device) {
-        // stage host fields through one temporary device buffer
-        CK(cudaMallocAsync(&tmp, sizeof(double) * N * (u ? 5 : 2), h->stream), "lbm_init_fields: staging");
-        double *t = (double *)tmp;
+        double *t = (double *)spare;
+        if (stage + rest > cap) {   // not reached by the built formats (at most 104 of 304 B per cell)
+            CK(cudaMallocAsync(&tmp, stage, h->stream), "lbm_init_fields: staging");
+            t = (double *)tmp;
+        }
         lbm_status st;
         if ((st = copy_in(h, t, rho1, sizeof(double) * N, 0)) != LBM_OK) return st;
         if ((st = copy_in(h, t + N, rho2, sizeof(double) * N, 0)) != LBM_OK) return st;
@@ -305,11 +313,11 @@ lbm_status lbm_init_fields(lbm_lattice *h, const double *rho1, const double *rho
     h->cur = 0;
     h->steps = 0;
     h->init_at_rest = u == nullptr;
-    CK(lbm::launch_init_feq(h->phys, d1, d2, du, h->f[0], h->stream), "lbm_init_fields: launch");
-    if (tmp) {
-        CK(cudaFreeAsync(tmp, h->stream), "lbm_init_fields: free staging");
-        CK(cudaStreamSynchronize(h->stream), "lbm_init_fields: sync");
-    }
+    void *scratch = tmp ? (void *)spare : (stage + rest <= cap ? (void *)(spare + stage) : nullptr);
+    CK(lbm::launch_init_feq(h->phys, d1, d2, du, h->f[0], scratch, h->stream), "lbm_init_fields: launch");
+    if (tmp) CK(cudaFreeAsync(tmp, h->stream), "lbm_init_fields: free staging");
+    // host inputs: the caller may reuse its buffers on return
+    if (!on_device) CK(cudaStreamSynchronize(h->stream), "lbm_init_fields: sync");
     return LBM_OK;
 }
 
@@ -479,7 +487,8 @@ lbm_status lbm_reduce(lbm_lattice *h, double out[6])
         acc[5] = fmax(acc[5], q[5]);
         bad += q[6];
     }
-    for (int k = 0; k < 6; ++k) out[k] = acc[k];
+    for (int k = 0; k < 5; ++k) out[k] = acc[k];
+    out[5] = sqrt(acc[5]);   // the blocks reduce max |u_F|^2
     if (bad > 0 || !isfinite(acc[0]) || !isfinite(acc[1]))
         return fail(LBM_ENUMERIC, "lbm_reduce: %.0f cells with a non-finite or non-positive density", bad);
     return LBM_OK;

@@ -314,18 +314,43 @@ k_collide(const typename Store<S>::T *__restrict__ fin, typename Store<S>::T *__
     }
 }
 
+// Rest-state values of one cell, formed once per cell in FP64 and rounded to
+// the arithmetic type: rho^a w for the three weight classes (w = 1/3, 1/18,
+// 1/36) and rho^a itself, at slot (2 q + a) N + c (q = 0, 1, 2, 3).  The
+// initial populations at rest gather these instead of forming 38 FP64
+// products per cell, each repeated by up to seven readers (the FP64 pipe is
+// a small fraction of the FP32 one on this GPU); the values are the same
+// roundings of the same FP64 products.
+template <class R>
+__global__ void __launch_bounds__(kThreads)
+k_rest_values(const double *__restrict__ rho1, const double *__restrict__ rho2, R *__restrict__ out, long long N)
+{
+    const long long c = (long long)blockIdx.x * kThreads + threadIdx.x;
+    if (c >= N) return;
+    const double r[2] = {rho1[c], rho2[c]};
+#pragma unroll
+    for (int a = 0; a < 2; ++a) {
+        out[(0 + a) * N + c] = (R)(r[a] * wd(0));
+        out[(2 + a) * N + c] = (R)(r[a] * wd(1));
+        out[(4 + a) * N + c] = (R)(r[a] * wd(7));
+        out[(6 + a) * N + c] = (R)r[a];
+    }
+}
+
 // Stored value s_j(y): the population that the gather of step 0 reads as
-// f_j(y + c_j), or, when y + c_j is a wall site, as f_opp(j)(y).
+// f_j(y + c_j), or, when y + c_j is a wall site, as f_opp(j)(y).  rest: the
+// values of k_rest_values (the state at rest, u == NULL), or NULL.
 template <int S>
 __global__ void __launch_bounds__(kThreads)
 k_init_feq(const double *__restrict__ rho1, const double *__restrict__ rho2,
-           const double *__restrict__ u, typename Store<S>::T *__restrict__ f,
-           PhysF<typename Store<S>::R> p)
+           const double *__restrict__ u, const typename Store<S>::R *__restrict__ rest,
+           typename Store<S>::T *__restrict__ f, PhysF<typename Store<S>::R> p)
 {
     using R = typename Store<S>::R;
     Nbr n;
     if (!decode_cell(p, (long long)blockIdx.x * kThreads + threadIdx.x, n)) return;
     const bool here_solid = p.solid && p.solid[n.cell];
+    const long long N = p.N;
 #pragma unroll
     for (int j = 0; j < Q; ++j) {
         const long long dst = n.zo[1 + cz(j)] + n.yo[1 + cy(j)] + n.xo[1 + cx(j)];
@@ -333,15 +358,27 @@ k_init_feq(const double *__restrict__ rho1, const double *__restrict__ rho2,
                           (j != 0 && p.solid && p.solid[dst]);
         const long long src = wall ? n.cell : dst;
         const int k = wall ? opp(j) : j;
-        double ux = 0, uy = 0, uz = 0;
-        if (u) { ux = u[3 * src]; uy = u[3 * src + 1]; uz = u[3 * src + 2]; }
-        const double usq = ux * ux + uy * uy + uz * uz;
-        const double cu = cdot<double>(k, ux, uy, uz);
-        const double P = 1.0 - 1.5 * usq + cu * (3.0 - 4.5 * usq) + 4.5 * cu * cu * (1.0 + cu);
-        const R v1 = here_solid ? R(0) : (R)(rho1[src] * wd(k) * P);
-        const R v2 = here_solid ? R(0) : (R)(rho2[src] * wd(k) * P);
+        R v1, v2, e1 = R(1), e2 = R(1);
+        if (rest) {
+            const int q = k == 0 ? 0 : (k < 7 ? 1 : 2);
+            v1 = rest[(2 * q + 0) * N + src];
+            v2 = rest[(2 * q + 1) * N + src];
+            if constexpr (Store<S>::kRel) { e1 = rest[6 * N + src]; e2 = rest[7 * N + src]; }
+        } else {
+            // f^eq of Eq. 3 at (rho^a, u) of the source cell (u == NULL: at rest)
+            double P = 1.0;
+            if (u) {
+                const double ux = u[3 * src], uy = u[3 * src + 1], uz = u[3 * src + 2];
+                const double usq = ux * ux + uy * uy + uz * uz;
+                const double cu = cdot<double>(k, ux, uy, uz);
+                P = 1.0 - 1.5 * usq + cu * (3.0 - 4.5 * usq) + 4.5 * cu * cu * (1.0 + cu);
+            }
+            v1 = (R)(rho1[src] * wd(k) * P);
+            v2 = (R)(rho2[src] * wd(k) * P);
+            if constexpr (Store<S>::kRel) { e1 = (R)rho1[src]; e2 = (R)rho2[src]; }
+        }
+        if (here_solid) { v1 = v2 = R(0); e1 = e2 = R(1); }
         if constexpr (Store<S>::kRel) {   // coded relative to the reader's initial density
-            const R e1 = here_solid ? R(1) : (R)rho1[src], e2 = here_solid ? R(1) : (R)rho2[src];
             Store<S>::store2(f + pair_index(j, n.cell, p.N), v1, v2, Store<S>::enc(w<R>(j) * e1),
                              Store<S>::enc(w<R>(j) * e2));
         } else {
@@ -493,8 +530,9 @@ k_reduce(const typename Store<S>::T *__restrict__ f, const typename Store<S>::R 
         acc[2] += rho_t * (double)fx;
         acc[3] += rho_t * (double)fy;
         acc[4] += rho_t * (double)fz;
-        const double m = sqrt((double)fx * fx + (double)fy * fy + (double)fz * fz);
-        acc[5] = fmax(acc[5], m);
+        // max |u_F|^2; the host takes the square root of the maximum, which
+        // equals the maximum of the (correctly rounded, monotonic) roots
+        acc[5] = fmax(acc[5], (double)fx * fx + (double)fy * fy + (double)fz * fz);
     }
     // fixed-order block reduction (deterministic)
     __shared__ double sh[7][kThreads];
@@ -573,11 +611,18 @@ cudaError_t step_split_t(const HostPhys &h, const void *fin, void *fout, void *r
 
 template <int S>
 cudaError_t init_t(const HostPhys &h, const double *r1, const double *r2, const double *u, void *f,
-                   cudaStream_t s)
+                   void *scratch, cudaStream_t s)
 {
     using T = typename Store<S>::T;
     using R = typename Store<S>::R;
-    k_init_feq<S><<<grid_for(h.N), kThreads, 0, s>>>(r1, r2, u, (T *)f, make_phys<R>(h));
+    // the eight rest values per cell fit in the other state copy
+    static_assert(8 * sizeof(R) <= 2 * Q * sizeof(T), "rest values exceed a state copy");
+    R *rest = nullptr;
+    if (!u && scratch) {
+        rest = (R *)scratch;
+        k_rest_values<R><<<grid_for(h.N), kThreads, 0, s>>>(r1, r2, rest, h.N);
+    }
+    k_init_feq<S><<<grid_for(h.N), kThreads, 0, s>>>(r1, r2, u, rest, (T *)f, make_phys<R>(h));
     return cudaGetLastError();
 }
 
@@ -646,15 +691,15 @@ cudaError_t launch_step_split(const HostPhys &p, const void *f_in, void *f_out, 
 }
 
 cudaError_t launch_init_feq(const HostPhys &p, const double *r1, const double *r2, const double *u,
-                            void *f, cudaStream_t s)
+                            void *f, void *scratch, cudaStream_t s)
 {
     switch (p.storage) {
-    case ST_F64: return init_t<ST_F64>(p, r1, r2, u, f, s);
-    case ST_F32: return init_t<ST_F32>(p, r1, r2, u, f, s);
-    case ST_F16_DEV: return init_t<ST_F16_DEV>(p, r1, r2, u, f, s);
-    case ST_BF16_DEV: return init_t<ST_BF16_DEV>(p, r1, r2, u, f, s);
-    case ST_F16_REL: return init_t<ST_F16_REL>(p, r1, r2, u, f, s);
-    case ST_BF16_REL: return init_t<ST_BF16_REL>(p, r1, r2, u, f, s);
+    case ST_F64: return init_t<ST_F64>(p, r1, r2, u, f, scratch, s);
+    case ST_F32: return init_t<ST_F32>(p, r1, r2, u, f, scratch, s);
+    case ST_F16_DEV: return init_t<ST_F16_DEV>(p, r1, r2, u, f, scratch, s);
+    case ST_BF16_DEV: return init_t<ST_BF16_DEV>(p, r1, r2, u, f, scratch, s);
+    case ST_F16_REL: return init_t<ST_F16_REL>(p, r1, r2, u, f, scratch, s);
+    case ST_BF16_REL: return init_t<ST_BF16_REL>(p, r1, r2, u, f, scratch, s);
     default: return cudaErrorInvalidValue;
     }
 }

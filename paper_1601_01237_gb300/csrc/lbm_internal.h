@@ -78,8 +78,10 @@ cudaError_t launch_mask_setup(const HostPhys &h, const unsigned char *solid, flo
 
 // State set-up: populations from (rho1, rho2, u) via f^eq (u may be NULL),
 // or from explicit populations f[a][i][cell] in library order (doubles).
+// scratch (may be NULL): a second state copy, overwritten by the rest values
+// of a state at rest (u == NULL).
 cudaError_t launch_init_feq(const HostPhys &p, const double *rho1, const double *rho2,
-                            const double *u, void *f, cudaStream_t s);
+                            const double *u, void *f, void *scratch, cudaStream_t s);
 cudaError_t launch_set_populations(const HostPhys &p, const double *src, void *f, cudaStream_t s);
 cudaError_t launch_get_populations(const HostPhys &p, const void *f, double *dst, cudaStream_t s);
 

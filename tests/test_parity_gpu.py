@@ -221,6 +221,23 @@ def test_low_precision_storage(gpu_lib, storage):
     assert drift < (1e-3 if storage == "f16_dev" else 1e-2)
 
 
+@pytest.mark.parametrize("periodic", [(1, 1, 1), (1, 1, 0)])
+def test_init_at_rest_f32_is_rounded_oracle(gpu_lib, periodic):
+    """A state at rest (u omitted) stored in FP32 is the oracle's FP64 f^eq
+    (Eq. 3, P = 1) rounded once to FP32, bit for bit, also next to z walls:
+    the per-cell rest values the initialisation gathers are the same
+    roundings of the same FP64 products."""
+    import oracle
+    perm = direction_map()
+    shape = (6, 5, 7)
+    r1, r2, _ = wl.random_state(shape, seed=5)
+    p = oracle.make_params(shape, periodic=periodic)
+    f0 = oracle.init(p, r1, r2, None)[:, perm]
+    lat = gpu_run(shape, r1, r2, None, 0, storage="f32", periodic=periodic)
+    assert np.array_equal(lat.get_populations(), f0.astype(np.float32).astype(np.float64))
+    lat.close()
+
+
 def test_init_and_set_populations_roundtrip(gpu_lib):
     """lbm_set_populations / lbm_get_populations are inverse; lbm_init_fields
     equals f^eq of the oracle (Eq. 3)."""
