@@ -471,3 +471,29 @@ def test_graph_replay_is_bitwise(gpu_lib, monkeypatch, storage, shape):
         out[graphs] = lat.get_populations()
         lat.close()
     assert np.array_equal(out["1"], out["0"])
+
+
+@pytest.mark.parametrize("storage", ["f64", "f32", "f16_dev", "bf16_dev", "f16_rel", "bf16_rel"])
+@pytest.mark.parametrize("with_u", [False, True])
+def test_init_from_host_equals_init_from_device(gpu_lib, storage, with_u):
+    """lbm_init_fields stages host fields in the lattice's second population
+    copy; the state (and, after steps, its evolution) is the same bit for bit
+    as from device pointers, also next to z walls and for the formats whose
+    rest values take the rest of that copy."""
+    import torch
+    shape = (10, 9, 33)
+    r1, r2, u = wl.random_state(shape, seed=11, u_max=0.03)
+    u = u if with_u else None
+    extra = dict(rho0_dev=0.5) if storage.endswith("_dev") else {}
+    kw = dict(storage=storage, tau=(0.8, 1.0), G12=-1.2, periodic=(1, 1, 0), **extra)
+    host = gpu_run(shape, r1, r2, u, 0, **kw)
+    from paper_1601_01237_gb300 import Lattice
+    dev = Lattice(shape, **kw)
+    dev.init_fields(torch.from_numpy(r1).cuda(), torch.from_numpy(r2).cuda(),
+                    None if u is None else torch.from_numpy(np.ascontiguousarray(u)).cuda())
+    assert np.array_equal(host.get_populations(), dev.get_populations())
+    host.step(3)
+    dev.step(3)
+    assert np.array_equal(host.get_populations(), dev.get_populations())
+    host.close()
+    dev.close()
