@@ -316,3 +316,58 @@ def test_adjoint_graph_replay_is_bitwise(gpu_lib, monkeypatch):
         out[graphs] = (d1, list(par))
     assert np.array_equal(out["1"][0], out["0"][0])
     assert out["1"][1] == out["0"][1]
+
+
+# ---- the differentiation case at full size ---------------------------------
+# 96^3, 500 steps, checkpoints every 25: the configuration and launch shapes
+# the benchmark times.  The oracle is too slow for finite differences at this
+# size, so the check is a property that holds at any size: the reverse pass's
+# gradient projected on a direction equals the central difference of the loss
+# along it, the loss evaluated by FP64 forward runs of this library (whose
+# step the oracle pins on smaller lattices).  Central differences at h = 1e-4
+# differ from those at h = 1e-3 by 5.7e-7 (relative, for G), so their
+# truncation error is about 6e-9; bars 1e-6 for the FP64 reverse pass and the
+# gradient bar 1e-4 for FP32.
+
+def _c3_full():
+    c = wl.CONFIGS["c3_adjoint96"]
+    r1, r2 = wl.droplet(c["shape"], c["R"])
+    tgt, _ = wl.ellipsoid(c["shape"], c["target_axes"])
+    delta = wl.uniform_pm1(20260401, int(np.prod(c["shape"]))).reshape(c["shape"])
+    return c, r1, r2, tgt, delta
+
+
+@pytest.fixture(scope="module")
+def c3_full_fd():
+    from paper_1601_01237_gb300 import Lattice
+    c, r1, r2, tgt, delta = _c3_full()
+    G, (t1, t2) = c["G"], c["tau"]
+
+    def loss(dr=0.0, dG=0.0, dT=0.0):
+        lat = Lattice(c["shape"], storage="f64", tau=(t1 + dT, t2), G12=G + dG, G21=G + dG)
+        lat.init_fields(r1 + dr * delta, r2)
+        lat.step(c["steps"])
+        a, _, _ = lat.moments()
+        lat.close()
+        return float(((a - tgt) ** 2).sum())
+
+    h = 1e-4
+    return ((loss(dG=h) - loss(dG=-h)) / (2 * h), (loss(dT=h) - loss(dT=-h)) / (2 * h),
+            (loss(dr=h) - loss(dr=-h)) / (2 * h))
+
+
+@pytest.mark.parametrize("storage,bar", [("f64", 1e-6), ("f32", 1e-4)])
+def test_adjoint_full_size_directional_derivatives(gpu_lib, c3_full_fd, storage, bar):
+    from paper_1601_01237_gb300 import Lattice
+    c, r1, r2, tgt, delta = _c3_full()
+    lat = Lattice(c["shape"], storage=storage, tau=c["tau"], G12=c["G"], G21=c["G"])
+    lat.init_fields(r1, r2)
+    lat.record(c["steps"], c["ckpt_every"])
+    a, _, _ = lat.moments()
+    g0 = np.empty(c["shape"])
+    par = lat.adjoint(2 * (a - tgt), None, g0, None)
+    lat.close()
+    got = (par[0] + par[1], par[2], float((g0 * delta).sum()))
+    err = [abs(x - y) / abs(y) for x, y in zip(got, c3_full_fd)]
+    print("c3 96^3 %s: dL/dG %.3g, dL/dtau1 %.3g, dL/drho1_0 . delta %.3g" % (storage, *err))
+    assert max(err) <= bar, (got, c3_full_fd)
